@@ -1,0 +1,167 @@
+/*
+ * h2mul.h -- C-ABI of the GB300 (sm_103a) adaptive H^2-matrix product.
+ *
+ * The library computes Z <- Z + X Y for H^2-matrices X, Y, Z (S. Boerm,
+ * "Adaptive fast multiplication of H^2-matrices", arXiv 2309.09061, Sec. 1:
+ * the product in the general form Z <- Z + XY).  It first builds compressed
+ * induced row and column bases and the product on the refined block tree
+ * T^XY (Sec. 4-5), then coarsens that representation to Z's block tree with
+ * new adaptive, nested, isometric cluster bases (Sec. 6).
+ *
+ * Conventions for every entry point:
+ *   - Return value 0 (H2_OK) on success, a negative H2_ERR_* code on failure;
+ *     h2_error_string() names the code.  No entry point aborts the process.
+ *   - Dense matrices are column-major doubles with a leading dimension.
+ *   - A handle (h2_matrix*) owns all of its device buffers; h2_free releases
+ *     them.  Handles live on the CUDA device that was current when they were
+ *     created; every call must be made with that device current.
+ *   - `opts` may be NULL (defaults: eps = 1e-6, H2_FP64, legacy default
+ *     stream, no statistics).  Work is issued on opts->stream; every entry
+ *     point returns after that stream has finished the call's work.
+ */
+#ifndef H2MUL_H
+#define H2MUL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define H2_OK 0
+#define H2_ERR_ARG (-1)         /* invalid argument (NULL pointer, bad size, bad enum) */
+#define H2_ERR_SHAPE (-2)       /* operands do not share one cluster tree / block tree */
+#define H2_ERR_OOM (-3)         /* device or host allocation failed */
+#define H2_ERR_NUMERIC (-4)     /* NaN or Inf met in an input or an intermediate */
+#define H2_ERR_TIMEOUT (-5)     /* an iterative device routine ran out of its bounded sweeps */
+#define H2_ERR_UNSUPPORTED (-6) /* a case outside the supported operand relations */
+#define H2_ERR_CUDA (-7)        /* a CUDA runtime call failed */
+
+/* Kernel functions g(x, y) for h2_build_interp (Sec. 7 and the workloads):
+ *   H2_K_LAPLACE  1 / (4 pi |x - y|), 0 on coinciding points
+ *   H2_K_YUKAWA   exp(-|x - y|) / |x - y|, 0 on coinciding points
+ *   H2_K_POLY2    (1 + x.y)^2      (degree 2 per coordinate: interpolated exactly for order >= 3)
+ *   H2_K_CONST    1                (the all-ones matrix)
+ *   H2_K_DELTA    1 if x == y else 0 (the identity matrix for distinct points) */
+#define H2_K_LAPLACE 0
+#define H2_K_YUKAWA 1
+#define H2_K_POLY2 2
+#define H2_K_CONST 3
+#define H2_K_DELTA 4
+
+/* Precision of the contractions (products of coupling, transfer, basis and
+ * auxiliary matrices).  QR factorisations, singular value decompositions and
+ * the choice of ranks always run in FP64.
+ *   H2_FP64   every product in FP64 (the plain FP64 GPU form)
+ *   H2_MIXED  products in FP32 with FP32 accumulation, storage in FP64 */
+#define H2_FP64 0
+#define H2_MIXED 1
+
+typedef struct h2_matrix h2_matrix;
+
+/* Per-call statistics, filled when opts->stats is not NULL. Times are device
+ * times between CUDA events on opts->stream, in milliseconds. */
+typedef struct {
+    double t_prep_ms;      /* basis products, basis weights, total weights */
+    double t_rows_a_ms;    /* compressed induced row basis (Fig. 4) */
+    double t_cols_a_ms;    /* compressed induced column basis */
+    double t_mat_a_ms;     /* H^2-matrix on T^XY in the induced bases */
+    double t_rows_b_ms;    /* coarsened row basis (Fig. 7) */
+    double t_cols_b_ms;    /* coarsened column basis */
+    double t_mat_b_ms;     /* final couplings on the target block tree */
+    double t_total_ms;     /* the whole call, host synchronisations included */
+    int64_t kernel_launches; /* kernels launched by the call */
+    int64_t product_nodes;   /* nodes of T^XY */
+    int64_t triples;         /* (t,s,r) contributions to T^XY couplings */
+    int max_rank_a;          /* largest rank of the induced bases */
+    int max_rank_b;          /* largest rank of the final bases */
+    double bytes_moved;      /* algorithmic bytes of the contractions (model) */
+    double flops;            /* algorithmic flops of the contractions (model) */
+} h2_stats;
+
+typedef struct {
+    double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */
+    int precision;    /* H2_FP64 or H2_MIXED */
+    void* stream;     /* cudaStream_t; NULL selects the legacy default stream */
+    h2_stats* stats;  /* optional output, may be NULL */
+} h2_opts;
+
+/* Structure and sizes of a handle (h2_info). */
+typedef struct {
+    int64_t n;          /* number of points (rows = columns) */
+    int depth;          /* depth L of the cluster tree; all leaves sit on level L */
+    int nclusters;      /* 2^(L+1) - 1, numbered level by level (heap order) */
+    int64_t nblocks;    /* nodes of the block tree */
+    int64_t nadmissible;/* admissible leaves (coupling matrices) */
+    int64_t ndense;     /* inadmissible leaves (dense blocks) */
+    int leaf_size;
+    int order;          /* Chebyshev order m of the input bases (rank m^3), 0 after a product */
+    double eta;
+    int max_row_rank;
+    int max_col_rank;
+    double device_bytes;/* device memory held by the handle */
+} h2_info_t;
+
+/* Build the H^2-matrix of g(x_i, x_j) by tensor Chebyshev interpolation of
+ * order `cheb_order` (rank cheb_order^3), Sec. 2, Example "Integral operator"
+ * (point evaluation in place of the Galerkin integrals):
+ *   V_t[i, nu] = l_{t,nu}(x_i) on leaves, E_t'[nu', nu] = l_{t,nu}(xi_{t',nu'}),
+ *   S_ts[nu, mu] = g(xi_{t,nu}, xi_{s,mu}), dense N_ts[i, j] = g(x_i, x_j).
+ * The cluster tree is a median bisection along the longest box axis down to
+ * the depth L where every cluster holds at most `leaf_size` points; the block
+ * tree uses max(diam B_t, diam B_s) <= eta dist(B_t, B_s) (Def. "Block tree").
+ *   points      host array, n x 3, row-major (x0 y0 z0 x1 ...); read only,
+ *               copied; owned by the caller.
+ *   n >= 1, 1 <= leaf_size, 1 <= cheb_order <= 8, eta >= 0, kernel H2_K_*.
+ *   out         receives the new handle; untouched on error.
+ * Errors: H2_ERR_ARG, H2_ERR_NUMERIC (non-finite point), H2_ERR_OOM, H2_ERR_CUDA. */
+int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta,
+                    int cheb_order, const h2_opts* opts, h2_matrix** out);
+
+/* Z <- Z + X Y (Sec. 1), approximated to the block-relative tolerance
+ * opts->eps in both phases (Sec. 5, Sec. 6, Sec. 7).  X, Y and Z must share
+ * one cluster tree and block tree (built from the same points, leaf size and
+ * eta), and Z's row basis must be X's row basis and Z's column basis Y's
+ * column basis (same Chebyshev order); otherwise H2_ERR_SHAPE /
+ * H2_ERR_UNSUPPORTED.  The same handle may be passed as X, Y and Z.  On
+ * success Z holds new adaptive bases and couplings on its own block tree; on
+ * error Z is unchanged (the result is built aside and swapped in at the end).
+ * X and Y are only read. */
+int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts);
+
+/* Expand A into a dense n x n matrix in the ORIGINAL point order (row i and
+ * column j belong to points i and j), column-major with leading dimension
+ * ld >= n.  `out` is a host pointer if out_on_device == 0, else a device
+ * pointer on the handle's device.  Meant for tests at small n (n^2 doubles).
+ * Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
+int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, const h2_opts* opts);
+
+/* Sizes and structure of a handle.  Errors: H2_ERR_ARG. */
+int h2_info(const h2_matrix* A, h2_info_t* info);
+
+/* Copy structure arrays of a handle to host memory (any pointer may be NULL):
+ *   perm        n entries: original index of the point at tree position p
+ *   offsets     nclusters entries: first tree position of each cluster
+ *   sizes       nclusters entries: number of points of each cluster
+ *   row_ranks   nclusters entries: rank of the row basis per cluster
+ *   col_ranks   nclusters entries: rank of the column basis per cluster
+ * Errors: H2_ERR_ARG. */
+int h2_get_structure(const h2_matrix* A, int64_t* perm, int64_t* offsets, int64_t* sizes,
+                     int* row_ranks, int* col_ranks);
+
+/* Release a handle and its device memory; NULL is ignored. */
+void h2_free(h2_matrix* A);
+
+/* Static description of an error code. */
+const char* h2_error_string(int code);
+
+/* Message of the last failed call on the calling thread ("" if none); valid
+ * until the next call on that thread. */
+const char* h2_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* H2MUL_H */

@@ -1,0 +1,167 @@
+"""Python binding of the GB300 H^2-matrix product library (libh2mul.so).
+
+Argument marshalling only: every step of the product runs in the library's
+CUDA kernels.  The entry points carry the names of the C-ABI in
+``include/h2mul.h``: h2_build_interp, h2_mul_add, h2_to_dense, h2_free.
+There is no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB, build
+
+H2_OK = 0
+ERRORS = {-1: "H2_ERR_ARG", -2: "H2_ERR_SHAPE", -3: "H2_ERR_OOM", -4: "H2_ERR_NUMERIC",
+          -5: "H2_ERR_TIMEOUT", -6: "H2_ERR_UNSUPPORTED", -7: "H2_ERR_CUDA"}
+H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
+H2_FP64, H2_MIXED = 0, 1
+
+EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_free",
+            "h2_error_string", "h2_last_error_message"]
+
+
+class H2Error(RuntimeError):
+    def __init__(self, code, what, msg=""):
+        self.code = code
+        super().__init__(f"{what} failed: {ERRORS.get(code, code)} ({msg})")
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("t_prep_ms", ctypes.c_double), ("t_rows_a_ms", ctypes.c_double),
+                ("t_cols_a_ms", ctypes.c_double), ("t_mat_a_ms", ctypes.c_double),
+                ("t_rows_b_ms", ctypes.c_double), ("t_cols_b_ms", ctypes.c_double),
+                ("t_mat_b_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64), ("product_nodes", ctypes.c_int64),
+                ("triples", ctypes.c_int64), ("max_rank_a", ctypes.c_int), ("max_rank_b", ctypes.c_int),
+                ("bytes_moved", ctypes.c_double), ("flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("stats", ctypes.POINTER(Stats))]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("depth", ctypes.c_int), ("nclusters", ctypes.c_int),
+                ("nblocks", ctypes.c_int64), ("nadmissible", ctypes.c_int64), ("ndense", ctypes.c_int64),
+                ("leaf_size", ctypes.c_int), ("order", ctypes.c_int), ("eta", ctypes.c_double),
+                ("max_row_rank", ctypes.c_int), ("max_col_rank", ctypes.c_int), ("device_bytes", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libh2mul.so (built in-tree by build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libh2mul.so not found at {path}; run paper_2309_09061_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.h2_build_interp.argtypes = [vp, i64, ci, ci, cd, ci, vp, ctypes.POINTER(vp)]
+    lib.h2_mul_add.argtypes = [vp, vp, vp, vp]
+    lib.h2_to_dense.argtypes = [vp, vp, i64, ci, vp]
+    lib.h2_info.argtypes = [vp, vp]
+    lib.h2_get_structure.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.h2_free.argtypes = [vp]
+    lib.h2_free.restype = None
+    lib.h2_error_string.restype = ctypes.c_char_p
+    lib.h2_error_string.argtypes = [ci]
+    lib.h2_last_error_message.restype = ctypes.c_char_p
+    for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure"):
+        getattr(lib, f).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(code, what):
+    if code != H2_OK:
+        msg = load().h2_last_error_message().decode(errors="replace")
+        raise H2Error(code, what, msg)
+
+
+def _opts(eps=1e-6, precision=H2_FP64, stream=None, stats=None):
+    o = Opts(eps, precision, ctypes.c_void_p(stream or 0), None)
+    if stats is not None:
+        o.stats = ctypes.pointer(stats)
+    return o
+
+
+class H2Matrix:
+    """Owning wrapper of an h2_matrix handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "handle", None):
+            load().h2_free(self.handle)
+            self.handle = None
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().h2_info(self.handle, ctypes.byref(inf)), "h2_info")
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def structure(self):
+        inf = self.info()
+        n, nc = inf["n"], inf["nclusters"]
+        perm = np.empty(n, np.int64)
+        off = np.empty(nc, np.int64)
+        size = np.empty(nc, np.int64)
+        rr = np.empty(nc, np.int32)
+        cr = np.empty(nc, np.int32)
+        _check(load().h2_get_structure(self.handle, perm.ctypes.data, off.ctypes.data, size.ctypes.data,
+                                       rr.ctypes.data, cr.ctypes.data), "h2_get_structure")
+        return perm, off, size, rr, cr
+
+
+def h2_build_interp(points: np.ndarray, kernel: int, leaf_size: int, eta: float, cheb_order: int,
+                    stream: int | None = None) -> H2Matrix:
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 3:
+        raise ValueError("points must be an n x 3 array")
+    h = ctypes.c_void_p()
+    o = _opts(stream=stream)
+    _check(load().h2_build_interp(pts.ctypes.data, pts.shape[0], kernel, leaf_size, eta, cheb_order,
+                                  ctypes.byref(o), ctypes.byref(h)), "h2_build_interp")
+    return H2Matrix(h)
+
+
+def h2_mul_add(Z: H2Matrix, X: H2Matrix, Y: H2Matrix, eps: float, precision: int = H2_FP64,
+               stream: int | None = None) -> dict:
+    """Z <- Z + X Y; returns the call's statistics."""
+    st = Stats()
+    o = _opts(eps, precision, stream, st)
+    _check(load().h2_mul_add(Z.handle, X.handle, Y.handle, ctypes.byref(o)), "h2_mul_add")
+    return st.as_dict()
+
+
+def h2_to_dense(A: H2Matrix, out=None, stream: int | None = None) -> np.ndarray:
+    """Dense n x n expansion in the original point order (host array), or into a
+    device buffer when ``out`` is a CUDA tensor (column-major view of its storage)."""
+    n = A.info()["n"]
+    o = _opts(stream=stream)
+    if out is None:
+        buf = np.empty((n, n), dtype=np.float64, order="F")
+        _check(load().h2_to_dense(A.handle, buf.ctypes.data, n, 0, ctypes.byref(o)), "h2_to_dense")
+        return buf
+    _check(load().h2_to_dense(A.handle, out.data_ptr(), n, 1, ctypes.byref(o)), "h2_to_dense")
+    return out
+
+
+def h2_free(A: H2Matrix) -> None:
+    A.free()

@@ -1,0 +1,437 @@
+// Runtime of the H^2 library: device buffers, the batched-op runner, and the
+// entry points h2_build_interp, h2_to_dense, h2_info, h2_get_structure,
+// h2_free, h2_error_string.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+// ---------------------------------------------------------------- memory
+static cudaMemPool_t lib_pool(int dev) {
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) throw Error(H2_ERR_CUDA, "device index out of range");
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        H2_CUDA(cudaMemPoolCreate(&pools[dev], &props));
+        uint64_t thr = UINT64_MAX;
+        H2_CUDA(cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &thr));
+    }
+    return pools[dev];
+}
+
+void DevBuf::alloc(size_t n) {
+    reset();
+    if (n == 0) return;
+    void* p2 = nullptr;
+    H2_CUDA(cudaMalloc(&p2, n * sizeof(double)));
+    p = (double*)p2;
+    len = n;
+}
+
+void DevBuf::reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    len = 0;
+}
+
+// ---------------------------------------------------------------- runner
+Runner::~Runner() { release_all(); }
+
+double* Runner::dalloc(size_t n) {
+    if (n == 0) n = 1;
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    void* p = nullptr;
+    H2_CUDA(cudaMallocFromPoolAsync(&p, n * sizeof(double), lib_pool(dev), st_));
+    owned_.push_back(p);
+    return (double*)p;
+}
+
+template <class T>
+T* Runner::upload(const std::vector<T>& v) {
+    size_t bytes = std::max<size_t>(v.size() * sizeof(T), 8);
+    double* d = dalloc((bytes + 7) / 8);
+    if (!v.empty()) H2_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
+    return (T*)d;
+}
+template int* Runner::upload<int>(const std::vector<int>&);
+template int64_t* Runner::upload<int64_t>(const std::vector<int64_t>&);
+template double* Runner::upload<double>(const std::vector<double>&);
+template double** Runner::upload<double*>(const std::vector<double*>&);
+
+void Runner::release_all() {
+    for (void* p : owned_) cudaFreeAsync(p, st_);
+    owned_.clear();
+    d_flag_ = nullptr;
+}
+
+void Runner::ensure_flag() {
+    if (!d_flag_) {
+        d_flag_ = (int*)dalloc(1);
+        H2_CUDA(cudaMemsetAsync(d_flag_, 0, sizeof(int), st_));
+    }
+}
+
+void Runner::job(double* C, int m, int n, int ldc, double beta) {
+    jobs_.push_back(GJob{C, m, n, ldc, (int)terms_.size(), 0, beta});
+}
+
+void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha,
+                  const double* scale) {
+    if (k <= 0 || jobs_.empty()) return;
+    terms_.push_back(GTerm{A, B, scale, alpha, k, lda, ldb, ta, tb});
+    jobs_.back().nt++;
+}
+
+void Runner::flush_gemm(int precision_override) {
+    if (jobs_.empty()) return;
+    std::vector<GTile> tiles;
+    for (int j = 0; j < (int)jobs_.size(); ++j) {
+        const GJob& J = jobs_[j];
+        for (int i0 = 0; i0 < J.m; i0 += 32)
+            for (int j0 = 0; j0 < J.n; j0 += 32) tiles.push_back(GTile{j, i0, j0});
+    }
+    if (!tiles.empty()) {
+        GTerm* dt = upload(terms_);
+        GJob* dj = upload(jobs_);
+        GTile* dti = upload(tiles);
+        // split very large launches to stay well inside the grid limit
+        const int chunk = 1 << 30;
+        for (size_t off = 0; off < tiles.size(); off += chunk) {
+            int nt = (int)std::min<size_t>(chunk, tiles.size() - off);
+            launch_gemm(dt, dj, dti + off, nt, precision_override >= 0 ? precision_override : prec_, st_);
+            ++launches;
+        }
+    }
+    terms_.clear();
+    jobs_.clear();
+}
+
+void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q) {
+    if (m <= 0 || n <= 0) return;
+    double* tau = dalloc(std::min(m, n));
+    qrs_.push_back(QRJob{A, R, Q, tau, m, n, lda, ldr, ldq, q});
+}
+
+void Runner::flush_qr() {
+    if (qrs_.empty()) return;
+    QRJob* d = upload(qrs_);
+    launch_qr(d, (int)qrs_.size(), st_);
+    ++launches;
+    qrs_.clear();
+}
+
+void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps) {
+    ensure_flag();
+    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, m, n, ldb, ldu, eps});
+    svd_maxn_ = std::max(svd_maxn_, n);
+}
+
+void Runner::flush_svd() {
+    if (svds_.empty()) return;
+    SVDJob* d = upload(svds_);
+    launch_svd(d, (int)svds_.size(), svd_maxn_, st_);
+    ++launches;
+    svds_.clear();
+    svd_maxn_ = 0;
+}
+
+void Runner::norm(const double* A, int m, int n, int lda, double* inv, double* nrm) {
+    if (m > 2048 || n > 2048) throw Error(H2_ERR_UNSUPPORTED, "block too large for the norm kernel");
+    norms_.push_back(NormJob{A, inv, nrm, m, n, lda});
+}
+
+void Runner::flush_norm() {
+    if (norms_.empty()) return;
+    NormJob* d = upload(norms_);
+    launch_norm(d, (int)norms_.size(), st_);
+    ++launches;
+    norms_.clear();
+}
+
+void Runner::copy(const double* src, int lds, double* dst, int ldd, int rows, int cols, int trans, double alpha,
+                  const double* scale, double beta) {
+    if (rows <= 0 || cols <= 0) return;
+    copies_.push_back(CopyJob{src, dst, scale, alpha, beta, rows, cols, lds, ldd, trans});
+}
+
+void Runner::flush_copy() {
+    if (copies_.empty()) return;
+    CopyJob* d = upload(copies_);
+    launch_copy(d, (int)copies_.size(), st_);
+    ++launches;
+    copies_.clear();
+}
+
+void Runner::flush_all() {
+    flush_copy();
+    flush_gemm();
+    flush_norm();
+    flush_qr();
+    flush_svd();
+}
+
+template GTerm* Runner::upload<GTerm>(const std::vector<GTerm>&);
+template GJob* Runner::upload<GJob>(const std::vector<GJob>&);
+template GTile* Runner::upload<GTile>(const std::vector<GTile>&);
+template QRJob* Runner::upload<QRJob>(const std::vector<QRJob>&);
+template SVDJob* Runner::upload<SVDJob>(const std::vector<SVDJob>&);
+template NormJob* Runner::upload<NormJob>(const std::vector<NormJob>&);
+template CopyJob* Runner::upload<CopyJob>(const std::vector<CopyJob>&);
+template SumSqJob* Runner::upload<SumSqJob>(const std::vector<SumSqJob>&);
+
+cudaStream_t stream_of(const h2_opts* o) { return o ? (cudaStream_t)o->stream : (cudaStream_t)0; }
+
+}  // namespace h2
+
+using namespace h2;
+
+static thread_local std::string g_last_error;
+
+void h2_set_last_error(const char* m) { g_last_error = m ? m : ""; }
+
+
+static int run_guarded(const std::function<void()>& f) {
+    try {
+        f();
+        return H2_OK;
+    } catch (const Error& e) {
+        g_last_error = e.what();
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        g_last_error = "host allocation failed";
+        return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return H2_ERR_CUDA;
+    }
+}
+
+extern "C" {
+
+const char* h2_error_string(int code) {
+    switch (code) {
+        case H2_OK: return "success";
+        case H2_ERR_ARG: return "invalid argument";
+        case H2_ERR_SHAPE: return "operands do not share one cluster tree and block tree";
+        case H2_ERR_OOM: return "out of memory";
+        case H2_ERR_NUMERIC: return "non-finite value";
+        case H2_ERR_TIMEOUT: return "iteration limit reached";
+        case H2_ERR_UNSUPPORTED: return "unsupported case";
+        case H2_ERR_CUDA: return "CUDA runtime error";
+        default: return "unknown error";
+    }
+}
+
+const char* h2_last_error_message(void) { return g_last_error.c_str(); }
+
+int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta, int cheb_order,
+                    const h2_opts* opts, h2_matrix** out) {
+    if (!points || !out || n < 1 || leaf_size < 1 || cheb_order < 1 || cheb_order > 8 || !(eta >= 0.0) ||
+        !std::isfinite(eta) || kernel < H2_K_LAPLACE || kernel > H2_K_DELTA)
+        return H2_ERR_ARG;
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(points[i])) return H2_ERR_NUMERIC;
+    return run_guarded([&] {
+        cudaStream_t st = stream_of(opts);
+        auto M = std::make_unique<h2_matrix>();
+        H2_CUDA(cudaGetDevice(&M->device));
+        M->st = build_structure(points, n, leaf_size, eta);
+        M->kernel = kernel;
+        M->order = cheb_order;
+        const Tree& T = M->st->tree;
+        const BlockTree& B = M->st->blocks;
+        const int m = cheb_order, k = m * m * m;
+        Runner R(st, H2_FP64);
+        // structure arrays on the device
+        double* d_pts = R.upload(M->st->points);
+        int64_t* d_perm = R.upload(T.perm);
+        int64_t* d_off = R.upload(T.off);
+        int64_t* d_size = R.upload(T.size);
+        double* d_lo = R.upload(T.lo);
+        double* d_hi = R.upload(T.hi);
+        // basis: leaves + transfers in one chunk
+        auto V = std::make_shared<Basis>();
+        V->rank.assign(T.nc, k);
+        V->leaf.assign(T.nc, nullptr);
+        V->tr.assign(T.nc, nullptr);
+        size_t total = 0;
+        for (int c = 0; c < T.nc; ++c) {
+            if (T.is_leaf(c)) total += (size_t)T.size[c] * k;
+            if (c > 0) total += (size_t)k * k;
+        }
+        auto chunk = std::make_shared<DevBuf>();
+        chunk->alloc(total);
+        V->chunks.push_back(chunk);
+        size_t o = 0;
+        int64_t max_size = 0;
+        for (int c = 0; c < T.nc; ++c) {
+            if (T.is_leaf(c)) {
+                V->leaf[c] = chunk->p + o;
+                o += (size_t)T.size[c] * k;
+                max_size = std::max(max_size, T.size[c]);
+            }
+            if (c > 0) {
+                V->tr[c] = chunk->p + o;
+                o += (size_t)k * k;
+            }
+        }
+        double** d_leafp = R.upload(V->leaf);
+        double** d_trp = R.upload(V->tr);
+        launch_interp_leaf(d_pts, d_perm, d_off, d_size, d_lo, d_hi, d_leafp, Tree::first(T.L), Tree::count(T.L), m,
+                           max_size, st);
+        launch_interp_transfer(d_lo, d_hi, d_trp, T.nc, m, st);
+        // couplings and dense blocks
+        size_t stot = 0, ntot = 0;
+        int nb = (int)B.kind.size();
+        M->blk.assign(nb, nullptr);
+        for (int b = 0; b < nb; ++b) {
+            if (B.kind[b] == ADM) stot += (size_t)k * k;
+            if (B.kind[b] == DENSE) ntot += (size_t)T.size[B.t[b]] * T.size[B.s[b]];
+        }
+        auto cs = std::make_shared<DevBuf>(), cn = std::make_shared<DevBuf>();
+        cs->alloc(stot);
+        cn->alloc(ntot);
+        M->chunks = {cs, cn};
+        std::vector<int> at, as, dt, ds;
+        std::vector<double*> ap, dp;
+        size_t so = 0, no = 0;
+        for (int b = 0; b < nb; ++b) {
+            if (B.kind[b] == ADM) {
+                M->blk[b] = cs->p + so;
+                so += (size_t)k * k;
+                at.push_back(B.t[b]);
+                as.push_back(B.s[b]);
+                ap.push_back(M->blk[b]);
+            } else if (B.kind[b] == DENSE) {
+                M->blk[b] = cn->p + no;
+                no += (size_t)T.size[B.t[b]] * T.size[B.s[b]];
+                dt.push_back(B.t[b]);
+                ds.push_back(B.s[b]);
+                dp.push_back(M->blk[b]);
+            }
+        }
+        launch_interp_coupling(d_lo, d_hi, R.upload(at), R.upload(as), R.upload(ap), (int)at.size(), m, kernel, st);
+        launch_interp_dense(d_pts, d_perm, d_off, d_size, R.upload(dt), R.upload(ds), R.upload(dp), (int)dt.size(),
+                            kernel, st);
+        M->V = V;
+        M->W = V;
+        H2_CUDA(cudaGetLastError());
+        R.release_all();
+        H2_CUDA(cudaStreamSynchronize(st));
+        *out = M.release();
+    });
+}
+
+int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, const h2_opts* opts) {
+    if (!A || !out || ld < A->st->tree.n) return H2_ERR_ARG;
+    return run_guarded([&] {
+        cudaStream_t st = stream_of(opts);
+        const Tree& T = A->st->tree;
+        const BlockTree& B = A->st->blocks;
+        const int64_t n = T.n;
+        Runner R(st, H2_FP64);
+        // expanded bases per cluster: rows of the cluster x rank
+        auto expand = [&](const Basis& b) {
+            std::vector<double*> ex(T.nc, nullptr);
+            for (int c = 0; c < T.nc; ++c) ex[c] = R.dalloc((size_t)T.size[c] * std::max(1, b.rank[c]));
+            for (int c = Tree::first(T.L); c < T.nc; ++c)
+                R.copy(b.leaf[c], (int)T.size[c], ex[c], (int)T.size[c], (int)T.size[c], b.rank[c], 0);
+            R.flush_copy();
+            for (int l = T.L - 1; l >= 0; --l) {
+                for (int c = Tree::first(l); c < Tree::first(l) + Tree::count(l); ++c) {
+                    for (int i = 0; i < 2; ++i) {
+                        int ch = Tree::child(c, i);
+                        R.job(ex[c] + (T.off[ch] - T.off[c]), (int)T.size[ch], b.rank[c], (int)T.size[c], 0.0);
+                        R.term(ex[ch], 0, (int)T.size[ch], b.tr[ch], 0, b.rank[ch], b.rank[ch]);
+                    }
+                }
+                R.flush_gemm(H2_FP64);
+            }
+            return ex;
+        };
+        auto ev = expand(*A->V);
+        auto ew = (A->W == A->V) ? ev : expand(*A->W);
+        double* dense = R.dalloc((size_t)n * n);
+        H2_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * n * n, st));
+        std::vector<double*> tmp(B.kind.size(), nullptr);
+        for (int b = 0; b < (int)B.kind.size(); ++b) {
+            int t = B.t[b], s = B.s[b];
+            if (B.kind[b] == ADM) {
+                tmp[b] = R.dalloc((size_t)T.size[t] * std::max(1, A->W->rank[s]));
+                R.job(tmp[b], (int)T.size[t], A->W->rank[s], (int)T.size[t], 0.0);
+                R.term(ev[t], 0, (int)T.size[t], A->blk[b], 0, A->V->rank[t], A->V->rank[t]);
+            } else if (B.kind[b] == DENSE) {
+                R.copy(A->blk[b], (int)T.size[t], dense + T.off[t] + T.off[s] * n, (int)n, (int)T.size[t],
+                       (int)T.size[s], 0);
+            }
+        }
+        R.flush_gemm(H2_FP64);
+        R.flush_copy();
+        for (int b = 0; b < (int)B.kind.size(); ++b) {
+            int t = B.t[b], s = B.s[b];
+            if (B.kind[b] != ADM) continue;
+            R.job(dense + T.off[t] + T.off[s] * n, (int)T.size[t], (int)T.size[s], (int)n, 0.0);
+            R.term(tmp[b], 0, (int)T.size[t], ew[s], 1, (int)T.size[s], A->W->rank[s]);
+        }
+        R.flush_gemm(H2_FP64);
+        int64_t* d_perm = R.upload(T.perm);
+        double* target = out;
+        if (!out_on_device) target = R.dalloc((size_t)ld * n);
+        launch_scatter_dense(dense, n, d_perm, target, ld, st);
+        if (!out_on_device)
+            H2_CUDA(cudaMemcpyAsync(out, target, sizeof(double) * ld * n, cudaMemcpyDeviceToHost, st));
+        H2_CUDA(cudaGetLastError());
+        H2_CUDA(cudaStreamSynchronize(st));
+        R.release_all();
+        H2_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int h2_info(const h2_matrix* A, h2_info_t* info) {
+    if (!A || !info) return H2_ERR_ARG;
+    const Tree& T = A->st->tree;
+    const BlockTree& B = A->st->blocks;
+    info->n = T.n;
+    info->depth = T.L;
+    info->nclusters = T.nc;
+    info->nblocks = (int64_t)B.kind.size();
+    info->nadmissible = B.count(ADM);
+    info->ndense = B.count(DENSE);
+    info->leaf_size = T.leaf_size;
+    info->order = A->order;
+    info->eta = A->st->eta;
+    info->max_row_rank = A->V->max_rank();
+    info->max_col_rank = A->W->max_rank();
+    double bytes = A->V->bytes() + (A->W != A->V ? A->W->bytes() : 0.0);
+    for (auto& c : A->chunks) bytes += 8.0 * c->len;
+    info->device_bytes = bytes;
+    return H2_OK;
+}
+
+int h2_get_structure(const h2_matrix* A, int64_t* perm, int64_t* offsets, int64_t* sizes, int* row_ranks,
+                     int* col_ranks) {
+    if (!A) return H2_ERR_ARG;
+    const Tree& T = A->st->tree;
+    if (perm) std::copy(T.perm.begin(), T.perm.end(), perm);
+    if (offsets) std::copy(T.off.begin(), T.off.end(), offsets);
+    if (sizes) std::copy(T.size.begin(), T.size.end(), sizes);
+    if (row_ranks) std::copy(A->V->rank.begin(), A->V->rank.end(), row_ranks);
+    if (col_ranks) std::copy(A->W->rank.begin(), A->W->rank.end(), col_ranks);
+    return H2_OK;
+}
+
+void h2_free(h2_matrix* A) {
+    if (!A) return;
+    cudaDeviceSynchronize();
+    delete A;
+}
+
+}  // extern "C"

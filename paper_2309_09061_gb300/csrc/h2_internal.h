@@ -1,0 +1,292 @@
+// Internal declarations of the H^2 product library: host structures (cluster
+// tree, block trees, product block tree), device storage of a handle, and the
+// descriptors of the batched device operations.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/h2mul.h"
+
+namespace h2 {
+
+// ---------------------------------------------------------------- errors
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& what) : std::runtime_error(what), code(c) {}
+};
+
+#define H2_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            throw ::h2::Error(e_ == cudaErrorMemoryAllocation ? H2_ERR_OOM : H2_ERR_CUDA, \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+// ---------------------------------------------------------------- trees
+// Complete binary cluster tree, numbered level by level: cluster c has
+// children 2c+1, 2c+2; level l holds clusters 2^l-1 .. 2^(l+1)-2.
+struct Tree {
+    int64_t n = 0;
+    int L = 0;
+    int nc = 0;
+    int leaf_size = 0;
+    std::vector<int64_t> perm;       // tree position -> original index
+    std::vector<int64_t> off, size;  // per cluster
+    std::vector<double> lo, hi;      // per cluster, 3 each (padded boxes)
+    static int first(int l) { return (1 << l) - 1; }
+    static int count(int l) { return 1 << l; }
+    static int parent(int c) { return (c - 1) / 2; }
+    static int child(int c, int i) { return 2 * c + 1 + i; }
+    static int level(int c) {
+        int l = 0;
+        while (((1 << (l + 1)) - 1) <= c) ++l;
+        return l;
+    }
+    bool is_leaf(int c) const { return c >= first(L); }
+};
+
+enum Kind : int8_t { ADM = 0, DENSE = 1, SPLIT = 2 };
+
+// A block tree over (rows x cols) of the same cluster tree (Def. "Block tree").
+struct BlockTree {
+    int nc = 0;
+    std::vector<int> t, s;
+    std::vector<int8_t> kind;
+    std::unordered_map<int64_t, int> id;     // t * nc + s -> block index
+    std::vector<std::vector<int>> by_row;    // t -> blocks of row t, by increasing s
+    std::vector<std::vector<int>> by_col;    // s -> blocks of column s, by increasing t
+    int find(int a, int b) const {
+        auto it = id.find((int64_t)a * nc + b);
+        return it == id.end() ? -1 : it->second;
+    }
+    int add(int a, int b, int8_t k) {
+        int i = (int)t.size();
+        t.push_back(a);
+        s.push_back(b);
+        kind.push_back(k);
+        id[(int64_t)a * nc + b] = i;
+        return i;
+    }
+    void finish();  // fills by_row / by_col
+    int64_t count(int8_t k) const {
+        int64_t c = 0;
+        for (auto x : kind) c += (x == k);
+        return c;
+    }
+};
+
+// Shared structure of matrices built from one point set.
+struct Structure {
+    Tree tree;
+    BlockTree blocks;
+    double eta = 0;
+    std::vector<double> points;  // n x 3, original order
+    uint64_t fingerprint = 0;
+};
+
+std::shared_ptr<Structure> build_structure(const double* pts, int64_t n, int leaf, double eta);
+
+// Product block tree T^XY (Sec. 6) with its triples: for node (t,r), the s with
+// (t,s) in T_IJ, (s,r) in T_JK, not both split.
+struct ProductTree {
+    BlockTree nodes;                       // kind ADM / DENSE / SPLIT
+    std::vector<std::vector<int>> triples; // per node: list of s
+};
+ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y);
+
+// ---------------------------------------------------------------- device storage
+struct DevBuf {
+    double* p = nullptr;
+    size_t len = 0;  // doubles
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { reset(); }
+    void alloc(size_t n);
+    void reset();
+};
+
+// A cluster basis: leaf matrices (size x rank, column-major) and transfer
+// matrices (rank x rank(parent)), one device pointer per cluster into chunks
+// owned by the basis (ranks are only known level by level).
+struct Basis {
+    std::vector<int> rank;
+    std::vector<double*> leaf;  // nullptr for non-leaves
+    std::vector<double*> tr;    // nullptr for the root
+    std::vector<std::shared_ptr<DevBuf>> chunks;
+    int max_rank() const {
+        int m = 0;
+        for (int r : rank) m = r > m ? r : m;
+        return m;
+    }
+    double bytes() const {
+        double b = 0;
+        for (auto& c : chunks) b += 8.0 * c->len;
+        return b;
+    }
+};
+
+}  // namespace h2
+
+struct h2_matrix {
+    std::shared_ptr<h2::Structure> st;
+    std::shared_ptr<h2::Basis> V, W;      // W may alias V
+    std::vector<double*> blk;             // per block: S (ADM, rank x rank) or N (DENSE, size x size); null for SPLIT
+    std::vector<std::shared_ptr<h2::DevBuf>> chunks;
+    int kernel = -1;
+    int order = 0;                        // Chebyshev order of the bases, 0 for product results
+    int device = 0;
+};
+
+namespace h2 {
+
+// ---------------------------------------------------------------- batched ops
+// One term op(A) op(B) of a product sum; op transposes when the flag is set.
+// The effective factor is alpha * (*scale) when scale is not null.
+struct GTerm {
+    const double* A;
+    const double* B;
+    const double* scale;
+    double alpha;
+    int k, lda, ldb;
+    int ta, tb;
+};
+// C (m x n, ldc) = beta C + sum of terms [t0, t0 + nt).
+struct GJob {
+    double* C;
+    int m, n, ldc;
+    int t0, nt;
+    double beta;
+};
+struct GTile {
+    int job, i0, j0;
+};
+
+// Householder QR of A (m x n, in place, lda).  R (min(m,n) x n, ldr) receives
+// the triangular factor (zeros below the diagonal); Q (m x q, ldq) the first q
+// columns of the orthogonal factor when Q is not null.
+struct QRJob {
+    double* A;
+    double* R;
+    double* Q;
+    double* tau;  // workspace, min(m,n) entries
+    int m, n, lda, ldr, ldq, q;
+};
+
+// One-sided Jacobi SVD of B (m x n, in place).  U (m x n, ldu) receives the
+// left singular vectors sorted by decreasing singular value, sigma the values,
+// *count the number of values above eps, *flag nonzero if the sweep limit was
+// reached without convergence.
+struct SVDJob {
+    double* B;
+    double* U;
+    double* sigma;
+    int* count;
+    int* flag;
+    int m, n, ldb, ldu;
+    double eps;
+};
+
+// Spectral norm of A (m x n) by power iteration; writes 1/||A|| (0 if the norm
+// is below tiny) to *inv and ||A|| to *nrm.
+struct NormJob {
+    const double* A;
+    double* inv;
+    double* nrm;
+    int m, n, lda;
+};
+
+// dst (rows x cols) = beta * dst + alpha * (*scale) * op(src), op = transpose if trans.
+struct CopyJob {
+    const double* src;
+    double* dst;
+    const double* scale;
+    double alpha, beta;
+    int rows, cols, lds, ldd, trans;
+};
+
+// Kernel launchers (h2_kernels.cu); job arrays are device pointers.
+void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
+                 cudaStream_t st);
+void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
+void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);
+void launch_norm(const NormJob* jobs, int njobs, cudaStream_t st);
+void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);
+void launch_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
+                        const double* lo, const double* hi, double* const* leafp, int first_leaf, int nleaves, int m,
+                        int64_t max_size, cudaStream_t st);
+void launch_interp_transfer(const double* lo, const double* hi, double* const* trp, int nc, int m, cudaStream_t st);
+void launch_interp_coupling(const double* lo, const double* hi, const int* bt, const int* bs, double* const* bp,
+                            int nblocks, int m, int kernel, cudaStream_t st);
+void launch_interp_dense(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
+                         const int* bt, const int* bs, double* const* bp, int nblocks, int kernel, cudaStream_t st);
+void launch_scatter_dense(const double* src, int64_t n, const int64_t* perm, double* out, int64_t ld,
+                          cudaStream_t st);
+void launch_set_identity(double* A, int m, int n, int lda, cudaStream_t st);
+void launch_check_finite(const double* A, size_t len, int* flag, cudaStream_t st);
+// Sum of squares of the entries of A (rows x cols, lda), added to out[slot].
+struct SumSqJob {
+    const double* A;
+    int rows, cols, lda, slot;
+};
+void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st);
+// w[i] = 1 / sqrt(v[i]) (0 where v[i] == 0), i < n
+void launch_inv_sqrt(const double* v, double* w, int n, cudaStream_t st);
+
+// Host-side driver of batched ops: collects jobs, uploads, launches.
+class Runner {
+public:
+    explicit Runner(cudaStream_t st, int precision) : st_(st), prec_(precision) {}
+    ~Runner();
+    cudaStream_t stream() const { return st_; }
+    int precision() const { return prec_; }
+    int64_t launches = 0;
+
+    // GEMM: start a job, add terms, the job is closed by the next job/flush.
+    void job(double* C, int m, int n, int ldc, double beta);
+    void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
+              const double* scale = nullptr);
+    void flush_gemm(int precision_override = -1);
+    void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q);
+    void flush_qr();
+    void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps);
+    void flush_svd();
+    void norm(const double* A, int m, int n, int lda, double* inv, double* nrm);
+    void flush_norm();
+    void copy(const double* src, int lds, double* dst, int ldd, int rows, int cols, int trans, double alpha = 1.0,
+              const double* scale = nullptr, double beta = 0.0);
+    void flush_copy();
+    void flush_all();
+    int* svd_flag() const { return d_flag_; }
+    void ensure_flag();
+
+    // device scratch from the stream-ordered pool
+    double* dalloc(size_t n);
+    template <class T>
+    T* upload(const std::vector<T>& v);
+    void release_all();  // frees every dalloc/upload of this runner (stream ordered)
+
+private:
+    cudaStream_t st_;
+    int prec_;
+    std::vector<GTerm> terms_;
+    std::vector<GJob> jobs_;
+    std::vector<QRJob> qrs_;
+    std::vector<SVDJob> svds_;
+    int svd_maxn_ = 0;
+    std::vector<NormJob> norms_;
+    std::vector<CopyJob> copies_;
+    std::vector<void*> owned_;
+    int* d_flag_ = nullptr;
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace h2

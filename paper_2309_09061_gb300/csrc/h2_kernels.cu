@@ -1,0 +1,536 @@
+// Device kernels of the H^2 product library (sm_103a).
+//
+// Batched small dense linear algebra: every launch covers all clusters or all
+// blocks of one tree level at once.  Each batched kernel reads a device array
+// of job descriptors built by the host executor.
+#include <cfloat>
+#include <cmath>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+// ------------------------------------------------------------------ GEMM
+// C = beta C + sum_terms alpha_t op(A_t) op(B_t) over 32 x 32 output tiles.
+// T is the arithmetic type: double (H2_FP64) or float (H2_MIXED; operands are
+// rounded to FP32 when staged in shared memory, accumulation in FP32).
+constexpr int GB = 32;   // tile edge
+constexpr int GK = 16;   // k-chunk
+constexpr int GT = 256;  // threads: 16 x 16, each 2 x 2 outputs
+
+template <class T>
+__global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
+                                             const GTile* __restrict__ tiles) {
+    __shared__ T As[GK][GB + 1];
+    __shared__ T Bs[GK][GB + 1];
+    const GTile tile = tiles[blockIdx.x];
+    const GJob J = jobs[tile.job];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T acc[2][2] = {{0, 0}, {0, 0}};
+    for (int it = 0; it < J.nt; ++it) {
+        const GTerm P = terms[J.t0 + it];
+        const double f = P.alpha * (P.scale ? *P.scale : 1.0);
+        if (f == 0.0) continue;
+        for (int k0 = 0; k0 < P.k; k0 += GK) {
+            // stage op(A)[i0:i0+32, k0:k0+16] and op(B)[k0:k0+16, j0:j0+32]
+            for (int e = threadIdx.x; e < GK * GB; e += GT) {
+                int i, kk;
+                if (!P.ta) { i = e % GB; kk = e / GB; } else { kk = e % GK; i = e / GK; }
+                int gi = tile.i0 + i, gk = k0 + kk;
+                double v = 0.0;
+                if (gi < J.m && gk < P.k) v = P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda];
+                As[kk][i] = (T)(f * v);
+                int j;
+                if (!P.tb) { kk = e % GK; j = e / GK; } else { j = e % GB; kk = e / GB; }
+                int gj = tile.j0 + j;
+                gk = k0 + kk;
+                double w = 0.0;
+                if (gj < J.n && gk < P.k) w = P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb];
+                Bs[kk][j] = (T)w;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < GK; ++kk) {
+                T a0 = As[kk][tx], a1 = As[kk][tx + 16];
+                T b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+                acc[0][0] += a0 * b0;
+                acc[1][0] += a1 * b0;
+                acc[0][1] += a0 * b1;
+                acc[1][1] += a1 * b1;
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            int gi = tile.i0 + tx + 16 * a, gj = tile.j0 + ty + 16 * b;
+            if (gi < J.m && gj < J.n) {
+                double* c = J.C + gi + (size_t)gj * J.ldc;
+                double v = (double)acc[a][b];
+                *c = (J.beta == 0.0) ? v : J.beta * *c + v;
+            }
+        }
+}
+
+void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
+                 cudaStream_t st) {
+    if (ntiles <= 0) return;
+    if (precision == H2_MIXED)
+        k_gemm<float><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
+    else
+        k_gemm<double><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < NT / 32) ? red[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) red[0] = s;
+    }
+    __syncthreads();
+    return red[0];
+}
+
+// ------------------------------------------------------------------ Householder QR
+// Column-by-column Householder reflections H_j = I - tau_j v_j v_j^* with
+// v_j(j) = 1 (Golub & Van Loan, Sec. 5.1-5.2), applied in place; the
+// orthogonal factor is accumulated backwards when requested.
+constexpr int QT = 256;
+
+__global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
+    __shared__ double red[QT / 32];
+    const QRJob J = jobs[blockIdx.x];
+    const int m = J.m, n = J.n, p = m < n ? m : n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = QT / 32;
+    for (int j = 0; j < p; ++j) {
+        double* col = J.A + (size_t)j * J.lda;
+        double s = 0.0;
+        for (int i = j + 1 + threadIdx.x; i < m; i += QT) s += col[i] * col[i];
+        s = block_sum<QT>(s, red);
+        const double x0 = col[j];
+        double tau = 0.0, beta = x0, sc = 0.0;
+        if (s > 0.0) {
+            beta = -copysign(sqrt(x0 * x0 + s), x0);
+            tau = (beta - x0) / beta;
+            sc = 1.0 / (x0 - beta);
+        }
+        __syncthreads();
+        if (s > 0.0)
+            for (int i = j + 1 + threadIdx.x; i < m; i += QT) col[i] *= sc;
+        if (threadIdx.x == 0) {
+            col[j] = beta;
+            J.tau[j] = tau;
+        }
+        __syncthreads();
+        if (tau != 0.0) {
+            for (int c = j + 1 + warp; c < n; c += nw) {
+                double* a = J.A + (size_t)c * J.lda;
+                double w = 0.0;
+                for (int i = j + 1 + lane; i < m; i += 32) w += col[i] * a[i];
+                w = warp_sum(w) + a[j];
+                w *= tau;
+                if (lane == 0) a[j] -= w;
+                for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * col[i];
+            }
+        }
+        __syncthreads();
+    }
+    if (J.R) {
+        for (int e = threadIdx.x; e < p * n; e += QT) {
+            int i = e % p, c = e / p;
+            J.R[i + (size_t)c * J.ldr] = (i <= c) ? J.A[i + (size_t)c * J.lda] : 0.0;
+        }
+    }
+    if (J.Q) {
+        for (int e = threadIdx.x; e < m * J.q; e += QT) {
+            int i = e % m, c = e / m;
+            J.Q[i + (size_t)c * J.ldq] = (i == c) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        for (int j = p - 1; j >= 0; --j) {
+            const double tau = J.tau[j];
+            if (tau == 0.0) continue;
+            const double* v = J.A + (size_t)j * J.lda;
+            for (int c = warp; c < J.q; c += nw) {
+                double* a = J.Q + (size_t)c * J.ldq;
+                double w = 0.0;
+                for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * a[i];
+                w = warp_sum(w) + a[j];
+                w *= tau;
+                if (lane == 0) a[j] -= w;
+                for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * v[i];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_qr<<<njobs, QT, 0, st>>>(jobs);
+}
+
+// ------------------------------------------------------------------ one-sided Jacobi SVD
+// Hestenes' method: plane rotations from the right make the columns of B
+// mutually orthogonal, B J = U Sigma; pairs follow a round-robin tournament so
+// that the pairs of one round are disjoint and run in parallel warps.  The
+// sweep count is bounded; *flag reports a run that hit the bound.
+constexpr int JT = 512;
+constexpr int JMAXSWEEP = 40;
+constexpr int JMAXN = 2048;
+
+__device__ __forceinline__ int rr_player(int pos, int round, int np) {
+    if (pos == 0) return 0;
+    return 1 + (pos - 1 + round) % (np - 1);
+}
+
+__global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
+    __shared__ int rotated;
+    __shared__ double sig[JMAXN];
+    const SVDJob J = jobs[blockIdx.x];
+    const int m = J.m, n = J.n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
+    const int np = n + (n & 1);
+    const double tol = (double)(m > 1 ? m : 1) * DBL_EPSILON;
+    int sweep = 0;
+    bool converged = (n < 2);
+    for (; sweep < JMAXSWEEP && !converged; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pr = warp; pr < np / 2; pr += nw) {
+                int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
+                if (p >= n || q >= n) continue;
+                if (p > q) { int t = p; p = q; q = t; }
+                double* ap = J.B + (size_t)p * J.ldb;
+                double* aq = J.B + (size_t)q * J.ldb;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < m; i += 32) {
+                    double x = ap[i], y = aq[i];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+                    double zeta = (be - al) / (2.0 * ga);
+                    double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
+                                                     : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                    for (int i = lane; i < m; i += 32) {
+                        double x = ap[i], y = aq[i];
+                        ap[i] = c * x - s * y;
+                        aq[i] = s * x + c * y;
+                    }
+                    if (lane == 0) rotated = 1;
+                }
+            }
+            __syncthreads();
+        }
+        converged = (rotated == 0);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
+    for (int c = warp; c < n; c += nw) {
+        const double* a = J.B + (size_t)c * J.ldb;
+        double s = 0.0;
+        for (int i = lane; i < m; i += 32) s += a[i] * a[i];
+        s = warp_sum(s);
+        if (lane == 0) sig[c] = sqrt(s);
+    }
+    __syncthreads();
+    for (int c = warp; c < n; c += nw) {
+        const double sc = sig[c];
+        int pos = 0;
+        for (int q = 0; q < n; ++q) pos += (sig[q] > sc) || (sig[q] == sc && q < c);
+        const double* a = J.B + (size_t)c * J.ldb;
+        double* u = J.U + (size_t)pos * J.ldu;
+        const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+        for (int i = lane; i < m; i += 32) u[i] = a[i] * inv;
+        if (lane == 0) J.sigma[pos] = sc;
+    }
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int q = 0; q < n; ++q) cnt += (sig[q] > J.eps);
+        *J.count = cnt;
+    }
+}
+
+void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
+    if (max_n > JMAXN) throw Error(H2_ERR_UNSUPPORTED, "SVD wider than 2048 columns");
+    if (njobs > 0) k_svd<<<njobs, JT, 0, st>>>(jobs);
+}
+
+// ------------------------------------------------------------------ spectral norm
+// Power iteration x <- A^* A x with normalisation; returns ||A x|| for the
+// final unit vector (a lower bound that converges to ||A||_2).
+constexpr int NT = 128;
+constexpr int NMAX = 2048;
+constexpr int NITER = 60;
+
+__global__ void __launch_bounds__(NT) k_norm(const NormJob* __restrict__ jobs) {
+    __shared__ double x[NMAX];
+    __shared__ double y[NMAX];
+    __shared__ double red[NT / 32];
+    const NormJob J = jobs[blockIdx.x];
+    const int m = J.m, n = J.n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double nx = 0.0;
+    for (int j = threadIdx.x; j < n; j += NT) {
+        x[j] = 1.0 + 0.37 * (double)j / (double)(n > 0 ? n : 1);
+        nx += x[j] * x[j];
+    }
+    nx = block_sum<NT>(nx, red);
+    double sigma = 0.0;
+    for (int it = 0; it <= NITER && nx > 0.0; ++it) {
+        const double ix = 1.0 / sqrt(nx);
+        for (int j = threadIdx.x; j < n; j += NT) x[j] *= ix;
+        __syncthreads();
+        double ny = 0.0;
+        for (int i = threadIdx.x; i < m; i += NT) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += J.A[i + (size_t)j * J.lda] * x[j];
+            y[i] = s;
+            ny += s * s;
+        }
+        ny = block_sum<NT>(ny, red);
+        sigma = sqrt(ny);
+        if (it == NITER || ny == 0.0) break;
+        nx = 0.0;
+        for (int j = warp; j < n; j += NT / 32) {
+            const double* a = J.A + (size_t)j * J.lda;
+            double s = 0.0;
+            for (int i = lane; i < m; i += 32) s += a[i] * y[i];
+            s = warp_sum(s);
+            if (lane == 0) x[j] = s;
+            nx += (lane == 0) ? s * s : 0.0;
+        }
+        nx = block_sum<NT>(nx, red);
+    }
+    if (threadIdx.x == 0) {
+        if (J.nrm) *J.nrm = sigma;
+        if (J.inv) *J.inv = sigma > 1e-300 ? 1.0 / sigma : 0.0;
+    }
+}
+
+void launch_norm(const NormJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_norm<<<njobs, NT, 0, st>>>(jobs);
+}
+
+// ------------------------------------------------------------------ copies
+__global__ void k_copy(const CopyJob* __restrict__ jobs) {
+    const CopyJob J = jobs[blockIdx.x];
+    const double f = J.alpha * (J.scale ? *J.scale : 1.0);
+    const int64_t tot = (int64_t)J.rows * J.cols;
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+        int i = (int)(e % J.rows), j = (int)(e / J.rows);
+        double v = J.trans ? J.src[j + (size_t)i * J.lds] : J.src[i + (size_t)j * J.lds];
+        double* d = J.dst + i + (size_t)j * J.ldd;
+        *d = (J.beta == 0.0) ? f * v : J.beta * *d + f * v;
+    }
+}
+
+void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_copy<<<njobs, 256, 0, st>>>(jobs);
+}
+
+__global__ void k_identity(double* A, int m, int n, int lda) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(e % m), j = (int)(e / m);
+        A[i + (size_t)j * lda] = (i == j) ? 1.0 : 0.0;
+    }
+}
+
+void launch_set_identity(double* A, int m, int n, int lda, cudaStream_t st) {
+    int64_t tot = (int64_t)m * n;
+    if (tot > 0) k_identity<<<(int)std::min<int64_t>(ceil_div(tot, 256), 4096), 256, 0, st>>>(A, m, n, lda);
+}
+
+__global__ void k_finite(const double* A, size_t len, int* flag) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len; e += (size_t)gridDim.x * blockDim.x)
+        if (!isfinite(A[e])) {
+            atomicOr(flag, 2);
+            return;
+        }
+}
+
+void launch_check_finite(const double* A, size_t len, int* flag, cudaStream_t st) {
+    if (len > 0) k_finite<<<(int)std::min<size_t>(ceil_div(len, 256), 2048), 256, 0, st>>>(A, len, flag);
+}
+
+// ------------------------------------------------------------------ interpolation
+// First-kind Chebyshev nodes on [a, b] and Lagrange polynomials (Example
+// "Integral operator"), tensor index nu = ix + m iy + m^2 iz.
+__device__ __forceinline__ double cheb_node(double a, double b, int i, int m) {
+    return 0.5 * (a + b) + 0.5 * (b - a) * cos((2 * i + 1) * M_PI / (2 * m));
+}
+
+__device__ double lagrange(double a, double b, int m, int i, double x) {
+    double xi = cheb_node(a, b, i, m), v = 1.0;
+    for (int j = 0; j < m; ++j)
+        if (j != i) {
+            double xj = cheb_node(a, b, j, m);
+            v *= (x - xj) / (xi - xj);
+        }
+    return v;
+}
+
+__device__ double kernel_eval(int kernel, const double* x, const double* y) {
+    if (kernel == H2_K_POLY2) {
+        double d = 1.0 + x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+        return d * d;
+    }
+    if (kernel == H2_K_CONST) return 1.0;
+    double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    if (kernel == H2_K_DELTA) return r == 0.0 ? 1.0 : 0.0;
+    if (r == 0.0) return 0.0;
+    if (kernel == H2_K_LAPLACE) return 1.0 / (4.0 * M_PI * r);
+    return exp(-r) / r;
+}
+
+// leaf bases: one thread per (point, nu)
+__global__ void k_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
+                              const double* lo, const double* hi, double* const* leafp, int first_leaf, int m) {
+    const int leaf = first_leaf + blockIdx.y;
+    const int k = m * m * m;
+    const int64_t cnt = size[leaf];
+    double* out = leafp[leaf];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt * k; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % cnt;
+        int nu = (int)(e / cnt);
+        int ix = nu % m, iy = (nu / m) % m, iz = nu / (m * m);
+        const double* x = pts + 3 * perm[off[leaf] + i];
+        const double* l = lo + 3 * leaf;
+        const double* h = hi + 3 * leaf;
+        out[i + (size_t)nu * cnt] = lagrange(l[0], h[0], m, ix, x[0]) * lagrange(l[1], h[1], m, iy, x[1]) *
+                                    lagrange(l[2], h[2], m, iz, x[2]);
+    }
+}
+
+void launch_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
+                        const double* lo, const double* hi, double* const* leafp, int first_leaf, int nleaves, int m,
+                        int64_t max_size, cudaStream_t st) {
+    int k = m * m * m;
+    int gx = (int)std::min<int64_t>(ceil_div(max_size * k, 128), 1024);
+    dim3 grid(gx, nleaves);
+    if (nleaves > 0) k_interp_leaf<<<grid, 128, 0, st>>>(pts, perm, off, size, lo, hi, leafp, first_leaf, m);
+}
+
+// transfers: E_c[nu', nu] = l_{parent, nu}(xi_{c, nu'}), one block per cluster c >= 1
+__global__ void k_interp_transfer(const double* lo, const double* hi, double* const* trp, int m) {
+    const int c = blockIdx.x + 1, p = (c - 1) / 2;
+    const int k = m * m * m;
+    const double *lc = lo + 3 * c, *hc = hi + 3 * c, *lp = lo + 3 * p, *hp = hi + 3 * p;
+    double* out = trp[c];
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        int nu1 = e % k, nu = e / k;
+        int a0 = nu1 % m, a1 = (nu1 / m) % m, a2 = nu1 / (m * m);
+        int b0 = nu % m, b1 = (nu / m) % m, b2 = nu / (m * m);
+        double x0 = cheb_node(lc[0], hc[0], a0, m), x1 = cheb_node(lc[1], hc[1], a1, m),
+               x2 = cheb_node(lc[2], hc[2], a2, m);
+        out[nu1 + (size_t)nu * k] =
+            lagrange(lp[0], hp[0], m, b0, x0) * lagrange(lp[1], hp[1], m, b1, x1) * lagrange(lp[2], hp[2], m, b2, x2);
+    }
+}
+
+void launch_interp_transfer(const double* lo, const double* hi, double* const* trp, int nc, int m, cudaStream_t st) {
+    if (nc > 1) k_interp_transfer<<<nc - 1, 256, 0, st>>>(lo, hi, trp, m);
+}
+
+// couplings: S_ts[nu, mu] = g(xi_{t,nu}, xi_{s,mu}), one block per admissible block
+__global__ void k_interp_coupling(const double* lo, const double* hi, const int* bt, const int* bs,
+                                  double* const* bp, int m, int kernel) {
+    const int b = blockIdx.x, t = bt[b], s = bs[b];
+    const int k = m * m * m;
+    const double *lt = lo + 3 * t, *ht = hi + 3 * t, *ls = lo + 3 * s, *hs = hi + 3 * s;
+    double* out = bp[b];
+    for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+        int nu = e % k, mu = e / k;
+        double x[3] = {cheb_node(lt[0], ht[0], nu % m, m), cheb_node(lt[1], ht[1], (nu / m) % m, m),
+                       cheb_node(lt[2], ht[2], nu / (m * m), m)};
+        double y[3] = {cheb_node(ls[0], hs[0], mu % m, m), cheb_node(ls[1], hs[1], (mu / m) % m, m),
+                       cheb_node(ls[2], hs[2], mu / (m * m), m)};
+        out[nu + (size_t)mu * k] = kernel_eval(kernel, x, y);
+    }
+}
+
+void launch_interp_coupling(const double* lo, const double* hi, const int* bt, const int* bs, double* const* bp,
+                            int nblocks, int m, int kernel, cudaStream_t st) {
+    if (nblocks > 0) k_interp_coupling<<<nblocks, 256, 0, st>>>(lo, hi, bt, bs, bp, m, kernel);
+}
+
+// dense blocks: N_ts[i, j] = g(x_i, x_j)
+__global__ void k_interp_dense(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
+                               const int* bt, const int* bs, double* const* bp, int kernel) {
+    const int b = blockIdx.x, t = bt[b], s = bs[b];
+    const int64_t mt = size[t], ms = size[s];
+    double* out = bp[b];
+    for (int64_t e = threadIdx.x; e < mt * ms; e += blockDim.x) {
+        int64_t i = e % mt, j = e / mt;
+        out[e] = kernel_eval(kernel, pts + 3 * perm[off[t] + i], pts + 3 * perm[off[s] + j]);
+    }
+}
+
+void launch_interp_dense(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
+                         const int* bt, const int* bs, double* const* bp, int nblocks, int kernel, cudaStream_t st) {
+    if (nblocks > 0) k_interp_dense<<<nblocks, 256, 0, st>>>(pts, perm, off, size, bt, bs, bp, kernel);
+}
+
+// ------------------------------------------------------------------ block norms
+__global__ void k_sumsq(const SumSqJob* __restrict__ jobs, double* out) {
+    __shared__ double red[256 / 32];
+    const SumSqJob J = jobs[blockIdx.x];
+    double s = 0.0;
+    for (int64_t e = threadIdx.x; e < (int64_t)J.rows * J.cols; e += 256) {
+        double v = J.A[(e % J.rows) + (size_t)(e / J.rows) * J.lda];
+        s += v * v;
+    }
+    s = block_sum<256>(s, red);
+    if (threadIdx.x == 0) atomicAdd(out + J.slot, s);
+}
+
+void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st) {
+    if (njobs > 0) k_sumsq<<<njobs, 256, 0, st>>>(jobs, out);
+}
+
+__global__ void k_inv_sqrt(const double* v, double* w, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] = v[i] > 0.0 ? 1.0 / sqrt(v[i]) : 0.0;
+}
+
+void launch_inv_sqrt(const double* v, double* w, int n, cudaStream_t st) {
+    if (n > 0) k_inv_sqrt<<<(int)ceil_div(n, 256), 256, 0, st>>>(v, w, n);
+}
+
+// dense n x n matrix in tree order -> original order
+__global__ void k_scatter(const double* src, int64_t n, const int64_t* perm, double* out, int64_t ld) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % n, j = e / n;
+        out[perm[i] + perm[j] * ld] = src[e];
+    }
+}
+
+void launch_scatter_dense(const double* src, int64_t n, const int64_t* perm, double* out, int64_t ld, cudaStream_t st) {
+    if (n > 0) k_scatter<<<(int)std::min<int64_t>(ceil_div(n * n, 256), 8192), 256, 0, st>>>(src, n, perm, out, ld);
+}
+
+}  // namespace h2

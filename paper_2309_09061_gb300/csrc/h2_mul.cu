@@ -1,0 +1,1388 @@
+// h2_mul_add: Z <- Z + X Y for H^2-matrices (S. Boerm, arXiv 2309.09061).
+//
+// The host walks the cluster tree level by level and, for each level, queues
+// one batched launch per step covering every cluster and block of that level:
+//   prep      cluster basis products (Sec. 4), basis weights (Fig. 1), total
+//             weights with block scaling (Fig. 2, Sec. 5)
+//   phase A   compressed induced row basis (Fig. 4), the column basis as the
+//             same procedure on Y^* X^*, couplings on T^XY ("t_mat")
+//   phase B   coarsening to Z's block tree (Fig. 7, Fig. 6), row basis and the
+//             column basis on G^*, then the final couplings
+// Ranks are chosen on the device; the host reads them back once per level to
+// size the next level's buffers.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <functional>
+#include <map>
+
+#include "h2_internal.h"
+
+namespace h2 {
+
+cudaStream_t stream_of(const h2_opts* o);
+
+// A matrix operand as stored: logical = tr ? stored^T : stored.
+struct Mv {
+    const double* p;
+    int ld;
+    int tr;
+};
+
+// ------------------------------------------------------------------ views
+// Logical view of an H^2-matrix, optionally transposed.
+struct OpView {
+    const h2_matrix* M;
+    bool T;
+    const Tree& tree() const { return M->st->tree; }
+    const BlockTree& bt() const { return M->st->blocks; }
+    const Basis& rowb() const { return T ? *M->W : *M->V; }
+    const Basis& colb() const { return T ? *M->V : *M->W; }
+    int block(int t, int s) const { return T ? bt().find(s, t) : bt().find(t, s); }
+    int8_t kind(int b) const { return bt().kind[b]; }
+    const std::vector<int>& row_list(int t) const { return T ? bt().by_col[t] : bt().by_row[t]; }
+    int other(int b) const { return T ? bt().t[b] : bt().s[b]; }  // column cluster of block b in the view
+    Mv S(int b) const {
+        int ld = M->V->rank[bt().t[b]];
+        return Mv{M->blk[b], ld, T ? 1 : 0};
+    }
+    Mv N(int b) const {
+        int ld = (int)tree().size[bt().t[b]];
+        return Mv{M->blk[b], ld, T ? 1 : 0};
+    }
+};
+
+// Per-cluster device matrices with their shapes.
+struct PerCl {
+    std::vector<double*> p;
+    std::vector<int> rows, cols;
+    void init(int nc) {
+        p.assign(nc, nullptr);
+        rows.assign(nc, 0);
+        cols.assign(nc, 0);
+    }
+};
+
+static void T_(Runner& R, Mv A, Mv B, int k, double alpha = 1.0, const double* scale = nullptr, int flipA = 0,
+               int flipB = 0) {
+    R.term(A.p, A.tr ^ flipA, A.ld, B.p, B.tr ^ flipB, B.ld, k, alpha, scale);
+}
+
+static Mv mv(const double* p, int ld) { return Mv{p, ld, 0}; }
+static Mv mvT(const double* p, int ld) { return Mv{p, ld, 1}; }
+
+// ------------------------------------------------------------------ timing / stats
+struct PhaseClock {
+    cudaStream_t st;
+    std::vector<cudaEvent_t> ev;
+    explicit PhaseClock(cudaStream_t s) : st(s) {}
+    ~PhaseClock() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+    void mark() {
+        cudaEvent_t e;
+        H2_CUDA(cudaEventCreate(&e));
+        H2_CUDA(cudaEventRecord(e, st));
+        ev.push_back(e);
+    }
+    double ms(int i) const {
+        float f = 0;
+        cudaEventElapsedTime(&f, ev[i], ev[i + 1]);
+        return f;
+    }
+};
+
+struct Counts {
+    double flops = 0, bytes = 0;
+    int64_t triples = 0;
+};
+
+// ------------------------------------------------------------------ prep: basis products
+// P_s = W_{X,s}^* V_{Y,s}: directly in leaves, sum_{s'} F_{s'}^* P_{s'} E_{s'} above.
+static PerCl basis_products(Runner& R, const Tree& T, const Basis& WX, const Basis& VY) {
+    PerCl P;
+    P.init(T.nc);
+    for (int c = 0; c < T.nc; ++c) {
+        P.rows[c] = WX.rank[c];
+        P.cols[c] = VY.rank[c];
+        P.p[c] = R.dalloc((size_t)std::max(1, P.rows[c] * P.cols[c]));
+    }
+    for (int c = Tree::first(T.L); c < T.nc; ++c) {
+        int sz = (int)T.size[c];
+        R.job(P.p[c], P.rows[c], P.cols[c], std::max(1, P.rows[c]), 0.0);
+        R.term(WX.leaf[c], 1, sz, VY.leaf[c], 0, sz, sz);
+    }
+    R.flush_gemm(H2_FP64);
+    for (int l = T.L - 1; l >= 0; --l) {
+        std::vector<double*> tmp(T.nc, nullptr);
+        for (int c = Tree::first(l + 1); c < Tree::first(l + 1) + Tree::count(l + 1); ++c) {
+            int p = Tree::parent(c);
+            tmp[c] = R.dalloc((size_t)std::max(1, WX.rank[c] * VY.rank[p]));
+            R.job(tmp[c], WX.rank[c], VY.rank[p], std::max(1, WX.rank[c]), 0.0);
+            R.term(P.p[c], 0, std::max(1, P.rows[c]), VY.tr[c], 0, std::max(1, VY.rank[c]), VY.rank[c]);
+        }
+        R.flush_gemm(H2_FP64);
+        for (int p = Tree::first(l); p < Tree::first(l) + Tree::count(l); ++p) {
+            R.job(P.p[p], P.rows[p], P.cols[p], std::max(1, P.rows[p]), 0.0);
+            for (int i = 0; i < 2; ++i) {
+                int c = Tree::child(p, i);
+                R.term(WX.tr[c], 1, std::max(1, WX.rank[c]), tmp[c], 0, std::max(1, WX.rank[c]), WX.rank[c]);
+            }
+        }
+        R.flush_gemm(H2_FP64);
+    }
+    return P;
+}
+
+// ------------------------------------------------------------------ prep: basis weights (Fig. 1)
+// R_r with W_r = Q_r R_r: QR of the leaf matrices, then QR of [R_{r1} F_{r1}; R_{r2} F_{r2}].
+static PerCl basis_weights(Runner& R, const Tree& T, const Basis& B) {
+    PerCl W;
+    W.init(T.nc);
+    for (int c = Tree::first(T.L); c < T.nc; ++c) {
+        int m = (int)T.size[c], k = B.rank[c];
+        double* work = R.dalloc((size_t)m * std::max(1, k));
+        R.copy(B.leaf[c], m, work, m, m, k, 0);
+        W.rows[c] = std::min(m, k);
+        W.cols[c] = k;
+        W.p[c] = R.dalloc((size_t)std::max(1, W.rows[c] * k));
+        R.qr(work, m, k, m, W.p[c], std::max(1, W.rows[c]), nullptr, 1, 0);
+    }
+    R.flush_copy();
+    R.flush_qr();
+    for (int l = T.L - 1; l >= 0; --l) {
+        std::vector<std::pair<double*, int>> stacks;
+        for (int p = Tree::first(l); p < Tree::first(l) + Tree::count(l); ++p) {
+            int c1 = Tree::child(p, 0), c2 = Tree::child(p, 1);
+            int rows = W.rows[c1] + W.rows[c2], k = B.rank[p];
+            double* st = R.dalloc((size_t)std::max(1, rows * k));
+            int o = 0;
+            for (int c : {c1, c2}) {
+                R.job(st + o, W.rows[c], k, std::max(1, rows), 0.0);
+                R.term(W.p[c], 0, std::max(1, W.rows[c]), B.tr[c], 0, std::max(1, B.rank[c]), B.rank[c]);
+                o += W.rows[c];
+            }
+            W.rows[p] = std::min(rows, k);
+            W.cols[p] = k;
+            W.p[p] = R.dalloc((size_t)std::max(1, W.rows[p] * k));
+            stacks.push_back({st, rows});
+            R.qr(st, rows, k, std::max(1, rows), W.p[p], std::max(1, W.rows[p]), nullptr, 1, 0);
+        }
+        R.flush_gemm(H2_FP64);
+        R.flush_qr();
+    }
+    return W;
+}
+
+// ------------------------------------------------------------------ prep: total weights (Fig. 2 + Sec. 5)
+// Z_s from the thin QR of [Z_{s+} E_s^*; R_r S_{sr}^* / ||S_{sr} R_r^*||_2 for admissible (s,r)].
+static PerCl total_weights(Runner& R, const OpView& Y, const PerCl& RW) {
+    const Tree& T = Y.tree();
+    const Basis& VY = Y.rowb();
+    PerCl Z;
+    Z.init(T.nc);
+    // scaled blocks S_{sr} R_r^* and their norms
+    std::map<int, std::pair<double*, double*>> SR;  // block -> (matrix k_s x l_r, inverse norm)
+    for (int b = 0; b < (int)Y.bt().kind.size(); ++b) {
+        if (Y.kind(b) != ADM) continue;
+        int s = Y.T ? Y.bt().s[b] : Y.bt().t[b];
+        int r = Y.other(b);
+        int ks = VY.rank[s], lr = RW.rows[r];
+        double* m = R.dalloc((size_t)std::max(1, ks * lr));
+        double* inv = R.dalloc(1);
+        R.job(m, ks, lr, std::max(1, ks), 0.0);
+        T_(R, Y.S(b), mvT(RW.p[r], std::max(1, lr)), Y.colb().rank[r]);
+        SR[b] = {m, inv};
+    }
+    R.flush_gemm(H2_FP64);
+    for (auto& kv : SR) {
+        int b = kv.first;
+        int s = Y.T ? Y.bt().s[b] : Y.bt().t[b];
+        int r = Y.other(b);
+        R.norm(kv.second.first, VY.rank[s], RW.rows[r], std::max(1, VY.rank[s]), kv.second.second, nullptr);
+    }
+    R.flush_norm();
+    for (int l = 0; l <= T.L; ++l) {
+        for (int s = Tree::first(l); s < Tree::first(l) + Tree::count(l); ++s) {
+            int k = VY.rank[s];
+            int rows = (s > 0) ? Z.rows[Tree::parent(s)] : 0;
+            for (int b : Y.row_list(s))
+                if (Y.kind(b) == ADM) rows += RW.rows[Y.other(b)];
+            Z.cols[s] = k;
+            Z.rows[s] = std::min(rows, k);
+            Z.p[s] = R.dalloc((size_t)std::max(1, Z.rows[s] * k));
+            if (rows == 0) continue;
+            double* st = R.dalloc((size_t)rows * std::max(1, k));
+            int o = 0;
+            if (s > 0) {
+                int p = Tree::parent(s);
+                if (Z.rows[p] > 0) {
+                    R.job(st, Z.rows[p], k, rows, 0.0);
+                    R.term(Z.p[p], 0, std::max(1, Z.rows[p]), VY.tr[s], 1, std::max(1, k), VY.rank[p]);
+                }
+                o = Z.rows[p];
+            }
+            for (int b : Y.row_list(s)) {
+                if (Y.kind(b) != ADM) continue;
+                int r = Y.other(b);
+                R.copy(SR[b].first, std::max(1, k), st + o, rows, RW.rows[r], k, 1, 1.0, SR[b].second);
+                o += RW.rows[r];
+            }
+            R.qr(st, rows, k, rows, Z.p[s], std::max(1, Z.rows[s]), nullptr, 1, 0);
+        }
+        R.flush_gemm(H2_FP64);
+        R.flush_copy();
+        R.flush_qr();
+    }
+    return Z;
+}
+
+// ------------------------------------------------------------------ left singular vectors
+// Batched left singular vectors.  Each job gives Bt (ncol x m, ld ncol), the
+// transpose of the matrix whose left singular vectors are wanted.  Wide
+// matrices (ncol > m) are first reduced by a thin QR of Bt = Q Rt, so that the
+// wanted vectors are those of Rt^* (m x m); then one-sided Jacobi.
+struct SvdOut {
+    double* U = nullptr;
+    int ldu = 1;
+};
+
+class SvdBatch {
+public:
+    explicit SvdBatch(Runner& R) : R_(R) {}
+    // queue a job; the returned index identifies its output after run()
+    int add(double* Bt, int ncol, int m, double eps, int* count_slot) {
+        Job j{Bt, ncol, m, eps, count_slot, nullptr, nullptr};
+        if (m > 0 && ncol > 0) {
+            if (ncol > m) {
+                j.Rt = R_.dalloc((size_t)m * m);
+                R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0);
+            }
+            j.B = R_.dalloc((size_t)m * std::min(m, ncol));
+        }
+        jobs_.push_back(j);
+        return (int)jobs_.size() - 1;
+    }
+    // run every queued step in order; fills out[i] for job i
+    std::vector<SvdOut> run() {
+        R_.flush_gemm();
+        R_.flush_copy();
+        R_.flush_qr();
+        std::vector<SvdOut> out(jobs_.size());
+        for (size_t i = 0; i < jobs_.size(); ++i) {
+            Job& j = jobs_[i];
+            if (!j.B) continue;
+            int w = std::min(j.m, j.ncol);
+            if (j.Rt)
+                R_.copy(j.Rt, j.m, j.B, j.m, j.m, j.m, 1);
+            else
+                R_.copy(j.Bt, j.ncol, j.B, j.m, j.m, j.ncol, 1);
+            out[i].U = R_.dalloc((size_t)j.m * w);
+            out[i].ldu = j.m;
+            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps);
+        }
+        R_.flush_copy();
+        R_.flush_svd();
+        jobs_.clear();
+        return out;
+    }
+
+private:
+    struct Job {
+        double* Bt;
+        int ncol, m;
+        double eps;
+        int* count;
+        double* Rt;
+        double* B;
+    };
+    Runner& R_;
+    std::vector<Job> jobs_;
+};
+
+static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
+    std::vector<int> h(n, 0);
+    if (n > 0) {
+        H2_CUDA(cudaMemcpyAsync(h.data(), d_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, R.stream()));
+        int flag = 0;
+        if (R.svd_flag())
+            H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, R.stream()));
+        H2_CUDA(cudaStreamSynchronize(R.stream()));
+        if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
+    }
+    return h;
+}
+
+// ------------------------------------------------------------------ phase A (Fig. 4)
+struct Induced {
+    std::shared_ptr<Basis> Q;
+    PerCl Rbar;                         // Q_t^* V_{X,t}: rank_Q(t) x rank_VX(t)
+    std::unordered_map<int, double*> A; // X block (not admissible) -> Q_t^* X_ts V_{Y,s}: rank_Q(t) x rank_VY(s)
+};
+
+static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double eps, Counts& cnt) {
+    const Tree& T = X.tree();
+    const Basis& VX = X.rowb();
+    const Basis& VY = Y.rowb();
+    PerCl P = basis_products(R, T, X.colb(), VY);
+    PerCl RW = basis_weights(R, T, Y.colb());
+    PerCl Zt = total_weights(R, Y, RW);
+    Induced out;
+    out.Q = std::make_shared<Basis>();
+    Basis& Q = *out.Q;
+    Q.rank.assign(T.nc, 0);
+    Q.leaf.assign(T.nc, nullptr);
+    Q.tr.assign(T.nc, nullptr);
+    out.Rbar.init(T.nc);
+    for (int l = T.L; l >= 0; --l) {
+        const int c0 = Tree::first(l), nl = Tree::count(l);
+        const bool leaf = (l == T.L);
+        std::vector<int> rows(nl), k1(nl), m2(nl);
+        std::vector<double*> VXh(nl), QX(nl);
+        std::vector<std::vector<int>> C(nl);
+        std::unordered_map<int, double*> M;
+        std::unordered_map<int, double*> inv;
+        // PE_{s'} = P_{s'} E_{Y,s'} for the children level
+        std::vector<double*> PE(T.nc, nullptr);
+        if (!leaf) {
+            for (int c = Tree::first(l + 1); c < Tree::first(l + 1) + Tree::count(l + 1); ++c) {
+                int p = Tree::parent(c);
+                PE[c] = R.dalloc((size_t)std::max(1, P.rows[c] * VY.rank[p]));
+                R.job(PE[c], P.rows[c], VY.rank[p], std::max(1, P.rows[c]), 0.0);
+                R.term(P.p[c], 0, std::max(1, P.rows[c]), VY.tr[c], 0, std::max(1, VY.rank[c]), VY.rank[c]);
+            }
+            R.flush_gemm();
+        }
+        // VX-hat and the admissible-child chains S_X(a,b) PE_b
+        std::unordered_map<int, double*> SPE;
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i;
+            for (int b : X.row_list(t))
+                if (X.kind(b) != ADM) C[i].push_back(b);
+            if (leaf) {
+                rows[i] = (int)T.size[t];
+                VXh[i] = R.dalloc((size_t)rows[i] * VX.rank[t]);
+                R.copy(VX.leaf[t], rows[i], VXh[i], rows[i], rows[i], VX.rank[t], 0);
+            } else {
+                int a1 = Tree::child(t, 0), a2 = Tree::child(t, 1);
+                rows[i] = Q.rank[a1] + Q.rank[a2];
+                VXh[i] = R.dalloc((size_t)std::max(1, rows[i] * VX.rank[t]));
+                int o = 0;
+                for (int a : {a1, a2}) {
+                    R.job(VXh[i] + o, Q.rank[a], VX.rank[t], rows[i], 0.0);
+                    R.term(out.Rbar.p[a], 0, std::max(1, Q.rank[a]), VX.tr[a], 0, std::max(1, VX.rank[a]),
+                           VX.rank[a]);
+                    o += Q.rank[a];
+                }
+                for (int b : C[i]) {
+                    int s = X.other(b);
+                    for (int a : {a1, a2})
+                        for (int j = 0; j < 2; ++j) {
+                            int sj = Tree::child(s, j);
+                            int bb = X.block(a, sj);
+                            if (X.kind(bb) != ADM) continue;
+                            double* m = R.dalloc((size_t)std::max(1, VX.rank[a] * VY.rank[s]));
+                            R.job(m, VX.rank[a], VY.rank[s], std::max(1, VX.rank[a]), 0.0);
+                            T_(R, X.S(bb), mv(PE[sj], std::max(1, P.rows[sj])), X.colb().rank[sj]);
+                            SPE[bb] = m;
+                            cnt.flops += 2.0 * VX.rank[a] * VY.rank[s] * X.colb().rank[sj];
+                        }
+                }
+            }
+        }
+        R.flush_copy();
+        R.flush_gemm();
+        // the blocks M_ts = X|ts V_Y,s (leaf) or A-hat_ts (Eq. induced_Ahat)
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i;
+            for (int b : C[i]) {
+                int s = X.other(b);
+                int ky = VY.rank[s];
+                double* m = R.dalloc((size_t)std::max(1, rows[i] * ky));
+                M[b] = m;
+                if (leaf) {
+                    R.job(m, rows[i], ky, rows[i], 0.0);
+                    T_(R, X.N(b), mv(VY.leaf[s], (int)T.size[s]), (int)T.size[s]);
+                    cnt.flops += 2.0 * rows[i] * ky * T.size[s];
+                } else {
+                    int o = 0;
+                    for (int a : {Tree::child(t, 0), Tree::child(t, 1)}) {
+                        R.job(m + o, Q.rank[a], ky, rows[i], 0.0);
+                        for (int j = 0; j < 2; ++j) {
+                            int sj = Tree::child(s, j);
+                            int bb = X.block(a, sj);
+                            if (X.kind(bb) == ADM) {
+                                R.term(out.Rbar.p[a], 0, std::max(1, Q.rank[a]), SPE[bb], 0,
+                                       std::max(1, VX.rank[a]), VX.rank[a]);
+                                cnt.flops += 2.0 * Q.rank[a] * ky * VX.rank[a];
+                            } else {
+                                R.term(out.A[bb], 0, std::max(1, Q.rank[a]), VY.tr[sj], 0,
+                                       std::max(1, VY.rank[sj]), VY.rank[sj]);
+                                cnt.flops += 2.0 * Q.rank[a] * ky * VY.rank[sj];
+                            }
+                        }
+                        o += Q.rank[a];
+                    }
+                }
+                inv[b] = R.dalloc(1);
+            }
+        }
+        R.flush_gemm();
+        for (int i = 0; i < nl; ++i)
+            for (int b : C[i]) R.norm(M[b], rows[i], VY.rank[X.other(b)], std::max(1, rows[i]), inv[b], nullptr);
+        R.flush_norm();
+        // complete QR of VX-hat; tall transposed remainder; SVD
+        int* d_counts = (int*)R.dalloc(nl);
+        H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i, kx = VX.rank[t];
+            k1[i] = std::min(rows[i], kx);
+            m2[i] = rows[i] - k1[i];
+            double* work = R.dalloc((size_t)std::max(1, rows[i] * kx));
+            R.copy(VXh[i], rows[i], work, rows[i], rows[i], kx, 0);
+            QX[i] = R.dalloc((size_t)std::max(1, rows[i] * rows[i]));
+            R.qr(work, rows[i], kx, rows[i], nullptr, 1, QX[i], rows[i], rows[i]);
+        }
+        R.flush_copy();
+        R.flush_qr();
+        std::vector<double*> Vts(nl, nullptr), Tts(nl, nullptr);
+        std::vector<int> ncols(nl, 0);
+        for (int i = 0; i < nl; ++i) {
+            int ncol = 0;
+            for (int b : C[i]) ncol += Zt.rows[X.other(b)];
+            ncols[i] = ncol;
+            if (m2[i] == 0 || ncol == 0) continue;
+            double* Tt = R.dalloc((size_t)ncol * rows[i]);
+            int o = 0;
+            for (int b : C[i]) {
+                int s = X.other(b);
+                if (Zt.rows[s] == 0) continue;
+                R.job(Tt + o, Zt.rows[s], rows[i], ncol, 0.0);
+                R.term(Zt.p[s], 0, Zt.rows[s], M[b], 1, rows[i], VY.rank[s], 1.0, inv[b]);
+                o += Zt.rows[s];
+            }
+            Vts[i] = R.dalloc((size_t)ncol * m2[i]);
+            Tts[i] = Tt;
+        }
+        R.flush_gemm();
+        for (int i = 0; i < nl; ++i) {
+            if (!Vts[i]) continue;
+            R.job(Vts[i], ncols[i], m2[i], ncols[i], 0.0);
+            R.term(Tts[i], 0, ncols[i], QX[i] + (size_t)k1[i] * rows[i], 0, rows[i], rows[i]);
+        }
+        R.flush_gemm();
+        SvdBatch sb(R);
+        for (int i = 0; i < nl; ++i)
+            if (Vts[i]) sb.add(Vts[i], ncols[i], m2[i], eps, d_counts + i);
+            else sb.add(nullptr, 0, 0, eps, d_counts + i);
+        std::vector<SvdOut> so = sb.run();
+        std::vector<int> k2 = read_counts(R, d_counts, nl);
+        // new basis: leaf matrices or transfers of the children
+        size_t need = 0;
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i;
+            Q.rank[t] = k1[i] + k2[i];
+            need += (size_t)rows[i] * Q.rank[t];
+        }
+        auto chunk = std::make_shared<DevBuf>();
+        chunk->alloc(std::max<size_t>(need, 1));
+        Q.chunks.push_back(chunk);
+        size_t off = 0;
+        std::vector<double*> Qh(nl);
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i, kt = Q.rank[t];
+            double* q = chunk->p + off;
+            off += (size_t)rows[i] * kt;
+            Qh[i] = q;
+            // Q-hat = [Q_X(:, :k1) | Q_X(:, k1:) U(:, :k2)]
+            R.copy(QX[i], rows[i], q, rows[i], rows[i], k1[i], 0);
+            if (k2[i] > 0) {
+                R.job(q + (size_t)k1[i] * rows[i], rows[i], k2[i], rows[i], 0.0);
+                R.term(QX[i] + (size_t)k1[i] * rows[i], 0, rows[i], so[i].U, 0, so[i].ldu, m2[i]);
+            }
+        }
+        R.flush_copy();
+        R.flush_gemm();
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i, kt = Q.rank[t];
+            if (leaf) {
+                Q.leaf[t] = Qh[i];
+            } else {
+                // split rows into the children's transfers (stored with ld = rank of the child)
+                int o = 0;
+                for (int a : {Tree::child(t, 0), Tree::child(t, 1)}) {
+                    auto ch = std::make_shared<DevBuf>();
+                    ch->alloc(std::max<size_t>((size_t)Q.rank[a] * kt, 1));
+                    Q.chunks.push_back(ch);
+                    R.copy(Qh[i] + o, rows[i], ch->p, std::max(1, Q.rank[a]), Q.rank[a], kt, 0);
+                    Q.tr[a] = ch->p;
+                    o += Q.rank[a];
+                }
+            }
+            // A_ts = Q-hat^* M_ts,  Rbar_t = Q-hat^* VX-hat
+            for (int b : C[i]) {
+                int s = X.other(b);
+                double* a = R.dalloc((size_t)std::max(1, kt * VY.rank[s]));
+                R.job(a, kt, VY.rank[s], std::max(1, kt), 0.0);
+                R.term(Qh[i], 1, rows[i], M[b], 0, std::max(1, rows[i]), rows[i]);
+                out.A[b] = a;
+                cnt.flops += 2.0 * kt * VY.rank[s] * rows[i];
+            }
+            out.Rbar.rows[t] = kt;
+            out.Rbar.cols[t] = VX.rank[t];
+            out.Rbar.p[t] = R.dalloc((size_t)std::max(1, kt * VX.rank[t]));
+            R.job(out.Rbar.p[t], kt, VX.rank[t], std::max(1, kt), 0.0);
+            R.term(Qh[i], 1, rows[i], VXh[i], 0, std::max(1, rows[i]), rows[i]);
+        }
+        R.flush_copy();
+        R.flush_gemm();
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ the intermediate matrix on T^XY
+// Couplings of every T^XY node in the compressed induced bases ("t_mat"):
+//   (t,s),(s,r) admissible: Rbar_t S_X P_s S_Y RbarW_r^*
+//   (t,s) inadmissible:     A_ts S_Y RbarW_r^*                 (Eq. semiuniform)
+//   (s,r) inadmissible:     Rbar_t S_X B_rs^*                  (Eq. semiuniform2)
+// grouped per node as U1 = sum S_X (P S_Y) + S_Z, U2 = Rbar U1 + sum A S_Y,
+// U3 = sum S_X B^*, C = U2 RbarW^* + Rbar U3; then pushed to the leaves with
+// the new transfer matrices.  Dense leaves hold the exact leaf-level products
+// plus the expansion of the pushed-down coupling.
+struct Intermediate {
+    ProductTree PT;
+    std::shared_ptr<Basis> Q, QW;  // row / column bases (isometric)
+    std::vector<double*> C;        // per node: coupling (ADM / SPLIT) or dense block (DENSE)
+};
+
+static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2_matrix* Z, const Induced& ra,
+                           const Induced& ca, Intermediate& G, Counts& cnt) {
+    const Tree& T = X.tree();
+    const Basis& Q = *ra.Q;
+    const Basis& QW = *ca.Q;
+    const Basis& VX = X.rowb();
+    const Basis& WX = X.colb();
+    const Basis& VY = Y.rowb();
+    const Basis& WY = Y.colb();
+    const BlockTree& N = G.PT.nodes;
+    const int nn = (int)N.kind.size();
+    const OpView ZV{Z, false};
+    PerCl P = basis_products(R, T, WX, VY);
+    // PSY_sr = P_s S_Y,sr for admissible Y blocks
+    std::unordered_map<int, double*> PSY;
+    for (int b = 0; b < (int)Y.bt().kind.size(); ++b) {
+        if (Y.kind(b) != ADM) continue;
+        int s = Y.bt().t[b], r = Y.bt().s[b];
+        double* m = R.dalloc((size_t)WX.rank[s] * WY.rank[r]);
+        R.job(m, WX.rank[s], WY.rank[r], WX.rank[s], 0.0);
+        T_(R, mv(P.p[s], std::max(1, P.rows[s])), Y.S(b), VY.rank[s]);
+        PSY[b] = m;
+        cnt.flops += 2.0 * WX.rank[s] * WY.rank[r] * VY.rank[s];
+    }
+    R.flush_gemm();
+    // U1 (all nodes): S_Z copied first, then += sum of S_X PSY
+    std::vector<double*> U1(nn, nullptr);
+    for (int n = 0; n < nn; ++n) {
+        int t = N.t[n], r = N.s[n];
+        U1[n] = R.dalloc((size_t)VX.rank[t] * WY.rank[r]);
+        H2_CUDA(cudaMemsetAsync(U1[n], 0, sizeof(double) * VX.rank[t] * WY.rank[r], R.stream()));
+        int bz = Z->st->blocks.find(t, r);
+        if (bz >= 0 && Z->st->blocks.kind[bz] == ADM)
+            R.copy(ZV.S(bz).p, ZV.S(bz).ld, U1[n], VX.rank[t], VX.rank[t], WY.rank[r], 0);
+    }
+    R.flush_copy();
+    for (int n = 0; n < nn; ++n) {
+        int t = N.t[n], r = N.s[n];
+        R.job(U1[n], VX.rank[t], WY.rank[r], VX.rank[t], 1.0);
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) == ADM && Y.kind(by) == ADM) {
+                T_(R, X.S(bx), mv(PSY[by], WX.rank[s]), WX.rank[s]);
+                cnt.flops += 2.0 * VX.rank[t] * WY.rank[r] * WX.rank[s];
+            }
+            cnt.triples++;
+        }
+    }
+    R.flush_gemm();
+    // U2, U3 for coupling nodes
+    std::vector<double*> U2(nn, nullptr), U3(nn, nullptr);
+    for (int n = 0; n < nn; ++n) {
+        if (N.kind[n] == DENSE) continue;
+        int t = N.t[n], r = N.s[n];
+        U2[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * WY.rank[r]));
+        R.job(U2[n], Q.rank[t], WY.rank[r], std::max(1, Q.rank[t]), 0.0);
+        R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U1[n], 0, VX.rank[t], VX.rank[t]);
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) != ADM && Y.kind(by) == ADM) {
+                T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
+                cnt.flops += 2.0 * Q.rank[t] * WY.rank[r] * VY.rank[s];
+            }
+        }
+        U3[n] = R.dalloc((size_t)std::max(1, VX.rank[t] * QW.rank[r]));
+        R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) == ADM && Y.kind(by) != ADM) {
+                T_(R, X.S(bx), mvT(ca.A.at(by), std::max(1, QW.rank[r])), WX.rank[s]);
+                cnt.flops += 2.0 * VX.rank[t] * QW.rank[r] * WX.rank[s];
+            }
+        }
+    }
+    R.flush_gemm();
+    G.C.assign(nn, nullptr);
+    std::vector<double*> Cup(nn, nullptr);
+    for (int n = 0; n < nn; ++n) {
+        int t = N.t[n], r = N.s[n];
+        size_t cs = (size_t)std::max(1, Q.rank[t] * QW.rank[r]);
+        Cup[n] = R.dalloc(cs);
+        H2_CUDA(cudaMemsetAsync(Cup[n], 0, sizeof(double) * cs, R.stream()));
+        if (N.kind[n] == DENSE) continue;
+        G.C[n] = R.dalloc(cs);
+        R.job(G.C[n], Q.rank[t], QW.rank[r], std::max(1, Q.rank[t]), 0.0);
+        R.term(U2[n], 0, std::max(1, Q.rank[t]), ca.Rbar.p[r], 1, std::max(1, QW.rank[r]), WY.rank[r]);
+        R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U3[n], 0, VX.rank[t], VX.rank[t]);
+        cnt.flops += 2.0 * Q.rank[t] * QW.rank[r] * (WY.rank[r] + VX.rank[t]);
+    }
+    R.flush_gemm();
+    // push down: Cup_child = E_a (C + Cup) F_b^*
+    for (int l = 0; l < T.L; ++l) {
+        std::vector<std::pair<int, double*>> tmp;  // (child node, C F_b^*)
+        for (int n = 0; n < nn; ++n) {
+            if (N.kind[n] != SPLIT || Tree::level(N.t[n]) != l) continue;
+            int t = N.t[n], r = N.s[n];
+            for (int j = 0; j < 2; ++j) {
+                int b = Tree::child(r, j);
+                double* m = R.dalloc((size_t)std::max(1, Q.rank[t] * QW.rank[b]));
+                R.job(m, Q.rank[t], QW.rank[b], std::max(1, Q.rank[t]), 0.0);
+                R.term(G.C[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
+                R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
+                for (int i = 0; i < 2; ++i) tmp.push_back({N.find(Tree::child(t, i), b), m});
+            }
+        }
+        R.flush_gemm();
+        for (auto& [c, m] : tmp) {
+            int a = N.t[c], b = N.s[c], t = Tree::parent(a);
+            R.job(Cup[c], Q.rank[a], QW.rank[b], std::max(1, Q.rank[a]), 0.0);
+            R.term(Q.tr[a], 0, std::max(1, Q.rank[a]), m, 0, std::max(1, Q.rank[t]), Q.rank[t]);
+            cnt.flops += 2.0 * Q.rank[a] * QW.rank[b] * Q.rank[t];
+        }
+        R.flush_gemm();
+    }
+    // admissible leaves: final coupling C + Cup
+    for (int n = 0; n < nn; ++n) {
+        if (N.kind[n] != ADM) continue;
+        int t = N.t[n], r = N.s[n];
+        R.copy(Cup[n], std::max(1, Q.rank[t]), G.C[n], std::max(1, Q.rank[t]), Q.rank[t], QW.rank[r], 0, 1.0, nullptr,
+               1.0);
+    }
+    R.flush_copy();
+    // dense leaves, exact: sum N N + L1 W_Y^* + V_X R1 + N_Z + Q (Cup QW^*)
+    std::unordered_map<int, double*> XV, WN;
+    std::vector<double*> L1(nn, nullptr), R1(nn, nullptr), CQ(nn, nullptr);
+    for (int n = 0; n < nn; ++n) {
+        if (N.kind[n] != DENSE) continue;
+        int t = N.t[n], r = N.s[n];
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.count(bx)) {
+                double* m = R.dalloc((size_t)T.size[t] * VY.rank[s]);
+                R.job(m, (int)T.size[t], VY.rank[s], (int)T.size[t], 0.0);
+                T_(R, X.N(bx), mv(VY.leaf[s], (int)T.size[s]), (int)T.size[s]);
+                XV[bx] = m;
+            }
+            if (X.kind(bx) == ADM && Y.kind(by) == DENSE && !WN.count(by)) {
+                double* m = R.dalloc((size_t)WX.rank[s] * T.size[r]);
+                R.job(m, WX.rank[s], (int)T.size[r], WX.rank[s], 0.0);
+                T_(R, mvT(WX.leaf[s], (int)T.size[s]), Y.N(by), (int)T.size[s]);
+                WN[by] = m;
+            }
+        }
+        CQ[n] = R.dalloc((size_t)std::max(1, Q.rank[t]) * T.size[r]);
+        R.job(CQ[n], Q.rank[t], (int)T.size[r], std::max(1, Q.rank[t]), 0.0);
+        R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.leaf[r], 1, (int)T.size[r], QW.rank[r]);
+    }
+    R.flush_gemm();
+    for (int n = 0; n < nn; ++n) {
+        if (N.kind[n] != DENSE) continue;
+        int t = N.t[n], r = N.s[n];
+        L1[n] = R.dalloc((size_t)T.size[t] * WY.rank[r]);
+        R.job(L1[n], (int)T.size[t], WY.rank[r], (int)T.size[t], 0.0);
+        R.term(VX.leaf[t], 0, (int)T.size[t], U1[n], 0, VX.rank[t], VX.rank[t]);
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) == DENSE && Y.kind(by) == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
+        }
+        R1[n] = R.dalloc((size_t)VX.rank[t] * T.size[r]);
+        R.job(R1[n], VX.rank[t], (int)T.size[r], VX.rank[t], 0.0);
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) == ADM && Y.kind(by) == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
+        }
+    }
+    R.flush_gemm();
+    for (int n = 0; n < nn; ++n) {
+        if (N.kind[n] != DENSE) continue;
+        int t = N.t[n], r = N.s[n];
+        int mt = (int)T.size[t], mr = (int)T.size[r];
+        G.C[n] = R.dalloc((size_t)mt * mr);
+        int bz = Z->st->blocks.find(t, r);
+        bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
+        if (zd) R.copy(ZV.N(bz).p, ZV.N(bz).ld, G.C[n], mt, mt, mr, 0);
+    }
+    R.flush_copy();
+    for (int n = 0; n < nn; ++n) {
+        if (N.kind[n] != DENSE) continue;
+        int t = N.t[n], r = N.s[n];
+        int mt = (int)T.size[t], mr = (int)T.size[r];
+        int bz = Z->st->blocks.find(t, r);
+        bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
+        R.job(G.C[n], mt, mr, mt, zd ? 1.0 : 0.0);
+        for (int s : G.PT.triples[n]) {
+            int bx = X.block(t, s), by = Y.block(s, r);
+            if (X.kind(bx) == DENSE && Y.kind(by) == DENSE) {
+                T_(R, X.N(bx), Y.N(by), (int)T.size[s]);
+                cnt.flops += 2.0 * mt * mr * T.size[s];
+            }
+        }
+        R.term(L1[n], 0, mt, WY.leaf[r], 1, mr, WY.rank[r]);
+        R.term(VX.leaf[t], 0, mt, R1[n], 0, VX.rank[t], VX.rank[t]);
+        R.term(Q.leaf[t], 0, mt, CQ[n], 0, std::max(1, Q.rank[t]), Q.rank[t]);
+    }
+    R.flush_gemm();
+}
+
+// ------------------------------------------------------------------ coarsening (Fig. 7, Fig. 6)
+// View of the intermediate matrix, optionally transposed (G^* for the column basis).
+struct GView {
+    const Intermediate* G;
+    const Tree* tree;
+    bool T;
+    const BlockTree& nodes() const { return G->PT.nodes; }
+    const Basis& rowb() const { return T ? *G->QW : *G->Q; }
+    const Basis& colb() const { return T ? *G->Q : *G->QW; }
+    int node(int t, int r) const { return T ? nodes().find(r, t) : nodes().find(t, r); }
+    const std::vector<int>& row_list(int t) const { return T ? nodes().by_col[t] : nodes().by_row[t]; }
+    int other(int n) const { return T ? nodes().t[n] : nodes().s[n]; }
+    int8_t kind(int n) const { return nodes().kind[n]; }
+    Mv C(int n) const { return Mv{G->C[n], std::max(1, G->Q->rank[nodes().t[n]]), T ? 1 : 0}; }
+    Mv D(int n) const { return Mv{G->C[n], (int)tree->size[nodes().t[n]], T ? 1 : 0}; }
+};
+
+// Q'_a^* G|_{a x b} as a matrix over the leaves of its column tree.
+struct Rep {
+    struct Leaf {
+        int c;
+        bool adm;
+        int col, width;
+    };
+    double* p = nullptr;
+    int ld = 1;
+    std::vector<Leaf> leaves;
+};
+
+struct Coarse {
+    std::shared_ptr<Basis> Qn;
+    PerCl Rt;  // Q'_t^* Q_t
+};
+
+// One chain X0 F1 F2 ... written to dst; no factors means a copy.
+struct Chain {
+    Mv src;
+    int rows, cols0;
+    std::vector<Mv> f;
+    std::vector<int> fcols;
+    double* dst;
+    int ldd;
+};
+
+static void run_chains(Runner& R, std::vector<Chain>& items) {
+    size_t maxlen = 0;
+    for (auto& c : items) maxlen = std::max(maxlen, c.f.size());
+    std::vector<Mv> cur(items.size());
+    std::vector<int> curc(items.size());
+    for (size_t i = 0; i < items.size(); ++i) {
+        cur[i] = items[i].src;
+        curc[i] = items[i].cols0;
+        if (items[i].f.empty())
+            R.copy(items[i].src.p, items[i].src.ld, items[i].dst, items[i].ldd, items[i].rows, items[i].cols0,
+                   items[i].src.tr);
+    }
+    R.flush_copy();
+    for (size_t st = 0; st < maxlen; ++st) {
+        for (size_t i = 0; i < items.size(); ++i) {
+            Chain& c = items[i];
+            if (st >= c.f.size()) continue;
+            bool last = (st + 1 == c.f.size());
+            int nc = c.fcols[st];
+            double* d = last ? c.dst : R.dalloc((size_t)std::max(1, c.rows * nc));
+            int ldd = last ? c.ldd : std::max(1, c.rows);
+            R.job(d, c.rows, nc, ldd, 0.0);
+            T_(R, cur[i], c.f[st], curc[i]);
+            cur[i] = mv(d, ldd);
+            curc[i] = nc;
+        }
+        R.flush_gemm();
+    }
+}
+
+static bool is_desc(int a, int d) {  // a is an ancestor of d (or equal)
+    while (d > a) d = Tree::parent(d);
+    return d == a;
+}
+
+static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cmap, const double* w, double eps) {
+    const Tree& T = *G.tree;
+    const Basis& Q = G.rowb();
+    const Basis& QW = G.colb();
+    Coarse out;
+    out.Qn = std::make_shared<Basis>();
+    Basis& Qn = *out.Qn;
+    Qn.rank.assign(T.nc, 0);
+    Qn.leaf.assign(T.nc, nullptr);
+    Qn.tr.assign(T.nc, nullptr);
+    out.Rt.init(T.nc);
+    // total weights of the product (Eq. Zt_condensation), top-down
+    PerCl Zt;
+    Zt.init(T.nc);
+    for (int l = 0; l <= T.L; ++l) {
+        for (int t = Tree::first(l); t < Tree::first(l) + Tree::count(l); ++t) {
+            int k = Q.rank[t];
+            int rows = (t > 0) ? Zt.rows[Tree::parent(t)] : 0;
+            for (int n : G.row_list(t))
+                if (G.kind(n) == ADM) rows += QW.rank[G.other(n)];
+            Zt.rows[t] = std::min(rows, k);
+            Zt.cols[t] = k;
+            Zt.p[t] = R.dalloc((size_t)std::max(1, Zt.rows[t] * k));
+            if (rows == 0 || k == 0) {
+                Zt.rows[t] = 0;
+                continue;
+            }
+            double* st = R.dalloc((size_t)rows * k);
+            int o = 0;
+            if (t > 0) {
+                int p = Tree::parent(t);
+                if (Zt.rows[p] > 0) {
+                    R.job(st, Zt.rows[p], k, rows, 0.0);
+                    R.term(Zt.p[p], 0, Zt.rows[p], Q.tr[t], 1, std::max(1, k), Q.rank[p]);
+                }
+                o = Zt.rows[p];
+            }
+            for (int n : G.row_list(t)) {
+                if (G.kind(n) != ADM) continue;
+                int r = G.other(n);
+                if (cmap[n] < 0) throw Error(H2_ERR_UNSUPPORTED, "admissible T^XY leaf outside the target's admissible blocks");
+                Mv c = G.C(n);
+                R.copy(c.p, c.ld, st + o, rows, QW.rank[r], k, c.tr ^ 1, 1.0, w + cmap[n]);
+                o += QW.rank[r];
+            }
+            R.qr(st, rows, k, rows, Zt.p[t], Zt.rows[t], nullptr, 1, 0);
+        }
+        R.flush_gemm();
+        R.flush_copy();
+        R.flush_qr();
+    }
+    std::unordered_map<int, Rep> A;  // node -> representation
+    for (int l = T.L; l >= 0; --l) {
+        const int c0 = Tree::first(l), nl = Tree::count(l);
+        const bool leaf = (l == T.L);
+        std::vector<int> rows(nl);
+        std::vector<double*> Vh(nl, nullptr);
+        std::vector<std::vector<int>> nodes(nl);   // dense (leaf) or split (non-leaf) coarse-admissible nodes
+        std::unordered_map<int, Rep> Ahat;          // split node -> A-hat before the projection
+        std::vector<Chain> chains;
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i;
+            for (int n : G.row_list(t))
+                if (cmap[n] >= 0 && G.kind(n) == (leaf ? DENSE : SPLIT)) nodes[i].push_back(n);
+            if (leaf) {
+                rows[i] = (int)T.size[t];
+                continue;
+            }
+            int a1 = Tree::child(t, 0), a2 = Tree::child(t, 1);
+            rows[i] = Qn.rank[a1] + Qn.rank[a2];
+            Vh[i] = R.dalloc((size_t)std::max(1, rows[i] * Q.rank[t]));
+            int o = 0;
+            for (int a : {a1, a2}) {
+                R.job(Vh[i] + o, Qn.rank[a], Q.rank[t], std::max(1, rows[i]), 0.0);
+                R.term(out.Rt.p[a], 0, std::max(1, Qn.rank[a]), Q.tr[a], 0, std::max(1, Q.rank[a]), Q.rank[a]);
+                o += Qn.rank[a];
+            }
+            // A-hat for every split coarse-admissible node (Eq. ct_nonleaf with match_column)
+            for (int n : nodes[i]) {
+                int r = G.other(n);
+                std::map<int, bool> target;  // cluster -> admissible (all reps agree)
+                for (int a : {a1, a2})
+                    for (int j = 0; j < 2; ++j) {
+                        int b = Tree::child(r, j);
+                        int nb = G.node(a, b);
+                        if (G.kind(nb) == ADM) {
+                            if (!target.count(b)) target[b] = true;
+                        } else {
+                            for (auto& lf : A.at(nb).leaves) {
+                                auto it = target.find(lf.c);
+                                target[lf.c] = (it == target.end() ? true : it->second) && lf.adm;
+                            }
+                        }
+                    }
+                Rep rep;
+                for (auto& [c, adm] : target) {
+                    bool finest = true;
+                    for (auto& kv : target)
+                        if (kv.first != c && is_desc(c, kv.first)) finest = false;
+                    if (finest) rep.leaves.push_back(Rep::Leaf{c, adm, 0, adm ? QW.rank[c] : (int)T.size[c]});
+                }
+                std::sort(rep.leaves.begin(), rep.leaves.end(),
+                          [&](const Rep::Leaf& x, const Rep::Leaf& y) { return T.off[x.c] < T.off[y.c]; });
+                int cols = 0;
+                for (auto& lf : rep.leaves) {
+                    lf.col = cols;
+                    cols += lf.width;
+                }
+                rep.ld = std::max(1, rows[i]);
+                rep.p = R.dalloc((size_t)rep.ld * std::max(1, cols));
+                int ro = 0;
+                for (int a : {a1, a2}) {
+                    for (auto& lf : rep.leaves) {
+                        int b = is_desc(Tree::child(r, 0), lf.c) ? Tree::child(r, 0) : Tree::child(r, 1);
+                        int nb = G.node(a, b);
+                        Chain ch;
+                        ch.rows = Qn.rank[a];
+                        ch.dst = rep.p + ro + (size_t)lf.col * rep.ld;
+                        ch.ldd = rep.ld;
+                        int src_c;
+                        bool src_adm;
+                        if (G.kind(nb) == ADM) {
+                            ch.src = mv(out.Rt.p[a], std::max(1, Qn.rank[a]));
+                            ch.cols0 = Q.rank[a];
+                            ch.f.push_back(G.C(nb));
+                            ch.fcols.push_back(QW.rank[b]);
+                            src_c = b;
+                            src_adm = true;
+                        } else {
+                            const Rep& cr = A.at(nb);
+                            const Rep::Leaf* sl = nullptr;
+                            for (auto& x : cr.leaves)
+                                if (is_desc(x.c, lf.c)) sl = &x;
+                            if (!sl) throw Error(H2_ERR_UNSUPPORTED, "column tree mismatch");
+                            ch.src = mv(cr.p + (size_t)sl->col * cr.ld, cr.ld);
+                            ch.cols0 = sl->width;
+                            src_c = sl->c;
+                            src_adm = sl->adm;
+                        }
+                        // split admissible representations down to the target leaf: A F^*
+                        std::vector<int> path;
+                        for (int c = lf.c; c != src_c; c = Tree::parent(c)) path.push_back(c);
+                        std::reverse(path.begin(), path.end());
+                        for (int c : path) {
+                            ch.f.push_back(mvT(QW.tr[c], std::max(1, QW.rank[c])));
+                            ch.fcols.push_back(QW.rank[c]);
+                        }
+                        if (src_adm && !lf.adm) {  // expand with the leaf basis: A W^*
+                            ch.f.push_back(mvT(QW.leaf[lf.c], (int)T.size[lf.c]));
+                            ch.fcols.push_back((int)T.size[lf.c]);
+                        }
+                        if (ch.rows > 0) chains.push_back(ch);
+                    }
+                    ro += Qn.rank[a];
+                }
+                Ahat[n] = rep;
+            }
+        }
+        R.flush_gemm();
+        run_chains(R, chains);
+        // condensed matrices (transposed): [Z_t V^*; w G_tr^* ...]; SVD
+        int* d_counts = (int*)R.dalloc(nl);
+        H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
+        SvdBatch sb(R);
+        std::vector<int> has(nl, 0);
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i;
+            int ncol = Zt.rows[t];
+            for (int n : nodes[i]) {
+                if (leaf) ncol += (int)T.size[G.other(n)];
+                else {
+                    auto& rp = Ahat.at(n);
+                    for (auto& lf : rp.leaves) ncol += lf.width;
+                }
+            }
+            if (ncol == 0 || rows[i] == 0) {
+                sb.add(nullptr, 0, 0, eps, d_counts + i);
+                continue;
+            }
+            has[i] = 1;
+            double* Ct = R.dalloc((size_t)ncol * rows[i]);
+            if (Zt.rows[t] > 0) {
+                R.job(Ct, Zt.rows[t], rows[i], ncol, 0.0);
+                if (leaf)
+                    R.term(Zt.p[t], 0, Zt.rows[t], Q.leaf[t], 1, rows[i], Q.rank[t]);
+                else
+                    R.term(Zt.p[t], 0, Zt.rows[t], Vh[i], 1, std::max(1, rows[i]), Q.rank[t]);
+            }
+            int o = Zt.rows[t];
+            for (int n : nodes[i]) {
+                if (leaf) {
+                    int r = G.other(n);
+                    Mv d = G.D(n);
+                    R.copy(d.p, d.ld, Ct + o, ncol, (int)T.size[r], rows[i], d.tr ^ 1, 1.0, w + cmap[n]);
+                    o += (int)T.size[r];
+                } else {
+                    auto& rp = Ahat.at(n);
+                    int wdt = 0;
+                    for (auto& lf : rp.leaves) wdt += lf.width;
+                    R.copy(rp.p, rp.ld, Ct + o, ncol, wdt, rows[i], 1, 1.0, w + cmap[n]);
+                    o += wdt;
+                }
+            }
+            sb.add(Ct, ncol, rows[i], eps, d_counts + i);
+        }
+        std::vector<SvdOut> so = sb.run();
+        std::vector<int> kk = read_counts(R, d_counts, nl);
+        size_t need = 0;
+        for (int i = 0; i < nl; ++i) {
+            Qn.rank[c0 + i] = (so[i].U ? kk[i] : 0);
+            need += (size_t)rows[i] * Qn.rank[c0 + i];
+        }
+        auto chunk = std::make_shared<DevBuf>();
+        chunk->alloc(std::max<size_t>(need, 1));
+        Qn.chunks.push_back(chunk);
+        size_t off = 0;
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i, kt = Qn.rank[t];
+            double* q = chunk->p + off;
+            off += (size_t)rows[i] * kt;
+            if (kt > 0) R.copy(so[i].U, so[i].ldu, q, rows[i], rows[i], kt, 0);
+            if (leaf) {
+                Qn.leaf[t] = q;
+            } else {
+                int o = 0;
+                for (int a : {Tree::child(t, 0), Tree::child(t, 1)}) {
+                    auto ch = std::make_shared<DevBuf>();
+                    ch->alloc(std::max<size_t>((size_t)Qn.rank[a] * kt, 1));
+                    Qn.chunks.push_back(ch);
+                    Qn.tr[a] = ch->p;
+                    if (kt > 0) R.copy(so[i].U + o, so[i].ldu, ch->p, std::max(1, Qn.rank[a]), Qn.rank[a], kt, 0);
+                    o += Qn.rank[a];
+                }
+            }
+            // keep a copy of the basis block for the projections below
+            out.Rt.rows[t] = kt;
+            out.Rt.cols[t] = Q.rank[t];
+            out.Rt.p[t] = R.dalloc((size_t)std::max(1, kt * Q.rank[t]));
+        }
+        R.flush_copy();
+        for (int i = 0; i < nl; ++i) {
+            int t = c0 + i, kt = Qn.rank[t];
+            double* q = (leaf ? Qn.leaf[t] : nullptr);
+            const double* U = so[i].U;
+            int ldu = so[i].ldu;
+            if (leaf) {
+                U = q;
+                ldu = rows[i];
+            }
+            // R_t = Q'^* V (Q_t at leaves, V-hat above)
+            R.job(out.Rt.p[t], kt, Q.rank[t], std::max(1, kt), 0.0);
+            if (kt > 0) {
+                if (leaf)
+                    R.term(U, 1, ldu, Q.leaf[t], 0, rows[i], rows[i]);
+                else
+                    R.term(U, 1, ldu, Vh[i], 0, std::max(1, rows[i]), rows[i]);
+            }
+            for (int n : nodes[i]) {
+                Rep rep;
+                rep.ld = std::max(1, kt);
+                if (leaf) {
+                    int r = G.other(n);
+                    rep.leaves.push_back(Rep::Leaf{r, false, 0, (int)T.size[r]});
+                    rep.p = R.dalloc((size_t)rep.ld * T.size[r]);
+                    R.job(rep.p, kt, (int)T.size[r], rep.ld, 0.0);
+                    if (kt > 0) T_(R, mvT(U, ldu), G.D(n), rows[i]);
+                } else {
+                    const Rep& ah = Ahat.at(n);
+                    rep.leaves = ah.leaves;
+                    int cols = 0;
+                    for (auto& lf : ah.leaves) cols += lf.width;
+                    rep.p = R.dalloc((size_t)rep.ld * std::max(1, cols));
+                    R.job(rep.p, kt, cols, rep.ld, 0.0);
+                    if (kt > 0) R.term(U, 1, ldu, ah.p, 0, ah.ld, rows[i]);
+                }
+                A[n] = rep;
+            }
+        }
+        R.flush_gemm();
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ final couplings on the target block tree
+// S'_tr = Q'_t^* G|_{t x r} Q'^W_r by upward accumulation over the T^XY subtree
+// of every admissible target block:
+//   admissible T^XY leaf: R_t S_tr R^W_r^*,  dense leaf: Q'_t^* D Q'^W_r,
+//   split node: sum over children E'_a^* Up_ab F'_b.
+static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, const Tree& T,
+                                            const std::vector<int>& cmap, const Coarse& rb, const Coarse& cb,
+                                            Counts& cnt) {
+    const BlockTree& N = G.PT.nodes;
+    const int nn = (int)N.kind.size();
+    const Basis& Qn = *rb.Qn;
+    const Basis& Wn = *cb.Qn;
+    const Basis& Q = *G.Q;
+    const Basis& QW = *G.QW;
+    std::vector<double*> Up(nn, nullptr);
+    for (int l = T.L; l >= 0; --l) {
+        std::vector<int> lv;
+        for (int n = 0; n < nn; ++n)
+            if (cmap[n] >= 0 && Tree::level(N.t[n]) == l) lv.push_back(n);
+        std::unordered_map<int, double*> m1;  // ADM/DENSE: node -> first factor; SPLIT: child -> Up F'
+        for (int n : lv) {
+            int t = N.t[n], r = N.s[n];
+            int kt = Qn.rank[t], kr = Wn.rank[r];
+            if (N.kind[n] == ADM) {
+                double* m = R.dalloc((size_t)std::max(1, kt * QW.rank[r]));
+                R.job(m, kt, QW.rank[r], std::max(1, kt), 0.0);
+                R.term(rb.Rt.p[t], 0, std::max(1, kt), G.C[n], 0, std::max(1, Q.rank[t]), Q.rank[t]);
+                m1[n] = m;
+                cnt.flops += 2.0 * kt * QW.rank[r] * Q.rank[t];
+            } else if (N.kind[n] == DENSE) {
+                double* m = R.dalloc((size_t)std::max(1, kt) * T.size[r]);
+                R.job(m, kt, (int)T.size[r], std::max(1, kt), 0.0);
+                R.term(Qn.leaf[t], 1, (int)T.size[t], G.C[n], 0, (int)T.size[t], (int)T.size[t]);
+                m1[n] = m;
+                cnt.flops += 2.0 * kt * T.size[r] * T.size[t];
+            } else {
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) {
+                        int a = Tree::child(t, i), b = Tree::child(r, j);
+                        int c = N.find(a, b);
+                        double* m = R.dalloc((size_t)std::max(1, Qn.rank[a] * kr));
+                        R.job(m, Qn.rank[a], kr, std::max(1, Qn.rank[a]), 0.0);
+                        R.term(Up[c], 0, std::max(1, Qn.rank[a]), Wn.tr[b], 0, std::max(1, Wn.rank[b]), Wn.rank[b]);
+                        m1[c] = m;
+                        cnt.flops += 2.0 * Qn.rank[a] * kr * Wn.rank[b];
+                    }
+            }
+        }
+        R.flush_gemm();
+        for (int n : lv) {
+            int t = N.t[n], r = N.s[n];
+            int kt = Qn.rank[t], kr = Wn.rank[r];
+            Up[n] = R.dalloc((size_t)std::max(1, kt * kr));
+            R.job(Up[n], kt, kr, std::max(1, kt), 0.0);
+            if (N.kind[n] == ADM) {
+                R.term(m1[n], 0, std::max(1, kt), cb.Rt.p[r], 1, std::max(1, kr), QW.rank[r]);
+                cnt.flops += 2.0 * kt * kr * QW.rank[r];
+            } else if (N.kind[n] == DENSE) {
+                R.term(m1[n], 0, std::max(1, kt), Wn.leaf[r], 0, (int)T.size[r], (int)T.size[r]);
+                cnt.flops += 2.0 * kt * kr * T.size[r];
+            } else {
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) {
+                        int a = Tree::child(t, i), b = Tree::child(r, j);
+                        int c = N.find(a, b);
+                        R.term(Qn.tr[a], 1, std::max(1, Qn.rank[a]), m1[c], 0, std::max(1, Qn.rank[a]), Qn.rank[a]);
+                        cnt.flops += 2.0 * kt * kr * Qn.rank[a];
+                    }
+            }
+        }
+        R.flush_gemm();
+    }
+    return Up;
+}
+
+// ------------------------------------------------------------------ driver
+static bool same_row_basis(const h2_matrix* A, const h2_matrix* B) {
+    // A's row basis equals B's row basis: the same object, or Chebyshev bases of
+    // the same structure and order (they are equal by construction)
+    if (A->V == B->V) return true;
+    return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint;
+}
+static bool same_col_basis(const h2_matrix* A, const h2_matrix* B) {
+    if (A->W == B->W) return true;
+    return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint;
+}
+
+static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, const h2_opts* opts) {
+    const double eps = opts ? opts->eps : 1e-6;
+    const int prec = opts ? opts->precision : H2_FP64;
+    cudaStream_t st = stream_of(opts);
+    auto t_host0 = std::chrono::steady_clock::now();
+    Runner R(st, prec);
+    PhaseClock clk(st);
+    Counts cnt;
+    const OpView X{Xm, false}, Y{Ym, false};
+    const Tree& T = X.tree();
+    clk.mark();
+    // phase A: compressed induced row and column bases (prep included)
+    Induced ra = induced_rows(R, X, Y, eps, cnt);
+    clk.mark();
+    const OpView Yt{Ym, true}, Xt{Xm, true};
+    Induced ca = induced_rows(R, Yt, Xt, eps, cnt);
+    clk.mark();
+    // the intermediate H^2-matrix on T^XY
+    Intermediate G;
+    G.PT = build_product_tree(Xm->st->blocks, Ym->st->blocks);
+    G.Q = ra.Q;
+    G.QW = ca.Q;
+    const BlockTree& Zb = Zm->st->blocks;
+    for (int b = 0; b < (int)Zb.kind.size(); ++b) {
+        int n = G.PT.nodes.find(Zb.t[b], Zb.s[b]);
+        if (n < 0 || (Zb.kind[b] == DENSE && G.PT.nodes.kind[n] != DENSE))
+            throw Error(H2_ERR_UNSUPPORTED, "the product block tree does not refine Z's block tree");
+    }
+    induced_matrix(R, X, Y, Zm, ra, ca, G, cnt);
+    clk.mark();
+    // phase B: coarsening to Z's block tree
+    const BlockTree& N = G.PT.nodes;
+    const int nn = (int)N.kind.size();
+    std::vector<int> cmap(nn, -1);
+    {
+        std::vector<int> stack{N.find(0, 0)};
+        std::vector<int> inh(nn, -1);
+        while (!stack.empty()) {
+            int n = stack.back();
+            stack.pop_back();
+            int b = inh[n];
+            if (b < 0) {
+                int zb = Zb.find(N.t[n], N.s[n]);
+                if (zb >= 0 && Zb.kind[zb] == ADM) b = zb;
+            }
+            cmap[n] = b;
+            if (N.kind[n] == SPLIT)
+                for (int i = 0; i < 2; ++i)
+                    for (int j = 0; j < 2; ++j) {
+                        int c = N.find(Tree::child(N.t[n], i), Tree::child(N.s[n], j));
+                        inh[c] = b;
+                        stack.push_back(c);
+                    }
+        }
+    }
+    // block weights 1 / ||G|_b||_F over the T^XY leaves of each admissible target block
+    double* sq = R.dalloc(std::max<size_t>(Zb.kind.size(), 1));
+    double* w = R.dalloc(std::max<size_t>(Zb.kind.size(), 1));
+    H2_CUDA(cudaMemsetAsync(sq, 0, sizeof(double) * std::max<size_t>(Zb.kind.size(), 1), st));
+    {
+        std::vector<SumSqJob> jobs;
+        for (int n = 0; n < nn; ++n) {
+            if (cmap[n] < 0 || N.kind[n] == SPLIT) continue;
+            int t = N.t[n], r = N.s[n];
+            if (N.kind[n] == ADM)
+                jobs.push_back(SumSqJob{G.C[n], G.Q->rank[t], G.QW->rank[r], std::max(1, G.Q->rank[t]), cmap[n]});
+            else
+                jobs.push_back(SumSqJob{G.C[n], (int)T.size[t], (int)T.size[r], (int)T.size[t], cmap[n]});
+        }
+        SumSqJob* dj = R.upload(jobs);
+        launch_sumsq(dj, (int)jobs.size(), sq, st);
+        launch_inv_sqrt(sq, w, (int)Zb.kind.size(), st);
+        R.launches += 2;
+    }
+    GView GR{&G, &T, false}, GC{&G, &T, true};
+    Coarse rb = coarsen_rows(R, GR, cmap, w, eps);
+    clk.mark();
+    Coarse cb = coarsen_rows(R, GC, cmap, w, eps);
+    clk.mark();
+    std::vector<double*> Up = final_couplings(R, G, T, cmap, rb, cb, cnt);
+    // assemble the result on Z's block tree in persistent memory
+    auto res = std::make_unique<h2_matrix>();
+    res->st = Zm->st;
+    res->V = rb.Qn;
+    res->W = cb.Qn;
+    res->kernel = -1;
+    res->order = 0;
+    res->device = Zm->device;
+    res->blk.assign(Zb.kind.size(), nullptr);
+    size_t tot = 0;
+    for (int b = 0; b < (int)Zb.kind.size(); ++b) {
+        int t = Zb.t[b], s = Zb.s[b];
+        if (Zb.kind[b] == ADM) tot += (size_t)rb.Qn->rank[t] * cb.Qn->rank[s];
+        if (Zb.kind[b] == DENSE) tot += (size_t)T.size[t] * T.size[s];
+    }
+    auto chunk = std::make_shared<DevBuf>();
+    chunk->alloc(std::max<size_t>(tot, 1));
+    res->chunks.push_back(chunk);
+    size_t o = 0;
+    for (int b = 0; b < (int)Zb.kind.size(); ++b) {
+        int t = Zb.t[b], s = Zb.s[b];
+        int n = N.find(t, s);
+        if (Zb.kind[b] == ADM) {
+            int kt = rb.Qn->rank[t], ks = cb.Qn->rank[s];
+            res->blk[b] = chunk->p + o;
+            o += (size_t)kt * ks;
+            R.copy(Up[n], std::max(1, kt), res->blk[b], std::max(1, kt), kt, ks, 0);
+        } else if (Zb.kind[b] == DENSE) {
+            res->blk[b] = chunk->p + o;
+            o += (size_t)T.size[t] * T.size[s];
+            R.copy(G.C[n], (int)T.size[t], res->blk[b], (int)T.size[t], (int)T.size[t], (int)T.size[s], 0);
+        }
+    }
+    R.flush_copy();
+    R.ensure_flag();
+    launch_check_finite(chunk->p, chunk->len, R.svd_flag(), st);
+    R.launches++;
+    clk.mark();
+    int flag = 0;
+    H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaGetLastError());
+    H2_CUDA(cudaStreamSynchronize(st));
+    if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
+    if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
+    if (opts && opts->stats) {
+        h2_stats* S = opts->stats;
+        S->t_prep_ms = 0.0;
+        S->t_rows_a_ms = clk.ms(0);
+        S->t_cols_a_ms = clk.ms(1);
+        S->t_mat_a_ms = clk.ms(2);
+        S->t_rows_b_ms = clk.ms(3);
+        S->t_cols_b_ms = clk.ms(4);
+        S->t_mat_b_ms = clk.ms(5);
+        S->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
+        S->kernel_launches = R.launches;
+        S->product_nodes = nn;
+        S->triples = cnt.triples;
+        S->max_rank_a = std::max(ra.Q->max_rank(), ca.Q->max_rank());
+        S->max_rank_b = std::max(rb.Qn->max_rank(), cb.Qn->max_rank());
+        S->flops = cnt.flops;
+        S->bytes_moved = cnt.bytes;
+    }
+    R.release_all();
+    H2_CUDA(cudaStreamSynchronize(st));
+    // swap the result into Z (X and Y may alias Z; they are no longer read)
+    Zm->V = res->V;
+    Zm->W = res->W;
+    Zm->blk = std::move(res->blk);
+    Zm->chunks = std::move(res->chunks);
+    Zm->kernel = -1;
+    Zm->order = 0;
+}
+
+}  // namespace h2
+
+extern "C" int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts) {
+    using namespace h2;
+    if (!Z || !X || !Y) return H2_ERR_ARG;
+    if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
+                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED)))
+        return H2_ERR_ARG;
+    if (X->st->fingerprint != Y->st->fingerprint || X->st->fingerprint != Z->st->fingerprint) return H2_ERR_SHAPE;
+    if (!same_row_basis(Z, X) || !same_col_basis(Z, Y)) return H2_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != Z->device) return H2_ERR_ARG;
+    extern int h2_run_guarded_mul(h2_matrix*, const h2_matrix*, const h2_matrix*, const h2_opts*);
+    return h2_run_guarded_mul(Z, X, Y, opts);
+}
+
+int h2_run_guarded_mul(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts) {
+    try {
+        h2::mul_add(Z, X, Y, opts);
+        return H2_OK;
+    } catch (const h2::Error& e) {
+        extern void h2_set_last_error(const char*);
+        h2_set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        extern void h2_set_last_error(const char*);
+        h2_set_last_error(e.what());
+        return H2_ERR_CUDA;
+    }
+}
