@@ -1,0 +1,337 @@
+"""Benchmark of the GB300 H^2 product Z <- Z + X Y.
+
+One step = one h2_mul_add call (the whole hot path: basis products, weights,
+compressed induced bases, the couplings on T^XY, coarsening, final
+couplings) on the n = 32768 unit-sphere workload: Laplace kernel, leaf 64,
+eta 2, Chebyshev order 4 (rank 64), X = Y = Z, eps = 1e-6.  The metric is
+rows per second (n / time).  The line's `value` is the FP64 GPU form (the
+workload's stated precision); the mixed-precision form of the same workload
+is reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own independent product (the products of
+a batch are independent: replicas only, weak scaling); value = all rows of
+all ranks / max-over-ranks time.  `--impl reference` times the FP64 CPU
+oracle (the reference for this method) on a bounded sample of the workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = dict(name="sphere-n32768-laplace-leaf64-eta2-m4-eps1e-6", geometry="sphere", n=32768, kernel=0,
+                leaf=64, eta=2.0, order=4, eps=1e-6, seed=2309090611)
+# bounded CPU sample of the same workload for the oracle: same geometry,
+# kernel, leaf, eta, order and eps at n = 4096 (about 10-20 s of CPU work)
+CPU_SAMPLE_N = 4096
+METRIC = "H2 Z<-Z+XY rows/s at eps (FP64 GPU form; mixed form beside it)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="override n (testing only)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def library_peaks(torch, dev):
+    """FP64 and FP32 (no TF32) GEMM throughput of cuBLAS on this GPU, measured
+    here: the denominators for the FP64 and FP32 contraction kernels, which
+    MEASURED_PEAKS.json does not cover."""
+    out = {}
+    for name, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        n = 8192 if dt == torch.float32 else 4096
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = False
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        out[name + "_tflops"] = 2.0 * n ** 3 / best / 1e12
+        del a, b
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_cpu_sample():
+    """The oracle as it stands on a bounded sample of the workload."""
+    from oracle import h2_oracle as O
+    w = WORKLOAD
+    pts = synth.make_points(w["geometry"], CPU_SAMPLE_N, w["seed"])
+    st = O.build_structure(pts, w["leaf"], w["eta"], w["order"])
+    G = O.build_interp(st, w["kernel"])
+    t0 = time.perf_counter()
+    O.mul_add(G, G, G, w["eps"])
+    dt = time.perf_counter() - t0
+    return CPU_SAMPLE_N / dt, dt
+
+
+def reference_arm(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    times = []
+    for i in range(args.warmup + args.steps):
+        v, dt = run_cpu_sample()
+        if i >= args.warmup:
+            times.append(dt)
+    value = CPU_SAMPLE_N * len(times) / sum(times)
+    cores = os.cpu_count()
+    sample = (f"oracle (numpy FP64) on n={CPU_SAMPLE_N} points of the same workload "
+              f"(sphere, Laplace, leaf 64, eta 2, order 4, eps 1e-6), X=Y=Z")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 points)",
+            "config": {"workload": WORKLOAD["name"] + f" (CPU sample n={CPU_SAMPLE_N})", "n": CPU_SAMPLE_N},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ours_arm(args):
+    import torch
+    import torch.distributed as tdist
+
+    import paper_2309_09061_gb300 as P
+
+    rank, world, local = dist_env()
+    if world > 1:
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.build()
+    P.load()
+    w = dict(WORKLOAD)
+    w["n"] = args.n
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    # each rank: its own independent product (seed offset by rank)
+    pts = synth.make_points(w["geometry"], w["n"], w["seed"] + 1000 * rank)
+    G = P.h2_build_interp(pts, w["kernel"], w["leaf"], w["eta"], w["order"], stream=sptr)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    def timed(precision, steps, warmup):
+        for _ in range(warmup):
+            Zw = P.h2_clone(G, stream=sptr)
+            P.h2_mul_add(Zw, G, G, w["eps"], precision, stream=sptr)
+            del Zw
+        Zs = [P.h2_clone(G, stream=sptr) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for Z in Zs:
+            stats.append(P.h2_mul_add(Z, G, G, w["eps"], precision, stream=sptr))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        dt = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            dt = float(t.item())
+        info = Zs[-1].info()
+        for Z in Zs:
+            Z.free()
+        return dt, wall, stats, info
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    dt64, wall64, st64, info64 = timed(P.H2_FP64, args.steps, args.warmup)
+    clocks = sampler.stop()
+    dtmx, wallmx, stmx, infomx = timed(P.H2_MIXED, args.steps, max(1, args.warmup // 2))
+    # end to end through the public API with host buffers: points host->device,
+    # build, product, result structure (ranks) device->host, per step
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        X = P.h2_build_interp(pts, w["kernel"], w["leaf"], w["eta"], w["order"], stream=sptr)
+        Z = P.h2_clone(X, stream=sptr)
+        P.h2_mul_add(Z, X, X, w["eps"], P.H2_FP64, stream=sptr)
+        _ = Z.structure()
+        Z.free()
+        X.free()
+    torch.cuda.synchronize(dev)
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    nclusters = info64["nclusters"]
+    d2h = w["n"] * 8 + 3 * nclusters * 8 + 2 * nclusters * 4
+
+    # roofline of the dominant kernel family (FP64 form)
+    fam = np.zeros(8)
+    fam_fl = np.zeros(8)
+    fam_by = np.zeros(8)
+    fam_n = np.zeros(8)
+    for s in st64:
+        fam += np.array(s["fam_ms"])
+        fam_fl += np.array(s["fam_flops"])
+        fam_by += np.array(s["fam_bytes"])
+        fam_n += np.array(s["fam_launches"])
+    top = int(np.argmax(fam))
+    peaks = measured_peaks()
+    lib_peaks = library_peaks(torch, dev) if rank == 0 else {}
+    names = P.FAMILIES + ["", ""]
+    avg_ms = fam[top] / max(1.0, fam_n[top])
+    if top == 0:  # FP64 products on the FP64 pipe
+        achieved = fam_fl[top] / (fam[top] / 1e3) / 1e12
+        roof = {"kernel": "k_gemm<double>", "bound": "alu", "achieved": achieved,
+                "peak": lib_peaks.get("fp64_tflops"), "unit": "TFLOP/s",
+                "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (no FP64 figure in MEASURED_PEAKS.json)"}
+    else:
+        achieved = fam_by[top] / (fam[top] / 1e3) / 1e9
+        roof = {"kernel": names[top], "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
+                "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
+    roof["traffic"] = None
+    roof["avg_launch_ms"] = avg_ms
+    roof["share_of_step"] = float(fam[top] / max(1e-9, fam.sum()))
+    fam_report = {names[i]: {"ms_per_step": fam[i] / len(st64), "launches_per_step": fam_n[i] / len(st64)}
+                  for i in range(6)}
+
+    n_all = w["n"] * world
+    value = n_all * args.steps / dt64
+    line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt64 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 points on the unit sphere)",
+            "config": {"workload": w["name"], "n": w["n"], "leaf": w["leaf"], "eta": w["eta"],
+                       "order": w["order"], "rank": w["order"] ** 3, "eps": w["eps"], "X=Y=Z": True,
+                       "precision": "FP64 products, FP64 QR/SVD",
+                       "l2": "inputs larger than L2 (X: %.0f MB)" % (G.info()["device_bytes"] / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "mixed": {"value": w["n"] * world * args.steps / dtmx, "unit": "rows/s",
+                      "ms_per_step": 1e3 * dtmx / args.steps, "speedup_vs_fp64": dt64 / dtmx,
+                      "precision": "FP32 products with FP32 accumulation, FP64 QR/SVD"},
+            "e2e": {"value": n_all / e2e_dt, "unit": "rows/s", "h2d_bytes_per_step": int(pts.nbytes),
+                    "d2h_bytes_per_step": int(d2h),
+                    "note": "h2_build_interp from host points + h2_clone + h2_mul_add + h2_get_structure"},
+            "gpu_launches": int(sum(s["kernel_launches"] for s in st64)),
+            "roofline": roof,
+            "kernel_families_fp64": fam_report,
+            "stats_fp64": {k: st64[-1][k] for k in ("t_rows_a_ms", "t_cols_a_ms", "t_mat_a_ms", "t_rows_b_ms",
+                                                     "t_cols_b_ms", "t_mat_b_ms", "product_nodes", "triples",
+                                                     "max_rank_a", "max_rank_b")},
+            "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        v, dt = run_cpu_sample()
+        line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"oracle on n={CPU_SAMPLE_N} points of the same workload, one product, "
+                                          f"{dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -25,6 +25,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define H2_API __attribute__((visibility("default")))
+#else
+#define H2_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -79,7 +85,23 @@ typedef struct {
     int max_rank_b;          /* largest rank of the final bases */
     double bytes_moved;      /* algorithmic bytes of the contractions (model) */
     double flops;            /* algorithmic flops of the contractions (model) */
+    /* Per kernel family (index H2_FAM_*): device time of all launches (sum of
+     * CUDA-event intervals around each launch on opts->stream), number of
+     * launches, algorithmic flops and bytes (every operand read once, every
+     * output written once; counted on the host from the launch descriptors). */
+    double fam_ms[8];
+    int64_t fam_launches[8];
+    double fam_flops[8];
+    double fam_bytes[8];
 } h2_stats;
+
+/* Kernel families of h2_stats.fam_*. */
+#define H2_FAM_GEMM 0   /* batched segmented products */
+#define H2_FAM_QR 1     /* batched Householder QR */
+#define H2_FAM_SVD 2    /* batched one-sided Jacobi SVD */
+#define H2_FAM_NORM 3   /* batched spectral norms (power iteration) */
+#define H2_FAM_COPY 4   /* batched copies, scalings, transpositions */
+#define H2_FAM_OTHER 5  /* norms of blocks, finiteness checks */
 
 typedef struct {
     double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */
@@ -117,7 +139,7 @@ typedef struct {
  *   n >= 1, 1 <= leaf_size, 1 <= cheb_order <= 8, eta >= 0, kernel H2_K_*.
  *   out         receives the new handle; untouched on error.
  * Errors: H2_ERR_ARG, H2_ERR_NUMERIC (non-finite point), H2_ERR_OOM, H2_ERR_CUDA. */
-int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta,
+H2_API int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta,
                     int cheb_order, const h2_opts* opts, h2_matrix** out);
 
 /* Z <- Z + X Y (Sec. 1), approximated to the block-relative tolerance
@@ -129,17 +151,17 @@ int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, 
  * success Z holds new adaptive bases and couplings on its own block tree; on
  * error Z is unchanged (the result is built aside and swapped in at the end).
  * X and Y are only read. */
-int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts);
+H2_API int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts);
 
 /* Expand A into a dense n x n matrix in the ORIGINAL point order (row i and
  * column j belong to points i and j), column-major with leading dimension
  * ld >= n.  `out` is a host pointer if out_on_device == 0, else a device
  * pointer on the handle's device.  Meant for tests at small n (n^2 doubles).
  * Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
-int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, const h2_opts* opts);
+H2_API int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, const h2_opts* opts);
 
 /* Sizes and structure of a handle.  Errors: H2_ERR_ARG. */
-int h2_info(const h2_matrix* A, h2_info_t* info);
+H2_API int h2_info(const h2_matrix* A, h2_info_t* info);
 
 /* Copy structure arrays of a handle to host memory (any pointer may be NULL):
  *   perm        n entries: original index of the point at tree position p
@@ -148,18 +170,34 @@ int h2_info(const h2_matrix* A, h2_info_t* info);
  *   row_ranks   nclusters entries: rank of the row basis per cluster
  *   col_ranks   nclusters entries: rank of the column basis per cluster
  * Errors: H2_ERR_ARG. */
-int h2_get_structure(const h2_matrix* A, int64_t* perm, int64_t* offsets, int64_t* sizes,
+H2_API int h2_get_structure(const h2_matrix* A, int64_t* perm, int64_t* offsets, int64_t* sizes,
                      int* row_ranks, int* col_ranks);
 
+/* Deep copy of a handle (same structure, bases and blocks) on the same device;
+ * the copy owns its own buffers.  Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
+H2_API int h2_clone(const h2_matrix* A, const h2_opts* opts, h2_matrix** out);
+
+/* Host-only planning, no device call: the cluster tree and block tree that
+ * h2_build_interp would build for these points (Def. "Cluster tree",
+ * Def. "Block tree"), and the product block tree T^XY of a product of two
+ * such matrices (Sec. 6).
+ *   perm     n entries (may be NULL): original index at each tree position
+ *   counts   8 entries (may be NULL): depth L, admissible, dense and split
+ *            blocks of the block tree, admissible, dense and split nodes of
+ *            T^XY, and the number of (t,s,r) triples contributing to T^XY.
+ * Errors: H2_ERR_ARG (bad sizes), H2_ERR_NUMERIC (non-finite point). */
+H2_API int h2_plan_structure(const double* points, int64_t n, int leaf_size, double eta, int64_t* perm,
+                             int64_t* counts);
+
 /* Release a handle and its device memory; NULL is ignored. */
-void h2_free(h2_matrix* A);
+H2_API void h2_free(h2_matrix* A);
 
 /* Static description of an error code. */
-const char* h2_error_string(int code);
+H2_API const char* h2_error_string(int code);
 
 /* Message of the last failed call on the calling thread ("" if none); valid
  * until the next call on that thread. */
-const char* h2_last_error_message(void);
+H2_API const char* h2_last_error_message(void);
 
 #ifdef __cplusplus
 }

@@ -20,8 +20,8 @@ ERRORS = {-1: "H2_ERR_ARG", -2: "H2_ERR_SHAPE", -3: "H2_ERR_OOM", -4: "H2_ERR_NU
 H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
 H2_FP64, H2_MIXED = 0, 1
 
-EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_free",
-            "h2_error_string", "h2_last_error_message"]
+EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
+            "h2_plan_structure", "h2_free", "h2_error_string", "h2_last_error_message"]
 
 
 class H2Error(RuntimeError):
@@ -37,10 +37,19 @@ class Stats(ctypes.Structure):
                 ("t_mat_b_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("product_nodes", ctypes.c_int64),
                 ("triples", ctypes.c_int64), ("max_rank_a", ctypes.c_int), ("max_rank_b", ctypes.c_int),
-                ("bytes_moved", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("bytes_moved", ctypes.c_double), ("flops", ctypes.c_double),
+                ("fam_ms", ctypes.c_double * 8), ("fam_launches", ctypes.c_int64 * 8),
+                ("fam_flops", ctypes.c_double * 8), ("fam_bytes", ctypes.c_double * 8)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if k.startswith("fam_") else v
+        return d
+
+
+FAMILIES = ["gemm", "qr", "svd", "norm", "copy", "other"]
 
 
 class Opts(ctypes.Structure):
@@ -73,12 +82,15 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_to_dense.argtypes = [vp, vp, i64, ci, vp]
     lib.h2_info.argtypes = [vp, vp]
     lib.h2_get_structure.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.h2_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
+    lib.h2_plan_structure.argtypes = [vp, i64, ci, cd, vp, vp]
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
     lib.h2_error_string.argtypes = [ci]
     lib.h2_last_error_message.restype = ctypes.c_char_p
-    for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure"):
+    for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
+              "h2_plan_structure"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -161,6 +173,24 @@ def h2_to_dense(A: H2Matrix, out=None, stream: int | None = None) -> np.ndarray:
         return buf
     _check(load().h2_to_dense(A.handle, out.data_ptr(), n, 1, ctypes.byref(o)), "h2_to_dense")
     return out
+
+
+def h2_clone(A: H2Matrix, stream: int | None = None) -> H2Matrix:
+    h = ctypes.c_void_p()
+    o = _opts(stream=stream)
+    _check(load().h2_clone(A.handle, ctypes.byref(o), ctypes.byref(h)), "h2_clone")
+    return H2Matrix(h)
+
+
+def h2_plan_structure(points: np.ndarray, leaf_size: int, eta: float):
+    """Host-only: (perm, counts) of the trees h2_build_interp would build; counts =
+    [depth, adm, dense, split blocks, adm, dense, split T^XY nodes, triples]."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    perm = np.empty(pts.shape[0], np.int64)
+    counts = np.empty(8, np.int64)
+    _check(load().h2_plan_structure(pts.ctypes.data, pts.shape[0], leaf_size, eta, perm.ctypes.data,
+                                    counts.ctypes.data), "h2_plan_structure")
+    return perm, counts
 
 
 def h2_free(A: H2Matrix) -> None:

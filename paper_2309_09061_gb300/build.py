@@ -10,7 +10,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libh2mul.so")
 SOURCES = ["h2_plan.cpp", "h2_core.cu", "h2_kernels.cu", "h2_mul.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler",
+         "-fvisibility=hidden"]
 
 
 def nvcc() -> str:

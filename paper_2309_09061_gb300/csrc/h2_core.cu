@@ -42,7 +42,52 @@ void DevBuf::reset() {
 }
 
 // ---------------------------------------------------------------- runner
-Runner::~Runner() { release_all(); }
+Runner::~Runner() {
+    release_all();
+    for (auto& m : marks_) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : pool_) cudaEventDestroy(e);
+}
+
+cudaEvent_t Runner::get_event() {
+    if (!pool_.empty()) {
+        cudaEvent_t e = pool_.back();
+        pool_.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    H2_CUDA(cudaEventCreate(&e));
+    return e;
+}
+
+void Runner::begin(int fam) {
+    (void)fam;
+    cur_ = get_event();
+    H2_CUDA(cudaEventRecord(cur_, st_));
+}
+
+void Runner::end(int fam, double flops, double bytes) {
+    cudaEvent_t b = get_event();
+    H2_CUDA(cudaEventRecord(b, st_));
+    marks_.push_back(Mark{fam, cur_, b, flops, bytes});
+    cur_ = nullptr;
+}
+
+void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes) {
+    for (auto& m : marks_) {
+        float f = 0.f;
+        cudaEventElapsedTime(&f, m.a, m.b);
+        if (ms) ms[m.fam] += f;
+        if (launches) launches[m.fam] += 1;
+        if (flops) flops[m.fam] += m.flops;
+        if (bytes) bytes[m.fam] += m.bytes;
+        pool_.push_back(m.a);
+        pool_.push_back(m.b);
+    }
+    marks_.clear();
+}
 
 double* Runner::dalloc(size_t n) {
     if (n == 0) n = 1;
@@ -102,13 +147,20 @@ void Runner::flush_gemm(int precision_override) {
         GTerm* dt = upload(terms_);
         GJob* dj = upload(jobs_);
         GTile* dti = upload(tiles);
-        // split very large launches to stay well inside the grid limit
-        const int chunk = 1 << 30;
-        for (size_t off = 0; off < tiles.size(); off += chunk) {
-            int nt = (int)std::min<size_t>(chunk, tiles.size() - off);
-            launch_gemm(dt, dj, dti + off, nt, precision_override >= 0 ? precision_override : prec_, st_);
-            ++launches;
+        // algorithmic work: every operand read once, every output written once
+        double fl = 0.0, by = 0.0;
+        for (const GJob& J : jobs_) {
+            for (int i = 0; i < J.nt; ++i) {
+                const GTerm& T = terms_[J.t0 + i];
+                fl += 2.0 * J.m * J.n * T.k;
+                by += 8.0 * ((double)J.m * T.k + (double)T.k * J.n);
+            }
+            by += 8.0 * J.m * J.n * (J.beta != 0.0 ? 2.0 : 1.0);
         }
+        begin(0);
+        launch_gemm(dt, dj, dti, (int)tiles.size(), precision_override >= 0 ? precision_override : prec_, st_);
+        end(0, fl, by);
+        ++launches;
     }
     terms_.clear();
     jobs_.clear();
@@ -123,7 +175,15 @@ void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q,
 void Runner::flush_qr() {
     if (qrs_.empty()) return;
     QRJob* d = upload(qrs_);
+    double fl = 0.0, by = 0.0;
+    for (auto& j : qrs_) {
+        double m = j.m, n = j.n, p = std::min(j.m, j.n);
+        fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p + (j.Q ? 4.0 * m * j.q * p : 0.0);
+        by += 8.0 * (2.0 * m * n + (j.R ? p * n : 0.0) + (j.Q ? m * j.q : 0.0));
+    }
+    begin(1);
     launch_qr(d, (int)qrs_.size(), st_);
+    end(1, fl, by);
     ++launches;
     qrs_.clear();
 }
@@ -137,7 +197,11 @@ void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* s
 void Runner::flush_svd() {
     if (svds_.empty()) return;
     SVDJob* d = upload(svds_);
+    double by = 0.0;
+    for (auto& j : svds_) by += 8.0 * 3.0 * j.m * j.n;
+    begin(2);
     launch_svd(d, (int)svds_.size(), svd_maxn_, st_);
+    end(2, 0.0, by);
     ++launches;
     svds_.clear();
     svd_maxn_ = 0;
@@ -151,7 +215,14 @@ void Runner::norm(const double* A, int m, int n, int lda, double* inv, double* n
 void Runner::flush_norm() {
     if (norms_.empty()) return;
     NormJob* d = upload(norms_);
+    double by = 0.0, fl = 0.0;
+    for (auto& j : norms_) {
+        by += 8.0 * j.m * j.n;
+        fl += 4.0 * 61.0 * j.m * j.n;
+    }
+    begin(3);
     launch_norm(d, (int)norms_.size(), st_);
+    end(3, fl, by);
     ++launches;
     norms_.clear();
 }
@@ -165,7 +236,11 @@ void Runner::copy(const double* src, int lds, double* dst, int ldd, int rows, in
 void Runner::flush_copy() {
     if (copies_.empty()) return;
     CopyJob* d = upload(copies_);
+    double by = 0.0;
+    for (auto& j : copies_) by += 8.0 * j.rows * j.cols * (j.beta != 0.0 ? 3.0 : 2.0);
+    begin(4);
     launch_copy(d, (int)copies_.size(), st_);
+    end(4, 0.0, by);
     ++launches;
     copies_.clear();
 }
@@ -426,6 +501,72 @@ int h2_get_structure(const h2_matrix* A, int64_t* perm, int64_t* offsets, int64_
     if (row_ranks) std::copy(A->V->rank.begin(), A->V->rank.end(), row_ranks);
     if (col_ranks) std::copy(A->W->rank.begin(), A->W->rank.end(), col_ranks);
     return H2_OK;
+}
+
+int h2_clone(const h2_matrix* A, const h2_opts* opts, h2_matrix** out) {
+    if (!A || !out) return H2_ERR_ARG;
+    return run_guarded([&] {
+        cudaStream_t st = stream_of(opts);
+        auto M = std::make_unique<h2_matrix>();
+        M->st = A->st;
+        M->kernel = A->kernel;
+        M->order = A->order;
+        M->device = A->device;
+        // copy every chunk and translate the pointers into it
+        std::vector<std::pair<const DevBuf*, DevBuf*>> map;
+        auto dup = [&](const std::vector<std::shared_ptr<DevBuf>>& src, std::vector<std::shared_ptr<DevBuf>>& dst) {
+            for (auto& c : src) {
+                auto d = std::make_shared<DevBuf>();
+                d->alloc(c->len);
+                if (c->len) H2_CUDA(cudaMemcpyAsync(d->p, c->p, 8 * c->len, cudaMemcpyDeviceToDevice, st));
+                map.push_back({c.get(), d.get()});
+                dst.push_back(d);
+            }
+        };
+        auto tr = [&](const double* p) -> double* {
+            if (!p) return nullptr;
+            for (auto& [a, b] : map)
+                if (p >= a->p && p < a->p + a->len) return b->p + (p - a->p);
+            throw Error(H2_ERR_ARG, "pointer outside the handle's buffers");
+        };
+        auto cloneb = [&](const Basis& B) {
+            auto nb = std::make_shared<Basis>();
+            nb->rank = B.rank;
+            dup(B.chunks, nb->chunks);
+            for (double* p : B.leaf) nb->leaf.push_back(tr(p));
+            for (double* p : B.tr) nb->tr.push_back(tr(p));
+            return nb;
+        };
+        M->V = cloneb(*A->V);
+        M->W = (A->W == A->V) ? M->V : cloneb(*A->W);
+        dup(A->chunks, M->chunks);
+        for (double* p : A->blk) M->blk.push_back(tr(p));
+        H2_CUDA(cudaStreamSynchronize(st));
+        *out = M.release();
+    });
+}
+
+int h2_plan_structure(const double* points, int64_t n, int leaf_size, double eta, int64_t* perm, int64_t* counts) {
+    if (!points || n < 1 || leaf_size < 1 || !(eta >= 0.0) || !std::isfinite(eta)) return H2_ERR_ARG;
+    for (int64_t i = 0; i < 3 * n; ++i)
+        if (!std::isfinite(points[i])) return H2_ERR_NUMERIC;
+    return run_guarded([&] {
+        auto st = build_structure(points, n, leaf_size, eta);
+        if (perm) std::copy(st->tree.perm.begin(), st->tree.perm.end(), perm);
+        if (counts) {
+            ProductTree P = build_product_tree(st->blocks, st->blocks);
+            int64_t tri = 0;
+            for (auto& v : P.triples) tri += (int64_t)v.size();
+            counts[0] = st->tree.L;
+            counts[1] = st->blocks.count(ADM);
+            counts[2] = st->blocks.count(DENSE);
+            counts[3] = st->blocks.count(SPLIT);
+            counts[4] = P.nodes.count(ADM);
+            counts[5] = P.nodes.count(DENSE);
+            counts[6] = P.nodes.count(SPLIT);
+            counts[7] = tri;
+        }
+    });
 }
 
 void h2_free(h2_matrix* A) {

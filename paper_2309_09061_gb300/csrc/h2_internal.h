@@ -267,6 +267,11 @@ public:
     int* svd_flag() const { return d_flag_; }
     void ensure_flag();
 
+    // per-family device time: events around every launch (collected after a sync)
+    void begin(int fam);
+    void end(int fam, double flops, double bytes);
+    void collect(double* ms, int64_t* launches, double* flops, double* bytes);
+
     // device scratch from the stream-ordered pool
     double* dalloc(size_t n);
     template <class T>
@@ -285,6 +290,15 @@ private:
     std::vector<CopyJob> copies_;
     std::vector<void*> owned_;
     int* d_flag_ = nullptr;
+    struct Mark {
+        int fam;
+        cudaEvent_t a, b;
+        double flops, bytes;
+    };
+    std::vector<Mark> marks_;
+    std::vector<cudaEvent_t> pool_;
+    cudaEvent_t cur_ = nullptr;
+    cudaEvent_t get_event();
 };
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -1271,8 +1271,10 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
                 jobs.push_back(SumSqJob{G.C[n], (int)T.size[t], (int)T.size[r], (int)T.size[t], cmap[n]});
         }
         SumSqJob* dj = R.upload(jobs);
+        R.begin(5);
         launch_sumsq(dj, (int)jobs.size(), sq, st);
         launch_inv_sqrt(sq, w, (int)Zb.kind.size(), st);
+        R.end(5, 0.0, 0.0);
         R.launches += 2;
     }
     GView GR{&G, &T, false}, GC{&G, &T, true};
@@ -1316,7 +1318,9 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     }
     R.flush_copy();
     R.ensure_flag();
+    R.begin(5);
     launch_check_finite(chunk->p, chunk->len, R.svd_flag(), st);
+    R.end(5, 0.0, 8.0 * chunk->len);
     R.launches++;
     clk.mark();
     int flag = 0;
@@ -1342,6 +1346,13 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
         S->max_rank_b = std::max(rb.Qn->max_rank(), cb.Qn->max_rank());
         S->flops = cnt.flops;
         S->bytes_moved = cnt.bytes;
+        for (int f = 0; f < 8; ++f) {
+            S->fam_ms[f] = 0.0;
+            S->fam_launches[f] = 0;
+            S->fam_flops[f] = 0.0;
+            S->fam_bytes[f] = 0.0;
+        }
+        R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
     }
     R.release_all();
     H2_CUDA(cudaStreamSynchronize(st));
@@ -1356,6 +1367,24 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
 
 }  // namespace h2
 
+void h2_set_last_error(const char* m);
+
+static int run_guarded_mul(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts) {
+    try {
+        h2::mul_add(Z, X, Y, opts);
+        return H2_OK;
+    } catch (const h2::Error& e) {
+        h2_set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        h2_set_last_error("host allocation failed");
+        return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        h2_set_last_error(e.what());
+        return H2_ERR_CUDA;
+    }
+}
+
 extern "C" int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts) {
     using namespace h2;
     if (!Z || !X || !Y) return H2_ERR_ARG;
@@ -1366,23 +1395,6 @@ extern "C" int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, 
     if (!same_row_basis(Z, X) || !same_col_basis(Z, Y)) return H2_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != Z->device) return H2_ERR_ARG;
-    extern int h2_run_guarded_mul(h2_matrix*, const h2_matrix*, const h2_matrix*, const h2_opts*);
-    return h2_run_guarded_mul(Z, X, Y, opts);
+    return run_guarded_mul(Z, X, Y, opts);
 }
 
-int h2_run_guarded_mul(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts) {
-    try {
-        h2::mul_add(Z, X, Y, opts);
-        return H2_OK;
-    } catch (const h2::Error& e) {
-        extern void h2_set_last_error(const char*);
-        h2_set_last_error(e.what());
-        return e.code;
-    } catch (const std::bad_alloc&) {
-        return H2_ERR_OOM;
-    } catch (const std::exception& e) {
-        extern void h2_set_last_error(const char*);
-        h2_set_last_error(e.what());
-        return H2_ERR_CUDA;
-    }
-}

@@ -1,0 +1,88 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every entry
+point that include/h2mul.h declares, validates arguments without touching a
+device, and its host planner builds the same trees as the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2309_09061_gb300 as P
+import synth
+from oracle import h2_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    P.build()
+    return P.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "h2mul.h")).read()
+    return sorted(set(re.findall(r"H2_API\s+[\w\s\*]*?\b(h2_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(P.EXPORTED) == set(names)
+
+
+def test_error_strings(lib):
+    for code in range(0, -8, -1):
+        assert lib.h2_error_string(code)
+    assert lib.h2_error_string(-99) == b"unknown error"
+
+
+def test_argument_validation_without_device(lib):
+    h = ctypes.c_void_p()
+    pts = np.zeros((4, 3))
+    # NULL points, bad sizes, bad kernel, bad order: rejected before any device call
+    assert lib.h2_build_interp(None, 4, 0, 2, 2.0, 3, None, ctypes.byref(h)) == -1
+    assert lib.h2_build_interp(pts.ctypes.data, 0, 0, 2, 2.0, 3, None, ctypes.byref(h)) == -1
+    assert lib.h2_build_interp(pts.ctypes.data, 4, 9, 2, 2.0, 3, None, ctypes.byref(h)) == -1
+    assert lib.h2_build_interp(pts.ctypes.data, 4, 0, 2, 2.0, 0, None, ctypes.byref(h)) == -1
+    assert lib.h2_build_interp(pts.ctypes.data, 4, 0, 2, -1.0, 3, None, ctypes.byref(h)) == -1
+    bad = pts.copy()
+    bad[1, 2] = np.nan
+    assert lib.h2_build_interp(bad.ctypes.data, 4, 0, 2, 2.0, 3, None, ctypes.byref(h)) == -4
+    assert lib.h2_mul_add(None, None, None, None) == -1
+    assert lib.h2_to_dense(None, None, 0, 0, None) == -1
+    assert lib.h2_info(None, None) == -1
+    assert lib.h2_clone(None, None, ctypes.byref(h)) == -1
+    lib.h2_free(None)
+
+
+@pytest.mark.parametrize("geometry,n,leaf,eta", [("sphere", 2048, 32, 2.0), ("cube", 1500, 20, 1.5),
+                                                  ("cube_surface", 3000, 64, 2.0), ("sphere", 777, 16, 0.0)])
+def test_planner_matches_oracle(lib, geometry, n, leaf, eta):
+    pts = synth.make_points(geometry, n, 2309090610)
+    perm, counts = P.h2_plan_structure(pts, leaf, eta)
+    st = O.build_structure(pts, leaf, eta, 2)
+    assert np.array_equal(perm, st.tree.perm)
+    kinds = list(st.blocks.kind.values())
+    assert counts[0] == st.tree.depth
+    assert counts[1:4].tolist() == [kinds.count(O.ADM), kinds.count(O.DENSE), kinds.count(O.SPLIT)]
+    X = O.build_interp(st, O.K_CONST) if n <= 800 else None
+    if X is not None:
+        PT = O.build_product_tree(X, X)
+        pk = list(PT.kind.values())
+        assert counts[4:7].tolist() == [pk.count(O.ADM), pk.count(O.DENSE), pk.count(O.SPLIT)]
+        assert counts[7] == sum(len(v) for v in PT.triples.values())
+
+
+def test_product_tree_counts_against_oracle(lib):
+    pts = synth.sphere(1024, 3)
+    perm, counts = P.h2_plan_structure(pts, 16, 2.0)
+    st = O.build_structure(pts, 16, 2.0, 1)
+    X = O.build_interp(st, O.K_CONST)
+    PT = O.build_product_tree(X, X)
+    pk = list(PT.kind.values())
+    assert counts[4:7].tolist() == [pk.count(O.ADM), pk.count(O.DENSE), pk.count(O.SPLIT)]
+    assert counts[7] == sum(len(v) for v in PT.triples.values())

@@ -1,0 +1,169 @@
+"""GPU parity of the CUDA product path against the FP64 oracle (element by
+element on the dense expansions) and, at the full size of the n = 32768
+sphere workload, against the definition Z + X Y on sampled rows.
+
+Tolerances: exact mode (eps = 0) reproduces Z + XY to 1e-12 in FP64; the
+truncated product matches the oracle within 10 eps in relative Frobenius
+norm (the target the method is built to) and the dense product within eps.
+The mixed mode runs the contractions in FP32 (unit roundoff 6e-8), so its
+exact-mode bound is 1e-5 and its truncated bound stays 10 eps for
+eps >= 1e-6."""
+import numpy as np
+import pytest
+
+import paper_2309_09061_gb300 as P
+import synth
+from oracle import h2_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+SEED_C1, SEED_C2 = 2309090610, 2309090611
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    return P.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_pair(pts, leaf, eta, order, eps, kx, ky, kz, precision):
+    X = P.h2_build_interp(pts, kx, leaf, eta, order)
+    Y = X if ky == kx else P.h2_build_interp(pts, ky, leaf, eta, order)
+    Z = P.h2_build_interp(pts, kz, leaf, eta, order)
+    stats = P.h2_mul_add(Z, X, Y, eps, precision)
+    st = O.build_structure(pts, leaf, eta, order)
+    Xo, Yo, Zo = O.build_interp(st, kx), O.build_interp(st, ky), O.build_interp(st, kz)
+    ref = Zo.to_dense() + Xo.to_dense() @ Yo.to_dense()
+    return Z, stats, st, (Xo, Yo, Zo), ref
+
+
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
+def test_c1_sphere_against_oracle(precision):
+    """n = 2048 on the sphere, Laplace, leaf 32, eta 2, order 3, X = Y = Z, eps 1e-4."""
+    eps = 1e-4
+    pts = synth.sphere(2048, SEED_C1)
+    Z, stats, st, (Xo, Yo, Zo), ref = run_pair(pts, 32, 2.0, 3, eps, 0, 0, 0, precision)
+    res = O.mul_add(Zo, Xo, Yo, eps)
+    Zg = P.h2_to_dense(Z)
+    Zor = res.result.to_dense()
+    assert rel(Zg, Zor) <= 10 * eps
+    assert rel(Zg, ref) <= eps
+    perm = Z.structure()[0]
+    assert np.array_equal(perm, st.tree.perm)
+    assert stats["max_rank_a"] > 0 and stats["kernel_launches"] > 0
+
+
+@pytest.mark.parametrize("precision,tol", [(P.H2_FP64, 1e-12), (P.H2_MIXED, 1e-5)])
+def test_exact_mode(precision, tol):
+    """eps = 0 keeps every nonzero singular value: Z + XY reproduced exactly
+    (Sec. 3); X Laplace, Y Yukawa, so XY is not symmetric."""
+    pts = synth.sphere(512, 11)
+    Z, stats, st, _, ref = run_pair(pts, 16, 2.0, 2, 0.0, 0, 1, 0, precision)
+    assert rel(P.h2_to_dense(Z), ref) <= tol
+
+
+@pytest.mark.parametrize("geometry,n,leaf,eta,order,eps,kernels", [
+    ("cube_surface", 600, 16, 1.5, 2, 1e-5, (0, 0, 0)),
+    ("cube", 1024, 32, 1.5, 3, 1e-4, (1, 1, 1)),
+    ("cube", 1024, 32, 1.5, 3, 1e-6, (1, 0, 1)),
+    ("sphere", 1000, 20, 2.0, 3, 1e-6, (0, 1, 0)),   # ragged leaves (sizes 15 and 16)
+])
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
+def test_workload_shapes_against_oracle(geometry, n, leaf, eta, order, eps, kernels, precision):
+    pts = synth.make_points(geometry, n, 5)
+    Z, stats, st, (Xo, Yo, Zo), ref = run_pair(pts, leaf, eta, order, eps, *kernels, precision)
+    Zor = O.mul_add(Zo, Xo, Yo, eps).result.to_dense()
+    Zg = P.h2_to_dense(Z)
+    assert rel(Zg, Zor) <= 10 * eps
+    assert rel(Zg, ref) <= 2 * eps
+
+
+def test_eta_zero_is_dense_product():
+    pts = synth.sphere(300, 2)
+    Z, stats, st, _, ref = run_pair(pts, 16, 0.0, 2, 1e-3, 0, 1, 0, P.H2_FP64)
+    assert rel(P.h2_to_dense(Z), ref) <= 1e-13
+
+
+def test_constant_kernel_closed_form():
+    n = 384
+    pts = synth.sphere(n, 4)
+    X = P.h2_build_interp(pts, P.H2_K_CONST, 16, 2.0, 2)
+    Z = P.h2_clone(X)
+    P.h2_mul_add(Z, X, X, 1e-6)
+    assert np.abs(P.h2_to_dense(Z) - (n + 1)).max() <= 1e-9 * (n + 1)
+
+
+def test_identity_factor():
+    pts = synth.sphere(512, 9)
+    eps = 1e-6
+    X = P.h2_build_interp(pts, P.H2_K_DELTA, 16, 2.0, 2)
+    Y = P.h2_build_interp(pts, P.H2_K_YUKAWA, 16, 2.0, 2)
+    Z = P.h2_build_interp(pts, P.H2_K_LAPLACE, 16, 2.0, 2)
+    ref = P.h2_to_dense(Z) + P.h2_to_dense(Y)
+    P.h2_mul_add(Z, X, Y, eps)
+    assert rel(P.h2_to_dense(Z), ref) <= eps
+
+
+def test_clone_and_repeat():
+    """A clone is independent of its source, and two products from the same
+    inputs agree to 10 eps."""
+    pts = synth.sphere(1024, 8)
+    eps = 1e-5
+    X = P.h2_build_interp(pts, 0, 32, 2.0, 3)
+    Z1, Z2 = P.h2_clone(X), P.h2_clone(X)
+    D0 = P.h2_to_dense(X)
+    P.h2_mul_add(Z1, X, X, eps)
+    P.h2_mul_add(Z2, X, X, eps)
+    assert np.array_equal(P.h2_to_dense(X), D0)
+    assert rel(P.h2_to_dense(Z1), P.h2_to_dense(Z2)) <= 10 * eps
+
+
+def test_error_codes():
+    pts = synth.sphere(256, 1)
+    X = P.h2_build_interp(pts, 0, 16, 2.0, 2)
+    other = P.h2_build_interp(synth.sphere(256, 2), 0, 16, 2.0, 2)
+    wrong_order = P.h2_build_interp(pts, 0, 16, 2.0, 3)
+    Z = P.h2_clone(X)
+    with pytest.raises(P.H2Error) as e:
+        P.h2_mul_add(Z, X, other, 1e-4)
+    assert e.value.code == -2
+    with pytest.raises(P.H2Error) as e:
+        P.h2_mul_add(wrong_order, X, X, 1e-4)
+    assert e.value.code == -6
+    with pytest.raises(P.H2Error) as e:
+        P.h2_mul_add(Z, X, X, -1.0)
+    assert e.value.code == -1
+    before = P.h2_to_dense(Z)
+    assert np.array_equal(before, P.h2_to_dense(X))
+
+
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
+def test_c2_full_size_sampled_rows(precision):
+    """n = 32768 on the sphere, Laplace, leaf 64, eta 2, order 4, X = Y = Z,
+    eps 1e-6 (the benchmark workload, same launch path): 64 sampled rows of
+    the result against rows of Z + X Y formed from the dense expansions."""
+    import torch
+    eps = 1e-6
+    n = 32768
+    pts = synth.sphere(n, SEED_C2)
+    G = P.h2_build_interp(pts, P.H2_K_LAPLACE, 64, 2.0, 4)
+    Z = P.h2_clone(G)
+    stats = P.h2_mul_add(Z, G, G, eps, precision)
+    dev = torch.device("cuda:0")
+    Gd = torch.empty((n, n), dtype=torch.float64, device=dev)
+    P.h2_to_dense(G, Gd)          # column-major fill: Gd.T is the matrix
+    rows = torch.as_tensor(np.sort(synth.splitmix64(77, 64) % n).astype(np.int64), device=dev)
+    Gm = Gd.T
+    exact = Gm[rows] + Gm[rows] @ Gm
+    Zd = torch.empty((n, n), dtype=torch.float64, device=dev)
+    P.h2_to_dense(Z, Zd)
+    got = Zd.T[rows]
+    err = float(torch.linalg.norm(got - exact) / torch.linalg.norm(exact))
+    assert err <= 10 * eps, (err, stats)
