@@ -287,8 +287,13 @@ def ours_arm(args):
     roof["traffic"] = None
     roof["avg_launch_ms"] = avg_ms
     roof["share_of_step"] = float(fam[top] / max(1e-9, fam.sum()))
-    fam_report = {names[i]: {"ms_per_step": fam[i] / len(st64), "launches_per_step": fam_n[i] / len(st64)}
+    fam_report = {names[i]: {"ms_per_step": fam[i] / len(st64), "launches_per_step": fam_n[i] / len(st64),
+                             "gflop_per_step": fam_fl[i] / len(st64) / 1e9, "gb_per_step": fam_by[i] / len(st64) / 1e9}
                   for i in range(6)}
+    fam_mx = np.zeros(8)
+    for s in stmx:
+        fam_mx += np.array(s["fam_ms"])
+    fam_report_mx = {names[i]: {"ms_per_step": fam_mx[i] / len(stmx)} for i in range(6)}
 
     n_all = w["n"] * world
     value = n_all * args.steps / dt64
@@ -310,6 +315,7 @@ def ours_arm(args):
             "gpu_launches": int(sum(s["kernel_launches"] for s in st64)),
             "roofline": roof,
             "kernel_families_fp64": fam_report,
+            "kernel_families_mixed": fam_report_mx,
             "stats_fp64": {k: st64[-1][k] for k in ("t_rows_a_ms", "t_cols_a_ms", "t_mat_a_ms", "t_rows_b_ms",
                                                      "t_cols_b_ms", "t_mat_b_ms", "product_nodes", "triples",
                                                      "max_rank_a", "max_rank_b")},

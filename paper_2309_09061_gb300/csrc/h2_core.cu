@@ -89,14 +89,30 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
     marks_.clear();
 }
 
+// Scratch of one call: bump allocation (256-byte aligned) from chunks of the
+// library's stream-ordered pool; everything is returned by release_all().
 double* Runner::dalloc(size_t n) {
     if (n == 0) n = 1;
-    int dev = 0;
-    H2_CUDA(cudaGetDevice(&dev));
-    void* p = nullptr;
-    H2_CUDA(cudaMallocFromPoolAsync(&p, n * sizeof(double), lib_pool(dev), st_));
-    owned_.push_back(p);
-    return (double*)p;
+    size_t bytes = (n * sizeof(double) + 255) & ~(size_t)255;
+#ifdef H2_EXACT_ALLOC
+    const size_t chunk_min = 0;  // one pool allocation per buffer (bounds-checking builds)
+#else
+    const size_t chunk_min = (size_t)64 << 20;
+#endif
+    if (bytes > cur_left_) {
+        size_t sz = std::max(bytes, chunk_min);
+        int dev = 0;
+        H2_CUDA(cudaGetDevice(&dev));
+        void* p = nullptr;
+        H2_CUDA(cudaMallocFromPoolAsync(&p, sz, lib_pool(dev), st_));
+        owned_.push_back(p);
+        cur_chunk_ = (char*)p;
+        cur_left_ = sz;
+    }
+    double* out = (double*)cur_chunk_;
+    cur_chunk_ += bytes;
+    cur_left_ -= bytes;
+    return out;
 }
 
 template <class T>
@@ -114,6 +130,8 @@ template double** Runner::upload<double*>(const std::vector<double*>&);
 void Runner::release_all() {
     for (void* p : owned_) cudaFreeAsync(p, st_);
     owned_.clear();
+    cur_chunk_ = nullptr;
+    cur_left_ = 0;
     d_flag_ = nullptr;
 }
 
@@ -166,13 +184,32 @@ void Runner::flush_gemm(int precision_override) {
     jobs_.clear();
 }
 
-void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q) {
+void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32) {
     if (m <= 0 || n <= 0) return;
     double* tau = dalloc(std::min(m, n));
-    qrs_.push_back(QRJob{A, R, Q, tau, m, n, lda, ldr, ldq, q});
+    if (fp32) {
+        float* a32 = (float*)dalloc(((size_t)m * n + 1) / 2);
+        qrs32_.push_back(QRJob{A, R, nullptr, tau, a32, m, n, lda, ldr, ldq, 0});
+    } else {
+        qrs_.push_back(QRJob{A, R, Q, tau, nullptr, m, n, lda, ldr, ldq, q});
+    }
 }
 
 void Runner::flush_qr() {
+    if (!qrs32_.empty()) {
+        QRJob* d = upload(qrs32_);
+        double fl = 0.0, by = 0.0;
+        for (auto& j : qrs32_) {
+            double m = j.m, n = j.n, p = std::min(j.m, j.n);
+            fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p;
+            by += 8.0 * m * n + 8.0 * p * n;
+        }
+        begin(1);
+        launch_qr32(d, (int)qrs32_.size(), st_);
+        end(1, fl, by);
+        ++launches;
+        qrs32_.clear();
+    }
     if (qrs_.empty()) return;
     QRJob* d = upload(qrs_);
     double fl = 0.0, by = 0.0;
@@ -205,6 +242,24 @@ void Runner::flush_svd() {
     ++launches;
     svds_.clear();
     svd_maxn_ = 0;
+}
+
+void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64) {
+    float* W = (float*)dalloc(((size_t)m * n + 1) / 2);
+    float* V = (float*)dalloc(((size_t)n * n + 1) / 2);
+    pres_.push_back(PreJob{B, W, V, V64, m, n, ldb});
+}
+
+void Runner::flush_pre() {
+    if (pres_.empty()) return;
+    PreJob* d = upload(pres_);
+    double by = 0.0;
+    for (auto& j : pres_) by += 8.0 * ((double)j.m * j.n + (double)j.n * j.n);
+    begin(2);
+    launch_jacobi_pre(d, (int)pres_.size(), st_);
+    end(2, 0.0, by);
+    ++launches;
+    pres_.clear();
 }
 
 void Runner::norm(const double* A, int m, int n, int lda, double* inv, double* nrm) {
@@ -258,6 +313,7 @@ template GJob* Runner::upload<GJob>(const std::vector<GJob>&);
 template GTile* Runner::upload<GTile>(const std::vector<GTile>&);
 template QRJob* Runner::upload<QRJob>(const std::vector<QRJob>&);
 template SVDJob* Runner::upload<SVDJob>(const std::vector<SVDJob>&);
+template PreJob* Runner::upload<PreJob>(const std::vector<PreJob>&);
 template NormJob* Runner::upload<NormJob>(const std::vector<NormJob>&);
 template CopyJob* Runner::upload<CopyJob>(const std::vector<CopyJob>&);
 template SumSqJob* Runner::upload<SumSqJob>(const std::vector<SumSqJob>&);

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
@@ -82,17 +83,6 @@ struct BlockTree {
     }
 };
 
-// Shared structure of matrices built from one point set.
-struct Structure {
-    Tree tree;
-    BlockTree blocks;
-    double eta = 0;
-    std::vector<double> points;  // n x 3, original order
-    uint64_t fingerprint = 0;
-};
-
-std::shared_ptr<Structure> build_structure(const double* pts, int64_t n, int leaf, double eta);
-
 // Product block tree T^XY (Sec. 6) with its triples: for node (t,r), the s with
 // (t,s) in T_IJ, (s,r) in T_JK, not both split.
 struct ProductTree {
@@ -100,6 +90,20 @@ struct ProductTree {
     std::vector<std::vector<int>> triples; // per node: list of s
 };
 ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y);
+
+// Shared structure of matrices built from one point set, with the cached
+// product block trees of products with other structures.
+struct Structure {
+    Tree tree;
+    BlockTree blocks;
+    double eta = 0;
+    std::vector<double> points;  // n x 3, original order
+    uint64_t fingerprint = 0;
+    std::mutex plan_mutex;
+    std::unordered_map<uint64_t, std::shared_ptr<ProductTree>> product_trees;
+};
+
+std::shared_ptr<Structure> build_structure(const double* pts, int64_t n, int leaf, double eta);
 
 // ---------------------------------------------------------------- device storage
 struct DevBuf {
@@ -177,6 +181,8 @@ struct QRJob {
     double* R;
     double* Q;
     double* tau;  // workspace, min(m,n) entries
+    float* A32;   // when set: FP32 workspace (m x n, ld m); A is only read and the
+                  // factorisation runs in FP32 (R written in FP64, Q not formed)
     int m, n, lda, ldr, ldq, q;
 };
 
@@ -192,6 +198,16 @@ struct SVDJob {
     int* flag;
     int m, n, ldb, ldu;
     double eps;
+};
+
+// FP32 preconditioning of a one-sided Jacobi SVD: sweeps on an FP32 copy W of
+// B (m x n) accumulate the right rotations in V; V64 (n x n) receives them.
+struct PreJob {
+    const double* B;
+    float* W;
+    float* V;
+    double* V64;
+    int m, n, ldb;
 };
 
 // Spectral norm of A (m x n) by power iteration; writes 1/||A|| (0 if the norm
@@ -216,7 +232,9 @@ struct CopyJob {
 void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
                  cudaStream_t st);
 void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
+void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);
+void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st);
 void launch_norm(const NormJob* jobs, int njobs, cudaStream_t st);
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);
 void launch_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
@@ -254,10 +272,12 @@ public:
     void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
               const double* scale = nullptr);
     void flush_gemm(int precision_override = -1);
-    void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q);
+    void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false);
     void flush_qr();
     void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps);
     void flush_svd();
+    void jacobi_pre(const double* B, int m, int n, int ldb, double* V64);
+    void flush_pre();
     void norm(const double* A, int m, int n, int lda, double* inv, double* nrm);
     void flush_norm();
     void copy(const double* src, int lds, double* dst, int ldd, int rows, int cols, int trans, double alpha = 1.0,
@@ -285,10 +305,14 @@ private:
     std::vector<GJob> jobs_;
     std::vector<QRJob> qrs_;
     std::vector<SVDJob> svds_;
+    std::vector<PreJob> pres_;
+    std::vector<QRJob> qrs32_;
     int svd_maxn_ = 0;
     std::vector<NormJob> norms_;
     std::vector<CopyJob> copies_;
-    std::vector<void*> owned_;
+    std::vector<void*> owned_;       // pool chunks
+    char* cur_chunk_ = nullptr;      // bump pointer into the last chunk
+    size_t cur_left_ = 0;
     int* d_flag_ = nullptr;
     struct Mark {
         int fam;

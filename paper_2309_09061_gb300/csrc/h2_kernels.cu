@@ -113,15 +113,37 @@ __device__ double block_sum(double v, double* red) {
 // orthogonal factor is accumulated backwards when requested.
 constexpr int QT = 256;
 
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// T = double: in place on A.  T = float: A (FP64) is converted into the FP32
+// workspace A32 first and the factorisation runs there.
+template <class T>
 __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
     __shared__ double red[QT / 32];
     const QRJob J = jobs[blockIdx.x];
     const int m = J.m, n = J.n, p = m < n ? m : n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = QT / 32;
+    T* A;
+    int lda;
+    if constexpr (sizeof(T) == 4) {
+        A = (T*)J.A32;
+        lda = m;
+        for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += QT)
+            A[e] = (T)J.A[(e % m) + (size_t)(e / m) * J.lda];
+        __syncthreads();
+    } else {
+        A = (T*)J.A;
+        lda = J.lda;
+    }
     for (int j = 0; j < p; ++j) {
-        double* col = J.A + (size_t)j * J.lda;
+        T* col = A + (size_t)j * lda;
         double s = 0.0;
-        for (int i = j + 1 + threadIdx.x; i < m; i += QT) s += col[i] * col[i];
+        for (int i = j + 1 + threadIdx.x; i < m; i += QT) s += (double)col[i] * (double)col[i];
         s = block_sum<QT>(s, red);
         const double x0 = col[j];
         double tau = 0.0, beta = x0, sc = 0.0;
@@ -132,19 +154,22 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
         }
         __syncthreads();
         if (s > 0.0)
-            for (int i = j + 1 + threadIdx.x; i < m; i += QT) col[i] *= sc;
+            for (int i = j + 1 + threadIdx.x; i < m; i += QT) col[i] = (T)(col[i] * sc);
         if (threadIdx.x == 0) {
-            col[j] = beta;
+            col[j] = (T)beta;
             J.tau[j] = tau;
         }
         __syncthreads();
         if (tau != 0.0) {
+            const T tt = (T)tau;
             for (int c = j + 1 + warp; c < n; c += nw) {
-                double* a = J.A + (size_t)c * J.lda;
-                double w = 0.0;
+                T* a = A + (size_t)c * lda;
+                T w = 0;
                 for (int i = j + 1 + lane; i < m; i += 32) w += col[i] * a[i];
-                w = warp_sum(w) + a[j];
-                w *= tau;
+                w = warp_sum_t<T>(w);
+                __syncwarp();
+                w = (w + a[j]) * tt;
+                __syncwarp();
                 if (lane == 0) a[j] -= w;
                 for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * col[i];
             }
@@ -154,10 +179,10 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
     if (J.R) {
         for (int e = threadIdx.x; e < p * n; e += QT) {
             int i = e % p, c = e / p;
-            J.R[i + (size_t)c * J.ldr] = (i <= c) ? J.A[i + (size_t)c * J.lda] : 0.0;
+            J.R[i + (size_t)c * J.ldr] = (i <= c) ? (double)A[i + (size_t)c * lda] : 0.0;
         }
     }
-    if (J.Q) {
+    if (sizeof(T) == 8 && J.Q) {
         for (int e = threadIdx.x; e < m * J.q; e += QT) {
             int i = e % m, c = e / m;
             J.Q[i + (size_t)c * J.ldq] = (i == c) ? 1.0 : 0.0;
@@ -166,15 +191,17 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
         for (int j = p - 1; j >= 0; --j) {
             const double tau = J.tau[j];
             if (tau == 0.0) continue;
-            const double* v = J.A + (size_t)j * J.lda;
+            const T* v = A + (size_t)j * lda;
             for (int c = warp; c < J.q; c += nw) {
                 double* a = J.Q + (size_t)c * J.ldq;
                 double w = 0.0;
-                for (int i = j + 1 + lane; i < m; i += 32) w += v[i] * a[i];
-                w = warp_sum(w) + a[j];
-                w *= tau;
+                for (int i = j + 1 + lane; i < m; i += 32) w += (double)v[i] * a[i];
+                w = warp_sum(w);
+                __syncwarp();
+                w = (w + a[j]) * tau;
+                __syncwarp();
                 if (lane == 0) a[j] -= w;
-                for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * v[i];
+                for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * (double)v[i];
             }
             __syncthreads();
         }
@@ -182,7 +209,11 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
 }
 
 void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st) {
-    if (njobs > 0) k_qr<<<njobs, QT, 0, st>>>(jobs);
+    if (njobs > 0) k_qr<double><<<njobs, QT, 0, st>>>(jobs);
+}
+
+void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_qr<float><<<njobs, QT, 0, st>>>(jobs);
 }
 
 // ------------------------------------------------------------------ one-sided Jacobi SVD
@@ -271,6 +302,73 @@ __global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
         for (int q = 0; q < n; ++q) cnt += (sig[q] > J.eps);
         *J.count = cnt;
     }
+}
+
+// FP32 preconditioning sweeps: the same rotations as k_svd on an FP32 copy W
+// of B, accumulated into V (V starts as the identity).  Bounded sweeps.
+constexpr int PMAXSWEEP = 30;
+
+__global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jobs) {
+    __shared__ int rotated;
+    const PreJob J = jobs[blockIdx.x];
+    const int m = J.m, n = J.n;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
+    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) J.W[e] = (float)J.B[(e % m) + (size_t)(e / m) * J.ldb];
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
+    __syncthreads();
+    const int np = n + (n & 1);
+    const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
+    bool converged = (n < 2);
+    for (int sweep = 0; sweep < PMAXSWEEP && !converged; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pr = warp; pr < np / 2; pr += nw) {
+                int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
+                if (p >= n || q >= n) continue;
+                if (p > q) { int t = p; p = q; q = t; }
+                float* ap = J.W + (size_t)p * m;
+                float* aq = J.W + (size_t)q * m;
+                float al = 0.f, be = 0.f, ga = 0.f;
+                for (int i = lane; i < m; i += 32) {
+                    float x = ap[i], y = aq[i];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum_t<float>(al);
+                be = warp_sum_t<float>(be);
+                ga = warp_sum_t<float>(ga);
+                if (ga != 0.f && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+                    float zeta = (be - al) / (2.f * ga);
+                    float t = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
+                                                    : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    float c = 1.f / sqrtf(1.f + t * t), s = c * t;
+                    for (int i = lane; i < m; i += 32) {
+                        float x = ap[i], y = aq[i];
+                        ap[i] = c * x - s * y;
+                        aq[i] = s * x + c * y;
+                    }
+                    float* vp = J.V + (size_t)p * n;
+                    float* vq = J.V + (size_t)q * n;
+                    for (int i = lane; i < n; i += 32) {
+                        float x = vp[i], y = vq[i];
+                        vp[i] = c * x - s * y;
+                        vq[i] = s * x + c * y;
+                    }
+                    if (lane == 0) rotated = 1;
+                }
+            }
+            __syncthreads();
+        }
+        converged = (rotated == 0);
+        __syncthreads();
+    }
+    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
+}
+
+void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_jacobi_pre<<<njobs, JT, 0, st>>>(jobs);
 }
 
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {

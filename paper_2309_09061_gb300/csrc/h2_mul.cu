@@ -15,6 +15,7 @@
 #include <cmath>
 #include <functional>
 #include <map>
+#include <mutex>
 
 #include "h2_internal.h"
 
@@ -256,7 +257,7 @@ public:
         if (m > 0 && ncol > 0) {
             if (ncol > m) {
                 j.Rt = R_.dalloc((size_t)m * m);
-                R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0);
+                R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0, R_.precision() == H2_MIXED);
             }
             j.B = R_.dalloc((size_t)m * std::min(m, ncol));
         }
@@ -279,9 +280,38 @@ public:
                 R_.copy(j.Bt, j.ncol, j.B, j.m, j.m, j.ncol, 1);
             out[i].U = R_.dalloc((size_t)j.m * w);
             out[i].ldu = j.m;
-            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps);
         }
         R_.flush_copy();
+        if (R_.precision() == H2_MIXED) {
+            // FP32 sweeps accumulate V, then C = B V in FP64 replaces B
+            std::vector<double*> V64(jobs_.size(), nullptr), C(jobs_.size(), nullptr);
+            for (size_t i = 0; i < jobs_.size(); ++i) {
+                Job& j = jobs_[i];
+                if (!j.B) continue;
+                int w = std::min(j.m, j.ncol);
+                if (w < 2) continue;
+                V64[i] = R_.dalloc((size_t)w * w);
+                R_.jacobi_pre(j.B, j.m, w, j.m, V64[i]);
+            }
+            R_.flush_pre();
+            for (size_t i = 0; i < jobs_.size(); ++i) {
+                if (!V64[i]) continue;
+                Job& j = jobs_[i];
+                int w = std::min(j.m, j.ncol);
+                C[i] = R_.dalloc((size_t)j.m * w);
+                R_.job(C[i], j.m, w, j.m, 0.0);
+                R_.term(j.B, 0, j.m, V64[i], 0, w, w);
+            }
+            R_.flush_gemm(H2_FP64);
+            for (size_t i = 0; i < jobs_.size(); ++i)
+                if (C[i]) jobs_[i].B = C[i];
+        }
+        for (size_t i = 0; i < jobs_.size(); ++i) {
+            Job& j = jobs_[i];
+            if (!j.B) continue;
+            int w = std::min(j.m, j.ncol);
+            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps);
+        }
         R_.flush_svd();
         jobs_.clear();
         return out;
@@ -550,7 +580,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
 // the new transfer matrices.  Dense leaves hold the exact leaf-level products
 // plus the expansion of the pushed-down coupling.
 struct Intermediate {
-    ProductTree PT;
+    const ProductTree* PT = nullptr;  // the cached plan
     std::shared_ptr<Basis> Q, QW;  // row / column bases (isometric)
     std::vector<double*> C;        // per node: coupling (ADM / SPLIT) or dense block (DENSE)
 };
@@ -564,7 +594,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     const Basis& WX = X.colb();
     const Basis& VY = Y.rowb();
     const Basis& WY = Y.colb();
-    const BlockTree& N = G.PT.nodes;
+    const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
     const OpView ZV{Z, false};
     PerCl P = basis_products(R, T, WX, VY);
@@ -582,10 +612,19 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     R.flush_gemm();
     // U1 (all nodes): S_Z copied first, then += sum of S_X PSY
     std::vector<double*> U1(nn, nullptr);
+    {
+        size_t tot = 0;
+        for (int n = 0; n < nn; ++n) tot += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
+        double* base = R.dalloc(std::max<size_t>(tot, 1));
+        H2_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * std::max<size_t>(tot, 1), R.stream()));
+        size_t o = 0;
+        for (int n = 0; n < nn; ++n) {
+            U1[n] = base + o;
+            o += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
+        }
+    }
     for (int n = 0; n < nn; ++n) {
         int t = N.t[n], r = N.s[n];
-        U1[n] = R.dalloc((size_t)VX.rank[t] * WY.rank[r]);
-        H2_CUDA(cudaMemsetAsync(U1[n], 0, sizeof(double) * VX.rank[t] * WY.rank[r], R.stream()));
         int bz = Z->st->blocks.find(t, r);
         if (bz >= 0 && Z->st->blocks.kind[bz] == ADM)
             R.copy(ZV.S(bz).p, ZV.S(bz).ld, U1[n], VX.rank[t], VX.rank[t], WY.rank[r], 0);
@@ -594,7 +633,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     for (int n = 0; n < nn; ++n) {
         int t = N.t[n], r = N.s[n];
         R.job(U1[n], VX.rank[t], WY.rank[r], VX.rank[t], 1.0);
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) == ADM && Y.kind(by) == ADM) {
                 T_(R, X.S(bx), mv(PSY[by], WX.rank[s]), WX.rank[s]);
@@ -612,7 +651,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         U2[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * WY.rank[r]));
         R.job(U2[n], Q.rank[t], WY.rank[r], std::max(1, Q.rank[t]), 0.0);
         R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U1[n], 0, VX.rank[t], VX.rank[t]);
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) != ADM && Y.kind(by) == ADM) {
                 T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
@@ -621,7 +660,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         }
         U3[n] = R.dalloc((size_t)std::max(1, VX.rank[t] * QW.rank[r]));
         R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) == ADM && Y.kind(by) != ADM) {
                 T_(R, X.S(bx), mvT(ca.A.at(by), std::max(1, QW.rank[r])), WX.rank[s]);
@@ -632,11 +671,20 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     R.flush_gemm();
     G.C.assign(nn, nullptr);
     std::vector<double*> Cup(nn, nullptr);
+    {
+        size_t tot = 0;
+        for (int n = 0; n < nn; ++n) tot += (size_t)std::max(1, Q.rank[N.t[n]] * QW.rank[N.s[n]]);
+        double* base = R.dalloc(tot);
+        H2_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * tot, R.stream()));
+        size_t o = 0;
+        for (int n = 0; n < nn; ++n) {
+            Cup[n] = base + o;
+            o += (size_t)std::max(1, Q.rank[N.t[n]] * QW.rank[N.s[n]]);
+        }
+    }
     for (int n = 0; n < nn; ++n) {
         int t = N.t[n], r = N.s[n];
         size_t cs = (size_t)std::max(1, Q.rank[t] * QW.rank[r]);
-        Cup[n] = R.dalloc(cs);
-        H2_CUDA(cudaMemsetAsync(Cup[n], 0, sizeof(double) * cs, R.stream()));
         if (N.kind[n] == DENSE) continue;
         G.C[n] = R.dalloc(cs);
         R.job(G.C[n], Q.rank[t], QW.rank[r], std::max(1, Q.rank[t]), 0.0);
@@ -683,7 +731,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     for (int n = 0; n < nn; ++n) {
         if (N.kind[n] != DENSE) continue;
         int t = N.t[n], r = N.s[n];
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.count(bx)) {
                 double* m = R.dalloc((size_t)T.size[t] * VY.rank[s]);
@@ -709,13 +757,13 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         L1[n] = R.dalloc((size_t)T.size[t] * WY.rank[r]);
         R.job(L1[n], (int)T.size[t], WY.rank[r], (int)T.size[t], 0.0);
         R.term(VX.leaf[t], 0, (int)T.size[t], U1[n], 0, VX.rank[t], VX.rank[t]);
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) == DENSE && Y.kind(by) == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
         }
         R1[n] = R.dalloc((size_t)VX.rank[t] * T.size[r]);
         R.job(R1[n], VX.rank[t], (int)T.size[r], VX.rank[t], 0.0);
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) == ADM && Y.kind(by) == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
         }
@@ -738,7 +786,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         int bz = Z->st->blocks.find(t, r);
         bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
         R.job(G.C[n], mt, mr, mt, zd ? 1.0 : 0.0);
-        for (int s : G.PT.triples[n]) {
+        for (int s : G.PT->triples[n]) {
             int bx = X.block(t, s), by = Y.block(s, r);
             if (X.kind(bx) == DENSE && Y.kind(by) == DENSE) {
                 T_(R, X.N(bx), Y.N(by), (int)T.size[s]);
@@ -758,7 +806,7 @@ struct GView {
     const Intermediate* G;
     const Tree* tree;
     bool T;
-    const BlockTree& nodes() const { return G->PT.nodes; }
+    const BlockTree& nodes() const { return G->PT->nodes; }
     const Basis& rowb() const { return T ? *G->QW : *G->Q; }
     const Basis& colb() const { return T ? *G->Q : *G->QW; }
     int node(int t, int r) const { return T ? nodes().find(r, t) : nodes().find(t, r); }
@@ -1122,7 +1170,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
 static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, const Tree& T,
                                             const std::vector<int>& cmap, const Coarse& rb, const Coarse& cb,
                                             Counts& cnt) {
-    const BlockTree& N = G.PT.nodes;
+    const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
     const Basis& Qn = *rb.Qn;
     const Basis& Wn = *cb.Qn;
@@ -1190,6 +1238,17 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
 }
 
 // ------------------------------------------------------------------ driver
+// The product block tree depends only on the two block trees: kept on the
+// structure of X, keyed by the fingerprint of Y's structure.
+static const ProductTree& cached_product_tree(Structure& xs, const Structure& ys) {
+    std::lock_guard<std::mutex> g(xs.plan_mutex);
+    auto it = xs.product_trees.find(ys.fingerprint);
+    if (it == xs.product_trees.end())
+        it = xs.product_trees.emplace(ys.fingerprint, std::make_shared<ProductTree>(build_product_tree(xs.blocks, ys.blocks)))
+                 .first;
+    return *it->second;
+}
+
 static bool same_row_basis(const h2_matrix* A, const h2_matrix* B) {
     // A's row basis equals B's row basis: the same object, or Chebyshev bases of
     // the same structure and order (they are equal by construction)
@@ -1220,19 +1279,19 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     clk.mark();
     // the intermediate H^2-matrix on T^XY
     Intermediate G;
-    G.PT = build_product_tree(Xm->st->blocks, Ym->st->blocks);
+    G.PT = &cached_product_tree(*Xm->st, *Ym->st);
     G.Q = ra.Q;
     G.QW = ca.Q;
     const BlockTree& Zb = Zm->st->blocks;
     for (int b = 0; b < (int)Zb.kind.size(); ++b) {
-        int n = G.PT.nodes.find(Zb.t[b], Zb.s[b]);
-        if (n < 0 || (Zb.kind[b] == DENSE && G.PT.nodes.kind[n] != DENSE))
+        int n = G.PT->nodes.find(Zb.t[b], Zb.s[b]);
+        if (n < 0 || (Zb.kind[b] == DENSE && G.PT->nodes.kind[n] != DENSE))
             throw Error(H2_ERR_UNSUPPORTED, "the product block tree does not refine Z's block tree");
     }
     induced_matrix(R, X, Y, Zm, ra, ca, G, cnt);
     clk.mark();
     // phase B: coarsening to Z's block tree
-    const BlockTree& N = G.PT.nodes;
+    const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
     std::vector<int> cmap(nn, -1);
     {
