@@ -96,12 +96,14 @@ typedef struct {
 } h2_stats;
 
 /* Kernel families of h2_stats.fam_*. */
-#define H2_FAM_GEMM 0   /* batched segmented products */
-#define H2_FAM_QR 1     /* batched Householder QR */
-#define H2_FAM_SVD 2    /* batched one-sided Jacobi SVD */
-#define H2_FAM_NORM 3   /* batched spectral norms (power iteration) */
-#define H2_FAM_COPY 4   /* batched copies, scalings, transpositions */
-#define H2_FAM_OTHER 5  /* norms of blocks, finiteness checks */
+#define H2_FAM_GEMM64 0  /* batched segmented products, FP64 arithmetic */
+#define H2_FAM_GEMM32 1  /* batched segmented products, FP32 arithmetic */
+#define H2_FAM_QR 2      /* Householder QR (FP64 or FP32) and pivoted Cholesky */
+#define H2_FAM_SVD 3     /* one-sided Jacobi SVD, FP64 sweeps */
+#define H2_FAM_SVDPRE 4  /* one-sided Jacobi preconditioning, FP32 sweeps */
+#define H2_FAM_NORM 5    /* spectral norms by power iteration */
+#define H2_FAM_COPY 6    /* batched copies, scalings, transpositions */
+#define H2_FAM_OTHER 7   /* block norms, finiteness checks */
 
 typedef struct {
     double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */

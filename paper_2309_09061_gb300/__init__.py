@@ -49,7 +49,7 @@ class Stats(ctypes.Structure):
         return d
 
 
-FAMILIES = ["gemm", "qr", "svd", "norm", "copy", "other"]
+FAMILIES = ["gemm_fp64", "gemm_fp32", "qr_chol", "svd_fp64", "svd_fp32_pre", "norm", "copy", "other"]
 
 
 class Opts(ctypes.Structure):

@@ -62,6 +62,12 @@ cudaEvent_t Runner::get_event() {
     return e;
 }
 
+double* Runner::dev_counter() {
+    double* c = dalloc(1);
+    H2_CUDA(cudaMemsetAsync(c, 0, sizeof(double), st_));
+    return c;
+}
+
 void Runner::begin(int fam) {
     (void)fam;
     cur_ = get_event();
@@ -71,7 +77,7 @@ void Runner::begin(int fam) {
 void Runner::end(int fam, double flops, double bytes) {
     cudaEvent_t b = get_event();
     H2_CUDA(cudaEventRecord(b, st_));
-    marks_.push_back(Mark{fam, cur_, b, flops, bytes});
+    marks_.push_back(Mark{fam, cur_, b, flops, bytes, nullptr});
     cur_ = nullptr;
 }
 
@@ -79,9 +85,11 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
     for (auto& m : marks_) {
         float f = 0.f;
         cudaEventElapsedTime(&f, m.a, m.b);
+        double df = 0.0;
+        if (m.dflops) cudaMemcpy(&df, m.dflops, sizeof(double), cudaMemcpyDeviceToHost);
         if (ms) ms[m.fam] += f;
         if (launches) launches[m.fam] += 1;
-        if (flops) flops[m.fam] += m.flops;
+        if (flops) flops[m.fam] += m.flops + df;
         if (bytes) bytes[m.fam] += m.bytes;
         pool_.push_back(m.a);
         pool_.push_back(m.b);
@@ -175,9 +183,11 @@ void Runner::flush_gemm(int precision_override) {
             }
             by += 8.0 * J.m * J.n * (J.beta != 0.0 ? 2.0 : 1.0);
         }
-        begin(0);
-        launch_gemm(dt, dj, dti, (int)tiles.size(), precision_override >= 0 ? precision_override : prec_, st_);
-        end(0, fl, by);
+        const int pr = precision_override >= 0 ? precision_override : prec_;
+        const int fam = (pr == H2_MIXED) ? 1 : 0;
+        begin(fam);
+        launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
+        end(fam, fl, by);
         ++launches;
     }
     terms_.clear();
@@ -204,9 +214,9 @@ void Runner::flush_qr() {
             fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p;
             by += 8.0 * m * n + 8.0 * p * n;
         }
-        begin(1);
+        begin(2);
         launch_qr32(d, (int)qrs32_.size(), st_);
-        end(1, fl, by);
+        end(2, fl, by);
         ++launches;
         qrs32_.clear();
     }
@@ -218,27 +228,30 @@ void Runner::flush_qr() {
         fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p + (j.Q ? 4.0 * m * j.q * p : 0.0);
         by += 8.0 * (2.0 * m * n + (j.R ? p * n : 0.0) + (j.Q ? m * j.q : 0.0));
     }
-    begin(1);
+    begin(2);
     launch_qr(d, (int)qrs_.size(), st_);
-    end(1, fl, by);
+    end(2, fl, by);
     ++launches;
     qrs_.clear();
 }
 
 void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps) {
     ensure_flag();
-    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, m, n, ldb, ldu, eps});
+    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, nullptr, m, n, ldb, ldu, eps});
     svd_maxn_ = std::max(svd_maxn_, n);
 }
 
 void Runner::flush_svd() {
     if (svds_.empty()) return;
+    double* cnt = dev_counter();
+    for (auto& j : svds_) j.flops = cnt;
     SVDJob* d = upload(svds_);
     double by = 0.0;
     for (auto& j : svds_) by += 8.0 * 3.0 * j.m * j.n;
-    begin(2);
+    begin(3);
     launch_svd(d, (int)svds_.size(), svd_maxn_, st_);
-    end(2, 0.0, by);
+    end(3, 0.0, by);
+    marks_.back().dflops = cnt;
     ++launches;
     svds_.clear();
     svd_maxn_ = 0;
@@ -247,19 +260,43 @@ void Runner::flush_svd() {
 void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64) {
     float* W = (float*)dalloc(((size_t)m * n + 1) / 2);
     float* V = (float*)dalloc(((size_t)n * n + 1) / 2);
-    pres_.push_back(PreJob{B, W, V, V64, m, n, ldb});
+    pres_.push_back(PreJob{B, W, V, V64, nullptr, m, n, ldb});
 }
 
 void Runner::flush_pre() {
     if (pres_.empty()) return;
+    double* cnt = dev_counter();
+    for (auto& j : pres_) j.flops = cnt;
     PreJob* d = upload(pres_);
     double by = 0.0;
     for (auto& j : pres_) by += 8.0 * ((double)j.m * j.n + (double)j.n * j.n);
-    begin(2);
+    begin(4);
     launch_jacobi_pre(d, (int)pres_.size(), st_);
-    end(2, 0.0, by);
+    end(4, 0.0, by);
+    marks_.back().dflops = cnt;
     ++launches;
     pres_.clear();
+}
+
+void Runner::pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol) {
+    if (k <= 0 || zrows <= 0) return;
+    if (k > 1024) throw Error(H2_ERR_UNSUPPORTED, "weight matrix larger than 1024");
+    chols_.push_back(CholJob{G, dalloc((size_t)k * k), Z, k, ldg, zrows, rel_tol});
+}
+
+void Runner::flush_pchol() {
+    if (chols_.empty()) return;
+    CholJob* d = upload(chols_);
+    double fl = 0.0, by = 0.0;
+    for (auto& j : chols_) {
+        fl += (double)j.k * j.k * j.k / 3.0;
+        by += 16.0 * j.k * j.k;
+    }
+    begin(2);
+    launch_pchol(d, (int)chols_.size(), st_);
+    end(2, fl, by);
+    ++launches;
+    chols_.clear();
 }
 
 void Runner::norm(const double* A, int m, int n, int lda, double* inv, double* nrm) {
@@ -275,9 +312,9 @@ void Runner::flush_norm() {
         by += 8.0 * j.m * j.n;
         fl += 4.0 * 61.0 * j.m * j.n;
     }
-    begin(3);
-    launch_norm(d, (int)norms_.size(), st_);
-    end(3, fl, by);
+    begin(5);
+    launch_norm(d, (int)norms_.size(), prec_, st_);
+    end(5, fl, by);
     ++launches;
     norms_.clear();
 }
@@ -293,9 +330,9 @@ void Runner::flush_copy() {
     CopyJob* d = upload(copies_);
     double by = 0.0;
     for (auto& j : copies_) by += 8.0 * j.rows * j.cols * (j.beta != 0.0 ? 3.0 : 2.0);
-    begin(4);
+    begin(6);
     launch_copy(d, (int)copies_.size(), st_);
-    end(4, 0.0, by);
+    end(6, 0.0, by);
     ++launches;
     copies_.clear();
 }
@@ -314,6 +351,7 @@ template GTile* Runner::upload<GTile>(const std::vector<GTile>&);
 template QRJob* Runner::upload<QRJob>(const std::vector<QRJob>&);
 template SVDJob* Runner::upload<SVDJob>(const std::vector<SVDJob>&);
 template PreJob* Runner::upload<PreJob>(const std::vector<PreJob>&);
+template CholJob* Runner::upload<CholJob>(const std::vector<CholJob>&);
 template NormJob* Runner::upload<NormJob>(const std::vector<NormJob>&);
 template CopyJob* Runner::upload<CopyJob>(const std::vector<CopyJob>&);
 template SumSqJob* Runner::upload<SumSqJob>(const std::vector<SumSqJob>&);

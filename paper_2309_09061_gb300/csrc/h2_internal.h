@@ -196,6 +196,7 @@ struct SVDJob {
     double* sigma;
     int* count;
     int* flag;
+    double* flops;  // optional accumulator: executed sweep flops (12 m per pair)
     int m, n, ldb, ldu;
     double eps;
 };
@@ -207,7 +208,19 @@ struct PreJob {
     float* W;
     float* V;
     double* V64;
+    double* flops;  // optional accumulator: executed sweep flops
     int m, n, ldb;
+};
+
+// Pivoted Cholesky of a symmetric positive semidefinite G (k x k, FP64): Z
+// (k x k, ld k) receives a factor with Z^* Z = G up to the pivots below
+// rel_tol * max(diag G), which are dropped (their rows of Z stay zero).
+struct CholJob {
+    const double* G;
+    double* W;  // workspace k x k
+    double* Z;  // zrows x k, ld zrows; at most zrows pivots are taken
+    int k, ldg, zrows;
+    double rel_tol;
 };
 
 // Spectral norm of A (m x n) by power iteration; writes 1/||A|| (0 if the norm
@@ -235,7 +248,8 @@ void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);
 void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st);
-void launch_norm(const NormJob* jobs, int njobs, cudaStream_t st);
+void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st);
+void launch_norm(const NormJob* jobs, int njobs, int precision, cudaStream_t st);
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);
 void launch_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
                         const double* lo, const double* hi, double* const* leafp, int first_leaf, int nleaves, int m,
@@ -256,7 +270,7 @@ struct SumSqJob {
 };
 void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st);
 // w[i] = 1 / sqrt(v[i]) (0 where v[i] == 0), i < n
-void launch_inv_sqrt(const double* v, double* w, int n, cudaStream_t st);
+void launch_inv_sqrt(const double* v, double* w, double* w2, int n, cudaStream_t st);
 
 // Host-side driver of batched ops: collects jobs, uploads, launches.
 class Runner {
@@ -278,6 +292,8 @@ public:
     void flush_svd();
     void jacobi_pre(const double* B, int m, int n, int ldb, double* V64);
     void flush_pre();
+    void pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol);
+    void flush_pchol();
     void norm(const double* A, int m, int n, int lda, double* inv, double* nrm);
     void flush_norm();
     void copy(const double* src, int lds, double* dst, int ldd, int rows, int cols, int trans, double alpha = 1.0,
@@ -306,6 +322,7 @@ private:
     std::vector<QRJob> qrs_;
     std::vector<SVDJob> svds_;
     std::vector<PreJob> pres_;
+    std::vector<CholJob> chols_;
     std::vector<QRJob> qrs32_;
     int svd_maxn_ = 0;
     std::vector<NormJob> norms_;
@@ -318,7 +335,9 @@ private:
         int fam;
         cudaEvent_t a, b;
         double flops, bytes;
+        double* dflops;  // device-side flop count of the launch, read at collect()
     };
+    double* dev_counter();
     std::vector<Mark> marks_;
     std::vector<cudaEvent_t> pool_;
     cudaEvent_t cur_ = nullptr;

@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
         __syncthreads();
     }
     if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
+    if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * m * (0.5 * n * (n - 1.0)) * sweep);
     for (int c = warp; c < n; c += nw) {
         const double* a = J.B + (size_t)c * J.ldb;
         double s = 0.0;
@@ -319,7 +320,8 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     const int np = n + (n & 1);
     const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
     bool converged = (n < 2);
-    for (int sweep = 0; sweep < PMAXSWEEP && !converged; ++sweep) {
+    int sweep = 0;
+    for (; sweep < PMAXSWEEP && !converged; ++sweep) {
         if (threadIdx.x == 0) rotated = 0;
         __syncthreads();
         for (int round = 0; round < np - 1; ++round) {
@@ -365,6 +367,7 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
         __syncthreads();
     }
     for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
+    if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
 }
 
 void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st) {
@@ -376,49 +379,161 @@ void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
     if (njobs > 0) k_svd<<<njobs, JT, 0, st>>>(jobs);
 }
 
+// ------------------------------------------------------------------ pivoted Cholesky
+// Symmetric pivoting on the largest remaining diagonal entry (Higham,
+// "Accuracy and Stability of Numerical Algorithms", Sec. 10.3), stopped when
+// the pivot falls below rel_tol times the largest initial diagonal entry.
+constexpr int CT = 256;
+constexpr int CMAXK = 1024;
+
+__global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) {
+    __shared__ int perm[CMAXK];
+    __shared__ double rv[CT / 32];
+    __shared__ int ri[CT / 32];
+    __shared__ int piv;
+    __shared__ double pval;
+    const CholJob J = jobs[blockIdx.x];
+    const int k = J.k;
+    double* W = J.W;
+    for (int e = threadIdx.x; e < k * k; e += CT) W[e] = J.G[(e % k) + (size_t)(e / k) * J.ldg];
+    for (int i = threadIdx.x; i < k; i += CT) perm[i] = i;
+    for (int e = threadIdx.x; e < J.zrows * k; e += CT) J.Z[e] = 0.0;
+    __syncthreads();
+    // largest initial diagonal entry
+    double md = 0.0;
+    for (int i = threadIdx.x; i < k; i += CT) md = fmax(md, W[i + (size_t)i * k]);
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+    if ((threadIdx.x & 31) == 0) rv[threadIdx.x >> 5] = md;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < CT / 32; ++w) m = fmax(m, rv[w]);
+        pval = m;
+    }
+    __syncthreads();
+    const double tol = J.rel_tol * pval;
+    const int jmax = J.zrows < k ? J.zrows : k;
+    int rank = jmax;
+    for (int j = 0; j < jmax; ++j) {
+        // pivot: argmax of the remaining diagonal (lowest index on ties)
+        double best = -1.0;
+        int bi = j;
+        for (int i = j + threadIdx.x; i < k; i += CT) {
+            double d = W[i + (size_t)i * k];
+            if (d > best) { best = d; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = rv[0];
+            int i0 = ri[0];
+            for (int w = 1; w < CT / 32; ++w)
+                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+            piv = i0;
+            pval = b;
+        }
+        __syncthreads();
+        if (!(pval > tol) || !(pval > 0.0)) {
+            rank = j;
+            break;
+        }
+        const int p = piv;
+        if (p != j) {  // symmetric swap of rows and columns j and p
+            for (int c = threadIdx.x; c < k; c += CT) {
+                double t = W[j + (size_t)c * k];
+                W[j + (size_t)c * k] = W[p + (size_t)c * k];
+                W[p + (size_t)c * k] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < k; r += CT) {
+                double t = W[r + (size_t)j * k];
+                W[r + (size_t)j * k] = W[r + (size_t)p * k];
+                W[r + (size_t)p * k] = t;
+            }
+            if (threadIdx.x == 0) {
+                int t = perm[j];
+                perm[j] = perm[p];
+                perm[p] = t;
+            }
+            __syncthreads();
+        }
+        const double d = sqrt(W[j + (size_t)j * k]);
+        const double inv = 1.0 / d;
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < k; i += CT) W[i + (size_t)j * k] *= inv;
+        if (threadIdx.x == 0) W[j + (size_t)j * k] = d;
+        __syncthreads();
+        // trailing update of the whole trailing square (kept symmetric for the swaps)
+        const int rem = k - j - 1;
+        for (int64_t e = threadIdx.x; e < (int64_t)rem * rem; e += CT) {
+            int i = j + 1 + (int)(e % rem), l = j + 1 + (int)(e / rem);
+            W[i + (size_t)l * k] -= W[i + (size_t)j * k] * W[l + (size_t)j * k];
+        }
+        __syncthreads();
+    }
+    // Z = L^* P^*: Z[j, perm[i]] = L[i, j] for i >= j, j < rank
+    for (int64_t e = threadIdx.x; e < (int64_t)k * rank; e += CT) {
+        int i = (int)(e % k), j = (int)(e / k);
+        if (i >= j) J.Z[j + (size_t)perm[i] * J.zrows] = W[i + (size_t)j * k];
+    }
+}
+
+void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_pchol<<<njobs, CT, 0, st>>>(jobs);
+}
+
 // ------------------------------------------------------------------ spectral norm
 // Power iteration x <- A^* A x with normalisation; returns ||A x|| for the
-// final unit vector (a lower bound that converges to ||A||_2).
+// final unit vector (a lower bound that converges to ||A||_2).  Stops when
+// the estimate changes by less than rtol (relative) or after NITER steps.
+// T = float in the mixed mode: the norm only scales a block.
 constexpr int NT = 128;
 constexpr int NMAX = 2048;
 constexpr int NITER = 60;
 
-__global__ void __launch_bounds__(NT) k_norm(const NormJob* __restrict__ jobs) {
-    __shared__ double x[NMAX];
-    __shared__ double y[NMAX];
+template <class T>
+__global__ void __launch_bounds__(NT) k_norm(const NormJob* __restrict__ jobs, T rtol) {
+    __shared__ T x[NMAX];
+    __shared__ T y[NMAX];
     __shared__ double red[NT / 32];
     const NormJob J = jobs[blockIdx.x];
     const int m = J.m, n = J.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double nx = 0.0;
     for (int j = threadIdx.x; j < n; j += NT) {
-        x[j] = 1.0 + 0.37 * (double)j / (double)(n > 0 ? n : 1);
-        nx += x[j] * x[j];
+        x[j] = (T)(1.0 + 0.37 * (double)j / (double)(n > 0 ? n : 1));
+        nx += (double)x[j] * x[j];
     }
     nx = block_sum<NT>(nx, red);
-    double sigma = 0.0;
+    double sigma = 0.0, prev = -1.0;
     for (int it = 0; it <= NITER && nx > 0.0; ++it) {
-        const double ix = 1.0 / sqrt(nx);
+        const T ix = (T)(1.0 / sqrt(nx));
         for (int j = threadIdx.x; j < n; j += NT) x[j] *= ix;
         __syncthreads();
         double ny = 0.0;
         for (int i = threadIdx.x; i < m; i += NT) {
-            double s = 0.0;
-            for (int j = 0; j < n; ++j) s += J.A[i + (size_t)j * J.lda] * x[j];
+            T s = 0;
+            for (int j = 0; j < n; ++j) s += (T)J.A[i + (size_t)j * J.lda] * x[j];
             y[i] = s;
-            ny += s * s;
+            ny += (double)s * s;
         }
         ny = block_sum<NT>(ny, red);
         sigma = sqrt(ny);
-        if (it == NITER || ny == 0.0) break;
+        if (it == NITER || ny == 0.0 || fabs(sigma - prev) <= (double)rtol * sigma) break;
+        prev = sigma;
         nx = 0.0;
         for (int j = warp; j < n; j += NT / 32) {
             const double* a = J.A + (size_t)j * J.lda;
-            double s = 0.0;
-            for (int i = lane; i < m; i += 32) s += a[i] * y[i];
-            s = warp_sum(s);
+            T s = 0;
+            for (int i = lane; i < m; i += 32) s += (T)a[i] * y[i];
+            s = warp_sum_t<T>(s);
             if (lane == 0) x[j] = s;
-            nx += (lane == 0) ? s * s : 0.0;
+            nx += (lane == 0) ? (double)s * s : 0.0;
         }
         nx = block_sum<NT>(nx, red);
     }
@@ -428,8 +543,12 @@ __global__ void __launch_bounds__(NT) k_norm(const NormJob* __restrict__ jobs) {
     }
 }
 
-void launch_norm(const NormJob* jobs, int njobs, cudaStream_t st) {
-    if (njobs > 0) k_norm<<<njobs, NT, 0, st>>>(jobs);
+void launch_norm(const NormJob* jobs, int njobs, int precision, cudaStream_t st) {
+    if (njobs <= 0) return;
+    if (precision == H2_MIXED)
+        k_norm<float><<<njobs, NT, 0, st>>>(jobs, 1e-5f);
+    else
+        k_norm<double><<<njobs, NT, 0, st>>>(jobs, 1e-10);
 }
 
 // ------------------------------------------------------------------ copies
@@ -610,13 +729,16 @@ void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st)
     if (njobs > 0) k_sumsq<<<njobs, 256, 0, st>>>(jobs, out);
 }
 
-__global__ void k_inv_sqrt(const double* v, double* w, int n) {
+__global__ void k_inv_sqrt(const double* v, double* w, double* w2, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) w[i] = v[i] > 0.0 ? 1.0 / sqrt(v[i]) : 0.0;
+    if (i < n) {
+        w[i] = v[i] > 0.0 ? 1.0 / sqrt(v[i]) : 0.0;
+        if (w2) w2[i] = v[i] > 0.0 ? 1.0 / v[i] : 0.0;
+    }
 }
 
-void launch_inv_sqrt(const double* v, double* w, int n, cudaStream_t st) {
-    if (n > 0) k_inv_sqrt<<<(int)ceil_div(n, 256), 256, 0, st>>>(v, w, n);
+void launch_inv_sqrt(const double* v, double* w, double* w2, int n, cudaStream_t st) {
+    if (n > 0) k_inv_sqrt<<<(int)ceil_div(n, 256), 256, 0, st>>>(v, w, w2, n);
 }
 
 // dense n x n matrix in tree order -> original order

@@ -238,6 +238,97 @@ static PerCl total_weights(Runner& R, const OpView& Y, const PerCl& RW) {
     return Z;
 }
 
+// ------------------------------------------------------------------ prep: total weights by Gram matrices
+// Only Z_s^* Z_s enters the method (every use of Z_s is through products whose
+// Gram matrices it weights), so the stacked QR of Fig. 2 can be replaced by
+// its Gram matrix, accumulated top-down,
+//   G_s = E_s G_{s+} E_s^* + sum_r S_sr (W_r^* W_r) S_sr^* / ||S_sr R_r^*||_2^2,
+// with ||S_sr R_r^*||_2^2 = lambda_max(S_sr W_r^* W_r S_sr^*), and factored by a
+// pivoted Cholesky (Z_s^* Z_s = G_s).  The Gram matrix resolves weights down
+// to about 1e-8 of the largest, so this route serves tolerances eps >= 1e-7.
+static constexpr double kGramMinEps = 1e-7;
+static constexpr double kCholTol = 1e-15;
+
+static PerCl total_weights_gram(Runner& R, const OpView& Y) {
+    const Tree& T = Y.tree();
+    const Basis& VY = Y.rowb();
+    const Basis& WY = Y.colb();
+    PerCl Wg = basis_products(R, T, WY, WY);  // W_r^* W_r
+    std::unordered_map<int, std::pair<double*, double*>> TS;  // block -> (Wg_r S_sr^*, 1 / lambda_max)
+    std::vector<int> adm;
+    for (int b = 0; b < (int)Y.bt().kind.size(); ++b) {
+        if (Y.kind(b) != ADM) continue;
+        adm.push_back(b);
+        int s = Y.T ? Y.bt().s[b] : Y.bt().t[b];
+        int r = Y.other(b);
+        int ks = VY.rank[s], kr = WY.rank[r];
+        double* t = R.dalloc((size_t)std::max(1, kr * ks));
+        R.job(t, kr, ks, std::max(1, kr), 0.0);
+        T_(R, mv(Wg.p[r], std::max(1, kr)), Y.S(b), kr, 1.0, nullptr, 0, 1);
+        TS[b] = {t, R.dalloc(1)};
+    }
+    R.flush_gemm(H2_FP64);
+    std::vector<double*> M(adm.size());
+    for (size_t i = 0; i < adm.size(); ++i) {
+        int b = adm[i];
+        int s = Y.T ? Y.bt().s[b] : Y.bt().t[b];
+        int r = Y.other(b);
+        int ks = VY.rank[s];
+        M[i] = R.dalloc((size_t)std::max(1, ks * ks));
+        R.job(M[i], ks, ks, std::max(1, ks), 0.0);
+        T_(R, Y.S(b), mv(TS[b].first, std::max(1, WY.rank[r])), WY.rank[r]);
+    }
+    R.flush_gemm(H2_FP64);
+    for (size_t i = 0; i < adm.size(); ++i) {
+        int b = adm[i];
+        int s = Y.T ? Y.bt().s[b] : Y.bt().t[b];
+        R.norm(M[i], VY.rank[s], VY.rank[s], std::max(1, VY.rank[s]), TS[b].second, nullptr);
+    }
+    R.flush_norm();
+    PerCl Z, G;
+    Z.init(T.nc);
+    G.init(T.nc);
+    for (int l = 0; l <= T.L; ++l) {
+        const int c0 = Tree::first(l), nl = Tree::count(l);
+        std::vector<double*> EG(nl, nullptr);
+        if (l > 0) {
+            for (int i = 0; i < nl; ++i) {
+                int s = c0 + i, p = Tree::parent(s);
+                EG[i] = R.dalloc((size_t)std::max(1, VY.rank[s] * VY.rank[p]));
+                R.job(EG[i], VY.rank[s], VY.rank[p], std::max(1, VY.rank[s]), 0.0);
+                R.term(VY.tr[s], 0, std::max(1, VY.rank[s]), G.p[p], 0, std::max(1, VY.rank[p]), VY.rank[p]);
+            }
+            R.flush_gemm(H2_FP64);
+        }
+        for (int i = 0; i < nl; ++i) {
+            int s = c0 + i, k = VY.rank[s];
+            int rows = (l > 0) ? Z.rows[Tree::parent(s)] : 0;
+            for (int b : Y.row_list(s))
+                if (Y.kind(b) == ADM) rows += std::min(WY.rank[Y.other(b)], (int)T.size[Y.other(b)]);
+            G.rows[s] = G.cols[s] = k;
+            G.p[s] = R.dalloc((size_t)std::max(1, k * k));
+            R.job(G.p[s], k, k, std::max(1, k), 0.0);
+            if (l > 0)
+                R.term(EG[i], 0, std::max(1, k), VY.tr[s], 1, std::max(1, k), VY.rank[Tree::parent(s)]);
+            for (int b : Y.row_list(s)) {
+                if (Y.kind(b) != ADM) continue;
+                int r = Y.other(b);
+                T_(R, Y.S(b), mv(TS[b].first, std::max(1, WY.rank[r])), WY.rank[r], 1.0, TS[b].second);
+            }
+            Z.rows[s] = std::min(rows, k);
+            Z.cols[s] = k;
+            Z.p[s] = R.dalloc((size_t)std::max(1, Z.rows[s] * k));
+        }
+        R.flush_gemm(H2_FP64);
+        for (int i = 0; i < nl; ++i) {
+            int s = c0 + i;
+            R.pchol(G.p[s], VY.rank[s], std::max(1, VY.rank[s]), Z.p[s], Z.rows[s], kCholTol);
+        }
+        R.flush_pchol();
+    }
+    return Z;
+}
+
 // ------------------------------------------------------------------ left singular vectors
 // Batched left singular vectors.  Each job gives Bt (ncol x m, ld ncol), the
 // transpose of the matrix whose left singular vectors are wanted.  Wide
@@ -355,8 +446,13 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
     const Basis& VX = X.rowb();
     const Basis& VY = Y.rowb();
     PerCl P = basis_products(R, T, X.colb(), VY);
-    PerCl RW = basis_weights(R, T, Y.colb());
-    PerCl Zt = total_weights(R, Y, RW);
+    PerCl Zt;
+    if (eps >= kGramMinEps) {
+        Zt = total_weights_gram(R, Y);
+    } else {
+        PerCl RW = basis_weights(R, T, Y.colb());
+        Zt = total_weights(R, Y, RW);
+    }
     Induced out;
     out.Q = std::make_shared<Basis>();
     Basis& Q = *out.Q;
@@ -879,7 +975,8 @@ static bool is_desc(int a, int d) {  // a is an ancestor of d (or equal)
     return d == a;
 }
 
-static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cmap, const double* w, double eps) {
+static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cmap, const double* w,
+                           const double* w2, double eps) {
     const Tree& T = *G.tree;
     const Basis& Q = G.rowb();
     const Basis& QW = G.colb();
@@ -893,7 +990,50 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
     // total weights of the product (Eq. Zt_condensation), top-down
     PerCl Zt;
     Zt.init(T.nc);
-    for (int l = 0; l <= T.L; ++l) {
+    if (eps >= kGramMinEps) {
+        // Gram form: G_t = E_t G_{t+} E_t^* + sum_r w_b^2 S_tr S_tr^*, Z_t by pivoted Cholesky
+        PerCl Gm;
+        Gm.init(T.nc);
+        for (int l = 0; l <= T.L; ++l) {
+            const int c0 = Tree::first(l), nl = Tree::count(l);
+            std::vector<double*> EG(nl, nullptr);
+            if (l > 0) {
+                for (int i = 0; i < nl; ++i) {
+                    int t = c0 + i, p = Tree::parent(t);
+                    EG[i] = R.dalloc((size_t)std::max(1, Q.rank[t] * Q.rank[p]));
+                    R.job(EG[i], Q.rank[t], Q.rank[p], std::max(1, Q.rank[t]), 0.0);
+                    R.term(Q.tr[t], 0, std::max(1, Q.rank[t]), Gm.p[p], 0, std::max(1, Q.rank[p]), Q.rank[p]);
+                }
+                R.flush_gemm(H2_FP64);
+            }
+            for (int i = 0; i < nl; ++i) {
+                int t = c0 + i, k = Q.rank[t];
+                int rows = (l > 0) ? Zt.rows[Tree::parent(t)] : 0;
+                Gm.p[t] = R.dalloc((size_t)std::max(1, k * k));
+                R.job(Gm.p[t], k, k, std::max(1, k), 0.0);
+                if (l > 0) R.term(EG[i], 0, std::max(1, k), Q.tr[t], 1, std::max(1, k), Q.rank[Tree::parent(t)]);
+                for (int n : G.row_list(t)) {
+                    if (G.kind(n) != ADM) continue;
+                    int r = G.other(n);
+                    if (cmap[n] < 0) throw Error(H2_ERR_UNSUPPORTED, "admissible T^XY leaf outside the target's admissible blocks");
+                    Mv c = G.C(n);
+                    R.term(c.p, c.tr, c.ld, c.p, c.tr ^ 1, c.ld, QW.rank[r], 1.0, w2 + cmap[n]);
+                    rows += QW.rank[r];
+                }
+                Zt.rows[t] = std::min(rows, k);
+                Zt.cols[t] = k;
+                Zt.p[t] = R.dalloc((size_t)std::max(1, Zt.rows[t] * k));
+                if (Zt.rows[t] == 0 || k == 0) Zt.rows[t] = 0;
+            }
+            R.flush_gemm(H2_FP64);
+            for (int i = 0; i < nl; ++i) {
+                int t = c0 + i;
+                if (Zt.rows[t] > 0) R.pchol(Gm.p[t], Q.rank[t], std::max(1, Q.rank[t]), Zt.p[t], Zt.rows[t], kCholTol);
+            }
+            R.flush_pchol();
+        }
+    }
+    for (int l = 0; l <= T.L && eps < kGramMinEps; ++l) {
         for (int t = Tree::first(l); t < Tree::first(l) + Tree::count(l); ++t) {
             int k = Q.rank[t];
             int rows = (t > 0) ? Zt.rows[Tree::parent(t)] : 0;
@@ -1318,6 +1458,7 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     // block weights 1 / ||G|_b||_F over the T^XY leaves of each admissible target block
     double* sq = R.dalloc(std::max<size_t>(Zb.kind.size(), 1));
     double* w = R.dalloc(std::max<size_t>(Zb.kind.size(), 1));
+    double* w2 = R.dalloc(std::max<size_t>(Zb.kind.size(), 1));
     H2_CUDA(cudaMemsetAsync(sq, 0, sizeof(double) * std::max<size_t>(Zb.kind.size(), 1), st));
     {
         std::vector<SumSqJob> jobs;
@@ -1330,16 +1471,16 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
                 jobs.push_back(SumSqJob{G.C[n], (int)T.size[t], (int)T.size[r], (int)T.size[t], cmap[n]});
         }
         SumSqJob* dj = R.upload(jobs);
-        R.begin(5);
+        R.begin(7);
         launch_sumsq(dj, (int)jobs.size(), sq, st);
-        launch_inv_sqrt(sq, w, (int)Zb.kind.size(), st);
-        R.end(5, 0.0, 0.0);
+        launch_inv_sqrt(sq, w, w2, (int)Zb.kind.size(), st);
+        R.end(7, 0.0, 0.0);
         R.launches += 2;
     }
     GView GR{&G, &T, false}, GC{&G, &T, true};
-    Coarse rb = coarsen_rows(R, GR, cmap, w, eps);
+    Coarse rb = coarsen_rows(R, GR, cmap, w, w2, eps);
     clk.mark();
-    Coarse cb = coarsen_rows(R, GC, cmap, w, eps);
+    Coarse cb = coarsen_rows(R, GC, cmap, w, w2, eps);
     clk.mark();
     std::vector<double*> Up = final_couplings(R, G, T, cmap, rb, cb, cnt);
     // assemble the result on Z's block tree in persistent memory
@@ -1377,9 +1518,9 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     }
     R.flush_copy();
     R.ensure_flag();
-    R.begin(5);
+    R.begin(7);
     launch_check_finite(chunk->p, chunk->len, R.svd_flag(), st);
-    R.end(5, 0.0, 8.0 * chunk->len);
+    R.end(7, 0.0, 8.0 * chunk->len);
     R.launches++;
     clk.mark();
     int flag = 0;
