@@ -191,6 +191,31 @@ H2_API int h2_clone(const h2_matrix* A, const h2_opts* opts, h2_matrix** out);
 H2_API int h2_plan_structure(const double* points, int64_t n, int leaf_size, double eta, int64_t* perm,
                              int64_t* counts);
 
+/* h2_to_dense without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while
+ * they run -- for example code inside a stream whose memory is managed by
+ * another allocator, or a real-time phase that forbids cudaMalloc/cudaFree --
+ * but still need the dense expansion of a handle.
+ * It writes the same result as h2_to_dense(A, out, ld, 1, ...): A expanded
+ * into the n x n device matrix `out` (original point order, column-major,
+ * ld >= n), issued on `stream` (a cudaStream_t, NULL for the legacy default
+ * stream) and finished before the call returns.
+ * Scratch: one fixed device array of 4 Mi doubles (32 MiB) in the library,
+ * held on every GPU that loads the library until the process exits.  The
+ * call needs n^2 + (the expanded cluster bases, about n x rank per level) +
+ * (n x rank per admissible block row) doubles to fit in 15/16 of it (the
+ * rest holds descriptor arrays); larger matrices are rejected with
+ * H2_ERR_UNSUPPORTED before any device work is issued.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * last call's contents (the call clears what must start at zero), so calls
+ * that overlap on the GPU -- from several threads or streams -- race and
+ * must be serialised by the caller.
+ * Errors: H2_ERR_ARG, H2_ERR_UNSUPPORTED (too large), H2_ERR_CUDA. */
+H2_API int h2_to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, void* stream);
+
 /* Release a handle and its device memory; NULL is ignored. */
 H2_API void h2_free(h2_matrix* A);
 

@@ -21,7 +21,7 @@ H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
 H2_FP64, H2_MIXED = 0, 1
 
 EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-            "h2_plan_structure", "h2_free", "h2_error_string", "h2_last_error_message"]
+            "h2_plan_structure", "h2_to_dense_noalloc", "h2_free", "h2_error_string", "h2_last_error_message"]
 
 
 class H2Error(RuntimeError):
@@ -84,13 +84,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_get_structure.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.h2_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     lib.h2_plan_structure.argtypes = [vp, i64, ci, cd, vp, vp]
+    lib.h2_to_dense_noalloc.argtypes = [vp, vp, i64, vp]
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
     lib.h2_error_string.argtypes = [ci]
     lib.h2_last_error_message.restype = ctypes.c_char_p
     for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-              "h2_plan_structure"):
+              "h2_plan_structure", "h2_to_dense_noalloc"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -191,6 +192,16 @@ def h2_plan_structure(points: np.ndarray, leaf_size: int, eta: float):
     _check(load().h2_plan_structure(pts.ctypes.data, pts.shape[0], leaf_size, eta, perm.ctypes.data,
                                     counts.ctypes.data), "h2_plan_structure")
     return perm, counts
+
+
+def h2_to_dense_noalloc(A: H2Matrix, out, stream: int | None = None):
+    """Dense expansion into the CUDA tensor ``out`` (n x n float64, column-major
+    view of its storage) without device allocation: the library's fixed
+    32 MiB scratch holds all intermediates.  Calls must not overlap."""
+    n = A.info()["n"]
+    _check(load().h2_to_dense_noalloc(A.handle, out.data_ptr(), n, ctypes.c_void_p(stream or 0)),
+           "h2_to_dense_noalloc")
+    return out
 
 
 def h2_free(A: H2Matrix) -> None:

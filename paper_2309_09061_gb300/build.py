@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libh2mul.so")
-SOURCES = ["h2_plan.cpp", "h2_core.cu", "h2_kernels.cu", "h2_mul.cu"]
+SOURCES = ["h2_plan.cpp", "h2_core.cu", "h2_kernels.cu", "h2_mul.cu", "h2_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler",
          "-fvisibility=hidden"]
