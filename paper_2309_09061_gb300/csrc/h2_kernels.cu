@@ -3,6 +3,8 @@
 // Batched small dense linear algebra: every launch covers all clusters or all
 // blocks of one tree level at once.  Each batched kernel reads a device array
 // of job descriptors built by the host executor.
+#include <cooperative_groups.h>
+
 #include <cfloat>
 #include <cmath>
 
@@ -370,121 +372,207 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
 }
 
-void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st) {
-    if (njobs > 0) k_jacobi_pre<<<njobs, JT, 0, st>>>(jobs);
+
+
+// ------------------------------------------------------------------ clustered Jacobi
+// The same sweeps with one matrix shared by a thread-block cluster: the
+// disjoint pairs of a round are spread over the cluster's CTAs (one CTA per
+// SM), a cluster barrier separates rounds, columns move through L2
+// (ld/st.cg), and the rotation flag of a sweep is OR-ed across the cluster
+// through distributed shared memory.  Used when a level has fewer matrices
+// than SMs.  T = double: SVDJob (FP64 sweeps + singular vectors); T = float:
+// PreJob (FP32 preconditioning with accumulated rotations).
+namespace cg = cooperative_groups;
+
+__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tsign(float x) { return copysignf(1.f, x); }
+__device__ __forceinline__ double tsign(double x) { return copysign(1.0, x); }
+
+template <class T>
+__device__ __forceinline__ void rot_pair(T* ap, T* aq, int m, T c, T s, int lane) {
+    for (int i = lane; i < m; i += 32) {
+        T x = __ldcg(ap + i), y = __ldcg(aq + i);
+        __stcg(ap + i, c * x - s * y);
+        __stcg(aq + i, s * x + c * y);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(JT) k_jacobi_cluster(const SVDJob* __restrict__ sjobs,
+                                                       const PreJob* __restrict__ pjobs) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
+    const int job = blockIdx.x / cs;
+    __shared__ int rotated;
+    __shared__ double sig[JMAXN];
+    constexpr bool PRE = sizeof(T) == 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
+    int m, n;
+    T* B;
+    T* V = nullptr;
+    if constexpr (PRE) {
+        const PreJob& J = pjobs[job];
+        m = J.m;
+        n = J.n;
+        B = (T*)J.W;
+        V = (T*)J.V;
+        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)m * n; e += (int64_t)JT * cs)
+            __stcg(B + e, (T)J.B[(e % m) + (size_t)(e / m) * J.ldb]);
+        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
+            __stcg(V + e, ((e % n) == (e / n)) ? (T)1 : (T)0);
+    } else {
+        const SVDJob& J = sjobs[job];
+        m = J.m;
+        n = J.n;
+        B = (T*)J.B;
+    }
+    const int ldb = PRE ? m : (int)sjobs[job].ldb;
+    cl.sync();
+    const int np = n + (n & 1);
+    const T tol = (T)(m > 1 ? m : 1) * (PRE ? (T)FLT_EPSILON : (T)DBL_EPSILON);
+    const int maxsweep = PRE ? PMAXSWEEP : JMAXSWEEP;
+    bool converged = (n < 2);
+    int sweep = 0;
+    for (; sweep < maxsweep && !converged; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        cl.sync();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int pr = cr * nw + warp; pr < np / 2; pr += nw * cs) {
+                int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
+                if (p >= n || q >= n) continue;
+                if (p > q) { int t = p; p = q; q = t; }
+                T* ap = B + (size_t)p * ldb;
+                T* aq = B + (size_t)q * ldb;
+                T al = 0, be = 0, ga = 0;
+                for (int i = lane; i < m; i += 32) {
+                    T x = __ldcg(ap + i), y = __ldcg(aq + i);
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                al = warp_sum_t<T>(al);
+                be = warp_sum_t<T>(be);
+                ga = warp_sum_t<T>(ga);
+                if (ga != (T)0 && al > (T)0 && be > (T)0 && tabs(ga) > tol * tsqrt(al) * tsqrt(be)) {
+                    T zeta = (be - al) / ((T)2 * ga);
+                    const T big = PRE ? (T)1e18 : (T)1e150;
+                    T t = (tabs(zeta) > big) ? (T)0.5 / zeta : tsign(zeta) / (tabs(zeta) + tsqrt((T)1 + zeta * zeta));
+                    T c = (T)1 / tsqrt((T)1 + t * t), s = c * t;
+                    rot_pair<T>(ap, aq, m, c, s, lane);
+                    if (PRE) rot_pair<T>(V + (size_t)p * n, V + (size_t)q * n, n, c, s, lane);
+                    if (lane == 0) rotated = 1;
+                }
+            }
+            cl.sync();
+        }
+        int any = 0;
+        for (int r = 0; r < cs; ++r) any |= *cl.map_shared_rank(&rotated, r);
+        converged = (any == 0);
+        cl.sync();
+    }
+    if constexpr (PRE) {
+        const PreJob& J = pjobs[job];
+        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
+            J.V64[e] = (double)__ldcg(V + e);
+        if (cr == 0 && threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
+        return;
+    } else {
+        const SVDJob& J = sjobs[job];
+        if (cr != 0) return;
+        if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
+        if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * m * (0.5 * n * (n - 1.0)) * sweep);
+        for (int c = warp; c < n; c += nw) {
+            const T* a = B + (size_t)c * ldb;
+            double s = 0.0;
+            for (int i = lane; i < m; i += 32) {
+                double v = (double)__ldcg(a + i);
+                s += v * v;
+            }
+            s = warp_sum(s);
+            if (lane == 0) sig[c] = sqrt(s);
+        }
+        __syncthreads();
+        for (int c = warp; c < n; c += nw) {
+            const double sc = sig[c];
+            int pos = 0;
+            for (int q = 0; q < n; ++q) pos += (sig[q] > sc) || (sig[q] == sc && q < c);
+            const T* a = B + (size_t)c * ldb;
+            double* u = J.U + (size_t)pos * J.ldu;
+            const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+            for (int i = lane; i < m; i += 32) u[i] = (double)__ldcg(a + i) * inv;
+            if (lane == 0) J.sigma[pos] = sc;
+        }
+        if (threadIdx.x == 0) {
+            int cnt = 0;
+            for (int q = 0; q < n; ++q) cnt += (sig[q] > J.eps);
+            *J.count = cnt;
+        }
+    }
+}
+
+static int num_sms() {
+    static int sms[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 1;
+    if (!sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        sms[dev] = v > 0 ? v : 1;
+    }
+    return sms[dev];
+}
+
+// cluster size for njobs matrices: the largest power of two <= 8 that keeps
+// njobs * size within the SM count (1 = plain kernel)
+static int jacobi_cluster_size(int njobs) {
+    int sms = num_sms(), cs = 1;
+    while (cs < 8 && njobs * cs * 2 <= sms) cs *= 2;
+    return cs;
+}
+
+// one CTA per SM: request enough dynamic shared memory that two do not fit
+constexpr int kClusterDynSmem = 120 * 1024;
+
+// returns false (and clears the error) when the cluster launch is refused
+template <class T>
+static bool launch_jacobi_cluster(const SVDJob* sj, const PreJob* pj, int njobs, int cs, cudaStream_t st) {
+    auto kern = k_jacobi_cluster<T>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterDynSmem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(njobs * cs, 1, 1);
+    cfg.blockDim = dim3(JT, 1, 1);
+    cfg.dynamicSmemBytes = kClusterDynSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, sj, pj);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
 }
 
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
     if (max_n > JMAXN) throw Error(H2_ERR_UNSUPPORTED, "SVD wider than 2048 columns");
-    if (njobs > 0) k_svd<<<njobs, JT, 0, st>>>(jobs);
+    if (njobs <= 0) return;
+    int cs = jacobi_cluster_size(njobs);
+    if (cs <= 1 || !launch_jacobi_cluster<double>(jobs, nullptr, njobs, cs, st)) k_svd<<<njobs, JT, 0, st>>>(jobs);
 }
 
-// ------------------------------------------------------------------ pivoted Cholesky
-// Symmetric pivoting on the largest remaining diagonal entry (Higham,
-// "Accuracy and Stability of Numerical Algorithms", Sec. 10.3), stopped when
-// the pivot falls below rel_tol times the largest initial diagonal entry.
-constexpr int CT = 256;
-constexpr int CMAXK = 1024;
-
-__global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) {
-    __shared__ int perm[CMAXK];
-    __shared__ double rv[CT / 32];
-    __shared__ int ri[CT / 32];
-    __shared__ int piv;
-    __shared__ double pval;
-    const CholJob J = jobs[blockIdx.x];
-    const int k = J.k;
-    double* W = J.W;
-    for (int e = threadIdx.x; e < k * k; e += CT) W[e] = J.G[(e % k) + (size_t)(e / k) * J.ldg];
-    for (int i = threadIdx.x; i < k; i += CT) perm[i] = i;
-    for (int e = threadIdx.x; e < J.zrows * k; e += CT) J.Z[e] = 0.0;
-    __syncthreads();
-    // largest initial diagonal entry
-    double md = 0.0;
-    for (int i = threadIdx.x; i < k; i += CT) md = fmax(md, W[i + (size_t)i * k]);
-    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
-    if ((threadIdx.x & 31) == 0) rv[threadIdx.x >> 5] = md;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < CT / 32; ++w) m = fmax(m, rv[w]);
-        pval = m;
-    }
-    __syncthreads();
-    const double tol = J.rel_tol * pval;
-    const int jmax = J.zrows < k ? J.zrows : k;
-    int rank = jmax;
-    for (int j = 0; j < jmax; ++j) {
-        // pivot: argmax of the remaining diagonal (lowest index on ties)
-        double best = -1.0;
-        int bi = j;
-        for (int i = j + threadIdx.x; i < k; i += CT) {
-            double d = W[i + (size_t)i * k];
-            if (d > best) { best = d; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double b = rv[0];
-            int i0 = ri[0];
-            for (int w = 1; w < CT / 32; ++w)
-                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
-            piv = i0;
-            pval = b;
-        }
-        __syncthreads();
-        if (!(pval > tol) || !(pval > 0.0)) {
-            rank = j;
-            break;
-        }
-        const int p = piv;
-        if (p != j) {  // symmetric swap of rows and columns j and p
-            for (int c = threadIdx.x; c < k; c += CT) {
-                double t = W[j + (size_t)c * k];
-                W[j + (size_t)c * k] = W[p + (size_t)c * k];
-                W[p + (size_t)c * k] = t;
-            }
-            __syncthreads();
-            for (int r = threadIdx.x; r < k; r += CT) {
-                double t = W[r + (size_t)j * k];
-                W[r + (size_t)j * k] = W[r + (size_t)p * k];
-                W[r + (size_t)p * k] = t;
-            }
-            if (threadIdx.x == 0) {
-                int t = perm[j];
-                perm[j] = perm[p];
-                perm[p] = t;
-            }
-            __syncthreads();
-        }
-        const double d = sqrt(W[j + (size_t)j * k]);
-        const double inv = 1.0 / d;
-        __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += CT) W[i + (size_t)j * k] *= inv;
-        if (threadIdx.x == 0) W[j + (size_t)j * k] = d;
-        __syncthreads();
-        // trailing update of the whole trailing square (kept symmetric for the swaps)
-        const int rem = k - j - 1;
-        for (int64_t e = threadIdx.x; e < (int64_t)rem * rem; e += CT) {
-            int i = j + 1 + (int)(e % rem), l = j + 1 + (int)(e / rem);
-            W[i + (size_t)l * k] -= W[i + (size_t)j * k] * W[l + (size_t)j * k];
-        }
-        __syncthreads();
-    }
-    // Z = L^* P^*: Z[j, perm[i]] = L[i, j] for i >= j, j < rank
-    for (int64_t e = threadIdx.x; e < (int64_t)k * rank; e += CT) {
-        int i = (int)(e % k), j = (int)(e / k);
-        if (i >= j) J.Z[j + (size_t)perm[i] * J.zrows] = W[i + (size_t)j * k];
-    }
-}
-
-void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st) {
-    if (njobs > 0) k_pchol<<<njobs, CT, 0, st>>>(jobs);
+void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs <= 0) return;
+    int cs = jacobi_cluster_size(njobs);
+    if (cs <= 1 || !launch_jacobi_cluster<float>(nullptr, jobs, njobs, cs, st)) k_jacobi_pre<<<njobs, JT, 0, st>>>(jobs);
 }
 
 // ------------------------------------------------------------------ spectral norm
