@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
             return LIB
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(_compile, SOURCES))
-    cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", LIB + ".tmp", *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -575,6 +575,114 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st) {
     if (cs <= 1 || !launch_jacobi_cluster<float>(nullptr, jobs, njobs, cs, st)) k_jacobi_pre<<<njobs, JT, 0, st>>>(jobs);
 }
 
+// ------------------------------------------------------------------ pivoted Cholesky
+// Symmetric pivoting on the largest remaining diagonal entry (Higham,
+// "Accuracy and Stability of Numerical Algorithms", Sec. 10.3), stopped when
+// the pivot falls below rel_tol times the largest initial diagonal entry.
+constexpr int CT = 256;
+constexpr int CMAXK = 1024;
+
+__global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) {
+    __shared__ int perm[CMAXK];
+    __shared__ double rv[CT / 32];
+    __shared__ int ri[CT / 32];
+    __shared__ int piv;
+    __shared__ double pval;
+    const CholJob J = jobs[blockIdx.x];
+    const int k = J.k;
+    double* W = J.W;
+    for (int e = threadIdx.x; e < k * k; e += CT) W[e] = J.G[(e % k) + (size_t)(e / k) * J.ldg];
+    for (int i = threadIdx.x; i < k; i += CT) perm[i] = i;
+    for (int e = threadIdx.x; e < J.zrows * k; e += CT) J.Z[e] = 0.0;
+    __syncthreads();
+    // largest initial diagonal entry
+    double md = 0.0;
+    for (int i = threadIdx.x; i < k; i += CT) md = fmax(md, W[i + (size_t)i * k]);
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+    if ((threadIdx.x & 31) == 0) rv[threadIdx.x >> 5] = md;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < CT / 32; ++w) m = fmax(m, rv[w]);
+        pval = m;
+    }
+    __syncthreads();
+    const double tol = J.rel_tol * pval;
+    const int jmax = J.zrows < k ? J.zrows : k;
+    int rank = jmax;
+    for (int j = 0; j < jmax; ++j) {
+        // pivot: argmax of the remaining diagonal (lowest index on ties)
+        double best = -1.0;
+        int bi = j;
+        for (int i = j + threadIdx.x; i < k; i += CT) {
+            double d = W[i + (size_t)i * k];
+            if (d > best) { best = d; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = rv[0];
+            int i0 = ri[0];
+            for (int w = 1; w < CT / 32; ++w)
+                if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+            piv = i0;
+            pval = b;
+        }
+        __syncthreads();
+        if (!(pval > tol) || !(pval > 0.0)) {
+            rank = j;
+            break;
+        }
+        const int p = piv;
+        if (p != j) {  // symmetric swap of rows and columns j and p
+            for (int c = threadIdx.x; c < k; c += CT) {
+                double t = W[j + (size_t)c * k];
+                W[j + (size_t)c * k] = W[p + (size_t)c * k];
+                W[p + (size_t)c * k] = t;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < k; r += CT) {
+                double t = W[r + (size_t)j * k];
+                W[r + (size_t)j * k] = W[r + (size_t)p * k];
+                W[r + (size_t)p * k] = t;
+            }
+            if (threadIdx.x == 0) {
+                int t = perm[j];
+                perm[j] = perm[p];
+                perm[p] = t;
+            }
+            __syncthreads();
+        }
+        const double d = sqrt(W[j + (size_t)j * k]);
+        const double inv = 1.0 / d;
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < k; i += CT) W[i + (size_t)j * k] *= inv;
+        if (threadIdx.x == 0) W[j + (size_t)j * k] = d;
+        __syncthreads();
+        // trailing update of the whole trailing square (kept symmetric for the swaps)
+        const int rem = k - j - 1;
+        for (int64_t e = threadIdx.x; e < (int64_t)rem * rem; e += CT) {
+            int i = j + 1 + (int)(e % rem), l = j + 1 + (int)(e / rem);
+            W[i + (size_t)l * k] -= W[i + (size_t)j * k] * W[l + (size_t)j * k];
+        }
+        __syncthreads();
+    }
+    // Z = L^* P^*: Z[j, perm[i]] = L[i, j] for i >= j, j < rank
+    for (int64_t e = threadIdx.x; e < (int64_t)k * rank; e += CT) {
+        int i = (int)(e % k), j = (int)(e / k);
+        if (i >= j) J.Z[j + (size_t)perm[i] * J.zrows] = W[i + (size_t)j * k];
+    }
+}
+
+void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st) {
+    if (njobs > 0) k_pchol<<<njobs, CT, 0, st>>>(jobs);
+}
+
 // ------------------------------------------------------------------ spectral norm
 // Power iteration x <- A^* A x with normalisation; returns ||A x|| for the
 // final unit vector (a lower bound that converges to ||A||_2).  Stops when
