@@ -240,10 +240,17 @@ __global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
     const int np = n + (n & 1);
     const double tol = (double)(m > 1 ? m : 1) * DBL_EPSILON;
+    // a sweep whose rotation measures all stay below skip = 0.1 sqrt(tol) leaves an
+    // off-diagonality below tol (quadratic convergence): the verifying sweep is skipped
+    const double skip = 0.1 * sqrt(tol);
+    __shared__ int large;
     int sweep = 0;
     bool converged = (n < 2);
     for (; sweep < JMAXSWEEP && !converged; ++sweep) {
-        if (threadIdx.x == 0) rotated = 0;
+        if (threadIdx.x == 0) {
+            rotated = 0;
+            large = 0;
+        }
         __syncthreads();
         for (int round = 0; round < np - 1; ++round) {
             for (int pr = warp; pr < np / 2; pr += nw) {
@@ -272,12 +279,15 @@ __global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
                         ap[i] = c * x - s * y;
                         aq[i] = s * x + c * y;
                     }
-                    if (lane == 0) rotated = 1;
+                    if (lane == 0) {
+                        rotated = 1;
+                        if (fabs(ga) > skip * sqrt(al) * sqrt(be)) large = 1;
+                    }
                 }
             }
             __syncthreads();
         }
-        converged = (rotated == 0);
+        converged = (rotated == 0) || (large == 0);
         __syncthreads();
     }
     if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
@@ -321,10 +331,15 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     __syncthreads();
     const int np = n + (n & 1);
     const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
+    const float skip = 0.1f * sqrtf(tol);
+    __shared__ int large;
     bool converged = (n < 2);
     int sweep = 0;
     for (; sweep < PMAXSWEEP && !converged; ++sweep) {
-        if (threadIdx.x == 0) rotated = 0;
+        if (threadIdx.x == 0) {
+            rotated = 0;
+            large = 0;
+        }
         __syncthreads();
         for (int round = 0; round < np - 1; ++round) {
             for (int pr = warp; pr < np / 2; pr += nw) {
@@ -360,12 +375,15 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
                         vp[i] = c * x - s * y;
                         vq[i] = s * x + c * y;
                     }
-                    if (lane == 0) rotated = 1;
+                    if (lane == 0) {
+                        rotated = 1;
+                        if (fabsf(ga) > skip * sqrtf(al) * sqrtf(be)) large = 1;
+                    }
                 }
             }
             __syncthreads();
         }
-        converged = (rotated == 0);
+        converged = (rotated == 0) || (large == 0);
         __syncthreads();
     }
     for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
@@ -434,10 +452,15 @@ __global__ void __launch_bounds__(JT) k_jacobi_cluster(const SVDJob* __restrict_
     const int np = n + (n & 1);
     const T tol = (T)(m > 1 ? m : 1) * (PRE ? (T)FLT_EPSILON : (T)DBL_EPSILON);
     const int maxsweep = PRE ? PMAXSWEEP : JMAXSWEEP;
+    const T skip = (T)0.1 * tsqrt(tol);
+    __shared__ int large;
     bool converged = (n < 2);
     int sweep = 0;
     for (; sweep < maxsweep && !converged; ++sweep) {
-        if (threadIdx.x == 0) rotated = 0;
+        if (threadIdx.x == 0) {
+            rotated = 0;
+            large = 0;
+        }
         cl.sync();
         for (int round = 0; round < np - 1; ++round) {
             for (int pr = cr * nw + warp; pr < np / 2; pr += nw * cs) {
@@ -463,14 +486,20 @@ __global__ void __launch_bounds__(JT) k_jacobi_cluster(const SVDJob* __restrict_
                     T c = (T)1 / tsqrt((T)1 + t * t), s = c * t;
                     rot_pair<T>(ap, aq, m, c, s, lane);
                     if (PRE) rot_pair<T>(V + (size_t)p * n, V + (size_t)q * n, n, c, s, lane);
-                    if (lane == 0) rotated = 1;
+                    if (lane == 0) {
+                        rotated = 1;
+                        if (tabs(ga) > skip * tsqrt(al) * tsqrt(be)) large = 1;
+                    }
                 }
             }
             cl.sync();
         }
-        int any = 0;
-        for (int r = 0; r < cs; ++r) any |= *cl.map_shared_rank(&rotated, r);
-        converged = (any == 0);
+        int any = 0, anylarge = 0;
+        for (int r = 0; r < cs; ++r) {
+            any |= *cl.map_shared_rank(&rotated, r);
+            anylarge |= *cl.map_shared_rank(&large, r);
+        }
+        converged = (any == 0) || (anylarge == 0);
         cl.sync();
     }
     if constexpr (PRE) {
