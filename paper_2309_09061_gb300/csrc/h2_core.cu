@@ -63,7 +63,7 @@ cudaEvent_t Runner::get_event() {
 }
 
 double* Runner::dev_counter() {
-    double* c = dalloc(1);
+    double* c = palloc(1);
     H2_CUDA(cudaMemsetAsync(c, 0, sizeof(double), st_));
     return c;
 }
@@ -97,9 +97,9 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
     marks_.clear();
 }
 
-// Scratch of one call: bump allocation (256-byte aligned) from chunks of the
-// library's stream-ordered pool; everything is returned by release_all().
-double* Runner::dalloc(size_t n) {
+// Bump allocation (256-byte aligned) from chunks of the library's
+// stream-ordered pool.
+double* Arena::alloc(size_t n) {
     if (n == 0) n = 1;
     size_t bytes = (n * sizeof(double) + 255) & ~(size_t)255;
 #ifdef H2_EXACT_ALLOC
@@ -107,20 +107,36 @@ double* Runner::dalloc(size_t n) {
 #else
     const size_t chunk_min = (size_t)64 << 20;
 #endif
-    if (bytes > cur_left_) {
+    if (bytes > left_) {
         size_t sz = std::max(bytes, chunk_min);
         int dev = 0;
         H2_CUDA(cudaGetDevice(&dev));
         void* p = nullptr;
         H2_CUDA(cudaMallocFromPoolAsync(&p, sz, lib_pool(dev), st_));
-        owned_.push_back(p);
-        cur_chunk_ = (char*)p;
-        cur_left_ = sz;
+        chunks_.push_back(p);
+        cur_ = (char*)p;
+        left_ = sz;
     }
-    double* out = (double*)cur_chunk_;
-    cur_chunk_ += bytes;
-    cur_left_ -= bytes;
+    double* out = (double*)cur_;
+    cur_ += bytes;
+    left_ -= bytes;
     return out;
+}
+
+void Arena::release(const Mark& m) {
+    while (chunks_.size() > m.nchunks) {
+        cudaFreeAsync(chunks_.back(), st_);
+        chunks_.pop_back();
+    }
+    cur_ = m.cur;
+    left_ = m.left;
+}
+
+void Arena::release_all() {
+    for (void* p : chunks_) cudaFreeAsync(p, st_);
+    chunks_.clear();
+    cur_ = nullptr;
+    left_ = 0;
 }
 
 template <class T>
@@ -136,16 +152,14 @@ template double* Runner::upload<double>(const std::vector<double>&);
 template double** Runner::upload<double*>(const std::vector<double*>&);
 
 void Runner::release_all() {
-    for (void* p : owned_) cudaFreeAsync(p, st_);
-    owned_.clear();
-    cur_chunk_ = nullptr;
-    cur_left_ = 0;
+    scratch_.release_all();
+    persist_.release_all();
     d_flag_ = nullptr;
 }
 
 void Runner::ensure_flag() {
     if (!d_flag_) {
-        d_flag_ = (int*)dalloc(1);
+        d_flag_ = (int*)palloc(1);
         H2_CUDA(cudaMemsetAsync(d_flag_, 0, sizeof(int), st_));
     }
 }

@@ -272,10 +272,36 @@ void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st)
 // w[i] = 1 / sqrt(v[i]) (0 where v[i] == 0), i < n
 void launch_inv_sqrt(const double* v, double* w, double* w2, int n, cudaStream_t st);
 
+// Stream-ordered bump allocator over chunks of the library's memory pool.
+// mark()/release() return everything allocated after a mark (stream order
+// makes the reuse safe: later work on the stream runs after earlier work).
+class Arena {
+public:
+    explicit Arena(cudaStream_t st) : st_(st) {}
+    ~Arena() { release_all(); }
+    Arena(const Arena&) = delete;
+    Arena& operator=(const Arena&) = delete;
+    double* alloc(size_t n);
+    struct Mark {
+        size_t nchunks;
+        char* cur;
+        size_t left;
+    };
+    Mark mark() const { return Mark{chunks_.size(), cur_, left_}; }
+    void release(const Mark& m);
+    void release_all();
+
+private:
+    cudaStream_t st_;
+    std::vector<void*> chunks_;
+    char* cur_ = nullptr;
+    size_t left_ = 0;
+};
+
 // Host-side driver of batched ops: collects jobs, uploads, launches.
 class Runner {
 public:
-    explicit Runner(cudaStream_t st, int precision) : st_(st), prec_(precision) {}
+    explicit Runner(cudaStream_t st, int precision) : st_(st), prec_(precision), scratch_(st), persist_(st) {}
     ~Runner();
     cudaStream_t stream() const { return st_; }
     int precision() const { return prec_; }
@@ -309,10 +335,14 @@ public:
     void collect(double* ms, int64_t* launches, double* flops, double* bytes);
 
     // device scratch from the stream-ordered pool
-    double* dalloc(size_t n);
+    double* dalloc(size_t n) { return scratch_.alloc(n); }
+    // device memory that lives until the end of the call (release_all)
+    double* palloc(size_t n) { return persist_.alloc(n); }
+    Arena::Mark mark() const { return scratch_.mark(); }
+    void release(const Arena::Mark& m) { scratch_.release(m); }
     template <class T>
     T* upload(const std::vector<T>& v);
-    void release_all();  // frees every dalloc/upload of this runner (stream ordered)
+    void release_all();  // frees every allocation of this runner (stream ordered)
 
 private:
     cudaStream_t st_;
@@ -327,9 +357,8 @@ private:
     int svd_maxn_ = 0;
     std::vector<NormJob> norms_;
     std::vector<CopyJob> copies_;
-    std::vector<void*> owned_;       // pool chunks
-    char* cur_chunk_ = nullptr;      // bump pointer into the last chunk
-    size_t cur_left_ = 0;
+    Arena scratch_;
+    Arena persist_;
     int* d_flag_ = nullptr;
     struct Mark {
         int fam;

@@ -253,6 +253,7 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
     const Tree& T = Y.tree();
     const Basis& VY = Y.rowb();
     const Basis& WY = Y.colb();
+    const Arena::Mark mk = R.mark();  // everything but Z is scratch of this function
     PerCl Wg = basis_products(R, T, WY, WY);  // W_r^* W_r
     std::unordered_map<int, std::pair<double*, double*>> TS;  // block -> (Wg_r S_sr^*, 1 / lambda_max)
     std::vector<int> adm;
@@ -317,7 +318,7 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
             }
             Z.rows[s] = std::min(rows, k);
             Z.cols[s] = k;
-            Z.p[s] = R.dalloc((size_t)std::max(1, Z.rows[s] * k));
+            Z.p[s] = R.palloc((size_t)std::max(1, Z.rows[s] * k));
         }
         R.flush_gemm(H2_FP64);
         for (int i = 0; i < nl; ++i) {
@@ -326,6 +327,7 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
         }
         R.flush_pchol();
     }
+    R.release(mk);
     return Z;
 }
 
@@ -445,6 +447,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
     const Tree& T = X.tree();
     const Basis& VX = X.rowb();
     const Basis& VY = Y.rowb();
+    const Arena::Mark mk0 = R.mark();  // scratch of this phase; A and Rbar are persistent
     PerCl P = basis_products(R, T, X.colb(), VY);
     PerCl Zt;
     if (eps >= kGramMinEps) {
@@ -461,6 +464,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
     Q.tr.assign(T.nc, nullptr);
     out.Rbar.init(T.nc);
     for (int l = T.L; l >= 0; --l) {
+        const Arena::Mark mkl = R.mark();  // scratch of this level
         const int c0 = Tree::first(l), nl = Tree::count(l);
         const bool leaf = (l == T.L);
         std::vector<int> rows(nl), k1(nl), m2(nl);
@@ -648,7 +652,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             // A_ts = Q-hat^* M_ts,  Rbar_t = Q-hat^* VX-hat
             for (int b : C[i]) {
                 int s = X.other(b);
-                double* a = R.dalloc((size_t)std::max(1, kt * VY.rank[s]));
+                double* a = R.palloc((size_t)std::max(1, kt * VY.rank[s]));
                 R.job(a, kt, VY.rank[s], std::max(1, kt), 0.0);
                 R.term(Qh[i], 1, rows[i], M[b], 0, std::max(1, rows[i]), rows[i]);
                 out.A[b] = a;
@@ -656,13 +660,15 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             }
             out.Rbar.rows[t] = kt;
             out.Rbar.cols[t] = VX.rank[t];
-            out.Rbar.p[t] = R.dalloc((size_t)std::max(1, kt * VX.rank[t]));
+            out.Rbar.p[t] = R.palloc((size_t)std::max(1, kt * VX.rank[t]));
             R.job(out.Rbar.p[t], kt, VX.rank[t], std::max(1, kt), 0.0);
             R.term(Qh[i], 1, rows[i], VXh[i], 0, std::max(1, rows[i]), rows[i]);
         }
         R.flush_copy();
         R.flush_gemm();
+        R.release(mkl);
     }
+    R.release(mk0);
     return out;
 }
 
@@ -693,207 +699,237 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
     const OpView ZV{Z, false};
+    const Arena::Mark mk0 = R.mark();
     PerCl P = basis_products(R, T, WX, VY);
-    // PSY_sr = P_s S_Y,sr for admissible Y blocks
-    std::unordered_map<int, double*> PSY;
-    for (int b = 0; b < (int)Y.bt().kind.size(); ++b) {
-        if (Y.kind(b) != ADM) continue;
-        int s = Y.bt().t[b], r = Y.bt().s[b];
-        double* m = R.dalloc((size_t)WX.rank[s] * WY.rank[r]);
-        R.job(m, WX.rank[s], WY.rank[r], WX.rank[s], 0.0);
-        T_(R, mv(P.p[s], std::max(1, P.rows[s])), Y.S(b), VY.rank[s]);
-        PSY[b] = m;
-        cnt.flops += 2.0 * WX.rank[s] * WY.rank[r] * VY.rank[s];
-    }
-    R.flush_gemm();
-    // U1 (all nodes): S_Z copied first, then += sum of S_X PSY
-    std::vector<double*> U1(nn, nullptr);
-    {
+    // nodes by level (same-level pairs: the level of (t,r) is the level of t)
+    std::vector<std::vector<int>> lv(T.L + 1);
+    for (int n = 0; n < nn; ++n) lv[Tree::level(N.t[n])].push_back(n);
+    G.C.assign(nn, nullptr);
+    // couplings pushed down from the ancestors live in two alternating arenas
+    Arena pp0(R.stream()), pp1(R.stream());
+    Arena* pp[2] = {&pp0, &pp1};
+    std::vector<double*> Cup(nn, nullptr);
+    auto alloc_cup = [&](int l) {
         size_t tot = 0;
-        for (int n = 0; n < nn; ++n) tot += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
-        double* base = R.dalloc(std::max<size_t>(tot, 1));
+        for (int n : lv[l]) tot += (size_t)std::max(1, Q.rank[N.t[n]] * QW.rank[N.s[n]]);
+        double* base = pp[l & 1]->alloc(std::max<size_t>(tot, 1));
         H2_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * std::max<size_t>(tot, 1), R.stream()));
         size_t o = 0;
-        for (int n = 0; n < nn; ++n) {
-            U1[n] = base + o;
-            o += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
-        }
-    }
-    for (int n = 0; n < nn; ++n) {
-        int t = N.t[n], r = N.s[n];
-        int bz = Z->st->blocks.find(t, r);
-        if (bz >= 0 && Z->st->blocks.kind[bz] == ADM)
-            R.copy(ZV.S(bz).p, ZV.S(bz).ld, U1[n], VX.rank[t], VX.rank[t], WY.rank[r], 0);
-    }
-    R.flush_copy();
-    for (int n = 0; n < nn; ++n) {
-        int t = N.t[n], r = N.s[n];
-        R.job(U1[n], VX.rank[t], WY.rank[r], VX.rank[t], 1.0);
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) == ADM && Y.kind(by) == ADM) {
-                T_(R, X.S(bx), mv(PSY[by], WX.rank[s]), WX.rank[s]);
-                cnt.flops += 2.0 * VX.rank[t] * WY.rank[r] * WX.rank[s];
-            }
-            cnt.triples++;
-        }
-    }
-    R.flush_gemm();
-    // U2, U3 for coupling nodes
-    std::vector<double*> U2(nn, nullptr), U3(nn, nullptr);
-    for (int n = 0; n < nn; ++n) {
-        if (N.kind[n] == DENSE) continue;
-        int t = N.t[n], r = N.s[n];
-        U2[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * WY.rank[r]));
-        R.job(U2[n], Q.rank[t], WY.rank[r], std::max(1, Q.rank[t]), 0.0);
-        R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U1[n], 0, VX.rank[t], VX.rank[t]);
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) != ADM && Y.kind(by) == ADM) {
-                T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
-                cnt.flops += 2.0 * Q.rank[t] * WY.rank[r] * VY.rank[s];
-            }
-        }
-        U3[n] = R.dalloc((size_t)std::max(1, VX.rank[t] * QW.rank[r]));
-        R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) == ADM && Y.kind(by) != ADM) {
-                T_(R, X.S(bx), mvT(ca.A.at(by), std::max(1, QW.rank[r])), WX.rank[s]);
-                cnt.flops += 2.0 * VX.rank[t] * QW.rank[r] * WX.rank[s];
-            }
-        }
-    }
-    R.flush_gemm();
-    G.C.assign(nn, nullptr);
-    std::vector<double*> Cup(nn, nullptr);
-    {
-        size_t tot = 0;
-        for (int n = 0; n < nn; ++n) tot += (size_t)std::max(1, Q.rank[N.t[n]] * QW.rank[N.s[n]]);
-        double* base = R.dalloc(tot);
-        H2_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * tot, R.stream()));
-        size_t o = 0;
-        for (int n = 0; n < nn; ++n) {
+        for (int n : lv[l]) {
             Cup[n] = base + o;
             o += (size_t)std::max(1, Q.rank[N.t[n]] * QW.rank[N.s[n]]);
         }
-    }
-    for (int n = 0; n < nn; ++n) {
-        int t = N.t[n], r = N.s[n];
-        size_t cs = (size_t)std::max(1, Q.rank[t] * QW.rank[r]);
-        if (N.kind[n] == DENSE) continue;
-        G.C[n] = R.dalloc(cs);
-        R.job(G.C[n], Q.rank[t], QW.rank[r], std::max(1, Q.rank[t]), 0.0);
-        R.term(U2[n], 0, std::max(1, Q.rank[t]), ca.Rbar.p[r], 1, std::max(1, QW.rank[r]), WY.rank[r]);
-        R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U3[n], 0, VX.rank[t], VX.rank[t]);
-        cnt.flops += 2.0 * Q.rank[t] * QW.rank[r] * (WY.rank[r] + VX.rank[t]);
-    }
-    R.flush_gemm();
-    // push down: Cup_child = E_a (C + Cup) F_b^*
-    for (int l = 0; l < T.L; ++l) {
-        std::vector<std::pair<int, double*>> tmp;  // (child node, C F_b^*)
-        for (int n = 0; n < nn; ++n) {
-            if (N.kind[n] != SPLIT || Tree::level(N.t[n]) != l) continue;
+    };
+    alloc_cup(0);
+    // nodes of a level are processed in chunks that bound the scratch
+#ifndef H2_TMAT_CHUNK
+#define H2_TMAT_CHUNK 16384
+#endif
+    constexpr size_t kChunkNodes = H2_TMAT_CHUNK;
+    for (int l = 0; l <= T.L; ++l) {
+      if (l < T.L) alloc_cup(l + 1);
+      for (size_t ch0 = 0; ch0 < lv[l].size(); ch0 += kChunkNodes) {
+        const Arena::Mark mkl = R.mark();
+        const std::vector<int> nodes(lv[l].begin() + ch0,
+                                     lv[l].begin() + std::min(lv[l].size(), ch0 + kChunkNodes));
+        // PSY_sr = P_s S_Y,sr for the admissible Y blocks met at this level
+        std::unordered_map<int, double*> PSY;
+        for (int n : nodes) {
             int t = N.t[n], r = N.s[n];
-            for (int j = 0; j < 2; ++j) {
-                int b = Tree::child(r, j);
-                double* m = R.dalloc((size_t)std::max(1, Q.rank[t] * QW.rank[b]));
-                R.job(m, Q.rank[t], QW.rank[b], std::max(1, Q.rank[t]), 0.0);
-                R.term(G.C[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
-                R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
-                for (int i = 0; i < 2; ++i) tmp.push_back({N.find(Tree::child(t, i), b), m});
+            for (int s : G.PT->triples[n]) {
+                int bx = X.block(t, s), by = Y.block(s, r);
+                if (X.kind(bx) != ADM || Y.kind(by) != ADM || PSY.count(by)) continue;
+                double* m = R.dalloc((size_t)WX.rank[s] * WY.rank[r]);
+                R.job(m, WX.rank[s], WY.rank[r], WX.rank[s], 0.0);
+                T_(R, mv(P.p[s], std::max(1, P.rows[s])), Y.S(by), VY.rank[s]);
+                PSY[by] = m;
+                cnt.flops += 2.0 * WX.rank[s] * WY.rank[r] * VY.rank[s];
             }
         }
         R.flush_gemm();
-        for (auto& [c, m] : tmp) {
-            int a = N.t[c], b = N.s[c], t = Tree::parent(a);
-            R.job(Cup[c], Q.rank[a], QW.rank[b], std::max(1, Q.rank[a]), 0.0);
-            R.term(Q.tr[a], 0, std::max(1, Q.rank[a]), m, 0, std::max(1, Q.rank[t]), Q.rank[t]);
-            cnt.flops += 2.0 * Q.rank[a] * QW.rank[b] * Q.rank[t];
+        // U1 = S_Z (copied first) + sum_a S_X PSY
+        std::unordered_map<int, double*> U1;
+        {
+            size_t tot = 0;
+            for (int n : nodes) tot += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
+            double* base = R.dalloc(std::max<size_t>(tot, 1));
+            H2_CUDA(cudaMemsetAsync(base, 0, sizeof(double) * std::max<size_t>(tot, 1), R.stream()));
+            size_t o = 0;
+            for (int n : nodes) {
+                U1[n] = base + o;
+                o += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
+            }
+        }
+        for (int n : nodes) {
+            int t = N.t[n], r = N.s[n];
+            int bz = Z->st->blocks.find(t, r);
+            if (bz >= 0 && Z->st->blocks.kind[bz] == ADM)
+                R.copy(ZV.S(bz).p, ZV.S(bz).ld, U1[n], VX.rank[t], VX.rank[t], WY.rank[r], 0);
+        }
+        R.flush_copy();
+        for (int n : nodes) {
+            int t = N.t[n], r = N.s[n];
+            R.job(U1[n], VX.rank[t], WY.rank[r], VX.rank[t], 1.0);
+            for (int s : G.PT->triples[n]) {
+                int bx = X.block(t, s), by = Y.block(s, r);
+                if (X.kind(bx) == ADM && Y.kind(by) == ADM) {
+                    T_(R, X.S(bx), mv(PSY[by], WX.rank[s]), WX.rank[s]);
+                    cnt.flops += 2.0 * VX.rank[t] * WY.rank[r] * WX.rank[s];
+                }
+                cnt.triples++;
+            }
         }
         R.flush_gemm();
-    }
-    // admissible leaves: final coupling C + Cup
-    for (int n = 0; n < nn; ++n) {
-        if (N.kind[n] != ADM) continue;
-        int t = N.t[n], r = N.s[n];
-        R.copy(Cup[n], std::max(1, Q.rank[t]), G.C[n], std::max(1, Q.rank[t]), Q.rank[t], QW.rank[r], 0, 1.0, nullptr,
-               1.0);
-    }
-    R.flush_copy();
-    // dense leaves, exact: sum N N + L1 W_Y^* + V_X R1 + N_Z + Q (Cup QW^*)
-    std::unordered_map<int, double*> XV, WN;
-    std::vector<double*> L1(nn, nullptr), R1(nn, nullptr), CQ(nn, nullptr);
-    for (int n = 0; n < nn; ++n) {
-        if (N.kind[n] != DENSE) continue;
-        int t = N.t[n], r = N.s[n];
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.count(bx)) {
-                double* m = R.dalloc((size_t)T.size[t] * VY.rank[s]);
-                R.job(m, (int)T.size[t], VY.rank[s], (int)T.size[t], 0.0);
-                T_(R, X.N(bx), mv(VY.leaf[s], (int)T.size[s]), (int)T.size[s]);
-                XV[bx] = m;
+        // U2 = Rbar U1 + sum_b A S_Y,  U3 = sum_c S_X B^*  (coupling nodes)
+        std::unordered_map<int, double*> U2, U3;
+        for (int n : nodes) {
+            if (N.kind[n] == DENSE) continue;
+            int t = N.t[n], r = N.s[n];
+            U2[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * WY.rank[r]));
+            R.job(U2[n], Q.rank[t], WY.rank[r], std::max(1, Q.rank[t]), 0.0);
+            R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U1[n], 0, VX.rank[t], VX.rank[t]);
+            for (int s : G.PT->triples[n]) {
+                int bx = X.block(t, s), by = Y.block(s, r);
+                if (X.kind(bx) != ADM && Y.kind(by) == ADM) {
+                    T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
+                    cnt.flops += 2.0 * Q.rank[t] * WY.rank[r] * VY.rank[s];
+                }
             }
-            if (X.kind(bx) == ADM && Y.kind(by) == DENSE && !WN.count(by)) {
-                double* m = R.dalloc((size_t)WX.rank[s] * T.size[r]);
-                R.job(m, WX.rank[s], (int)T.size[r], WX.rank[s], 0.0);
-                T_(R, mvT(WX.leaf[s], (int)T.size[s]), Y.N(by), (int)T.size[s]);
-                WN[by] = m;
+            U3[n] = R.dalloc((size_t)std::max(1, VX.rank[t] * QW.rank[r]));
+            R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
+            for (int s : G.PT->triples[n]) {
+                int bx = X.block(t, s), by = Y.block(s, r);
+                if (X.kind(bx) == ADM && Y.kind(by) != ADM) {
+                    T_(R, X.S(bx), mvT(ca.A.at(by), std::max(1, QW.rank[r])), WX.rank[s]);
+                    cnt.flops += 2.0 * VX.rank[t] * QW.rank[r] * WX.rank[s];
+                }
             }
         }
-        CQ[n] = R.dalloc((size_t)std::max(1, Q.rank[t]) * T.size[r]);
-        R.job(CQ[n], Q.rank[t], (int)T.size[r], std::max(1, Q.rank[t]), 0.0);
-        R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.leaf[r], 1, (int)T.size[r], QW.rank[r]);
-    }
-    R.flush_gemm();
-    for (int n = 0; n < nn; ++n) {
-        if (N.kind[n] != DENSE) continue;
-        int t = N.t[n], r = N.s[n];
-        L1[n] = R.dalloc((size_t)T.size[t] * WY.rank[r]);
-        R.job(L1[n], (int)T.size[t], WY.rank[r], (int)T.size[t], 0.0);
-        R.term(VX.leaf[t], 0, (int)T.size[t], U1[n], 0, VX.rank[t], VX.rank[t]);
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) == DENSE && Y.kind(by) == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
+        R.flush_gemm();
+        // C = U2 RbarW^* + Rbar U3 (persistent for admissible leaves, scratch for split nodes)
+        for (int n : nodes) {
+            if (N.kind[n] == DENSE) continue;
+            int t = N.t[n], r = N.s[n];
+            size_t cs = (size_t)std::max(1, Q.rank[t] * QW.rank[r]);
+            G.C[n] = (N.kind[n] == ADM) ? R.palloc(cs) : R.dalloc(cs);
+            R.job(G.C[n], Q.rank[t], QW.rank[r], std::max(1, Q.rank[t]), 0.0);
+            R.term(U2[n], 0, std::max(1, Q.rank[t]), ca.Rbar.p[r], 1, std::max(1, QW.rank[r]), WY.rank[r]);
+            R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U3[n], 0, VX.rank[t], VX.rank[t]);
+            cnt.flops += 2.0 * Q.rank[t] * QW.rank[r] * (WY.rank[r] + VX.rank[t]);
         }
-        R1[n] = R.dalloc((size_t)VX.rank[t] * T.size[r]);
-        R.job(R1[n], VX.rank[t], (int)T.size[r], VX.rank[t], 0.0);
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) == ADM && Y.kind(by) == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
-        }
-    }
-    R.flush_gemm();
-    for (int n = 0; n < nn; ++n) {
-        if (N.kind[n] != DENSE) continue;
-        int t = N.t[n], r = N.s[n];
-        int mt = (int)T.size[t], mr = (int)T.size[r];
-        G.C[n] = R.dalloc((size_t)mt * mr);
-        int bz = Z->st->blocks.find(t, r);
-        bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
-        if (zd) R.copy(ZV.N(bz).p, ZV.N(bz).ld, G.C[n], mt, mt, mr, 0);
-    }
-    R.flush_copy();
-    for (int n = 0; n < nn; ++n) {
-        if (N.kind[n] != DENSE) continue;
-        int t = N.t[n], r = N.s[n];
-        int mt = (int)T.size[t], mr = (int)T.size[r];
-        int bz = Z->st->blocks.find(t, r);
-        bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
-        R.job(G.C[n], mt, mr, mt, zd ? 1.0 : 0.0);
-        for (int s : G.PT->triples[n]) {
-            int bx = X.block(t, s), by = Y.block(s, r);
-            if (X.kind(bx) == DENSE && Y.kind(by) == DENSE) {
-                T_(R, X.N(bx), Y.N(by), (int)T.size[s]);
-                cnt.flops += 2.0 * mt * mr * T.size[s];
+        R.flush_gemm();
+        // push down to the next level: Cup_child = E_a (C + Cup) F_b^*
+        if (l < T.L) {
+            std::vector<std::pair<int, double*>> tmp;
+            for (int n : nodes) {
+                if (N.kind[n] != SPLIT) continue;
+                int t = N.t[n], r = N.s[n];
+                for (int j = 0; j < 2; ++j) {
+                    int b = Tree::child(r, j);
+                    double* m = R.dalloc((size_t)std::max(1, Q.rank[t] * QW.rank[b]));
+                    R.job(m, Q.rank[t], QW.rank[b], std::max(1, Q.rank[t]), 0.0);
+                    R.term(G.C[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
+                    R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
+                    for (int i = 0; i < 2; ++i) tmp.push_back({N.find(Tree::child(t, i), b), m});
+                }
             }
+            R.flush_gemm();
+            for (auto& [c, m] : tmp) {
+                int a = N.t[c], b = N.s[c], t = Tree::parent(a);
+                R.job(Cup[c], Q.rank[a], QW.rank[b], std::max(1, Q.rank[a]), 0.0);
+                R.term(Q.tr[a], 0, std::max(1, Q.rank[a]), m, 0, std::max(1, Q.rank[t]), Q.rank[t]);
+                cnt.flops += 2.0 * Q.rank[a] * QW.rank[b] * Q.rank[t];
+            }
+            R.flush_gemm();
         }
-        R.term(L1[n], 0, mt, WY.leaf[r], 1, mr, WY.rank[r]);
-        R.term(VX.leaf[t], 0, mt, R1[n], 0, VX.rank[t], VX.rank[t]);
-        R.term(Q.leaf[t], 0, mt, CQ[n], 0, std::max(1, Q.rank[t]), Q.rank[t]);
+        // admissible leaves: final coupling C + Cup
+        for (int n : nodes) {
+            if (N.kind[n] != ADM) continue;
+            int t = N.t[n], r = N.s[n];
+            R.copy(Cup[n], std::max(1, Q.rank[t]), G.C[n], std::max(1, Q.rank[t]), Q.rank[t], QW.rank[r], 0, 1.0,
+                   nullptr, 1.0);
+        }
+        R.flush_copy();
+        // dense leaves, exact: sum N N + L1 W_Y^* + V_X R1 + N_Z + Q (Cup QW^*)
+        bool any_dense = false;
+        for (int n : nodes) any_dense |= (N.kind[n] == DENSE);
+        if (any_dense) {
+            std::unordered_map<int, double*> XV, WN, L1, R1, CQ;
+            for (int n : nodes) {
+                if (N.kind[n] != DENSE) continue;
+                int t = N.t[n], r = N.s[n];
+                for (int s : G.PT->triples[n]) {
+                    int bx = X.block(t, s), by = Y.block(s, r);
+                    if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.count(bx)) {
+                        double* m = R.dalloc((size_t)T.size[t] * VY.rank[s]);
+                        R.job(m, (int)T.size[t], VY.rank[s], (int)T.size[t], 0.0);
+                        T_(R, X.N(bx), mv(VY.leaf[s], (int)T.size[s]), (int)T.size[s]);
+                        XV[bx] = m;
+                    }
+                    if (X.kind(bx) == ADM && Y.kind(by) == DENSE && !WN.count(by)) {
+                        double* m = R.dalloc((size_t)WX.rank[s] * T.size[r]);
+                        R.job(m, WX.rank[s], (int)T.size[r], WX.rank[s], 0.0);
+                        T_(R, mvT(WX.leaf[s], (int)T.size[s]), Y.N(by), (int)T.size[s]);
+                        WN[by] = m;
+                    }
+                }
+                CQ[n] = R.dalloc((size_t)std::max(1, Q.rank[t]) * T.size[r]);
+                R.job(CQ[n], Q.rank[t], (int)T.size[r], std::max(1, Q.rank[t]), 0.0);
+                R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.leaf[r], 1, (int)T.size[r], QW.rank[r]);
+            }
+            R.flush_gemm();
+            for (int n : nodes) {
+                if (N.kind[n] != DENSE) continue;
+                int t = N.t[n], r = N.s[n];
+                L1[n] = R.dalloc((size_t)T.size[t] * WY.rank[r]);
+                R.job(L1[n], (int)T.size[t], WY.rank[r], (int)T.size[t], 0.0);
+                R.term(VX.leaf[t], 0, (int)T.size[t], U1[n], 0, VX.rank[t], VX.rank[t]);
+                for (int s : G.PT->triples[n]) {
+                    int bx = X.block(t, s), by = Y.block(s, r);
+                    if (X.kind(bx) == DENSE && Y.kind(by) == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
+                }
+                R1[n] = R.dalloc((size_t)VX.rank[t] * T.size[r]);
+                R.job(R1[n], VX.rank[t], (int)T.size[r], VX.rank[t], 0.0);
+                for (int s : G.PT->triples[n]) {
+                    int bx = X.block(t, s), by = Y.block(s, r);
+                    if (X.kind(bx) == ADM && Y.kind(by) == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
+                }
+            }
+            R.flush_gemm();
+            for (int n : nodes) {
+                if (N.kind[n] != DENSE) continue;
+                int t = N.t[n], r = N.s[n];
+                int mt = (int)T.size[t], mr = (int)T.size[r];
+                G.C[n] = R.palloc((size_t)mt * mr);
+                int bz = Z->st->blocks.find(t, r);
+                if (bz >= 0 && Z->st->blocks.kind[bz] == DENSE) R.copy(ZV.N(bz).p, ZV.N(bz).ld, G.C[n], mt, mt, mr, 0);
+            }
+            R.flush_copy();
+            for (int n : nodes) {
+                if (N.kind[n] != DENSE) continue;
+                int t = N.t[n], r = N.s[n];
+                int mt = (int)T.size[t], mr = (int)T.size[r];
+                int bz = Z->st->blocks.find(t, r);
+                bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
+                R.job(G.C[n], mt, mr, mt, zd ? 1.0 : 0.0);
+                for (int s : G.PT->triples[n]) {
+                    int bx = X.block(t, s), by = Y.block(s, r);
+                    if (X.kind(bx) == DENSE && Y.kind(by) == DENSE) {
+                        T_(R, X.N(bx), Y.N(by), (int)T.size[s]);
+                        cnt.flops += 2.0 * mt * mr * T.size[s];
+                    }
+                }
+                R.term(L1[n], 0, mt, WY.leaf[r], 1, mr, WY.rank[r]);
+                R.term(VX.leaf[t], 0, mt, R1[n], 0, VX.rank[t], VX.rank[t]);
+                R.term(Q.leaf[t], 0, mt, CQ[n], 0, std::max(1, Q.rank[t]), Q.rank[t]);
+            }
+            R.flush_gemm();
+        }
+        R.release(mkl);
+      }
+      pp[l & 1]->release_all();  // this level's pushed-down couplings are consumed
     }
-    R.flush_gemm();
+    R.release(mk0);
 }
 
 // ------------------------------------------------------------------ coarsening (Fig. 7, Fig. 6)
@@ -980,6 +1016,9 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
     const Tree& T = *G.tree;
     const Basis& Q = G.rowb();
     const Basis& QW = G.colb();
+    const Arena::Mark mk0 = R.mark();
+    Arena pp0(R.stream()), pp1(R.stream());  // representations of two consecutive levels
+    Arena* pp[2] = {&pp0, &pp1};
     Coarse out;
     out.Qn = std::make_shared<Basis>();
     Basis& Qn = *out.Qn;
@@ -1072,6 +1111,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
     }
     std::unordered_map<int, Rep> A;  // node -> representation
     for (int l = T.L; l >= 0; --l) {
+        const Arena::Mark mkl = R.mark();
         const int c0 = Tree::first(l), nl = Tree::count(l);
         const bool leaf = (l == T.L);
         std::vector<int> rows(nl);
@@ -1253,10 +1293,10 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                     o += Qn.rank[a];
                 }
             }
-            // keep a copy of the basis block for the projections below
+            // basis change R_t = Q'^* V, kept for the level above and the final couplings
             out.Rt.rows[t] = kt;
             out.Rt.cols[t] = Q.rank[t];
-            out.Rt.p[t] = R.dalloc((size_t)std::max(1, kt * Q.rank[t]));
+            out.Rt.p[t] = R.palloc((size_t)std::max(1, kt * Q.rank[t]));
         }
         R.flush_copy();
         for (int i = 0; i < nl; ++i) {
@@ -1282,7 +1322,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                 if (leaf) {
                     int r = G.other(n);
                     rep.leaves.push_back(Rep::Leaf{r, false, 0, (int)T.size[r]});
-                    rep.p = R.dalloc((size_t)rep.ld * T.size[r]);
+                    rep.p = pp[l & 1]->alloc((size_t)rep.ld * T.size[r]);
                     R.job(rep.p, kt, (int)T.size[r], rep.ld, 0.0);
                     if (kt > 0) T_(R, mvT(U, ldu), G.D(n), rows[i]);
                 } else {
@@ -1290,7 +1330,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                     rep.leaves = ah.leaves;
                     int cols = 0;
                     for (auto& lf : ah.leaves) cols += lf.width;
-                    rep.p = R.dalloc((size_t)rep.ld * std::max(1, cols));
+                    rep.p = pp[l & 1]->alloc((size_t)rep.ld * std::max(1, cols));
                     R.job(rep.p, kt, cols, rep.ld, 0.0);
                     if (kt > 0) R.term(U, 1, ldu, ah.p, 0, ah.ld, rows[i]);
                 }
@@ -1298,7 +1338,15 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             }
         }
         R.flush_gemm();
+        // the representations of the level below are consumed
+        if (l < T.L) {
+            for (int c = Tree::first(l + 1); c < Tree::first(l + 1) + Tree::count(l + 1); ++c)
+                for (int n : G.row_list(c)) A.erase(n);
+            pp[(l + 1) & 1]->release_all();
+        }
+        R.release(mkl);
     }
+    R.release(mk0);
     return out;
 }
 
@@ -1309,7 +1357,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
 //   split node: sum over children E'_a^* Up_ab F'_b.
 static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, const Tree& T,
                                             const std::vector<int>& cmap, const Coarse& rb, const Coarse& cb,
-                                            Counts& cnt) {
+                                            const BlockTree& Zb, Counts& cnt) {
     const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
     const Basis& Qn = *rb.Qn;
@@ -1317,7 +1365,10 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
     const Basis& Q = *G.Q;
     const Basis& QW = *G.QW;
     std::vector<double*> Up(nn, nullptr);
+    Arena pp0(R.stream()), pp1(R.stream());  // Up of two consecutive levels
+    Arena* pp[2] = {&pp0, &pp1};
     for (int l = T.L; l >= 0; --l) {
+        const Arena::Mark mkl = R.mark();
         std::vector<int> lv;
         for (int n = 0; n < nn; ++n)
             if (cmap[n] >= 0 && Tree::level(N.t[n]) == l) lv.push_back(n);
@@ -1354,7 +1405,9 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
         for (int n : lv) {
             int t = N.t[n], r = N.s[n];
             int kt = Qn.rank[t], kr = Wn.rank[r];
-            Up[n] = R.dalloc((size_t)std::max(1, kt * kr));
+            // the couplings of the target blocks themselves outlive this function
+            const bool root = (Zb.find(t, r) == cmap[n]);
+            Up[n] = root ? R.palloc((size_t)std::max(1, kt * kr)) : pp[l & 1]->alloc((size_t)std::max(1, kt * kr));
             R.job(Up[n], kt, kr, std::max(1, kt), 0.0);
             if (N.kind[n] == ADM) {
                 R.term(m1[n], 0, std::max(1, kt), cb.Rt.p[r], 1, std::max(1, kr), QW.rank[r]);
@@ -1373,6 +1426,8 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
             }
         }
         R.flush_gemm();
+        if (l < T.L) pp[(l + 1) & 1]->release_all();
+        R.release(mkl);
     }
     return Up;
 }
@@ -1482,7 +1537,7 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     clk.mark();
     Coarse cb = coarsen_rows(R, GC, cmap, w, w2, eps);
     clk.mark();
-    std::vector<double*> Up = final_couplings(R, G, T, cmap, rb, cb, cnt);
+    std::vector<double*> Up = final_couplings(R, G, T, cmap, rb, cb, Zb, cnt);
     // assemble the result on Z's block tree in persistent memory
     auto res = std::make_unique<h2_matrix>();
     res->st = Zm->st;
