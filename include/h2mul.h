@@ -162,6 +162,15 @@ H2_API int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, cons
  * Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
 H2_API int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, const h2_opts* opts);
 
+/* y = A x (trans = 0) or y = A^* x (trans = 1) for nvec vectors: x and y are
+ * device arrays of n x nvec doubles, column-major with leading dimension n,
+ * rows in the ORIGINAL point order; x is read, y overwritten (no aliasing).
+ * Forward transformation through the column basis, couplings, backward
+ * transformation through the row basis and dense blocks (the O(nk)
+ * H^2-matrix-vector product the paper relies on, Sec. 2).  Row i of A is
+ * A^* e_i.  Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
+H2_API int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t nvec, int trans, const h2_opts* opts);
+
 /* Sizes and structure of a handle.  Errors: H2_ERR_ARG. */
 H2_API int h2_info(const h2_matrix* A, h2_info_t* info);
 

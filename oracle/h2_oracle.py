@@ -278,6 +278,57 @@ class H2Matrix:
                         {(s, t): m.T for (t, s), m in self.S.items()},
                         {(s, t): m.T for (t, s), m in self.N.items()})
 
+    def matvec(self, x: np.ndarray, trans: bool = False) -> np.ndarray:
+        """G x (or G^* x) for x in the original point order (n x nv), by the
+        forward transformation x_s = W_s^* x|_s (leaves directly, parents
+        through the transfer matrices), the couplings y_t = sum_s S_ts x_s, the
+        backward transformation and the dense blocks (Sec. 2: O(nk) work)."""
+        A = self.transpose() if trans else self
+        x = np.asarray(x, dtype=np.float64)
+        one = x.ndim == 1
+        X = x[:, None] if one else x
+        rt, ct = A.rows, A.cols
+        xt = X[ct.perm]
+        xh = {}
+
+        def fwd(s):
+            if ct.is_leaf(s):
+                xh[s] = A.W.leaf[s].T @ xt[ct.off[s]:ct.off[s] + ct.size[s]]
+            else:
+                acc = np.zeros((A.W.rank[s], X.shape[1]))
+                for c in ct.children[s]:
+                    fwd(c)
+                    acc += A.W.transfer[c].T @ xh[c]
+                xh[s] = acc
+
+        fwd(0)
+        yh = {t: np.zeros((A.V.rank[t], X.shape[1])) for t in range(rt.nclusters)}
+        yt = np.zeros((len(rt.perm), X.shape[1]))
+        for (t, s), k in A.blocks.kind.items():
+            if k == ADM:
+                yh[t] += A.S[(t, s)] @ xh[s]
+            elif k == DENSE:
+                yt[rt.off[t]:rt.off[t] + rt.size[t]] += A.N[(t, s)] @ xt[ct.off[s]:ct.off[s] + ct.size[s]]
+
+        def bwd(t, acc):
+            acc = yh[t] if acc is None else yh[t] + acc
+            if rt.is_leaf(t):
+                yt[rt.off[t]:rt.off[t] + rt.size[t]] += A.V.leaf[t] @ acc
+            else:
+                for c in rt.children[t]:
+                    bwd(c, A.V.transfer[c] @ acc)
+
+        bwd(0, None)
+        out = np.empty_like(yt)
+        out[rt.perm] = yt
+        return out[:, 0] if one else out
+
+    def rows_of(self, idx) -> np.ndarray:
+        """Rows idx of G (len(idx) x n) as G^* applied to unit vectors."""
+        E = np.zeros((len(self.cols.perm), len(idx)))
+        E[np.asarray(idx), np.arange(len(idx))] = 1.0
+        return self.matvec(E, trans=True).T
+
     def to_dense(self, original_order: bool = True) -> np.ndarray:
         rt, ct = self.rows, self.cols
         G = np.zeros((len(rt.perm), len(ct.perm)))

@@ -21,7 +21,8 @@ H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
 H2_FP64, H2_MIXED = 0, 1
 
 EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-            "h2_plan_structure", "h2_to_dense_noalloc", "h2_free", "h2_error_string", "h2_last_error_message"]
+            "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_free", "h2_error_string",
+            "h2_last_error_message"]
 
 
 class H2Error(RuntimeError):
@@ -85,13 +86,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_clone.argtypes = [vp, vp, ctypes.POINTER(vp)]
     lib.h2_plan_structure.argtypes = [vp, i64, ci, cd, vp, vp]
     lib.h2_to_dense_noalloc.argtypes = [vp, vp, i64, vp]
+    lib.h2_matvec.argtypes = [vp, vp, vp, i64, ci, vp]
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
     lib.h2_error_string.argtypes = [ci]
     lib.h2_last_error_message.restype = ctypes.c_char_p
     for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-              "h2_plan_structure", "h2_to_dense_noalloc"):
+              "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -201,6 +203,29 @@ def h2_to_dense_noalloc(A: H2Matrix, out, stream: int | None = None):
     n = A.info()["n"]
     _check(load().h2_to_dense_noalloc(A.handle, out.data_ptr(), n, ctypes.c_void_p(stream or 0)),
            "h2_to_dense_noalloc")
+    return out
+
+
+def h2_matvec(A: H2Matrix, x, y, trans: bool = False, stream: int | None = None):
+    """y = A x or A^* x for CUDA tensors x, y holding n x nvec float64 matrices
+    column-major (the storage of an (nvec, n) row-major tensor)."""
+    n = A.info()["n"]
+    nv = x.numel() // n
+    o = _opts(stream=stream)
+    _check(load().h2_matvec(A.handle, x.data_ptr(), y.data_ptr(), nv, 1 if trans else 0, ctypes.byref(o)),
+           "h2_matvec")
+    return y
+
+
+def h2_rows(A: H2Matrix, idx):
+    """Rows idx of A as an (len(idx), n) float64 CUDA tensor, computed as A^* e_i."""
+    import torch
+    n = A.info()["n"]
+    idx = torch.as_tensor(idx, dtype=torch.int64)
+    e = torch.zeros((len(idx), n), dtype=torch.float64, device="cuda")
+    e[torch.arange(len(idx)), idx.to("cuda")] = 1.0
+    out = torch.empty_like(e)
+    h2_matvec(A, e, out, trans=True)
     return out
 
 

@@ -262,6 +262,10 @@ void launch_interp_dense(const double* pts, const int64_t* perm, const int64_t* 
 void launch_scatter_dense(const double* src, int64_t n, const int64_t* perm, double* out, int64_t ld,
                           cudaStream_t st);
 void launch_set_identity(double* A, int m, int n, int lda, cudaStream_t st);
+// rows of an n x nv matrix: gather dst[i] = src[perm[i]] (scatter = 0) or
+// scatter dst[perm[i]] = src[i] (scatter = 1)
+void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* perm, int64_t n,
+                         int64_t nv, int scatter, cudaStream_t st);
 void launch_check_finite(const double* A, size_t len, int* flag, cudaStream_t st);
 // Sum of squares of the entries of A (rows x cols, lda), added to out[slot].
 struct SumSqJob {

@@ -966,6 +966,25 @@ void launch_inv_sqrt(const double* v, double* w, double* w2, int n, cudaStream_t
     if (n > 0) k_inv_sqrt<<<(int)ceil_div(n, 256), 256, 0, st>>>(v, w, w2, n);
 }
 
+// row permutation of an n x nv matrix (gather or scatter)
+__global__ void k_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* perm,
+                               int64_t n, int64_t nv, int scatter) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nv; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e % n, j = e / n;
+        if (scatter)
+            dst[perm[i] + j * ldd] = src[i + j * lds];
+        else
+            dst[i + j * ldd] = src[perm[i] + j * lds];
+    }
+}
+
+void launch_permute_rows(const double* src, int64_t lds, double* dst, int64_t ldd, const int64_t* perm, int64_t n,
+                         int64_t nv, int scatter, cudaStream_t st) {
+    if (n > 0 && nv > 0)
+        k_permute_rows<<<(int)std::min<int64_t>(ceil_div(n * nv, 256), 8192), 256, 0, st>>>(src, lds, dst, ldd, perm,
+                                                                                             n, nv, scatter);
+}
+
 // dense n x n matrix in tree order -> original order
 __global__ void k_scatter(const double* src, int64_t n, const int64_t* perm, double* out, int64_t ld) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {

@@ -1432,6 +1432,77 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
     return Up;
 }
 
+// ------------------------------------------------------------------ matrix-vector product
+// y = A x for a (possibly transposed) view: forward transformation of x
+// through the column basis, couplings, backward transformation through the
+// row basis, dense blocks (Sec. 2: O(nk) work per vector).
+static void matvec(const h2_matrix* M, bool trans, const double* x, double* y, int64_t nv, cudaStream_t st) {
+    const OpView A{M, trans};
+    const Tree& T = A.tree();
+    const Basis& V = A.rowb();
+    const Basis& W = A.colb();
+    const int64_t n = T.n;
+    const int w = (int)nv;
+    Runner R(st, H2_FP64);
+    int64_t* d_perm = R.upload(T.perm);
+    double* xt = R.dalloc((size_t)n * nv);
+    double* yt = R.dalloc((size_t)n * nv);
+    launch_permute_rows(x, n, xt, n, d_perm, n, nv, 0, st);
+    std::vector<double*> xh(T.nc), yh(T.nc);
+    for (int c = 0; c < T.nc; ++c) {
+        xh[c] = R.dalloc((size_t)std::max(1, W.rank[c]) * nv);
+        yh[c] = R.dalloc((size_t)std::max(1, V.rank[c]) * nv);
+    }
+    // forward: x_s = W_s^* x|_s at leaves, sum_c F_c^* x_c above
+    for (int c = Tree::first(T.L); c < T.nc; ++c) {
+        R.job(xh[c], W.rank[c], w, std::max(1, W.rank[c]), 0.0);
+        R.term(W.leaf[c], 1, (int)T.size[c], xt + T.off[c], 0, (int)n, (int)T.size[c]);
+    }
+    R.flush_gemm();
+    for (int l = T.L - 1; l >= 0; --l) {
+        for (int p = Tree::first(l); p < Tree::first(l) + Tree::count(l); ++p) {
+            R.job(xh[p], W.rank[p], w, std::max(1, W.rank[p]), 0.0);
+            for (int i = 0; i < 2; ++i) {
+                int c = Tree::child(p, i);
+                R.term(W.tr[c], 1, std::max(1, W.rank[c]), xh[c], 0, std::max(1, W.rank[c]), W.rank[c]);
+            }
+        }
+        R.flush_gemm();
+    }
+    // couplings: y_t = sum_s S_ts x_s
+    for (int t = 0; t < T.nc; ++t) {
+        R.job(yh[t], V.rank[t], w, std::max(1, V.rank[t]), 0.0);
+        for (int b : A.row_list(t))
+            if (A.kind(b) == ADM) T_(R, A.S(b), mv(xh[A.other(b)], std::max(1, W.rank[A.other(b)])), W.rank[A.other(b)]);
+    }
+    R.flush_gemm();
+    // backward: y_c += E_c y_p, level by level from the root
+    for (int l = 1; l <= T.L; ++l) {
+        for (int c = Tree::first(l); c < Tree::first(l) + Tree::count(l); ++c) {
+            int p = Tree::parent(c);
+            R.job(yh[c], V.rank[c], w, std::max(1, V.rank[c]), 1.0);
+            R.term(V.tr[c], 0, std::max(1, V.rank[c]), yh[p], 0, std::max(1, V.rank[p]), V.rank[p]);
+        }
+        R.flush_gemm();
+    }
+    // leaves: y|_t = V_t y_t + sum_s N_ts x|_s
+    for (int t = Tree::first(T.L); t < T.nc; ++t) {
+        R.job(yt + T.off[t], (int)T.size[t], w, (int)n, 0.0);
+        R.term(V.leaf[t], 0, (int)T.size[t], yh[t], 0, std::max(1, V.rank[t]), V.rank[t]);
+        for (int b : A.row_list(t))
+            if (A.kind(b) == DENSE) {
+                int s = A.other(b);
+                T_(R, A.N(b), mv(xt + T.off[s], (int)n), (int)T.size[s]);
+            }
+    }
+    R.flush_gemm();
+    launch_permute_rows(yt, n, y, n, d_perm, n, nv, 1, st);
+    H2_CUDA(cudaGetLastError());
+    H2_CUDA(cudaStreamSynchronize(st));
+    R.release_all();
+    H2_CUDA(cudaStreamSynchronize(st));
+}
+
 // ------------------------------------------------------------------ driver
 // The product block tree depends only on the two block trees: kept on the
 // structure of X, keyed by the fingerprint of Y's structure.
@@ -1634,6 +1705,21 @@ static int run_guarded_mul(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y,
     } catch (const std::bad_alloc&) {
         h2_set_last_error("host allocation failed");
         return H2_ERR_OOM;
+    } catch (const std::exception& e) {
+        h2_set_last_error(e.what());
+        return H2_ERR_CUDA;
+    }
+}
+
+extern "C" int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t nvec, int trans,
+                         const h2_opts* opts) {
+    if (!A || !x || !y || nvec < 1 || nvec > (1 << 20) || (trans != 0 && trans != 1)) return H2_ERR_ARG;
+    try {
+        h2::matvec(A, trans != 0, x, y, nvec, h2::stream_of(opts));
+        return H2_OK;
+    } catch (const h2::Error& e) {
+        h2_set_last_error(e.what());
+        return e.code;
     } catch (const std::exception& e) {
         h2_set_last_error(e.what());
         return H2_ERR_CUDA;

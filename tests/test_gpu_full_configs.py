@@ -1,0 +1,65 @@
+"""Parity at the full sizes of the workloads, on sampled rows.
+
+The oracle builds the same H^2-matrix G = X = Y = Z in numpy and computes
+rows i of Z + X Y as G^* e_i + G^* (G^* e_i) with its own forward/backward
+transformation matvec; the GPU result's rows come from the library's
+h2_matvec.  The bound is 10 eps in relative Frobenius norm over the sampled
+rows.  The n = 32768 sphere case runs in the benchmark's launch path (fresh
+clone of Z, one h2_mul_add); the cube-volume and the n = 524288 sphere cases
+run in the precision their workloads state."""
+import numpy as np
+import pytest
+
+import paper_2309_09061_gb300 as P
+import synth
+from oracle import h2_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # name: geometry, n, kernel, leaf, eta, order, eps, precision, seed
+    "sphere-n32768-fp64": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_FP64, 2309090611),
+    "sphere-n32768-mixed": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_MIXED, 2309090611),
+    "cube-n131072-yukawa-mixed-1e-4": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-4, P.H2_MIXED, 2309090612),
+    "cube-n131072-yukawa-mixed-1e-6": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-6, P.H2_MIXED, 2309090612),
+    "sphere-n524288-order5-mixed": ("sphere", 524288, O.K_LAPLACE, 64, 2.0, 5, 1e-6, P.H2_MIXED, 2309090614),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    return P.load()
+
+
+_oracle_cache = {}
+
+
+def oracle_matrix(geometry, n, kernel, leaf, eta, order, seed):
+    key = (geometry, n, kernel, leaf, eta, order, seed)
+    if key not in _oracle_cache:
+        _oracle_cache.clear()
+        pts = synth.make_points(geometry, n, seed)
+        _oracle_cache[key] = O.build_interp(O.build_structure(pts, leaf, eta, order), kernel)
+    return _oracle_cache[key]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_sampled_rows_full_size(name):
+    geometry, n, kernel, leaf, eta, order, eps, prec, seed = CASES[name]
+    pts = synth.make_points(geometry, n, seed)
+    G = P.h2_build_interp(pts, kernel, leaf, eta, order)
+    Z = P.h2_clone(G)
+    stats = P.h2_mul_add(Z, G, G, eps, prec)
+    G.free()
+    rows = np.unique(synth.splitmix64(77, 24) % n).astype(np.int64)
+    got = P.h2_rows(Z, rows).cpu().numpy()
+    Z.free()
+    Go = oracle_matrix(geometry, n, kernel, leaf, eta, order, seed)
+    Rg = Go.rows_of(rows)
+    ref = Rg + Go.matvec(Rg.T, trans=True).T
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    assert err <= 10 * eps, (name, err, stats["t_total_ms"])

@@ -142,28 +142,3 @@ def test_error_codes():
     assert e.value.code == -1
     before = P.h2_to_dense(Z)
     assert np.array_equal(before, P.h2_to_dense(X))
-
-
-@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
-def test_c2_full_size_sampled_rows(precision):
-    """n = 32768 on the sphere, Laplace, leaf 64, eta 2, order 4, X = Y = Z,
-    eps 1e-6 (the benchmark workload, same launch path): 64 sampled rows of
-    the result against rows of Z + X Y formed from the dense expansions."""
-    import torch
-    eps = 1e-6
-    n = 32768
-    pts = synth.sphere(n, SEED_C2)
-    G = P.h2_build_interp(pts, P.H2_K_LAPLACE, 64, 2.0, 4)
-    Z = P.h2_clone(G)
-    stats = P.h2_mul_add(Z, G, G, eps, precision)
-    dev = torch.device("cuda:0")
-    Gd = torch.empty((n, n), dtype=torch.float64, device=dev)
-    P.h2_to_dense(G, Gd)          # column-major fill: Gd.T is the matrix
-    rows = torch.as_tensor(np.sort(synth.splitmix64(77, 64) % n).astype(np.int64), device=dev)
-    Gm = Gd.T
-    exact = Gm[rows] + Gm[rows] @ Gm
-    Zd = torch.empty((n, n), dtype=torch.float64, device=dev)
-    P.h2_to_dense(Z, Zd)
-    got = Zd.T[rows]
-    err = float(torch.linalg.norm(got - exact) / torch.linalg.norm(exact))
-    assert err <= 10 * eps, (err, stats)

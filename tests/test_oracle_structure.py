@@ -123,3 +123,18 @@ def test_kernels_closed_form():
     y = O.kernel_matrix(O.K_YUKAWA, x, x)
     assert y[1, 1] == 0.0 and abs(y[1, 0] - math.exp(-5.0) / 5.0) < 1e-17
     assert np.array_equal(O.kernel_matrix(O.K_DELTA, x, x), np.eye(2))
+
+
+@pytest.mark.parametrize("trans", [False, True])
+def test_matvec_against_dense(trans):
+    """The forward/backward transformation matvec equals the dense product."""
+    st = structure(order=3)
+    X = O.build_interp(st, O.K_YUKAWA)
+    res = O.mul_add(O.build_interp(st, O.K_LAPLACE), O.build_interp(st, O.K_LAPLACE), X, 1e-4).result
+    for M in (X, res):  # interpolation bases and adaptive bases of a product
+        D = M.to_dense()
+        x = synth.normal01(5, D.shape[0] * 3).reshape(-1, 3)
+        ref = (D.T if trans else D) @ x
+        assert np.abs(M.matvec(x, trans) - ref).max() <= 1e-12 * np.abs(ref).max()
+    rows = [0, 7, 100]
+    assert np.allclose(X.rows_of(rows), X.to_dense()[rows], rtol=0, atol=1e-13 * np.abs(X.to_dense()).max())
