@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="override n (testing only)")
+    ap.add_argument("--workload", default="sphere32768", choices=["sphere32768", "batched64"],
+                    help="sphere32768: the default line; batched64: 64 independent products in one batched call")
     return ap.parse_args()
 
 
@@ -341,8 +343,73 @@ def ours_arm(args):
         tdist.destroy_process_group()
 
 
+BATCH = dict(count=64, nmin=2048, nmax=65536, eps=1e-5, leaf=64, eta=2.0, seed=2309090613)
+
+
+def batch_members():
+    """The 64 products of the batched workload: n_i = round(2048 * 32^u_i), u_i
+    uniform, half on the sphere and half on the cube surface, Chebyshev order
+    3, 4 or 5 uniformly (ranks 27, 64, 125), Laplace kernel, leaf 64, eta 2."""
+    b = BATCH
+    u = synth.uniform01(b["seed"], 2 * b["count"])
+    out = []
+    for i in range(b["count"]):
+        n = int(round(b["nmin"] * (b["nmax"] / b["nmin"]) ** u[2 * i]))
+        order = 3 + min(2, int(3 * u[2 * i + 1]))
+        geom = "sphere" if i % 2 == 0 else "cube_surface"
+        out.append((geom, n, order, b["seed"] + 1000 * i))
+    return out
+
+
+def batched_arm(args):
+    import torch
+
+    import paper_2309_09061_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P.build()
+    P.load()
+    members = batch_members()
+    Gs = [P.h2_build_interp(synth.make_points(g, n, seed + rank), 0, BATCH["leaf"], BATCH["eta"], m)
+          for g, n, m, seed in members]
+    rows = sum(n for _, n, _, _ in members) * world
+    out = {}
+    for name, prec in (("mixed", P.H2_MIXED), ("fp64", P.H2_FP64)):
+        times, stats = [], None
+        for it in range(args.warmup + args.steps):
+            Zs = [P.h2_clone(G) for G in Gs]
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            stats, codes = P.h2_mul_add_batched(Zs, Gs, Gs, BATCH["eps"], prec)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            assert codes == [0] * len(Zs)
+            for Z in Zs:
+                Z.free()
+            if it >= args.warmup:
+                times.append(dt)
+        out[name] = {"value": rows * len(times) / sum(times), "unit": "rows/s",
+                     "ms_per_step": 1e3 * sum(times) / len(times), "kernel_launches": stats["kernel_launches"]}
+    line = {"metric": "H2 Z<-Z+XY rows/s, 64 independent products in one batched call", "value": out["mixed"]["value"],
+            "unit": "rows/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["mixed"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 products, f64 factorisations", "data": "synthetic",
+            "config": {"workload": "batched64", "products": len(members), "rows": rows,
+                       "n_range": [min(n for _, n, _, _ in members), max(n for _, n, _, _ in members)],
+                       "orders": sorted(set(m for _, _, m, _ in members)), "eps": BATCH["eps"]},
+            "fp64": out["fp64"], "speedup_mixed_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
+            "gpu_launches": out["mixed"]["kernel_launches"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.impl != "reference" and args.workload == "batched64":
+        batched_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -155,6 +155,20 @@ H2_API int h2_build_interp(const double* points, int64_t n, int kernel, int leaf
  * X and Y are only read. */
 H2_API int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts);
 
+/* Z[i] <- Z[i] + X[i] Y[i] for count independent products (different sizes,
+ * orders, geometries), each with the relations and semantics of h2_mul_add
+ * and opts->eps / opts->precision.  The products run concurrently on
+ * internal non-blocking streams that start after the work already issued on
+ * opts->stream; the call returns when all of them are done.  A Z handle may
+ * not appear twice.  status (may be NULL) receives count per-product codes;
+ * the return value is the first nonzero one (products that failed leave
+ * their Z unchanged, the others are updated).  opts->stats receives sums over
+ * the products (times are summed device times, not the elapsed time).
+ * Errors: as h2_mul_add, plus H2_ERR_ARG when a Z handle appears twice or as
+ * an operand of another product of the batch. */
+H2_API int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X, const h2_matrix* const* Y, int count,
+                              const h2_opts* opts, int* status);
+
 /* Expand A into a dense n x n matrix in the ORIGINAL point order (row i and
  * column j belong to points i and j), column-major with leading dimension
  * ld >= n.  `out` is a host pointer if out_on_device == 0, else a device

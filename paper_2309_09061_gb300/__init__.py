@@ -21,7 +21,7 @@ H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
 H2_FP64, H2_MIXED = 0, 1
 
 EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-            "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_free", "h2_error_string",
+            "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_free", "h2_error_string",
             "h2_last_error_message"]
 
 
@@ -87,13 +87,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_plan_structure.argtypes = [vp, i64, ci, cd, vp, vp]
     lib.h2_to_dense_noalloc.argtypes = [vp, vp, i64, vp]
     lib.h2_matvec.argtypes = [vp, vp, vp, i64, ci, vp]
+    lib.h2_mul_add_batched.argtypes = [vp, vp, vp, ci, vp, vp]
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
     lib.h2_error_string.argtypes = [ci]
     lib.h2_last_error_message.restype = ctypes.c_char_p
     for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-              "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec"):
+              "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -163,6 +164,20 @@ def h2_mul_add(Z: H2Matrix, X: H2Matrix, Y: H2Matrix, eps: float, precision: int
     o = _opts(eps, precision, stream, st)
     _check(load().h2_mul_add(Z.handle, X.handle, Y.handle, ctypes.byref(o)), "h2_mul_add")
     return st.as_dict()
+
+
+def h2_mul_add_batched(Zs, Xs, Ys, eps: float, precision: int = H2_FP64, stream: int | None = None):
+    """Z_i <- Z_i + X_i Y_i for independent products, run concurrently;
+    returns (statistics summed over the products, per-product codes)."""
+    n = len(Zs)
+    arr = ctypes.c_void_p * max(n, 1)
+    za, xa, ya = arr(*[z.handle for z in Zs]), arr(*[x.handle for x in Xs]), arr(*[y.handle for y in Ys])
+    codes = (ctypes.c_int * max(n, 1))()
+    st = Stats()
+    o = _opts(eps, precision, stream, st)
+    rc = load().h2_mul_add_batched(za, xa, ya, n, ctypes.byref(o), codes)
+    _check(rc, "h2_mul_add_batched")
+    return st.as_dict(), list(codes)[:n]
 
 
 def h2_to_dense(A: H2Matrix, out=None, stream: int | None = None) -> np.ndarray:

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <mutex>
 
 #include "h2_internal.h"
 
@@ -13,7 +14,9 @@ namespace h2 {
 // ---------------------------------------------------------------- memory
 static cudaMemPool_t lib_pool(int dev) {
     static cudaMemPool_t pools[64] = {};
+    static std::mutex mu;
     if (dev < 0 || dev >= 64) throw Error(H2_ERR_CUDA, "device index out of range");
+    std::lock_guard<std::mutex> g(mu);
     if (!pools[dev]) {
         cudaMemPoolProps props = {};
         props.allocType = cudaMemAllocationTypePinned;

@@ -14,8 +14,10 @@
 #include <chrono>
 #include <cmath>
 #include <functional>
+#include <atomic>
 #include <map>
 #include <mutex>
+#include <thread>
 
 #include "h2_internal.h"
 
@@ -1709,6 +1711,87 @@ static int run_guarded_mul(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y,
         h2_set_last_error(e.what());
         return H2_ERR_CUDA;
     }
+}
+
+// Independent products run concurrently: worker threads, each with its own
+// non-blocking stream, take products from a shared counter; the host work of
+// one product overlaps the device work of the others.
+extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X, const h2_matrix* const* Y,
+                                  int count, const h2_opts* opts, int* status) {
+    using namespace h2;
+    if (count < 0 || (count > 0 && (!Z || !X || !Y))) return H2_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!Z[i] || !X[i] || !Y[i]) return H2_ERR_ARG;
+    if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
+                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED)))
+        return H2_ERR_ARG;
+    // a Z may not appear twice, nor as an operand of another product (its swap would race)
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < count; ++j)
+            if (i != j && (Z[i] == Z[j] || Z[i] == X[j] || Z[i] == Y[j])) return H2_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return H2_ERR_CUDA;
+    cudaStream_t outer = stream_of(opts);
+    cudaEvent_t start = nullptr;
+    if (cudaEventCreateWithFlags(&start, cudaEventDisableTiming) != cudaSuccess) return H2_ERR_CUDA;
+    cudaEventRecord(start, outer);  // products start after the caller's earlier work
+    const int workers = std::max(1, std::min(count, 8));
+    std::vector<int> codes(count, H2_OK);
+    std::atomic<int> next{0};
+    std::vector<h2_stats> stats(count);
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            for (int i = next.fetch_add(count); i < count; ++i) codes[i] = H2_ERR_CUDA;
+            return;
+        }
+        cudaStreamWaitEvent(st, start, 0);
+        for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+            h2_opts o = opts ? *opts : h2_opts{1e-6, H2_FP64, nullptr, nullptr};
+            o.stream = st;
+            o.stats = opts && opts->stats ? &stats[i] : nullptr;
+            codes[i] = h2_mul_add(Z[i], X[i], Y[i], &o);
+        }
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < workers; ++w) pool.emplace_back(work);
+    for (auto& t : pool) t.join();
+    cudaEventDestroy(start);
+    if (opts && opts->stats) {  // sums over the products (times: device time of each product)
+        h2_stats S{};
+        for (const h2_stats& x : stats) {
+            S.t_rows_a_ms += x.t_rows_a_ms;
+            S.t_cols_a_ms += x.t_cols_a_ms;
+            S.t_mat_a_ms += x.t_mat_a_ms;
+            S.t_rows_b_ms += x.t_rows_b_ms;
+            S.t_cols_b_ms += x.t_cols_b_ms;
+            S.t_mat_b_ms += x.t_mat_b_ms;
+            S.t_total_ms += x.t_total_ms;
+            S.kernel_launches += x.kernel_launches;
+            S.product_nodes += x.product_nodes;
+            S.triples += x.triples;
+            S.max_rank_a = std::max(S.max_rank_a, x.max_rank_a);
+            S.max_rank_b = std::max(S.max_rank_b, x.max_rank_b);
+            S.flops += x.flops;
+            S.bytes_moved += x.bytes_moved;
+            for (int f = 0; f < 8; ++f) {
+                S.fam_ms[f] += x.fam_ms[f];
+                S.fam_launches[f] += x.fam_launches[f];
+                S.fam_flops[f] += x.fam_flops[f];
+                S.fam_bytes[f] += x.fam_bytes[f];
+            }
+        }
+        *opts->stats = S;
+    }
+    int first = H2_OK;
+    for (int i = 0; i < count; ++i) {
+        if (status) status[i] = codes[i];
+        if (first == H2_OK && codes[i] != H2_OK) first = codes[i];
+    }
+    return first;
 }
 
 extern "C" int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t nvec, int trans,
