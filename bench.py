@@ -262,10 +262,10 @@ def ours_arm(args):
     d2h = w["n"] * 8 + 3 * nclusters * 8 + 2 * nclusters * 4
 
     # roofline of the dominant kernel family (FP64 form)
-    fam = np.zeros(8)
-    fam_fl = np.zeros(8)
-    fam_by = np.zeros(8)
-    fam_n = np.zeros(8)
+    fam = np.zeros(12)
+    fam_fl = np.zeros(12)
+    fam_by = np.zeros(12)
+    fam_n = np.zeros(12)
     for s in st64:
         fam += np.array(s["fam_ms"])
         fam_fl += np.array(s["fam_flops"])
@@ -276,14 +276,15 @@ def ours_arm(args):
     lib_peaks = library_peaks(torch, dev) if rank == 0 else {}
     names = P.FAMILIES
     avg_ms = fam[top] / max(1.0, fam_n[top])
-    kernel_of = {0: "k_gemm<double>", 1: "k_gemm<float>", 2: "k_qr / k_pchol", 3: "k_svd", 4: "k_jacobi_pre",
-                 5: "k_norm", 6: "k_copy", 7: "k_sumsq / k_finite"}
-    if top in (0, 2, 3, 5):  # FP64 arithmetic: bound by the FP64 pipe
+    kernel_of = {0: "k_gemm<double>", 1: "k_gemm<float>", 2: "k_qr<double>", 3: "k_qr<float>", 4: "k_pchol",
+                 5: "k_svd / k_jacobi_cluster<double>", 6: "k_jacobi_pre / k_jacobi_cluster<float>", 7: "k_norm",
+                 8: "k_copy", 9: "k_sumsq / k_finite"}
+    if top in (0, 2, 4, 5, 7):  # FP64 arithmetic: bound by the FP64 pipe
         achieved = fam_fl[top] / (fam[top] / 1e3) / 1e12
         roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": achieved, "peak": lib_peaks.get("fp64_tflops"),
                 "unit": "TFLOP/s (FP64)",
                 "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (MEASURED_PEAKS.json has no FP64 figure)"}
-    elif top in (1, 4):
+    elif top in (1, 3, 6):
         achieved = fam_fl[top] / (fam[top] / 1e3) / 1e12
         roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": achieved, "peak": lib_peaks.get("fp32_tflops"),
                 "unit": "TFLOP/s (FP32)", "peak_source": "cuBLAS SGEMM 8192^3 (no TF32) measured in this run"}
@@ -298,14 +299,14 @@ def ours_arm(args):
     roof["peaks_measured_here"] = lib_peaks
     fam_report = {names[i]: {"ms_per_step": fam[i] / len(st64), "launches_per_step": fam_n[i] / len(st64),
                              "gflop_per_step": fam_fl[i] / len(st64) / 1e9, "gb_per_step": fam_by[i] / len(st64) / 1e9}
-                  for i in range(8)}
-    fam_mx = np.zeros(8)
-    fam_mx_fl = np.zeros(8)
+                  for i in range(10)}
+    fam_mx = np.zeros(12)
+    fam_mx_fl = np.zeros(12)
     for s in stmx:
         fam_mx += np.array(s["fam_ms"])
         fam_mx_fl += np.array(s["fam_flops"])
     fam_report_mx = {names[i]: {"ms_per_step": fam_mx[i] / len(stmx), "gflop_per_step": fam_mx_fl[i] / len(stmx) / 1e9}
-                     for i in range(8)}
+                     for i in range(10)}
 
     n_all = w["n"] * world
     value = n_all * args.steps / dt64

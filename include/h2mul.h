@@ -89,21 +89,23 @@ typedef struct {
      * CUDA-event intervals around each launch on opts->stream), number of
      * launches, algorithmic flops and bytes (every operand read once, every
      * output written once; counted on the host from the launch descriptors). */
-    double fam_ms[8];
-    int64_t fam_launches[8];
-    double fam_flops[8];
-    double fam_bytes[8];
+    double fam_ms[12];
+    int64_t fam_launches[12];
+    double fam_flops[12];
+    double fam_bytes[12];
 } h2_stats;
 
 /* Kernel families of h2_stats.fam_*. */
 #define H2_FAM_GEMM64 0  /* batched segmented products, FP64 arithmetic */
 #define H2_FAM_GEMM32 1  /* batched segmented products, FP32 arithmetic */
-#define H2_FAM_QR 2      /* Householder QR (FP64 or FP32) and pivoted Cholesky */
-#define H2_FAM_SVD 3     /* one-sided Jacobi SVD, FP64 sweeps */
-#define H2_FAM_SVDPRE 4  /* one-sided Jacobi preconditioning, FP32 sweeps */
-#define H2_FAM_NORM 5    /* spectral norms by power iteration */
-#define H2_FAM_COPY 6    /* batched copies, scalings, transpositions */
-#define H2_FAM_OTHER 7   /* block norms, finiteness checks */
+#define H2_FAM_QR64 2    /* Householder QR, FP64 */
+#define H2_FAM_QR32 3    /* Householder QR, FP32 (wide-to-square reductions, mixed mode) */
+#define H2_FAM_CHOL 4    /* pivoted Cholesky of weight Gram matrices */
+#define H2_FAM_SVD 5     /* one-sided Jacobi SVD, FP64 sweeps */
+#define H2_FAM_SVDPRE 6  /* one-sided Jacobi preconditioning, FP32 sweeps */
+#define H2_FAM_NORM 7    /* spectral norms by power iteration */
+#define H2_FAM_COPY 8    /* batched copies, scalings, transpositions */
+#define H2_FAM_OTHER 9   /* block norms, finiteness checks */
 
 typedef struct {
     double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */

@@ -39,8 +39,8 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("product_nodes", ctypes.c_int64),
                 ("triples", ctypes.c_int64), ("max_rank_a", ctypes.c_int), ("max_rank_b", ctypes.c_int),
                 ("bytes_moved", ctypes.c_double), ("flops", ctypes.c_double),
-                ("fam_ms", ctypes.c_double * 8), ("fam_launches", ctypes.c_int64 * 8),
-                ("fam_flops", ctypes.c_double * 8), ("fam_bytes", ctypes.c_double * 8)]
+                ("fam_ms", ctypes.c_double * 12), ("fam_launches", ctypes.c_int64 * 12),
+                ("fam_flops", ctypes.c_double * 12), ("fam_bytes", ctypes.c_double * 12)]
 
     def as_dict(self):
         d = {}
@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
         return d
 
 
-FAMILIES = ["gemm_fp64", "gemm_fp32", "qr_chol", "svd_fp64", "svd_fp32_pre", "norm", "copy", "other"]
+FAMILIES = ["gemm_fp64", "gemm_fp32", "qr_fp64", "qr_fp32", "pchol", "svd_fp64", "svd_fp32_pre", "norm", "copy", "other",
+            "", ""]
 
 
 class Opts(ctypes.Structure):

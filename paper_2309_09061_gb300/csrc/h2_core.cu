@@ -231,9 +231,9 @@ void Runner::flush_qr() {
             fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p;
             by += 8.0 * m * n + 8.0 * p * n;
         }
-        begin(2);
+        begin(3);
         launch_qr32(d, (int)qrs32_.size(), st_);
-        end(2, fl, by);
+        end(3, fl, by);
         ++launches;
         qrs32_.clear();
     }
@@ -265,9 +265,9 @@ void Runner::flush_svd() {
     SVDJob* d = upload(svds_);
     double by = 0.0;
     for (auto& j : svds_) by += 8.0 * 3.0 * j.m * j.n;
-    begin(3);
+    begin(5);
     launch_svd(d, (int)svds_.size(), svd_maxn_, st_);
-    end(3, 0.0, by);
+    end(5, 0.0, by);
     marks_.back().dflops = cnt;
     ++launches;
     svds_.clear();
@@ -287,9 +287,9 @@ void Runner::flush_pre() {
     PreJob* d = upload(pres_);
     double by = 0.0;
     for (auto& j : pres_) by += 8.0 * ((double)j.m * j.n + (double)j.n * j.n);
-    begin(4);
+    begin(6);
     launch_jacobi_pre(d, (int)pres_.size(), st_);
-    end(4, 0.0, by);
+    end(6, 0.0, by);
     marks_.back().dflops = cnt;
     ++launches;
     pres_.clear();
@@ -309,9 +309,9 @@ void Runner::flush_pchol() {
         fl += (double)j.k * j.k * j.k / 3.0;
         by += 16.0 * j.k * j.k;
     }
-    begin(2);
+    begin(4);
     launch_pchol(d, (int)chols_.size(), st_);
-    end(2, fl, by);
+    end(4, fl, by);
     ++launches;
     chols_.clear();
 }
@@ -329,9 +329,9 @@ void Runner::flush_norm() {
         by += 8.0 * j.m * j.n;
         fl += 4.0 * 61.0 * j.m * j.n;
     }
-    begin(5);
+    begin(7);
     launch_norm(d, (int)norms_.size(), prec_, st_);
-    end(5, fl, by);
+    end(7, fl, by);
     ++launches;
     norms_.clear();
 }
@@ -347,9 +347,9 @@ void Runner::flush_copy() {
     CopyJob* d = upload(copies_);
     double by = 0.0;
     for (auto& j : copies_) by += 8.0 * j.rows * j.cols * (j.beta != 0.0 ? 3.0 : 2.0);
-    begin(6);
+    begin(8);
     launch_copy(d, (int)copies_.size(), st_);
-    end(6, 0.0, by);
+    end(8, 0.0, by);
     ++launches;
     copies_.clear();
 }

@@ -1599,10 +1599,10 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
                 jobs.push_back(SumSqJob{G.C[n], (int)T.size[t], (int)T.size[r], (int)T.size[t], cmap[n]});
         }
         SumSqJob* dj = R.upload(jobs);
-        R.begin(7);
+        R.begin(9);
         launch_sumsq(dj, (int)jobs.size(), sq, st);
         launch_inv_sqrt(sq, w, w2, (int)Zb.kind.size(), st);
-        R.end(7, 0.0, 0.0);
+        R.end(9, 0.0, 0.0);
         R.launches += 2;
     }
     GView GR{&G, &T, false}, GC{&G, &T, true};
@@ -1646,9 +1646,9 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     }
     R.flush_copy();
     R.ensure_flag();
-    R.begin(7);
+    R.begin(9);
     launch_check_finite(chunk->p, chunk->len, R.svd_flag(), st);
-    R.end(7, 0.0, 8.0 * chunk->len);
+    R.end(9, 0.0, 8.0 * chunk->len);
     R.launches++;
     clk.mark();
     int flag = 0;
@@ -1674,7 +1674,7 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
         S->max_rank_b = std::max(rb.Qn->max_rank(), cb.Qn->max_rank());
         S->flops = cnt.flops;
         S->bytes_moved = cnt.bytes;
-        for (int f = 0; f < 8; ++f) {
+        for (int f = 0; f < 12; ++f) {
             S->fam_ms[f] = 0.0;
             S->fam_launches[f] = 0;
             S->fam_flops[f] = 0.0;
@@ -1777,7 +1777,7 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
             S.max_rank_b = std::max(S.max_rank_b, x.max_rank_b);
             S.flops += x.flops;
             S.bytes_moved += x.bytes_moved;
-            for (int f = 0; f < 8; ++f) {
+            for (int f = 0; f < 12; ++f) {
                 S.fam_ms[f] += x.fam_ms[f];
                 S.fam_launches[f] += x.fam_launches[f];
                 S.fam_flops[f] += x.fam_flops[f];
