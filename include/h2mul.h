@@ -61,9 +61,16 @@ extern "C" {
  * auxiliary matrices).  QR factorisations, singular value decompositions and
  * the choice of ranks always run in FP64.
  *   H2_FP64   every product in FP64 (the plain FP64 GPU form)
- *   H2_MIXED  products in FP32 with FP32 accumulation, storage in FP64 */
+ *   H2_MIXED  products in FP32 with FP32 accumulation (CUDA cores), storage in FP64
+ *   H2_TC     products on the tensor cores (tcgen05, TF32 three-term split
+ *             hi*hi + hi*lo + lo*hi, about 21 bits, FP32 accumulation in TMEM)
+ * In H2_MIXED and H2_TC the wide-to-square reduction ahead of each SVD runs
+ * in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the weights'
+ * Gram matrices, the pivoted Cholesky, the final sweeps and every rank
+ * decision stay FP64. */
 #define H2_FP64 0
 #define H2_MIXED 1
+#define H2_TC 2
 
 typedef struct h2_matrix h2_matrix;
 
@@ -106,10 +113,11 @@ typedef struct {
 #define H2_FAM_NORM 7    /* spectral norms by power iteration */
 #define H2_FAM_COPY 8    /* batched copies, scalings, transpositions */
 #define H2_FAM_OTHER 9   /* block norms, finiteness checks */
+#define H2_FAM_GEMMTC 10 /* batched segmented products on tcgen05 (H2_TC) */
 
 typedef struct {
     double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */
-    int precision;    /* H2_FP64 or H2_MIXED */
+    int precision;    /* H2_FP64, H2_MIXED or H2_TC */
     void* stream;     /* cudaStream_t; NULL selects the legacy default stream */
     h2_stats* stats;  /* optional output, may be NULL */
 } h2_opts;

@@ -18,7 +18,7 @@ H2_OK = 0
 ERRORS = {-1: "H2_ERR_ARG", -2: "H2_ERR_SHAPE", -3: "H2_ERR_OOM", -4: "H2_ERR_NUMERIC",
           -5: "H2_ERR_TIMEOUT", -6: "H2_ERR_UNSUPPORTED", -7: "H2_ERR_CUDA"}
 H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
-H2_FP64, H2_MIXED = 0, 1
+H2_FP64, H2_MIXED, H2_TC = 0, 1, 2
 
 EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
             "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_free", "h2_error_string",
@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
 
 
 FAMILIES = ["gemm_fp64", "gemm_fp32", "qr_fp64", "qr_fp32", "pchol", "svd_fp64", "svd_fp32_pre", "norm", "copy", "other",
-            "", ""]
+            "gemm_tc", ""]
 
 
 class Opts(ctypes.Structure):

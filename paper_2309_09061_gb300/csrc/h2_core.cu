@@ -180,11 +180,14 @@ void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int
 
 void Runner::flush_gemm(int precision_override) {
     if (jobs_.empty()) return;
+    const int pr = precision_override >= 0 ? precision_override : prec_;
+    const bool tc = (pr == H2_TC);
+    const int tm = tc ? kTcTileM : 32, tn = tc ? kTcTileN : 32;
     std::vector<GTile> tiles;
     for (int j = 0; j < (int)jobs_.size(); ++j) {
         const GJob& J = jobs_[j];
-        for (int i0 = 0; i0 < J.m; i0 += 32)
-            for (int j0 = 0; j0 < J.n; j0 += 32) tiles.push_back(GTile{j, i0, j0});
+        for (int i0 = 0; i0 < J.m; i0 += tm)
+            for (int j0 = 0; j0 < J.n; j0 += tn) tiles.push_back(GTile{j, i0, j0});
     }
     if (!tiles.empty()) {
         GTerm* dt = upload(terms_);
@@ -200,10 +203,13 @@ void Runner::flush_gemm(int precision_override) {
             }
             by += 8.0 * J.m * J.n * (J.beta != 0.0 ? 2.0 : 1.0);
         }
-        const int pr = precision_override >= 0 ? precision_override : prec_;
-        const int fam = (pr == H2_MIXED) ? 1 : 0;
+        const int fam = tc ? 10 : (pr == H2_MIXED) ? 1 : 0;
+        if (tc) ensure_flag();
         begin(fam);
-        launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
+        if (tc)
+            launch_gemm_tc(dt, dj, dti, (int)tiles.size(), d_flag_, st_);
+        else
+            launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
         end(fam, fl, by);
         ++launches;
     }
@@ -330,7 +336,7 @@ void Runner::flush_norm() {
         fl += 4.0 * 61.0 * j.m * j.n;
     }
     begin(7);
-    launch_norm(d, (int)norms_.size(), prec_, st_);
+    launch_norm(d, (int)norms_.size(), low_precision(prec_) ? H2_MIXED : H2_FP64, st_);
     end(7, fl, by);
     ++launches;
     norms_.clear();

@@ -244,6 +244,11 @@ struct CopyJob {
 // Kernel launchers (h2_kernels.cu); job arrays are device pointers.
 void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
                  cudaStream_t st);
+// tcgen05 variant: tiles of 128 x 64; *err |= 4 if an MMA wait timed out
+void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st);
+constexpr int kTcTileM = 128, kTcTileN = 64;
+// precision modes that run the factorisation-side steps in FP32 as well
+inline bool low_precision(int precision) { return precision != H2_FP64; }
 void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);

@@ -85,6 +85,194 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
         k_gemm<double><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
 }
 
+// ------------------------------------------------------------------ GEMM on tcgen05 (H2_TC)
+// Same contract as k_gemm on the 5th-generation tensor cores.  One CTA of 128
+// threads computes a 128 x 64 output tile: the operands of each K chunk are
+// staged in shared memory as TF32 pairs (hi = rna(x), lo = rna(x - hi)) in the
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix), one thread
+// issues tcgen05.mma.kind::tf32 for hi*hi + hi*lo + lo*hi (about 21 bits of
+// the FP32 product), the FP32 accumulator lives in TMEM (128 lanes x 64
+// columns) and is read back with tcgen05.ld.  Waits on the MMA completion
+// barrier are bounded: on timeout the kernel records the error, frees its
+// TMEM and returns.
+constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 128;
+constexpr int TC_A = TC_M * TC_K, TC_B = TC_N * TC_K;  // elements per operand tile
+constexpr size_t TC_SMEM = 2 * (size_t)(TC_A + TC_B) * 4 + 64;
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// element (row r, k) of a K-major tile of `rows` rows and TC_K columns
+__device__ __forceinline__ int core_index(int r, int k) {
+    return ((r >> 3) * (TC_K / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// shared memory descriptor: K-major, no swizzle; LBO = 128 B (next core in K),
+// SBO = (TC_K / 4) * 128 B (next 8-row group)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    const uint64_t lbo = 128, sbo = (TC_K / 4) * 128;
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
+                                                  const GTile* __restrict__ tiles, int* err) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    uint32_t* a_hi = (uint32_t*)tc_smem;
+    uint32_t* a_lo = a_hi + TC_A;
+    uint32_t* b_hi = a_lo + TC_A;
+    uint32_t* b_lo = b_hi + TC_B;
+    uint64_t* mbar = (uint64_t*)(b_lo + TC_B);
+    uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
+    const GTile tile = tiles[blockIdx.x];
+    const GJob J = jobs[tile.job];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(tmem_slot)),
+                     "r"(TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_s));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+    uint32_t phase = 0;
+    bool issued = false, failed = false;
+    for (int it = 0; it < J.nt && !failed; ++it) {
+        const GTerm P = terms[J.t0 + it];
+        const double f = P.alpha * (P.scale ? *P.scale : 1.0);
+        if (f == 0.0) continue;
+        for (int k0 = 0; k0 < P.k && !failed; k0 += TC_K) {
+            // stage op(A)[i0:i0+128, k0:k0+32] and op(B)^T[j0:j0+64, k0:k0+32]
+            for (int e = threadIdx.x; e < TC_A; e += TC_T) {
+                int r, kk;
+                if (!P.ta) { r = e % TC_M; kk = e / TC_M; } else { kk = e % TC_K; r = e / TC_K; }
+                int gi = tile.i0 + r, gk = k0 + kk;
+                float x = 0.f;
+                if (gi < J.m && gk < P.k)
+                    x = (float)(f * (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]));
+                uint32_t h = tf32_rna(x);
+                int ci = core_index(r, kk);
+                a_hi[ci] = h;
+                a_lo[ci] = tf32_rna(x - __uint_as_float(h));
+            }
+            for (int e = threadIdx.x; e < TC_B; e += TC_T) {
+                int c, kk;
+                if (!P.tb) { kk = e % TC_K; c = e / TC_K; } else { c = e % TC_N; kk = e / TC_N; }
+                int gj = tile.j0 + c, gk = k0 + kk;
+                float x = 0.f;
+                if (gj < J.n && gk < P.k) x = (float)(P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]);
+                uint32_t h = tf32_rna(x);
+                int ci = core_index(c, kk);
+                b_hi[ci] = h;
+                b_lo[ci] = tf32_rna(x - __uint_as_float(h));
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t ah = (uint32_t)__cvta_generic_to_shared(a_hi), al = (uint32_t)__cvta_generic_to_shared(a_lo);
+                const uint32_t bh = (uint32_t)__cvta_generic_to_shared(b_hi), bl = (uint32_t)__cvta_generic_to_shared(b_lo);
+#pragma unroll
+                for (int ks = 0; ks < TC_K / 8; ++ks) {
+                    const uint32_t off = ks * 2 * 128;  // two core matrices of K per MMA
+                    const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
+                    const uint64_t dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
+                    const uint32_t acc0 = (issued || ks > 0) ? 1u : 0u;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                 "l"(dah), "l"(dbh), "r"(TC_IDESC), "r"(acc0));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                 "l"(dah), "l"(dbl), "r"(TC_IDESC), "r"(1u));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                 "l"(dal), "l"(dbh), "r"(TC_IDESC), "r"(1u));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    mbar_s));
+            }
+            issued = true;
+            // bounded wait for the MMAs of this chunk (the staging buffers are reused next)
+            uint32_t done = 0;
+            for (long spin = 0; spin < (1L << 24) && !done; ++spin) {
+                asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+                             : "=r"(done)
+                             : "r"(mbar_s), "r"(phase));
+            }
+            // one decision for the whole CTA (the barriers above and below must match)
+            failed = __syncthreads_or(done ? 0 : 1) != 0;
+            if (failed && threadIdx.x == 0 && err) atomicOr(err, 4);
+            phase ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+    }
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 (output rows), 64 columns
+    if (!failed) {
+        float v[TC_N];
+        if (issued) {
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            uint32_t* u = (uint32_t*)v;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+                "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+                : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                  "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                  "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
+                  "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
+                  "=r"(u[29]), "=r"(u[30]), "=r"(u[31]), "=r"(u[32]), "=r"(u[33]), "=r"(u[34]), "=r"(u[35]),
+                  "=r"(u[36]), "=r"(u[37]), "=r"(u[38]), "=r"(u[39]), "=r"(u[40]), "=r"(u[41]), "=r"(u[42]),
+                  "=r"(u[43]), "=r"(u[44]), "=r"(u[45]), "=r"(u[46]), "=r"(u[47]), "=r"(u[48]), "=r"(u[49]),
+                  "=r"(u[50]), "=r"(u[51]), "=r"(u[52]), "=r"(u[53]), "=r"(u[54]), "=r"(u[55]), "=r"(u[56]),
+                  "=r"(u[57]), "=r"(u[58]), "=r"(u[59]), "=r"(u[60]), "=r"(u[61]), "=r"(u[62]), "=r"(u[63])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+        } else {
+#pragma unroll
+            for (int c = 0; c < TC_N; ++c) v[c] = 0.f;
+        }
+        const int gi = tile.i0 + warp * 32 + lane;
+        if (gi < J.m) {
+#pragma unroll
+            for (int c = 0; c < TC_N; ++c) {
+                const int gj = tile.j0 + c;
+                if (gj < J.n) {
+                    double* cp = J.C + gi + (size_t)gj * J.ldc;
+                    *cp = (J.beta == 0.0) ? (double)v[c] : J.beta * *cp + (double)v[c];
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+}
+
+void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st) {
+    if (ntiles <= 0) return;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        attr_set[dev] = true;
+    }
+    k_gemm_tc<<<ntiles, TC_T, TC_SMEM, st>>>(terms, jobs, tiles, err);
+}
+
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -352,7 +352,7 @@ public:
         if (m > 0 && ncol > 0) {
             if (ncol > m) {
                 j.Rt = R_.dalloc((size_t)m * m);
-                R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0, R_.precision() == H2_MIXED);
+                R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0, low_precision(R_.precision()));
             }
             j.B = R_.dalloc((size_t)m * std::min(m, ncol));
         }
@@ -377,7 +377,7 @@ public:
             out[i].ldu = j.m;
         }
         R_.flush_copy();
-        if (R_.precision() == H2_MIXED) {
+        if (low_precision(R_.precision())) {
             // FP32 sweeps accumulate V, then C = B V in FP64 replaces B
             std::vector<double*> V64(jobs_.size(), nullptr), C(jobs_.size(), nullptr);
             for (size_t i = 0; i < jobs_.size(); ++i) {
@@ -1656,6 +1656,7 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     H2_CUDA(cudaGetLastError());
     H2_CUDA(cudaStreamSynchronize(st));
     if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
+    if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
     if (opts && opts->stats) {
         h2_stats* S = opts->stats;
@@ -1723,7 +1724,7 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
     for (int i = 0; i < count; ++i)
         if (!Z[i] || !X[i] || !Y[i]) return H2_ERR_ARG;
     if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
-                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED)))
+                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
         return H2_ERR_ARG;
     // a Z may not appear twice, nor as an operand of another product (its swap would race)
     for (int i = 0; i < count; ++i)
@@ -1813,7 +1814,7 @@ extern "C" int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, 
     using namespace h2;
     if (!Z || !X || !Y) return H2_ERR_ARG;
     if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
-                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED)))
+                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
         return H2_ERR_ARG;
     if (X->st->fingerprint != Y->st->fingerprint || X->st->fingerprint != Z->st->fingerprint) return H2_ERR_SHAPE;
     if (!same_row_basis(Z, X) || !same_col_basis(Z, Y)) return H2_ERR_UNSUPPORTED;

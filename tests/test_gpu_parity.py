@@ -5,8 +5,9 @@ sphere workload, against the definition Z + X Y on sampled rows.
 Tolerances: exact mode (eps = 0) reproduces Z + XY to 1e-12 in FP64; the
 truncated product matches the oracle within 10 eps in relative Frobenius
 norm (the target the method is built to) and the dense product within eps.
-The mixed mode runs the contractions in FP32 (unit roundoff 6e-8), so its
-exact-mode bound is 1e-5 and its truncated bound stays 10 eps for
+The mixed mode runs the contractions in FP32 (unit roundoff 6e-8) and the
+tensor-core mode in a TF32 three-term split (about 21 bits, 5e-7), so their
+exact-mode bound is 1e-5 and their truncated bound stays 10 eps for
 eps >= 1e-6."""
 import numpy as np
 import pytest
@@ -44,7 +45,7 @@ def run_pair(pts, leaf, eta, order, eps, kx, ky, kz, precision):
     return Z, stats, st, (Xo, Yo, Zo), ref
 
 
-@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED, P.H2_TC])
 def test_c1_sphere_against_oracle(precision):
     """n = 2048 on the sphere, Laplace, leaf 32, eta 2, order 3, X = Y = Z, eps 1e-4."""
     eps = 1e-4
@@ -60,7 +61,7 @@ def test_c1_sphere_against_oracle(precision):
     assert stats["max_rank_a"] > 0 and stats["kernel_launches"] > 0
 
 
-@pytest.mark.parametrize("precision,tol", [(P.H2_FP64, 1e-12), (P.H2_MIXED, 1e-5)])
+@pytest.mark.parametrize("precision,tol", [(P.H2_FP64, 1e-12), (P.H2_MIXED, 1e-5), (P.H2_TC, 1e-5)])
 def test_exact_mode(precision, tol):
     """eps = 0 keeps every nonzero singular value: Z + XY reproduced exactly
     (Sec. 3); X Laplace, Y Yukawa, so XY is not symmetric."""
@@ -75,7 +76,7 @@ def test_exact_mode(precision, tol):
     ("cube", 1024, 32, 1.5, 3, 1e-6, (1, 0, 1)),
     ("sphere", 1000, 20, 2.0, 3, 1e-6, (0, 1, 0)),   # ragged leaves (sizes 15 and 16)
 ])
-@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED, P.H2_TC])
 def test_workload_shapes_against_oracle(geometry, n, leaf, eta, order, eps, kernels, precision):
     pts = synth.make_points(geometry, n, 5)
     Z, stats, st, (Xo, Yo, Zo), ref = run_pair(pts, leaf, eta, order, eps, *kernels, precision)
