@@ -244,6 +244,7 @@ def ours_arm(args):
     dt64, wall64, st64, info64 = timed(P.H2_FP64, args.steps, args.warmup)
     clocks = sampler.stop()
     dtmx, wallmx, stmx, infomx = timed(P.H2_MIXED, args.steps, max(1, args.warmup // 2))
+    dttc, walltc, sttc, infotc = timed(P.H2_TC, args.steps, max(1, args.warmup // 2))
     # end to end through the public API with host buffers: points host->device,
     # build, product, result structure (ranks) device->host, per step
     e2e_steps = max(1, min(args.steps, 3))
@@ -321,7 +322,12 @@ def ours_arm(args):
                        "parallelism": f"replicas x{world}"},
             "mixed": {"value": w["n"] * world * args.steps / dtmx, "unit": "rows/s",
                       "ms_per_step": 1e3 * dtmx / args.steps, "speedup_vs_fp64": dt64 / dtmx,
-                      "precision": "FP32 products with FP32 accumulation, FP64 QR/SVD"},
+                      "precision": "FP32 products on CUDA cores, FP64 rank decisions"},
+            "tensor_core": {"value": w["n"] * world * args.steps / dttc, "unit": "rows/s",
+                            "ms_per_step": 1e3 * dttc / args.steps, "speedup_vs_fp64": dt64 / dttc,
+                            "precision": "tcgen05 TF32 three-term products, FP32 accumulation in TMEM, FP64 rank decisions",
+                            "gemm_tc_ms_per_step": sum(x["fam_ms"][10] for x in sttc) / len(sttc),
+                            "gemm_tc_gflop_per_step": sum(x["fam_flops"][10] for x in sttc) / len(sttc) / 1e9},
             "e2e": {"value": n_all / e2e_dt, "unit": "rows/s", "h2d_bytes_per_step": int(pts.nbytes),
                     "d2h_bytes_per_step": int(d2h),
                     "note": "h2_build_interp from host points + h2_clone + h2_mul_add + h2_get_structure"},

@@ -20,6 +20,7 @@ CASES = {
     # name: geometry, n, kernel, leaf, eta, order, eps, precision, seed
     "sphere-n32768-fp64": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_FP64, 2309090611),
     "sphere-n32768-mixed": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_MIXED, 2309090611),
+    "sphere-n32768-tc": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_TC, 2309090611),
     "cube-n131072-yukawa-mixed-1e-4": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-4, P.H2_MIXED, 2309090612),
     "cube-n131072-yukawa-mixed-1e-6": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-6, P.H2_MIXED, 2309090612),
     "sphere-n524288-order5-mixed": ("sphere", 524288, O.K_LAPLACE, 64, 2.0, 5, 1e-6, P.H2_MIXED, 2309090614),
