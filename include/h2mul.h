@@ -62,8 +62,9 @@ extern "C" {
  * the choice of ranks always run in FP64.
  *   H2_FP64   every product in FP64 (the plain FP64 GPU form)
  *   H2_MIXED  products in FP32 with FP32 accumulation (CUDA cores), storage in FP64
- *   H2_TC     products on the tensor cores (tcgen05, TF32 three-term split
- *             hi*hi + hi*lo + lo*hi, about 21 bits, FP32 accumulation in TMEM)
+ *   H2_TC     products on the tensor cores (tcgen05 kind::tf32): each FP32
+ *             operand split into three TF32 pieces, the six products of order
+ *             up to 2^-22 accumulated in FP32 in TMEM (FP32 accuracy)
  * In H2_MIXED and H2_TC the wide-to-square reduction ahead of each SVD runs
  * in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the weights'
  * Gram matrices, the pivoted Cholesky, the final sweeps and every rank

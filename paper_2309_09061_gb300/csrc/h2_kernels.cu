@@ -88,16 +88,19 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
 // ------------------------------------------------------------------ GEMM on tcgen05 (H2_TC)
 // Same contract as k_gemm on the 5th-generation tensor cores.  One CTA of 128
 // threads computes a 128 x 64 output tile: the operands of each K chunk are
-// staged in shared memory as TF32 pairs (hi = rna(x), lo = rna(x - hi)) in the
-// K-major core-matrix layout (8 rows x 16 bytes per core matrix), one thread
-// issues tcgen05.mma.kind::tf32 for hi*hi + hi*lo + lo*hi (about 21 bits of
-// the FP32 product), the FP32 accumulator lives in TMEM (128 lanes x 64
-// columns) and is read back with tcgen05.ld.  Waits on the MMA completion
+// rounded to FP32 and staged in shared memory as three TF32 pieces x = x0 +
+// x1 + x2 (each rna of the remainder; together they hold the 24 bits of the
+// FP32 value exactly) in the K-major core-matrix layout (8 rows x
+// 16 bytes per core matrix); one thread issues tcgen05.mma.kind::tf32 for the
+// six products of order up to 2^-22 (a0 b0, a0 b1, a1 b0, a0 b2, a1 b1, a2 b0),
+// so that the FP32 accumulation in TMEM (128 lanes x 64 columns) is the
+// accuracy limit, as for FP32 products; tcgen05.ld reads the tile back.  Waits on the MMA completion
 // barrier are bounded: on timeout the kernel records the error, frees its
 // TMEM and returns.
 constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 128;
 constexpr int TC_A = TC_M * TC_K, TC_B = TC_N * TC_K;  // elements per operand tile
-constexpr size_t TC_SMEM = 2 * (size_t)(TC_A + TC_B) * 4 + 64;
+constexpr int TC_PIECES = 3;
+constexpr size_t TC_SMEM = TC_PIECES * (size_t)(TC_A + TC_B) * 4 + 64;
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
     uint32_t r;
@@ -124,11 +127,9 @@ constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(T
 __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
                                                   const GTile* __restrict__ tiles, int* err) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    uint32_t* a_hi = (uint32_t*)tc_smem;
-    uint32_t* a_lo = a_hi + TC_A;
-    uint32_t* b_hi = a_lo + TC_A;
-    uint32_t* b_lo = b_hi + TC_B;
-    uint64_t* mbar = (uint64_t*)(b_lo + TC_B);
+    uint32_t* as = (uint32_t*)tc_smem;        // pieces 0..2 of A, TC_A elements each
+    uint32_t* bs = as + TC_PIECES * TC_A;     // pieces 0..2 of B, TC_B elements each
+    uint64_t* mbar = (uint64_t*)(bs + TC_PIECES * TC_B);
     uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
@@ -163,10 +164,14 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                 float x = 0.f;
                 if (gi < J.m && gk < P.k)
                     x = (float)(f * (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]));
-                uint32_t h = tf32_rna(x);
-                int ci = core_index(r, kk);
-                a_hi[ci] = h;
-                a_lo[ci] = tf32_rna(x - __uint_as_float(h));
+                const int ci = core_index(r, kk);
+                // three 11-bit pieces hold the 24 bits of x exactly (the remainders are exact in FP32)
+                const uint32_t p0 = tf32_rna(x);
+                const float r1 = x - __uint_as_float(p0);
+                const uint32_t p1 = tf32_rna(r1);
+                as[ci] = p0;
+                as[TC_A + ci] = p1;
+                as[2 * TC_A + ci] = tf32_rna(r1 - __uint_as_float(p1));
             }
             for (int e = threadIdx.x; e < TC_B; e += TC_T) {
                 int c, kk;
@@ -174,32 +179,35 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                 int gj = tile.j0 + c, gk = k0 + kk;
                 float x = 0.f;
                 if (gj < J.n && gk < P.k) x = (float)(P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]);
-                uint32_t h = tf32_rna(x);
-                int ci = core_index(c, kk);
-                b_hi[ci] = h;
-                b_lo[ci] = tf32_rna(x - __uint_as_float(h));
+                const int ci = core_index(c, kk);
+                const uint32_t p0 = tf32_rna(x);
+                const float r1 = x - __uint_as_float(p0);
+                const uint32_t p1 = tf32_rna(r1);
+                bs[ci] = p0;
+                bs[TC_B + ci] = p1;
+                bs[2 * TC_B + ci] = tf32_rna(r1 - __uint_as_float(p1));
             }
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
             if (threadIdx.x == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t ah = (uint32_t)__cvta_generic_to_shared(a_hi), al = (uint32_t)__cvta_generic_to_shared(a_lo);
-                const uint32_t bh = (uint32_t)__cvta_generic_to_shared(b_hi), bl = (uint32_t)__cvta_generic_to_shared(b_lo);
+                const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(as);
+                const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(bs);
+                // (A piece, B piece) pairs of the six products
+                constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
+                constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
                 for (int ks = 0; ks < TC_K / 8; ++ks) {
                     const uint32_t off = ks * 2 * 128;  // two core matrices of K per MMA
-                    const uint64_t dah = smem_desc(ah + off), dal = smem_desc(al + off);
-                    const uint64_t dbh = smem_desc(bh + off), dbl = smem_desc(bl + off);
-                    const uint32_t acc0 = (issued || ks > 0) ? 1u : 0u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                                 "l"(dah), "l"(dbh), "r"(TC_IDESC), "r"(acc0));
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                                 "l"(dah), "l"(dbl), "r"(TC_IDESC), "r"(1u));
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                                 "l"(dal), "l"(dbh), "r"(TC_IDESC), "r"(1u));
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const uint64_t da = smem_desc(a0 + (uint32_t)(pa[q] * TC_A * 4) + off);
+                        const uint64_t db = smem_desc(b0 + (uint32_t)(pb[q] * TC_B * 4) + off);
+                        const uint32_t acc = (issued || ks > 0 || q > 0) ? 1u : 0u;
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                                     "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
+                    }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     mbar_s));

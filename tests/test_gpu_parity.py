@@ -6,7 +6,8 @@ Tolerances: exact mode (eps = 0) reproduces Z + XY to 1e-12 in FP64; the
 truncated product matches the oracle within 10 eps in relative Frobenius
 norm (the target the method is built to) and the dense product within eps.
 The mixed mode runs the contractions in FP32 (unit roundoff 6e-8) and the
-tensor-core mode in a TF32 three-term split (about 21 bits, 5e-7), so their
+tensor-core mode in three TF32 pieces per operand with FP32 accumulation
+(the same accuracy), so their
 exact-mode bound is 1e-5 and their truncated bound stays 10 eps for
 eps >= 1e-6."""
 import numpy as np
