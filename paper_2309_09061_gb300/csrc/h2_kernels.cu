@@ -87,19 +87,22 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
 
 // ------------------------------------------------------------------ GEMM on tcgen05 (H2_TC)
 // Same contract as k_gemm on the 5th-generation tensor cores.  One CTA of 128
-// threads computes a 128 x 64 output tile: the operands of each K chunk are
-// rounded to FP32 and staged in shared memory as three TF32 pieces x = x0 +
-// x1 + x2 (each rna of the remainder; together they hold the 24 bits of the
-// FP32 value exactly) in the K-major core-matrix layout (8 rows x
-// 16 bytes per core matrix); one thread issues tcgen05.mma.kind::tf32 for the
-// six products of order up to 2^-22 (a0 b0, a0 b1, a1 b0, a0 b2, a1 b1, a2 b0),
-// so that the FP32 accumulation in TMEM (128 lanes x 64 columns) is the
-// accuracy limit, as for FP32 products; tcgen05.ld reads the tile back.  Waits on the MMA completion
-// barrier are bounded: on timeout the kernel records the error, frees its
-// TMEM and returns.
+// threads computes a 128 x 64 output tile.  The operands of each K chunk are
+// rounded to FP32 and staged in shared memory as three TF32 pieces x = x0 + x1
+// + x2 (each rna of the remainder; together they hold the 24 bits of the FP32
+// value exactly) in the K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix).  One thread issues tcgen05.mma.kind::tf32: a0 b0 into accumulator
+// D0 and the five correction products of order 2^-11 .. 2^-22 (a0 b1, a1 b0,
+// a0 b2, a1 b1, a2 b0) into D1 (two 128-lane x 64-column FP32 accumulators in
+// TMEM).  The tensor cores' FP32 accumulation rounds toward zero, so the
+// accumulators only live for one chunk: after each chunk tcgen05.ld moves them
+// into registers, where a compensated (Kahan) FP32 sum carries the result.
+// Waits on the MMA completion barrier are bounded: on timeout the kernel
+// records the error, frees its TMEM and returns.
 constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 128;
 constexpr int TC_A = TC_M * TC_K, TC_B = TC_N * TC_K;  // elements per operand tile
 constexpr int TC_PIECES = 3;
+constexpr int TC_COLS = 2 * TC_N;  // two accumulators
 constexpr size_t TC_SMEM = TC_PIECES * (size_t)(TC_A + TC_B) * 4 + 64;
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
@@ -108,7 +111,7 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return r;
 }
 
-// element (row r, k) of a K-major tile of `rows` rows and TC_K columns
+// element (row r, k) of a K-major tile with TC_K columns
 __device__ __forceinline__ int core_index(int r, int k) {
     return ((r >> 3) * (TC_K / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
 }
@@ -124,11 +127,34 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
 constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
 
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+    uint32_t* u = (uint32_t*)v;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+        "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+          "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+          "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31]),
+          "=r"(u[32]), "=r"(u[33]), "=r"(u[34]), "=r"(u[35]), "=r"(u[36]), "=r"(u[37]), "=r"(u[38]), "=r"(u[39]),
+          "=r"(u[40]), "=r"(u[41]), "=r"(u[42]), "=r"(u[43]), "=r"(u[44]), "=r"(u[45]), "=r"(u[46]), "=r"(u[47]),
+          "=r"(u[48]), "=r"(u[49]), "=r"(u[50]), "=r"(u[51]), "=r"(u[52]), "=r"(u[53]), "=r"(u[54]), "=r"(u[55]),
+          "=r"(u[56]), "=r"(u[57]), "=r"(u[58]), "=r"(u[59]), "=r"(u[60]), "=r"(u[61]), "=r"(u[62]), "=r"(u[63])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                 "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
+}
+
 __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
                                                   const GTile* __restrict__ tiles, int* err) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    uint32_t* as = (uint32_t*)tc_smem;        // pieces 0..2 of A, TC_A elements each
-    uint32_t* bs = as + TC_PIECES * TC_A;     // pieces 0..2 of B, TC_B elements each
+    uint32_t* as = (uint32_t*)tc_smem;     // pieces 0..2 of A, TC_A elements each
+    uint32_t* bs = as + TC_PIECES * TC_A;  // pieces 0..2 of B, TC_B elements each
     uint64_t* mbar = (uint64_t*)(bs + TC_PIECES * TC_B);
     uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
     const GTile tile = tiles[blockIdx.x];
@@ -138,7 +164,7 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(tmem_slot)),
-                     "r"(TC_N));
+                     "r"(TC_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 0) {
@@ -149,8 +175,12 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    float sum[TC_N], comp[TC_N], v[TC_N];
+#pragma unroll
+    for (int c = 0; c < TC_N; ++c) sum[c] = comp[c] = 0.f;
     uint32_t phase = 0;
-    bool issued = false, failed = false;
+    bool failed = false;
     for (int it = 0; it < J.nt && !failed; ++it) {
         const GTerm P = terms[J.t0 + it];
         const double f = P.alpha * (P.scale ? *P.scale : 1.0);
@@ -165,7 +195,6 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                 if (gi < J.m && gk < P.k)
                     x = (float)(f * (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]));
                 const int ci = core_index(r, kk);
-                // three 11-bit pieces hold the 24 bits of x exactly (the remainders are exact in FP32)
                 const uint32_t p0 = tf32_rna(x);
                 const float r1 = x - __uint_as_float(p0);
                 const uint32_t p1 = tf32_rna(r1);
@@ -193,7 +222,6 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(as);
                 const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(bs);
-                // (A piece, B piece) pairs of the six products
                 constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
                 constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
@@ -203,17 +231,17 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                     for (int q = 0; q < 6; ++q) {
                         const uint64_t da = smem_desc(a0 + (uint32_t)(pa[q] * TC_A * 4) + off);
                         const uint64_t db = smem_desc(b0 + (uint32_t)(pb[q] * TC_B * 4) + off);
-                        const uint32_t acc = (issued || ks > 0 || q > 0) ? 1u : 0u;
-                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                                     "l"(da), "l"(db), "r"(TC_IDESC), "r"(acc));
+                        // D0 (columns 0..63) takes a0 b0, D1 (columns 64..127) the corrections;
+                        // each starts afresh in every chunk
+                        const uint32_t d = (q == 0) ? tmem : tmem + TC_N;
+                        const uint32_t acc = (ks > 0 || q > 1) ? 1u : 0u;
+                        tc_mma(d, da, db, acc);
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                     mbar_s));
             }
-            issued = true;
-            // bounded wait for the MMAs of this chunk (the staging buffers are reused next)
+            // bounded wait for the MMAs of this chunk
             uint32_t done = 0;
             for (long spin = 0; spin < (1L << 24) && !done; ++spin) {
                 asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
@@ -224,34 +252,28 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
             failed = __syncthreads_or(done ? 0 : 1) != 0;
             if (failed && threadIdx.x == 0 && err) atomicOr(err, 4);
             phase ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!failed) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                // move both accumulators into the compensated register sums
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    tmem_ld64(tmem + lane_base + (uint32_t)(half * TC_N), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+                    for (int c = 0; c < TC_N; ++c) {
+                        const float y = v[c] - comp[c];
+                        const float t = sum[c] + y;
+                        comp[c] = (t - sum[c]) - y;
+                        sum[c] = t;
+                    }
+                }
+                // the next chunk's MMAs overwrite the accumulators only after these loads
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncthreads();
+            }
         }
     }
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 (output rows), 64 columns
     if (!failed) {
-        float v[TC_N];
-        if (issued) {
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-            uint32_t* u = (uint32_t*)v;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
-                "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-                : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-                  "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
-                  "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]),
-                  "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]),
-                  "=r"(u[29]), "=r"(u[30]), "=r"(u[31]), "=r"(u[32]), "=r"(u[33]), "=r"(u[34]), "=r"(u[35]),
-                  "=r"(u[36]), "=r"(u[37]), "=r"(u[38]), "=r"(u[39]), "=r"(u[40]), "=r"(u[41]), "=r"(u[42]),
-                  "=r"(u[43]), "=r"(u[44]), "=r"(u[45]), "=r"(u[46]), "=r"(u[47]), "=r"(u[48]), "=r"(u[49]),
-                  "=r"(u[50]), "=r"(u[51]), "=r"(u[52]), "=r"(u[53]), "=r"(u[54]), "=r"(u[55]), "=r"(u[56]),
-                  "=r"(u[57]), "=r"(u[58]), "=r"(u[59]), "=r"(u[60]), "=r"(u[61]), "=r"(u[62]), "=r"(u[63])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-        } else {
-#pragma unroll
-            for (int c = 0; c < TC_N; ++c) v[c] = 0.f;
-        }
         const int gi = tile.i0 + warp * 32 + lane;
         if (gi < J.m) {
 #pragma unroll
@@ -259,14 +281,15 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                 const int gj = tile.j0 + c;
                 if (gj < J.n) {
                     double* cp = J.C + gi + (size_t)gj * J.ldc;
-                    *cp = (J.beta == 0.0) ? (double)v[c] : J.beta * *cp + (double)v[c];
+                    const double val = (double)sum[c] - (double)comp[c];
+                    *cp = (J.beta == 0.0) ? val : J.beta * *cp + val;
                 }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_N));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
 }
 
 void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st) {
