@@ -1,6 +1,6 @@
 """Run products of the unit-sphere workload once, for profilers.
 
-    python -m paper_2309_09061_gb300.profile_run [--n 8192] [--precision fp64|mixed] [--reps 1]
+    python -m paper_2309_09061_gb300.profile_run [--n 8192] [--precision fp64|mixed|tc] [--reps 1]
 
 Builds the Laplace H^2-matrix (leaf 64, eta 2, Chebyshev order 4) of n seeded
 points on the unit sphere and computes Z <- Z + G G at eps (default 1e-6) on
@@ -21,7 +21,7 @@ import synth  # noqa: E402
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tc"])
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--reps", type=int, default=1)
@@ -30,7 +30,7 @@ def main():
     P.load()
     pts = synth.sphere(a.n, 2309090611)
     G = P.h2_build_interp(pts, P.H2_K_LAPLACE, 64, 2.0, a.order)
-    prec = P.H2_MIXED if a.precision == "mixed" else P.H2_FP64
+    prec = {"fp64": P.H2_FP64, "mixed": P.H2_MIXED, "tc": P.H2_TC}[a.precision]
     for _ in range(a.reps):
         Z = P.h2_clone(G)
         st = P.h2_mul_add(Z, G, G, a.eps, prec)
