@@ -293,8 +293,10 @@ void Runner::flush_pre() {
     PreJob* d = upload(pres_);
     double by = 0.0;
     for (auto& j : pres_) by += 8.0 * ((double)j.m * j.n + (double)j.n * j.n);
+    size_t max_mn = 0;
+    for (auto& j : pres_) max_mn = std::max(max_mn, (size_t)j.m * j.n);
     begin(6);
-    launch_jacobi_pre(d, (int)pres_.size(), st_);
+    launch_jacobi_pre(d, (int)pres_.size(), max_mn, st_);
     end(6, 0.0, by);
     marks_.back().dflops = cnt;
     ++launches;

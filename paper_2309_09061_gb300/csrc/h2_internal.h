@@ -252,7 +252,7 @@ inline bool low_precision(int precision) { return precision != H2_FP64; }
 void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);
-void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st);
+void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_t st);
 void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st);
 void launch_norm(const NormJob* jobs, int njobs, int precision, cudaStream_t st);
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
         const GTerm P = terms[J.t0 + it];
         const double f = P.alpha * (P.scale ? *P.scale : 1.0);
         if (f == 0.0) continue;
+        const float ff = (float)f;
         for (int k0 = 0; k0 < P.k && !failed; k0 += TC_K) {
             // stage op(A)[i0:i0+128, k0:k0+32] and op(B)^T[j0:j0+64, k0:k0+32]
             for (int e = threadIdx.x; e < TC_A; e += TC_T) {
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ term
                 int gi = tile.i0 + r, gk = k0 + kk;
                 float x = 0.f;
                 if (gi < J.m && gk < P.k)
-                    x = (float)(f * (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]));
+                    x = ff * (float)(P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]);
                 const int ci = core_index(r, kk);
                 const uint32_t p0 = tf32_rna(x);
                 const float r1 = x - __uint_as_float(p0);
@@ -540,12 +541,20 @@ __global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
 // of B, accumulated into V (V starts as the identity).  Bounded sweeps.
 constexpr int PMAXSWEEP = 30;
 
-__global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jobs) {
+// W lives in dynamic shared memory when its m * n floats fit in the launch's
+// smem_bytes (sized for the largest job, at most kPreSmem), else in its
+// global workspace.
+constexpr int kPreSmem = 160 * 1024;
+
+__global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jobs, int smem_bytes) {
+    extern __shared__ float pre_smem[];
     __shared__ int rotated;
     const PreJob J = jobs[blockIdx.x];
     const int m = J.m, n = J.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
-    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) J.W[e] = (float)J.B[(e % m) + (size_t)(e / m) * J.ldb];
+    const bool in_smem = (size_t)m * n * sizeof(float) <= (size_t)smem_bytes;
+    float* W = in_smem ? pre_smem : J.W;
+    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) W[e] = (float)J.B[(e % m) + (size_t)(e / m) * J.ldb];
     for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
     __syncthreads();
     const int np = n + (n & 1);
@@ -565,8 +574,8 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
                 int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
                 if (p >= n || q >= n) continue;
                 if (p > q) { int t = p; p = q; q = t; }
-                float* ap = J.W + (size_t)p * m;
-                float* aq = J.W + (size_t)q * m;
+                float* ap = W + (size_t)p * m;
+                float* aq = W + (size_t)q * m;
                 float al = 0.f, be = 0.f, ga = 0.f;
                 for (int i = lane; i < m; i += 32) {
                     float x = ap[i], y = aq[i];
@@ -608,8 +617,6 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
     if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
 }
-
-
 
 // ------------------------------------------------------------------ clustered Jacobi
 // The same sweeps with one matrix shared by a thread-block cluster: the
@@ -817,10 +824,20 @@ void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
     if (cs <= 1 || !launch_jacobi_cluster<double>(jobs, nullptr, njobs, cs, st)) k_svd<<<njobs, JT, 0, st>>>(jobs);
 }
 
-void launch_jacobi_pre(const PreJob* jobs, int njobs, cudaStream_t st) {
+void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_t st) {
     if (njobs <= 0) return;
     int cs = jacobi_cluster_size(njobs);
-    if (cs <= 1 || !launch_jacobi_cluster<float>(nullptr, jobs, njobs, cs, st)) k_jacobi_pre<<<njobs, JT, 0, st>>>(jobs);
+    if (cs <= 1 || !launch_jacobi_cluster<float>(nullptr, jobs, njobs, cs, st)) {
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            cudaFuncSetAttribute(k_jacobi_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
+            attr_set[dev] = true;
+        }
+        const int smem = (max_mn * sizeof(float) <= (size_t)kPreSmem) ? (int)(max_mn * sizeof(float)) : 0;
+        k_jacobi_pre<<<njobs, JT, smem, st>>>(jobs, smem);
+    }
 }
 
 // ------------------------------------------------------------------ pivoted Cholesky
