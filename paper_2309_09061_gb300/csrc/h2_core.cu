@@ -182,7 +182,7 @@ void Runner::flush_gemm(int precision_override) {
     if (jobs_.empty()) return;
     const int pr = precision_override >= 0 ? precision_override : prec_;
     const bool tc = (pr == H2_TC);
-    const int tm = tc ? kTcTileM : 32, tn = tc ? kTcTileN : 32;
+    const int tm = tc ? kTcTileM : (pr == H2_MIXED) ? kF32Tile : 32, tn = tc ? kTcTileN : (pr == H2_MIXED) ? kF32Tile : 32;
     std::vector<GTile> tiles;
     for (int j = 0; j < (int)jobs_.size(); ++j) {
         const GJob& J = jobs_[j];
@@ -217,14 +217,16 @@ void Runner::flush_gemm(int precision_override) {
     jobs_.clear();
 }
 
-void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32) {
+void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32,
+                int* piv) {
     if (m <= 0 || n <= 0) return;
+    if (piv && n > kQRPivMax) throw Error(H2_ERR_UNSUPPORTED, "pivoted QR wider than 2048 columns");
     double* tau = dalloc(std::min(m, n));
     if (fp32) {
         float* a32 = (float*)dalloc(((size_t)m * n + 1) / 2);
-        qrs32_.push_back(QRJob{A, R, nullptr, tau, a32, m, n, lda, ldr, ldq, 0});
+        qrs32_.push_back(QRJob{A, R, nullptr, tau, a32, m, n, lda, ldr, ldq, 0, piv});
     } else {
-        qrs_.push_back(QRJob{A, R, Q, tau, nullptr, m, n, lda, ldr, ldq, q});
+        qrs_.push_back(QRJob{A, R, Q, tau, nullptr, m, n, lda, ldr, ldq, q, piv});
     }
 }
 
@@ -258,9 +260,10 @@ void Runner::flush_qr() {
     qrs_.clear();
 }
 
-void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps) {
+void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
+                 const int* rowperm) {
     ensure_flag();
-    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, nullptr, m, n, ldb, ldu, eps});
+    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, nullptr, m, n, ldb, ldu, eps, rowperm});
     svd_maxn_ = std::max(svd_maxn_, n);
 }
 

@@ -184,7 +184,12 @@ struct QRJob {
     float* A32;   // when set: FP32 workspace (m x n, ld m); A is only read and the
                   // factorisation runs in FP32 (R written in FP64, Q not formed)
     int m, n, lda, ldr, ldq, q;
+    int* piv;     // when set (n <= kQRPivMax): column pivoting, A P = Q R with
+                  // column j of A P = column piv[j] of A
 };
+
+// widest matrix the column-pivoted QR takes (its norms live in shared memory)
+constexpr int kQRPivMax = 2048;
 
 // One-sided Jacobi SVD of B (m x n, in place).  U (m x n, ldu) receives the
 // left singular vectors sorted by decreasing singular value, sigma the values,
@@ -199,6 +204,7 @@ struct SVDJob {
     double* flops;  // optional accumulator: executed sweep flops (12 m per pair)
     int m, n, ldb, ldu;
     double eps;
+    const int* rowperm;  // when set: row i of the singular vectors goes to row rowperm[i] of U
 };
 
 // FP32 preconditioning of a one-sided Jacobi SVD: sweeps on an FP32 copy W of
@@ -246,6 +252,8 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
                  cudaStream_t st);
 // tcgen05 variant: tiles of 128 x 64; *err |= 4 if an MMA wait timed out
 void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st);
+// output tile edge of the batched GEMM in FP32 (H2_MIXED); FP64 uses 32
+constexpr int kF32Tile = 64;
 constexpr int kTcTileM = 128, kTcTileN = 64;
 // precision modes that run the factorisation-side steps in FP32 as well
 inline bool low_precision(int precision) { return precision != H2_FP64; }
@@ -321,9 +329,11 @@ public:
     void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
               const double* scale = nullptr);
     void flush_gemm(int precision_override = -1);
-    void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false);
+    void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false,
+            int* piv = nullptr);
     void flush_qr();
-    void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps);
+    void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
+             const int* rowperm = nullptr);
     void flush_svd();
     void jacobi_pre(const double* B, int m, int n, int ldb, double* V64);
     void flush_pre();

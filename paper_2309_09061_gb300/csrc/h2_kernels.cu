@@ -13,9 +13,8 @@
 namespace h2 {
 
 // ------------------------------------------------------------------ GEMM
-// C = beta C + sum_terms alpha_t op(A_t) op(B_t) over 32 x 32 output tiles.
-// T is the arithmetic type: double (H2_FP64) or float (H2_MIXED; operands are
-// rounded to FP32 when staged in shared memory, accumulation in FP32).
+// C = beta C + sum_terms alpha_t op(A_t) op(B_t) over 32 x 32 output tiles,
+// in FP64 (H2_FP64).
 constexpr int GB = 32;   // tile edge
 constexpr int GK = 16;   // k-chunk
 constexpr int GT = 256;  // threads: 16 x 16, each 2 x 2 outputs
@@ -76,11 +75,98 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
         }
 }
 
+// FP32 form (H2_MIXED) on kF32Tile x kF32Tile output tiles: 256 threads,
+// each a 4 x 4 register block; the FP64 operands are rounded to FP32 (and
+// scaled in FP32) as they are staged, and the next K chunk is fetched into
+// registers while the current one is multiplied.
+constexpr int G32K = 16;
+constexpr int G32E = kF32Tile * G32K / GT;  // staged elements per thread and operand
+
+__global__ void __launch_bounds__(GT) k_gemm32(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
+                                               const GTile* __restrict__ tiles) {
+    __shared__ float As[G32K][kF32Tile + 4];
+    __shared__ float Bs[G32K][kF32Tile + 4];
+    const GTile tile = tiles[blockIdx.x];
+    const GJob J = jobs[tile.job];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    float ra[G32E], rb[G32E];
+    for (int it = 0; it < J.nt; ++it) {
+        const GTerm P = terms[J.t0 + it];
+        const float f = (float)(P.alpha * (P.scale ? *P.scale : 1.0));
+        if (f == 0.f) continue;
+        // op(A)[i0 + i, k0 + kk] and op(B)[k0 + kk, j0 + j] of one chunk into registers
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int r = 0; r < G32E; ++r) {
+                const int e = threadIdx.x + r * GT;
+                int i, kk;
+                if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
+                int gi = tile.i0 + i, gk = k0 + kk;
+                double v = 0.0;
+                if (gi < J.m && gk < P.k) v = P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda];
+                ra[r] = (float)v;
+                int j;
+                if (!P.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
+                const int gj = tile.j0 + j;
+                gk = k0 + kk;
+                double w = 0.0;
+                if (gj < J.n && gk < P.k) w = P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb];
+                rb[r] = (float)w;
+            }
+        };
+        fetch(0);
+        for (int k0 = 0; k0 < P.k; k0 += G32K) {
+#pragma unroll
+            for (int r = 0; r < G32E; ++r) {
+                const int e = threadIdx.x + r * GT;
+                int i, kk;
+                if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
+                As[kk][i] = f * ra[r];
+                int j;
+                if (!P.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
+                Bs[kk][j] = rb[r];
+            }
+            __syncthreads();
+            if (k0 + G32K < P.k) fetch(k0 + G32K);
+#pragma unroll
+            for (int kk = 0; kk < G32K; ++kk) {
+                float a[4], b[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    a[q] = As[kk][tx + 16 * q];
+                    b[q] = Bs[kk][ty + 16 * q];
+                }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int gi = tile.i0 + tx + 16 * a, gj = tile.j0 + ty + 16 * b;
+            if (gi < J.m && gj < J.n) {
+                double* c = J.C + gi + (size_t)gj * J.ldc;
+                const double v = (double)acc[a][b];
+                *c = (J.beta == 0.0) ? v : J.beta * *c + v;
+            }
+        }
+}
+
 void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
                  cudaStream_t st) {
     if (ntiles <= 0) return;
     if (precision == H2_MIXED)
-        k_gemm<float><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
+        k_gemm32<<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
     else
         k_gemm<double><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
 }
@@ -333,6 +419,15 @@ __device__ double block_sum(double v, double* red) {
 // Column-by-column Householder reflections H_j = I - tau_j v_j v_j^* with
 // v_j(j) = 1 (Golub & Van Loan, Sec. 5.1-5.2), applied in place; the
 // orthogonal factor is accumulated backwards when requested.
+//
+// With a pivot array the factorisation is A P = Q R with column pivoting
+// (Businger & Golub 1965; Golub & Van Loan, Sec. 5.4.2): step j moves the
+// column of largest remaining norm to position j.  The remaining norms are
+// downdated by the new row of R after each step and recomputed from the
+// column when the downdate has cancelled below the square root of the unit
+// roundoff (the safeguard of Drmac & Bujanovic 2008).  The norms only steer
+// the pivot choice, so they are kept and downdated in FP32 (recomputations
+// accumulate in FP64).
 constexpr int QT = 256;
 
 template <class T>
@@ -347,9 +442,14 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 template <class T>
 __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
     __shared__ double red[QT / 32];
+    __shared__ int redi[QT / 32];
+    __shared__ float redf[QT / 32];
+    __shared__ float vn1[kQRPivMax], vn2[kQRPivMax];  // remaining / last recomputed column norms
     const QRJob J = jobs[blockIdx.x];
     const int m = J.m, n = J.n, p = m < n ? m : n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = QT / 32;
+    const bool pivot = J.piv != nullptr && n <= kQRPivMax;
+    const float ptol = 3.4526698e-4f;  // sqrt(FP32 unit roundoff)
     T* A;
     int lda;
     if constexpr (sizeof(T) == 4) {
@@ -362,7 +462,72 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
         A = (T*)J.A;
         lda = J.lda;
     }
+    if (pivot) {
+        for (int c = warp; c < n; c += nw) {
+            const T* a = A + (size_t)c * lda;
+            double s = 0.0;
+            for (int i = lane; i < m; i += 32) s += (double)a[i] * (double)a[i];
+            s = warp_sum(s);
+            if (lane == 0) {
+                vn1[c] = vn2[c] = (float)sqrt(s);
+                J.piv[c] = c;
+            }
+        }
+        __syncthreads();
+    }
     for (int j = 0; j < p; ++j) {
+        if (pivot) {
+            // the column of largest remaining norm (lowest index on ties) moves to j
+            float bv = -1.f;
+            int bi = j;
+            for (int c = j + threadIdx.x; c < n; c += QT)
+                if (vn1[c] > bv) {
+                    bv = vn1[c];
+                    bi = c;
+                }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) {
+                redf[warp] = bv;
+                redi[warp] = bi;
+            }
+            __syncthreads();
+            int pc = redi[0];
+            float pv = redf[0];
+            for (int w = 1; w < nw; ++w)
+                if (redf[w] > pv || (redf[w] == pv && redi[w] < pc)) {
+                    pv = redf[w];
+                    pc = redi[w];
+                }
+            if (pc != j) {
+                T* a = A + (size_t)j * lda;
+                T* b = A + (size_t)pc * lda;
+                for (int i = threadIdx.x; i < m; i += QT) {
+                    T t = a[i];
+                    a[i] = b[i];
+                    b[i] = t;
+                }
+                if (threadIdx.x == 0) {
+                    float t = vn1[j];
+                    vn1[j] = vn1[pc];
+                    vn1[pc] = t;
+                    t = vn2[j];
+                    vn2[j] = vn2[pc];
+                    vn2[pc] = t;
+                    int ti = J.piv[j];
+                    J.piv[j] = J.piv[pc];
+                    J.piv[pc] = ti;
+                }
+            }
+            __syncthreads();
+        }
         T* col = A + (size_t)j * lda;
         double s = 0.0;
         for (int i = j + 1 + threadIdx.x; i < m; i += QT) s += (double)col[i] * (double)col[i];
@@ -382,18 +547,45 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
             J.tau[j] = tau;
         }
         __syncthreads();
-        if (tau != 0.0) {
+        if (tau != 0.0 || pivot) {
             const T tt = (T)tau;
             for (int c = j + 1 + warp; c < n; c += nw) {
                 T* a = A + (size_t)c * lda;
-                T w = 0;
-                for (int i = j + 1 + lane; i < m; i += 32) w += col[i] * a[i];
-                w = warp_sum_t<T>(w);
-                __syncwarp();
-                w = (w + a[j]) * tt;
-                __syncwarp();
-                if (lane == 0) a[j] -= w;
-                for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * col[i];
+                if (tau != 0.0) {
+                    T w = 0;
+                    for (int i = j + 1 + lane; i < m; i += 32) w += col[i] * a[i];
+                    w = warp_sum_t<T>(w);
+                    __syncwarp();
+                    w = (w + a[j]) * tt;
+                    __syncwarp();
+                    if (lane == 0) a[j] -= w;
+                    for (int i = j + 1 + lane; i < m; i += 32) a[i] -= w * col[i];
+                }
+                if (pivot) {
+                    // row j of R is final: remove it from the remaining norm
+                    __syncwarp();
+                    float v1 = vn1[c];
+                    bool recompute = false;
+                    if (v1 != 0.f) {
+                        const float r = fabsf((float)a[j]) / v1;
+                        const float rest = fmaxf(0.f, (1.f - r) * (1.f + r));
+                        const float g = v1 / vn2[c];
+                        if (rest * g * g <= ptol)
+                            recompute = true;
+                        else
+                            v1 *= sqrtf(rest);
+                    }
+                    if (recompute) {
+                        double s2 = 0.0;
+                        for (int i = j + 1 + lane; i < m; i += 32) s2 += (double)a[i] * (double)a[i];
+                        v1 = (float)sqrt(warp_sum(s2));
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        vn1[c] = v1;
+                        if (recompute) vn2[c] = v1;
+                    }
+                }
             }
         }
         __syncthreads();
@@ -442,7 +634,10 @@ void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st) {
 // Hestenes' method: plane rotations from the right make the columns of B
 // mutually orthogonal, B J = U Sigma; pairs follow a round-robin tournament so
 // that the pairs of one round are disjoint and run in parallel warps.  The
-// sweep count is bounded; *flag reports a run that hit the bound.
+// sweep count is bounded; *flag reports a run that hit the bound.  A sweep
+// whose rotation measures |g| / sqrt(a b) all stay below 0.1 sqrt(tol) leaves
+// an off-diagonality below tol (quadratic convergence), so the verifying
+// sweep is skipped.
 constexpr int JT = 512;
 constexpr int JMAXSWEEP = 40;
 constexpr int JMAXN = 2048;
@@ -452,93 +647,8 @@ __device__ __forceinline__ int rr_player(int pos, int round, int np) {
     return 1 + (pos - 1 + round) % (np - 1);
 }
 
-__global__ void __launch_bounds__(JT) k_svd(const SVDJob* __restrict__ jobs) {
-    __shared__ int rotated;
-    __shared__ double sig[JMAXN];
-    const SVDJob J = jobs[blockIdx.x];
-    const int m = J.m, n = J.n;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
-    const int np = n + (n & 1);
-    const double tol = (double)(m > 1 ? m : 1) * DBL_EPSILON;
-    // a sweep whose rotation measures all stay below skip = 0.1 sqrt(tol) leaves an
-    // off-diagonality below tol (quadratic convergence): the verifying sweep is skipped
-    const double skip = 0.1 * sqrt(tol);
-    __shared__ int large;
-    int sweep = 0;
-    bool converged = (n < 2);
-    for (; sweep < JMAXSWEEP && !converged; ++sweep) {
-        if (threadIdx.x == 0) {
-            rotated = 0;
-            large = 0;
-        }
-        __syncthreads();
-        for (int round = 0; round < np - 1; ++round) {
-            for (int pr = warp; pr < np / 2; pr += nw) {
-                int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
-                if (p >= n || q >= n) continue;
-                if (p > q) { int t = p; p = q; q = t; }
-                double* ap = J.B + (size_t)p * J.ldb;
-                double* aq = J.B + (size_t)q * J.ldb;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < m; i += 32) {
-                    double x = ap[i], y = aq[i];
-                    al += x * x;
-                    be += y * y;
-                    ga += x * y;
-                }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga != 0.0 && al > 0.0 && be > 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-                    double zeta = (be - al) / (2.0 * ga);
-                    double t = (fabs(zeta) > 1e150) ? 0.5 / zeta
-                                                     : copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    for (int i = lane; i < m; i += 32) {
-                        double x = ap[i], y = aq[i];
-                        ap[i] = c * x - s * y;
-                        aq[i] = s * x + c * y;
-                    }
-                    if (lane == 0) {
-                        rotated = 1;
-                        if (fabs(ga) > skip * sqrt(al) * sqrt(be)) large = 1;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-        converged = (rotated == 0) || (large == 0);
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
-    if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * m * (0.5 * n * (n - 1.0)) * sweep);
-    for (int c = warp; c < n; c += nw) {
-        const double* a = J.B + (size_t)c * J.ldb;
-        double s = 0.0;
-        for (int i = lane; i < m; i += 32) s += a[i] * a[i];
-        s = warp_sum(s);
-        if (lane == 0) sig[c] = sqrt(s);
-    }
-    __syncthreads();
-    for (int c = warp; c < n; c += nw) {
-        const double sc = sig[c];
-        int pos = 0;
-        for (int q = 0; q < n; ++q) pos += (sig[q] > sc) || (sig[q] == sc && q < c);
-        const double* a = J.B + (size_t)c * J.ldb;
-        double* u = J.U + (size_t)pos * J.ldu;
-        const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-        for (int i = lane; i < m; i += 32) u[i] = a[i] * inv;
-        if (lane == 0) J.sigma[pos] = sc;
-    }
-    if (threadIdx.x == 0) {
-        int cnt = 0;
-        for (int q = 0; q < n; ++q) cnt += (sig[q] > J.eps);
-        *J.count = cnt;
-    }
-}
-
-// FP32 preconditioning sweeps: the same rotations as k_svd on an FP32 copy W
-// of B, accumulated into V (V starts as the identity).  Bounded sweeps.
+// FP32 preconditioning sweeps: Hestenes rotations on an FP32 copy W of B,
+// accumulated into V (V starts as the identity).  Bounded sweeps.
 constexpr int PMAXSWEEP = 30;
 
 // W lives in dynamic shared memory when its m * n floats fit in the launch's
@@ -618,71 +728,43 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
 }
 
-// ------------------------------------------------------------------ clustered Jacobi
-// The same sweeps with one matrix shared by a thread-block cluster: the
-// disjoint pairs of a round are spread over the cluster's CTAs (one CTA per
-// SM), a cluster barrier separates rounds, columns move through L2
-// (ld/st.cg), and the rotation flag of a sweep is OR-ed across the cluster
-// through distributed shared memory.  Used when a level has fewer matrices
-// than SMs.  T = double: SVDJob (FP64 sweeps + singular vectors); T = float:
-// PreJob (FP32 preconditioning with accumulated rotations).
+// ------------------------------------------------------------------ clustered FP32 preconditioning
+// The FP32 preconditioning sweeps with one matrix shared by a thread-block
+// cluster: the disjoint pairs of a round are spread over the cluster's CTAs
+// (one CTA per SM), a cluster barrier separates rounds, columns move through
+// L2 (ld/st.cg), and the rotation flags of a sweep are OR-ed across the
+// cluster through distributed shared memory.  Used when a level has fewer
+// matrices than SMs.
 namespace cg = cooperative_groups;
 
-__device__ __forceinline__ float tsqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
-__device__ __forceinline__ double tabs(double x) { return fabs(x); }
-__device__ __forceinline__ float tsign(float x) { return copysignf(1.f, x); }
-__device__ __forceinline__ double tsign(double x) { return copysign(1.0, x); }
-
-template <class T>
-__device__ __forceinline__ void rot_pair(T* ap, T* aq, int m, T c, T s, int lane) {
+__device__ __forceinline__ void rot_pair32(float* ap, float* aq, int m, float c, float s, int lane) {
     for (int i = lane; i < m; i += 32) {
-        T x = __ldcg(ap + i), y = __ldcg(aq + i);
+        float x = __ldcg(ap + i), y = __ldcg(aq + i);
         __stcg(ap + i, c * x - s * y);
         __stcg(aq + i, s * x + c * y);
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(JT) k_jacobi_cluster(const SVDJob* __restrict__ sjobs,
-                                                       const PreJob* __restrict__ pjobs) {
+__global__ void __launch_bounds__(JT) k_jacobi_pre_cluster(const PreJob* __restrict__ jobs) {
     cg::cluster_group cl = cg::this_cluster();
     const int cs = (int)cl.num_blocks(), cr = (int)cl.block_rank();
-    const int job = blockIdx.x / cs;
-    __shared__ int rotated;
-    __shared__ double sig[JMAXN];
-    constexpr bool PRE = sizeof(T) == 4;
+    const PreJob& J = jobs[blockIdx.x / cs];
+    __shared__ int rotated, large;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
-    int m, n;
-    T* B;
-    T* V = nullptr;
-    if constexpr (PRE) {
-        const PreJob& J = pjobs[job];
-        m = J.m;
-        n = J.n;
-        B = (T*)J.W;
-        V = (T*)J.V;
-        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)m * n; e += (int64_t)JT * cs)
-            __stcg(B + e, (T)J.B[(e % m) + (size_t)(e / m) * J.ldb]);
-        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
-            __stcg(V + e, ((e % n) == (e / n)) ? (T)1 : (T)0);
-    } else {
-        const SVDJob& J = sjobs[job];
-        m = J.m;
-        n = J.n;
-        B = (T*)J.B;
-    }
-    const int ldb = PRE ? m : (int)sjobs[job].ldb;
+    const int m = J.m, n = J.n;
+    float* B = J.W;  // m x n, ld m
+    float* V = J.V;  // n x n, ld n
+    for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)m * n; e += (int64_t)JT * cs)
+        __stcg(B + e, (float)J.B[(e % m) + (size_t)(e / m) * J.ldb]);
+    for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
+        __stcg(V + e, ((e % n) == (e / n)) ? 1.f : 0.f);
     cl.sync();
     const int np = n + (n & 1);
-    const T tol = (T)(m > 1 ? m : 1) * (PRE ? (T)FLT_EPSILON : (T)DBL_EPSILON);
-    const int maxsweep = PRE ? PMAXSWEEP : JMAXSWEEP;
-    const T skip = (T)0.1 * tsqrt(tol);
-    __shared__ int large;
+    const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
+    const float skip = 0.1f * sqrtf(tol);
     bool converged = (n < 2);
     int sweep = 0;
-    for (; sweep < maxsweep && !converged; ++sweep) {
+    for (; sweep < PMAXSWEEP && !converged; ++sweep) {
         if (threadIdx.x == 0) {
             rotated = 0;
             large = 0;
@@ -693,28 +775,28 @@ __global__ void __launch_bounds__(JT) k_jacobi_cluster(const SVDJob* __restrict_
                 int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
                 if (p >= n || q >= n) continue;
                 if (p > q) { int t = p; p = q; q = t; }
-                T* ap = B + (size_t)p * ldb;
-                T* aq = B + (size_t)q * ldb;
-                T al = 0, be = 0, ga = 0;
+                float* ap = B + (size_t)p * m;
+                float* aq = B + (size_t)q * m;
+                float al = 0.f, be = 0.f, ga = 0.f;
                 for (int i = lane; i < m; i += 32) {
-                    T x = __ldcg(ap + i), y = __ldcg(aq + i);
+                    float x = __ldcg(ap + i), y = __ldcg(aq + i);
                     al += x * x;
                     be += y * y;
                     ga += x * y;
                 }
-                al = warp_sum_t<T>(al);
-                be = warp_sum_t<T>(be);
-                ga = warp_sum_t<T>(ga);
-                if (ga != (T)0 && al > (T)0 && be > (T)0 && tabs(ga) > tol * tsqrt(al) * tsqrt(be)) {
-                    T zeta = (be - al) / ((T)2 * ga);
-                    const T big = PRE ? (T)1e18 : (T)1e150;
-                    T t = (tabs(zeta) > big) ? (T)0.5 / zeta : tsign(zeta) / (tabs(zeta) + tsqrt((T)1 + zeta * zeta));
-                    T c = (T)1 / tsqrt((T)1 + t * t), s = c * t;
-                    rot_pair<T>(ap, aq, m, c, s, lane);
-                    if (PRE) rot_pair<T>(V + (size_t)p * n, V + (size_t)q * n, n, c, s, lane);
+                al = warp_sum_t<float>(al);
+                be = warp_sum_t<float>(be);
+                ga = warp_sum_t<float>(ga);
+                if (ga != 0.f && al > 0.f && be > 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+                    float zeta = (be - al) / (2.f * ga);
+                    float t = (fabsf(zeta) > 1e18f) ? 0.5f / zeta
+                                                    : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    float c = 1.f / sqrtf(1.f + t * t), s = c * t;
+                    rot_pair32(ap, aq, m, c, s, lane);
+                    rot_pair32(V + (size_t)p * n, V + (size_t)q * n, n, c, s, lane);
                     if (lane == 0) {
                         rotated = 1;
-                        if (tabs(ga) > skip * tsqrt(al) * tsqrt(be)) large = 1;
+                        if (fabsf(ga) > skip * sqrtf(al) * sqrtf(be)) large = 1;
                     }
                 }
             }
@@ -728,43 +810,274 @@ __global__ void __launch_bounds__(JT) k_jacobi_cluster(const SVDJob* __restrict_
         converged = (any == 0) || (anylarge == 0);
         cl.sync();
     }
-    if constexpr (PRE) {
-        const PreJob& J = pjobs[job];
-        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
-            J.V64[e] = (double)__ldcg(V + e);
-        if (cr == 0 && threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
-        return;
-    } else {
-        const SVDJob& J = sjobs[job];
-        if (cr != 0) return;
-        if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
-        if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * m * (0.5 * n * (n - 1.0)) * sweep);
-        for (int c = warp; c < n; c += nw) {
-            const T* a = B + (size_t)c * ldb;
-            double s = 0.0;
+    for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
+        J.V64[e] = (double)__ldcg(V + e);
+    if (cr == 0 && threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
+}
+
+// ------------------------------------------------------------------ FP64 Jacobi
+// Hestenes sweeps in FP64, arranged so that few FP64 warp instructions are
+// spent per column pair (the FP64 pipe bounds this kernel):
+//  * the squared column norms are carried along under the rotations
+//    (a' = a - t g, b' = b + t g for the pair's inner product g) and
+//    recomputed from the columns at every rescaling point, so a pair costs one
+//    inner product instead of three;
+//  * rotations are applied in scaled form, like Gentleman's square-root-free
+//    Givens transformations (1973): column c is held as x_c with true column
+//    d_c x_c, so a rotation costs two FMAs per element (x_p - t1 x_q and
+//    x_q + t2 x_p) and multiplies d_p and d_q by cos(theta); the scales are
+//    folded back into the columns every kFoldRounds rounds and at the end;
+//  * each round first forms the inner products of its pairs (one warp per
+//    pair), then the rotation parameters with one thread per pair, so that the
+//    scalar FP64 work is shared by 32 pairs per instruction, then applies the
+//    rotations (one warp per pair).
+// t = tan(theta) comes from FP32 arithmetic on exactly rescaled FP64 inputs:
+// an angle error of relative size 1e-7 leaves an off-diagonal remainder 1e-7
+// times the one removed, which later sweeps take out (in the final sweeps t is
+// itself tiny).  cos(theta) = (1 + t^2)^(-1/2) is refined to FP64 by Newton's
+// iteration for the reciprocal square root, so that every rotation applied is
+// orthogonal to FP64 rounding.
+//
+// CLUSTER: one matrix per thread-block cluster, the pairs of a round spread
+// over its CTAs (one CTA per SM), the column state (norms, scales) in the
+// shared memory of CTA 0 reached through distributed shared memory, columns
+// through L2 (ld/st.cg) and a cluster barrier between rounds.  Otherwise one
+// CTA per matrix.
+constexpr int kFoldRounds = 64;
+
+template <bool CG>
+__device__ __forceinline__ double ldcol(const double* p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+template <bool CG>
+__device__ __forceinline__ void stcol(double* p, double v) {
+    if constexpr (CG) __stcg(p, v);
+    else *p = v;
+}
+template <bool CLUSTER>
+__device__ __forceinline__ void sync_all() {
+    if constexpr (CLUSTER) cg::this_cluster().sync();
+    else __syncthreads();
+}
+
+// w^(-1/2) for w in [1, 2]: FP32 seed (relative error about 2^-22), then two
+// Newton steps y <- y + y (1 - w y^2) / 2, each squaring the relative error.
+__device__ __forceinline__ double rsqrt_newton(double w) {
+    double y = (double)rsqrtf((float)w);
+    double h = fma(-w * y, y, 1.0);
+    y = fma(0.5 * y, h, y);
+    h = fma(-w * y, y, 1.0);
+    return fma(0.5 * y, h, y);
+}
+
+// t = sign(z) / (|z| + sqrt(1 + z^2)) with z = (b - a) / (2 g): the root of
+// t^2 + 2 z t - 1 = 0 of modulus <= 1, the tangent of the rotation that makes
+// the pair orthogonal.  Both z operands are scaled by the same power of two
+// (exact) so that FP32 can take their quotient.
+__device__ __forceinline__ double jacobi_tan(double a, double b, double g) {
+    const double diff = b - a, g2 = g + g;
+    int e = ((__double2hiint(g2) >> 20) & 0x7ff) - 1023;
+    e = max(-1022, min(1022, e));
+    const double sc = __hiloint2double((1023 - e) << 20, 0);  // 2^-e
+    const double ds = diff * sc;
+    if (fabs(ds) < 1e30) {
+        const float zf = (float)ds / (float)(g2 * sc);
+        const float af = fabsf(zf);
+        const float tf = af > 1e18f ? 0.5f / zf : copysignf(1.f, zf) / (af + sqrtf(fmaf(zf, zf, 1.f)));
+        return (double)tf;
+    }
+    return g / diff;  // |z| > 1e29: t = 1 / (2 z) to relative 1e-58
+}
+
+// Scales folded into the columns (x_c <- d_c x_c, d_c = 1) and squared norms
+// recomputed; first: the scales are not set yet (all one).
+template <bool CLUSTER>
+__device__ void j64_fold(double* B, int ldb, int m, int n, double* nrm, double* dsc, double* dinv, bool first,
+                         int cs, int cr) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
+    for (int c = cr * nw + warp; c < n; c += nw * cs) {
+        double* x = B + (size_t)c * ldb;
+        const double d = first ? 1.0 : dsc[c];
+        double s = 0.0;
+        if (d == 1.0) {
             for (int i = lane; i < m; i += 32) {
-                double v = (double)__ldcg(a + i);
-                s += v * v;
+                const double v = ldcol<CLUSTER>(x + i);
+                s = fma(v, v, s);
             }
-            s = warp_sum(s);
-            if (lane == 0) sig[c] = sqrt(s);
+        } else {
+            for (int i = lane; i < m; i += 32) {
+                const double v = ldcol<CLUSTER>(x + i) * d;
+                stcol<CLUSTER>(x + i, v);
+                s = fma(v, v, s);
+            }
         }
-        __syncthreads();
-        for (int c = warp; c < n; c += nw) {
-            const double sc = sig[c];
-            int pos = 0;
-            for (int q = 0; q < n; ++q) pos += (sig[q] > sc) || (sig[q] == sc && q < c);
-            const T* a = B + (size_t)c * ldb;
-            double* u = J.U + (size_t)pos * J.ldu;
-            const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-            for (int i = lane; i < m; i += 32) u[i] = (double)__ldcg(a + i) * inv;
-            if (lane == 0) J.sigma[pos] = sc;
+        s = warp_sum(s);
+        if (lane == 0) {
+            nrm[c] = s;
+            dsc[c] = 1.0;
+            dinv[c] = 1.0;
         }
+    }
+}
+
+// dynamic shared memory of k_jacobi64: column state (3 n) + per-CTA pair slots (2 kmax)
+static size_t j64_smem_bytes(int n, int cs) {
+    const int np = n + (n & 1), kmax = (np / 2 + cs - 1) / cs;
+    return sizeof(double) * (3 * (size_t)n + 2 * (size_t)kmax);
+}
+
+template <bool CLUSTER>
+__global__ void __launch_bounds__(JT) k_jacobi64(const SVDJob* __restrict__ jobs) {
+    extern __shared__ double j64[];
+    __shared__ int rotated, large, nrot;
+    int cs = 1, cr = 0;
+    if constexpr (CLUSTER) {
+        cs = (int)cg::this_cluster().num_blocks();
+        cr = (int)cg::this_cluster().block_rank();
+    }
+    const SVDJob& J = jobs[blockIdx.x / cs];
+    const int m = J.m, n = J.n, ldb = J.ldb, np = n + (n & 1), half = np / 2;
+    const int kmax = (half + cs - 1) / cs;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
+    double* B = J.B;
+    double* st = j64;
+    if constexpr (CLUSTER) st = cg::this_cluster().map_shared_rank(j64, 0);
+    double* nrm = st;           // squared column norms
+    double* dsc = st + n;       // column scales d_c
+    double* dinv = st + 2 * n;  // 1 / d_c
+    double* gk = j64 + 3 * n;   // per pair of this CTA: inner product, then t1
+    double* t2k = gk + kmax;    // per pair: t2
+    const double tol = (double)(m > 1 ? m : 1) * DBL_EPSILON;
+    const double tol2 = tol * tol, skip2 = 0.01 * tol;  // skip2 = (0.1 sqrt(tol))^2
+    if (threadIdx.x == 0) nrot = 0;
+    int myrot = 0;
+    j64_fold<CLUSTER>(B, ldb, m, n, nrm, dsc, dinv, true, cs, cr);
+    sync_all<CLUSTER>();
+    bool converged = (n < 2);
+    int sweep = 0;
+    for (; sweep < JMAXSWEEP && !converged; ++sweep) {
         if (threadIdx.x == 0) {
-            int cnt = 0;
-            for (int q = 0; q < n; ++q) cnt += (sig[q] > J.eps);
-            *J.count = cnt;
+            rotated = 0;
+            large = 0;
         }
+        for (int round = 0; round < np - 1; ++round) {
+            if (round % kFoldRounds == 0 && (sweep > 0 || round > 0)) {
+                j64_fold<CLUSTER>(B, ldb, m, n, nrm, dsc, dinv, false, cs, cr);
+                sync_all<CLUSTER>();
+            }
+            // inner products of the stored columns, one warp per pair
+            for (int k = warp; k < kmax; k += nw) {
+                const int pr = cr + k * cs;
+                if (pr >= half) break;
+                const int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
+                double g = 0.0;
+                if (p < n && q < n) {
+                    const double* x = B + (size_t)p * ldb;
+                    const double* y = B + (size_t)q * ldb;
+                    for (int i = lane; i < m; i += 32) g = fma(ldcol<CLUSTER>(x + i), ldcol<CLUSTER>(y + i), g);
+                    g = warp_sum(g);
+                }
+                if (lane == 0) gk[k] = g;
+            }
+            __syncthreads();
+            // rotation parameters, one thread per pair
+            for (int k = threadIdx.x; k < kmax; k += JT) {
+                const int pr = cr + k * cs;
+                double t1 = 0.0, t2 = 0.0;
+                int p = 0, q = 0;
+                if (pr < half) {
+                    p = rr_player(pr, round, np);
+                    q = rr_player(np - 1 - pr, round, np);
+                }
+                if (pr < half && p < n && q < n) {
+                    if (p > q) {
+                        const int t = p;
+                        p = q;
+                        q = t;
+                    }
+                    const double dp = dsc[p], dq = dsc[q];
+                    const double ga = gk[k] * dp * dq, al = nrm[p], be = nrm[q];
+                    if (ga != 0.0 && al > 0.0 && be > 0.0 && ga * ga > tol2 * (al * be)) {
+                        const double t = jacobi_tan(al, be, ga);
+                        const double w = fma(t, t, 1.0);
+                        const double c = rsqrt_newton(w), ci = w * c;  // cos and 1 / cos
+                        t1 = t * dq * dinv[p];
+                        t2 = t * dp * dinv[q];
+                        dsc[p] = c * dp;
+                        dsc[q] = c * dq;
+                        dinv[p] *= ci;
+                        dinv[q] *= ci;
+                        nrm[p] = fma(-t, ga, al);
+                        nrm[q] = fma(t, ga, be);
+                        rotated = 1;
+                        if (ga * ga > skip2 * (al * be)) large = 1;
+                        ++myrot;
+                    }
+                }
+                gk[k] = t1;
+                t2k[k] = t2;
+            }
+            __syncthreads();
+            // scaled rotations, one warp per pair (the pair's smaller index first)
+            for (int k = warp; k < kmax; k += nw) {
+                const double t1 = gk[k], t2 = t2k[k];
+                if (t1 == 0.0 && t2 == 0.0) continue;
+                const int pr = cr + k * cs;
+                int p = rr_player(pr, round, np), q = rr_player(np - 1 - pr, round, np);
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                double* x = B + (size_t)p * ldb;
+                double* y = B + (size_t)q * ldb;
+                for (int i = lane; i < m; i += 32) {
+                    const double u = ldcol<CLUSTER>(x + i), v = ldcol<CLUSTER>(y + i);
+                    stcol<CLUSTER>(x + i, fma(-t1, v, u));
+                    stcol<CLUSTER>(y + i, fma(t2, u, v));
+                }
+            }
+            sync_all<CLUSTER>();
+        }
+        int any = rotated, anylarge = large;
+        if constexpr (CLUSTER) {
+            for (int r = 0; r < cs; ++r) {
+                any |= *cg::this_cluster().map_shared_rank(&rotated, r);
+                anylarge |= *cg::this_cluster().map_shared_rank(&large, r);
+            }
+        }
+        converged = (any == 0) || (anylarge == 0);
+        sync_all<CLUSTER>();
+    }
+    j64_fold<CLUSTER>(B, ldb, m, n, nrm, dsc, dinv, false, cs, cr);
+    if (myrot) atomicAdd(&nrot, myrot);
+    sync_all<CLUSTER>();
+    // executed FP64 flops: 2 m per inner product, 4 m per rotation
+    if (threadIdx.x == 0 && J.flops)
+        atomicAdd(J.flops, 4.0 * m * nrot + (cr == 0 ? 2.0 * m * (0.5 * n * (n - 1.0)) * sweep : 0.0));
+    if (cr != 0) return;
+    if (threadIdx.x == 0 && !converged && J.flag) atomicOr(J.flag, 1);
+    for (int c = threadIdx.x; c < n; c += JT) nrm[c] = sqrt(nrm[c]);  // now the singular values
+    __syncthreads();
+    for (int c = warp; c < n; c += nw) {
+        const double sc = nrm[c];
+        int pos = 0;
+        for (int q = lane; q < n; q += 32) pos += (nrm[q] > sc) || (nrm[q] == sc && q < c);
+        pos = __reduce_add_sync(0xffffffffu, pos);
+        const double* a = B + (size_t)c * ldb;
+        double* u = J.U + (size_t)pos * J.ldu;
+        const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+        if (J.rowperm)
+            for (int i = lane; i < m; i += 32) u[J.rowperm[i]] = ldcol<CLUSTER>(a + i) * inv;
+        else
+            for (int i = lane; i < m; i += 32) u[i] = ldcol<CLUSTER>(a + i) * inv;
+        if (lane == 0) J.sigma[pos] = sc;
+    }
+    if (threadIdx.x == 0) {
+        int cnt = 0;
+        for (int q = 0; q < n; ++q) cnt += (nrm[q] > J.eps);
+        *J.count = cnt;
     }
 }
 
@@ -790,17 +1103,17 @@ static int jacobi_cluster_size(int njobs) {
 }
 
 // one CTA per SM: request enough dynamic shared memory that two do not fit
-constexpr int kClusterDynSmem = 120 * 1024;
+constexpr size_t kClusterDynSmem = 120 * 1024;
 
-// returns false (and clears the error) when the cluster launch is refused
-template <class T>
-static bool launch_jacobi_cluster(const SVDJob* sj, const PreJob* pj, int njobs, int cs, cudaStream_t st) {
-    auto kern = k_jacobi_cluster<T>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterDynSmem);
+// cluster launch of nblocks CTAs in clusters of cs; returns false (and clears
+// the error) when the launch is refused
+template <typename... Args>
+static bool launch_clustered(void (*kern)(Args...), int nblocks, int cs, size_t smem, cudaStream_t st, Args... args) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(njobs * cs, 1, 1);
+    cfg.gridDim = dim3(nblocks, 1, 1);
     cfg.blockDim = dim3(JT, 1, 1);
-    cfg.dynamicSmemBytes = kClusterDynSmem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -809,7 +1122,7 @@ static bool launch_jacobi_cluster(const SVDJob* sj, const PreJob* pj, int njobs,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, sj, pj);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -820,14 +1133,19 @@ static bool launch_jacobi_cluster(const SVDJob* sj, const PreJob* pj, int njobs,
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
     if (max_n > JMAXN) throw Error(H2_ERR_UNSUPPORTED, "SVD wider than 2048 columns");
     if (njobs <= 0) return;
-    int cs = jacobi_cluster_size(njobs);
-    if (cs <= 1 || !launch_jacobi_cluster<double>(jobs, nullptr, njobs, cs, st)) k_svd<<<njobs, JT, 0, st>>>(jobs);
+    const int cs = jacobi_cluster_size(njobs);
+    if (cs > 1 && launch_clustered(k_jacobi64<true>, njobs * cs, cs,
+                                   std::max(j64_smem_bytes(max_n, cs), kClusterDynSmem), st, jobs))
+        return;
+    const size_t smem = j64_smem_bytes(max_n, 1);
+    cudaFuncSetAttribute(k_jacobi64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi64<false><<<njobs, JT, smem, st>>>(jobs);
 }
 
 void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_t st) {
     if (njobs <= 0) return;
     int cs = jacobi_cluster_size(njobs);
-    if (cs <= 1 || !launch_jacobi_cluster<float>(nullptr, jobs, njobs, cs, st)) {
+    if (cs <= 1 || !launch_clustered(k_jacobi_pre_cluster, njobs * cs, cs, kClusterDynSmem, st, jobs)) {
         static bool attr_set[64] = {};
         int dev = 0;
         cudaGetDevice(&dev);

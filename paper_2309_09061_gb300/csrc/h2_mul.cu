@@ -336,8 +336,19 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
 // ------------------------------------------------------------------ left singular vectors
 // Batched left singular vectors.  Each job gives Bt (ncol x m, ld ncol), the
 // transpose of the matrix whose left singular vectors are wanted.  Wide
-// matrices (ncol > m) are first reduced by a thin QR of Bt = Q Rt, so that the
-// wanted vectors are those of Rt^* (m x m); then one-sided Jacobi.
+// matrices (ncol > m) are first reduced to m x m, then one-sided Jacobi runs on
+// the reduced matrix:
+//  * eps >= kGramMinEps, or a low-precision mode: the FP64 Gram matrix
+//    G = Bt^* Bt and its pivoted Cholesky factor Z^* Z = G; the wanted vectors
+//    are those of Z^* (Z^* Z^{**} = G = Bt^* Bt).  G resolves singular values
+//    down to about 3e-8 of the largest, well below these tolerances and below
+//    the FP32 sweeps of the low-precision modes.
+//  * otherwise: a column-pivoted thin QR Bt P = Q Rt; the wanted vectors are
+//    those of Rt^* with their rows permuted by P.
+// Jacobi on the transposed triangular factor of a pivoted QR needs far fewer
+// sweeps than on the matrix itself (Drmac & Veselic, SIAM J. Matrix Anal.
+// Appl. 29, 2008); the pivoted Cholesky factor is that factor (up to signs and
+// the column order), so both routes get the short sweep count.
 struct SvdOut {
     double* U = nullptr;
     int ldu = 1;
@@ -348,11 +359,16 @@ public:
     explicit SvdBatch(Runner& R) : R_(R) {}
     // queue a job; the returned index identifies its output after run()
     int add(double* Bt, int ncol, int m, double eps, int* count_slot) {
-        Job j{Bt, ncol, m, eps, count_slot, nullptr, nullptr};
+        Job j{Bt, ncol, m, eps, count_slot, nullptr, nullptr, nullptr, nullptr};
         if (m > 0 && ncol > 0) {
             if (ncol > m) {
                 j.Rt = R_.dalloc((size_t)m * m);
-                R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0, low_precision(R_.precision()));
+                if ((low_precision(R_.precision()) || eps >= kGramMinEps) && m <= 1024) {
+                    j.G = R_.dalloc((size_t)m * m);  // Gram route: formed and factored in run()
+                } else {
+                    if (m <= kQRPivMax) j.piv = (int*)R_.dalloc(((size_t)m + 1) / 2);
+                    R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0, low_precision(R_.precision()), j.piv);
+                }
             }
             j.B = R_.dalloc((size_t)m * std::min(m, ncol));
         }
@@ -363,6 +379,19 @@ public:
     std::vector<SvdOut> run() {
         R_.flush_gemm();
         R_.flush_copy();
+        bool gram = false;
+        for (Job& j : jobs_)
+            if (j.G) {
+                R_.job(j.G, j.m, j.m, j.m, 0.0);
+                R_.term(j.Bt, 1, j.ncol, j.Bt, 0, j.ncol, j.ncol);
+                gram = true;
+            }
+        if (gram) {
+            R_.flush_gemm(H2_FP64);
+            for (Job& j : jobs_)
+                if (j.G) R_.pchol(j.G, j.m, j.m, j.Rt, j.m, kCholTol);
+            R_.flush_pchol();
+        }
         R_.flush_qr();
         std::vector<SvdOut> out(jobs_.size());
         for (size_t i = 0; i < jobs_.size(); ++i) {
@@ -405,7 +434,7 @@ public:
             Job& j = jobs_[i];
             if (!j.B) continue;
             int w = std::min(j.m, j.ncol);
-            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps);
+            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps, j.piv);
         }
         R_.flush_svd();
         jobs_.clear();
@@ -418,8 +447,10 @@ private:
         int ncol, m;
         double eps;
         int* count;
-        double* Rt;
+        double* Rt;   // reduced m x m factor (QR's Rt, or the Cholesky factor Z)
         double* B;
+        int* piv;     // column pivots of the QR of Bt: rows of the wanted vectors
+        double* G;    // Gram route: Bt^* Bt
     };
     Runner& R_;
     std::vector<Job> jobs_;
