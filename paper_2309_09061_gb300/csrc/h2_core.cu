@@ -167,8 +167,8 @@ void Runner::ensure_flag() {
     }
 }
 
-void Runner::job(double* C, int m, int n, int ldc, double beta) {
-    jobs_.push_back(GJob{C, m, n, ldc, (int)terms_.size(), 0, beta});
+void Runner::job(double* C, int m, int n, int ldc, double beta, bool sym) {
+    jobs_.push_back(GJob{C, m, n, ldc, (int)terms_.size(), 0, beta, (sym && m == n) ? 1 : 0});
 }
 
 void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha,
@@ -185,9 +185,11 @@ void Runner::flush_gemm(int precision_override) {
     const int tm = tc ? kTcTileM : (pr == H2_MIXED) ? kF32Tile : 32, tn = tc ? kTcTileN : (pr == H2_MIXED) ? kF32Tile : 32;
     std::vector<GTile> tiles;
     for (int j = 0; j < (int)jobs_.size(); ++j) {
-        const GJob& J = jobs_[j];
+        GJob& J = jobs_[j];
+        if (tm != tn) J.sym = 0;  // symmetric jobs need a square tile grid
         for (int i0 = 0; i0 < J.m; i0 += tm)
-            for (int j0 = 0; j0 < J.n; j0 += tn) tiles.push_back(GTile{j, i0, j0});
+            for (int j0 = 0; j0 < J.n; j0 += tn)
+                if (!J.sym || i0 <= j0) tiles.push_back(GTile{j, i0, j0});
     }
     if (!tiles.empty()) {
         GTerm* dt = upload(terms_);
@@ -198,7 +200,7 @@ void Runner::flush_gemm(int precision_override) {
         for (const GJob& J : jobs_) {
             for (int i = 0; i < J.nt; ++i) {
                 const GTerm& T = terms_[J.t0 + i];
-                fl += 2.0 * J.m * J.n * T.k;
+                fl += (J.sym ? (double)J.m * (J.m + 1) : 2.0 * J.m * J.n) * T.k;
                 by += 8.0 * ((double)J.m * T.k + (double)T.k * J.n);
             }
             by += 8.0 * J.m * J.n * (J.beta != 0.0 ? 2.0 : 1.0);

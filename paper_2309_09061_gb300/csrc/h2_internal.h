@@ -168,6 +168,8 @@ struct GJob {
     int m, n, ldc;
     int t0, nt;
     double beta;
+    int sym;  // C is symmetric (m == n): only tiles with i0 <= j0 are launched, and
+              // the off-diagonal ones also write their transpose
 };
 struct GTile {
     int job, i0, j0;
@@ -325,7 +327,7 @@ public:
     int64_t launches = 0;
 
     // GEMM: start a job, add terms, the job is closed by the next job/flush.
-    void job(double* C, int m, int n, int ldc, double beta);
+    void job(double* C, int m, int n, int ldc, double beta, bool sym = false);
     void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
               const double* scale = nullptr);
     void flush_gemm(int precision_override = -1);

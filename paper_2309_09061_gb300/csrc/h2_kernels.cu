@@ -71,21 +71,45 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
                 double* c = J.C + gi + (size_t)gj * J.ldc;
                 double v = (double)acc[a][b];
                 *c = (J.beta == 0.0) ? v : J.beta * *c + v;
+                if (J.sym && tile.i0 != tile.j0) {
+                    double* ct = J.C + gj + (size_t)gi * J.ldc;
+                    *ct = (J.beta == 0.0) ? v : J.beta * *ct + v;
+                }
             }
         }
 }
 
 // FP32 form (H2_MIXED) on kF32Tile x kF32Tile output tiles: 256 threads,
-// each a 4 x 4 register block; the FP64 operands are rounded to FP32 (and
-// scaled in FP32) as they are staged, and the next K chunk is fetched into
-// registers while the current one is multiplied.
-constexpr int G32K = 16;
+// each a 4 x 4 register block.  The (term, K chunk) sequence of a job is
+// pipelined: while one chunk is multiplied from shared memory, the next one
+// is in flight as raw FP64 values in registers, and it is rounded to FP32 (and
+// scaled in FP32) only when it is stored to shared memory.  The term
+// descriptors and their factors are cached in shared memory, 32 at a time.
+constexpr int G32K = 32;
 constexpr int G32E = kF32Tile * G32K / GT;  // staged elements per thread and operand
+constexpr int G32TB = 32;                   // cached term descriptors
 
-__global__ void __launch_bounds__(GT) k_gemm32(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
+// FP64 -> FP32 with round to nearest (ties away from zero) by integer
+// operations on the IEEE 754 encodings, so that the conversion stays off the
+// FP64 pipe.  Magnitudes below the FP32 normal range give zero, magnitudes
+// from 2^128 up (and NaN) give infinity.
+__device__ __forceinline__ float f64_to_f32(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    unsigned r = __funnelshift_r(lo, hi, 29);  // 9 low exponent bits, 23 leading mantissa bits
+    r += (lo >> 28) & 1u;                      // round on the 29 dropped bits
+    r -= 896u << 23;                           // exponent bias 1023 -> 127
+    const unsigned mag = (e < 897u) ? 0u : (e > 1150u) ? 0x7f800000u : r;
+    return __uint_as_float((hi & 0x80000000u) | mag);
+}
+
+__global__ void __launch_bounds__(GT, 3) k_gemm32(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
                                                const GTile* __restrict__ tiles) {
     __shared__ float As[G32K][kF32Tile + 4];
     __shared__ float Bs[G32K][kF32Tile + 4];
+    __shared__ GTerm tc[G32TB];
+    __shared__ float tf[G32TB];
+    __shared__ int tbase;
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -94,60 +118,104 @@ __global__ void __launch_bounds__(GT) k_gemm32(const GTerm* __restrict__ terms, 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    float ra[G32E], rb[G32E];
-    for (int it = 0; it < J.nt; ++it) {
-        const GTerm P = terms[J.t0 + it];
-        const float f = (float)(P.alpha * (P.scale ? *P.scale : 1.0));
-        if (f == 0.f) continue;
-        // op(A)[i0 + i, k0 + kk] and op(B)[k0 + kk, j0 + j] of one chunk into registers
-        auto fetch = [&](int k0) {
-#pragma unroll
-            for (int r = 0; r < G32E; ++r) {
-                const int e = threadIdx.x + r * GT;
-                int i, kk;
-                if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
-                int gi = tile.i0 + i, gk = k0 + kk;
-                double v = 0.0;
-                if (gi < J.m && gk < P.k) v = P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda];
-                ra[r] = (float)v;
-                int j;
-                if (!P.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
-                const int gj = tile.j0 + j;
-                gk = k0 + kk;
-                double w = 0.0;
-                if (gj < J.n && gk < P.k) w = P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb];
-                rb[r] = (float)w;
-            }
-        };
-        fetch(0);
-        for (int k0 = 0; k0 < P.k; k0 += G32K) {
-#pragma unroll
-            for (int r = 0; r < G32E; ++r) {
-                const int e = threadIdx.x + r * GT;
-                int i, kk;
-                if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
-                As[kk][i] = f * ra[r];
-                int j;
-                if (!P.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
-                Bs[kk][j] = rb[r];
-            }
+    if (threadIdx.x == 0) tbase = -G32TB;
+    __syncthreads();
+    // term it of the job from the cache (loads the batch holding it; all threads call this together)
+    auto term_at = [&](int it, GTerm& P, float& f) {
+        if (it < tbase || it >= tbase + G32TB) {
             __syncthreads();
-            if (k0 + G32K < P.k) fetch(k0 + G32K);
-#pragma unroll
-            for (int kk = 0; kk < G32K; ++kk) {
-                float a[4], b[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    a[q] = As[kk][tx + 16 * q];
-                    b[q] = Bs[kk][ty + 16 * q];
-                }
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-#pragma unroll
-                    for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+            const int b0 = it - it % G32TB;
+            if (threadIdx.x < G32TB && b0 + (int)threadIdx.x < J.nt) {
+                const GTerm t = terms[J.t0 + b0 + threadIdx.x];
+                tc[threadIdx.x] = t;
+                tf[threadIdx.x] = (float)(t.alpha * (t.scale ? *t.scale : 1.0));
             }
+            if (threadIdx.x == 0) tbase = b0;
             __syncthreads();
         }
+        P = tc[it - tbase];
+        f = tf[it - tbase];
+    };
+    // the chunk after (it, k0), skipping terms with a zero factor or no columns
+    auto advance = [&](int& it, int& k0, GTerm& P, float& f) -> bool {
+        if (it >= 0 && k0 + G32K < P.k) {
+            k0 += G32K;
+            return true;
+        }
+        for (++it; it < J.nt; ++it) {
+            term_at(it, P, f);
+            if (f != 0.f && P.k > 0) {
+                k0 = 0;
+                return true;
+            }
+        }
+        return false;
+    };
+    double ra[G32E], rb[G32E];
+    auto fetch = [&](const GTerm& P, int k0) {
+#pragma unroll
+        for (int r = 0; r < G32E; ++r) {
+            const int e = threadIdx.x + r * GT;
+            int i, kk;
+            if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
+            int gi = tile.i0 + i, gk = k0 + kk;
+            ra[r] = (gi < J.m && gk < P.k) ? (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]) : 0.0;
+            int j;
+            if (!P.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
+            const int gj = tile.j0 + j;
+            gk = k0 + kk;
+            rb[r] = (gj < J.n && gk < P.k) ? (P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]) : 0.0;
+        }
+    };
+    auto mac = [&](int kk) {
+        float a[4], b[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[q] = As[kk][tx + 16 * q];
+            b[q] = Bs[kk][ty + 16 * q];
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+    };
+    int cit = -1, ck0 = 0;
+    GTerm CP;
+    float cf = 0.f;
+    bool have = advance(cit, ck0, CP, cf);
+    if (have) fetch(CP, ck0);
+    while (have) {
+        // the chunk in flight goes to shared memory, rounded and scaled in FP32
+#pragma unroll
+        for (int r = 0; r < G32E; ++r) {
+            const int e = threadIdx.x + r * GT;
+            int i, kk;
+            if (!CP.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
+            As[kk][i] = cf * f64_to_f32(ra[r]);
+            int j;
+            if (!CP.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
+            Bs[kk][j] = f64_to_f32(rb[r]);
+        }
+        const int kc = min(G32K, CP.k - ck0);
+        int nit = cit, nk0 = ck0;
+        GTerm NP = CP;
+        float nf = cf;
+        const bool more = advance(nit, nk0, NP, nf);  // may sync (term cache)
+        __syncthreads();
+        if (more) fetch(NP, nk0);
+        if (kc == G32K) {
+#pragma unroll
+            for (int kk = 0; kk < G32K; ++kk) mac(kk);
+        } else {
+#pragma unroll 4
+            for (int kk = 0; kk < kc; ++kk) mac(kk);
+        }
+        __syncthreads();
+        cit = nit;
+        ck0 = nk0;
+        CP = NP;
+        cf = nf;
+        have = more;
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -158,6 +226,10 @@ __global__ void __launch_bounds__(GT) k_gemm32(const GTerm* __restrict__ terms, 
                 double* c = J.C + gi + (size_t)gj * J.ldc;
                 const double v = (double)acc[a][b];
                 *c = (J.beta == 0.0) ? v : J.beta * *c + v;
+                if (J.sym && tile.i0 != tile.j0) {
+                    double* ct = J.C + gj + (size_t)gi * J.ldc;
+                    *ct = (J.beta == 0.0) ? v : J.beta * *ct + v;
+                }
             }
         }
 }

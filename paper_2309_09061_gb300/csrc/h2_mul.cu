@@ -278,7 +278,7 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
         int r = Y.other(b);
         int ks = VY.rank[s];
         M[i] = R.dalloc((size_t)std::max(1, ks * ks));
-        R.job(M[i], ks, ks, std::max(1, ks), 0.0);
+        R.job(M[i], ks, ks, std::max(1, ks), 0.0, true);
         T_(R, Y.S(b), mv(TS[b].first, std::max(1, WY.rank[r])), WY.rank[r]);
     }
     R.flush_gemm(H2_FP64);
@@ -310,7 +310,7 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
                 if (Y.kind(b) == ADM) rows += std::min(WY.rank[Y.other(b)], (int)T.size[Y.other(b)]);
             G.rows[s] = G.cols[s] = k;
             G.p[s] = R.dalloc((size_t)std::max(1, k * k));
-            R.job(G.p[s], k, k, std::max(1, k), 0.0);
+            R.job(G.p[s], k, k, std::max(1, k), 0.0, true);
             if (l > 0)
                 R.term(EG[i], 0, std::max(1, k), VY.tr[s], 1, std::max(1, k), VY.rank[Tree::parent(s)]);
             for (int b : Y.row_list(s)) {
@@ -382,7 +382,7 @@ public:
         bool gram = false;
         for (Job& j : jobs_)
             if (j.G) {
-                R_.job(j.G, j.m, j.m, j.m, 0.0);
+                R_.job(j.G, j.m, j.m, j.m, 0.0, true);
                 R_.term(j.Bt, 1, j.ncol, j.Bt, 0, j.ncol, j.ncol);
                 gram = true;
             }
@@ -1082,7 +1082,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                 int t = c0 + i, k = Q.rank[t];
                 int rows = (l > 0) ? Zt.rows[Tree::parent(t)] : 0;
                 Gm.p[t] = R.dalloc((size_t)std::max(1, k * k));
-                R.job(Gm.p[t], k, k, std::max(1, k), 0.0);
+                R.job(Gm.p[t], k, k, std::max(1, k), 0.0, true);
                 if (l > 0) R.term(EG[i], 0, std::max(1, k), Q.tr[t], 1, std::max(1, k), Q.rank[Tree::parent(t)]);
                 for (int n : G.row_list(t)) {
                     if (G.kind(n) != ADM) continue;
