@@ -88,6 +88,7 @@ struct BlockTree {
 struct ProductTree {
     BlockTree nodes;                       // kind ADM / DENSE / SPLIT
     std::vector<std::vector<int>> triples; // per node: list of s
+    std::vector<std::vector<std::pair<int, int>>> tri_blocks;  // per node and triple: blocks (t,s) of X, (s,r) of Y
 };
 ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y);
 

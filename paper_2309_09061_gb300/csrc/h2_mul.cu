@@ -66,6 +66,23 @@ struct PerCl {
     }
 };
 
+// Map from small integer keys (nodes, blocks) to device pointers; clear() is
+// proportional to the keys used since the last clear.
+struct Slots {
+    std::vector<double*> v;
+    std::vector<int> used;
+    explicit Slots(size_t n) : v(n, nullptr) {}
+    double*& operator[](int k) {
+        if (!v[k]) used.push_back(k);
+        return v[k];
+    }
+    bool has(int k) const { return v[k] != nullptr; }
+    void clear() {
+        for (int k : used) v[k] = nullptr;
+        used.clear();
+    }
+};
+
 static void T_(Runner& R, Mv A, Mv B, int k, double alpha = 1.0, const double* scale = nullptr, int flipA = 0,
                int flipB = 0) {
     R.term(A.p, A.tr ^ flipA, A.ld, B.p, B.tr ^ flipB, B.ld, k, alpha, scale);
@@ -597,13 +614,27 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         // complete QR of VX-hat; tall transposed remainder; SVD
         int* d_counts = (int*)R.dalloc(nl);
         H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
+        // With rows <= k_X the complete Q spans all of K^rows, which contains range(VX):
+        // the identity is an equally valid choice and needs no factorisation.
+        int rid = 0;
+        for (int i = 0; i < nl; ++i)
+            if (rows[i] > 0 && rows[i] <= VX.rank[c0 + i]) rid = std::max(rid, rows[i]);
+        double* ident = nullptr;
+        if (rid > 0) {
+            ident = R.dalloc((size_t)rid * rid);
+            launch_set_identity(ident, rid, rid, rid, R.stream());
+        }
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i, kx = VX.rank[t];
             k1[i] = std::min(rows[i], kx);
             m2[i] = rows[i] - k1[i];
+            QX[i] = R.dalloc((size_t)std::max(1, rows[i] * rows[i]));
+            if (rows[i] > 0 && rows[i] <= kx) {
+                R.copy(ident, rid, QX[i], rows[i], rows[i], rows[i], 0);
+                continue;
+            }
             double* work = R.dalloc((size_t)std::max(1, rows[i] * kx));
             R.copy(VXh[i], rows[i], work, rows[i], rows[i], kx, 0);
-            QX[i] = R.dalloc((size_t)std::max(1, rows[i] * rows[i]));
             R.qr(work, rows[i], kx, rows[i], nullptr, 1, QX[i], rows[i], rows[i]);
         }
         R.flush_copy();
@@ -754,6 +785,9 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         }
     };
     alloc_cup(0);
+    // per-chunk device pointers by node or block (cleared after each chunk)
+    Slots PSY(Y.bt().kind.size()), WN(Y.bt().kind.size()), XV(X.bt().kind.size());
+    Slots U1(nn), U2(nn), U3(nn), L1(nn), R1(nn), CQ(nn);
     // nodes of a level are processed in chunks that bound the scratch
 #ifndef H2_TMAT_CHUNK
 #define H2_TMAT_CHUNK 16384
@@ -766,12 +800,13 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         const std::vector<int> nodes(lv[l].begin() + ch0,
                                      lv[l].begin() + std::min(lv[l].size(), ch0 + kChunkNodes));
         // PSY_sr = P_s S_Y,sr for the admissible Y blocks met at this level
-        std::unordered_map<int, double*> PSY;
+        PSY.clear();
         for (int n : nodes) {
             int t = N.t[n], r = N.s[n];
-            for (int s : G.PT->triples[n]) {
-                int bx = X.block(t, s), by = Y.block(s, r);
-                if (X.kind(bx) != ADM || Y.kind(by) != ADM || PSY.count(by)) continue;
+            const auto& tb = G.PT->tri_blocks[n];
+            for (size_t q = 0; q < tb.size(); ++q) {
+                const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
+                if (X.kind(bx) != ADM || Y.kind(by) != ADM || PSY.has(by)) continue;
                 double* m = R.dalloc((size_t)WX.rank[s] * WY.rank[r]);
                 R.job(m, WX.rank[s], WY.rank[r], WX.rank[s], 0.0);
                 T_(R, mv(P.p[s], std::max(1, P.rows[s])), Y.S(by), VY.rank[s]);
@@ -781,7 +816,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         }
         R.flush_gemm();
         // U1 = S_Z (copied first) + sum_a S_X PSY
-        std::unordered_map<int, double*> U1;
+        U1.clear();
         {
             size_t tot = 0;
             for (int n : nodes) tot += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
@@ -803,8 +838,9 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         for (int n : nodes) {
             int t = N.t[n], r = N.s[n];
             R.job(U1[n], VX.rank[t], WY.rank[r], VX.rank[t], 1.0);
-            for (int s : G.PT->triples[n]) {
-                int bx = X.block(t, s), by = Y.block(s, r);
+            const auto& tb = G.PT->tri_blocks[n];
+            for (size_t q = 0; q < tb.size(); ++q) {
+                const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
                 if (X.kind(bx) == ADM && Y.kind(by) == ADM) {
                     T_(R, X.S(bx), mv(PSY[by], WX.rank[s]), WX.rank[s]);
                     cnt.flops += 2.0 * VX.rank[t] * WY.rank[r] * WX.rank[s];
@@ -814,15 +850,17 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         }
         R.flush_gemm();
         // U2 = Rbar U1 + sum_b A S_Y,  U3 = sum_c S_X B^*  (coupling nodes)
-        std::unordered_map<int, double*> U2, U3;
+        U2.clear();
+        U3.clear();
         for (int n : nodes) {
             if (N.kind[n] == DENSE) continue;
             int t = N.t[n], r = N.s[n];
             U2[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * WY.rank[r]));
             R.job(U2[n], Q.rank[t], WY.rank[r], std::max(1, Q.rank[t]), 0.0);
             R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U1[n], 0, VX.rank[t], VX.rank[t]);
-            for (int s : G.PT->triples[n]) {
-                int bx = X.block(t, s), by = Y.block(s, r);
+            const auto& tb = G.PT->tri_blocks[n];
+            for (size_t q = 0; q < tb.size(); ++q) {
+                const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
                 if (X.kind(bx) != ADM && Y.kind(by) == ADM) {
                     T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
                     cnt.flops += 2.0 * Q.rank[t] * WY.rank[r] * VY.rank[s];
@@ -830,8 +868,8 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
             }
             U3[n] = R.dalloc((size_t)std::max(1, VX.rank[t] * QW.rank[r]));
             R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
-            for (int s : G.PT->triples[n]) {
-                int bx = X.block(t, s), by = Y.block(s, r);
+            for (size_t q = 0; q < tb.size(); ++q) {
+                const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
                 if (X.kind(bx) == ADM && Y.kind(by) != ADM) {
                     T_(R, X.S(bx), mvT(ca.A.at(by), std::max(1, QW.rank[r])), WX.rank[s]);
                     cnt.flops += 2.0 * VX.rank[t] * QW.rank[r] * WX.rank[s];
@@ -887,19 +925,24 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         bool any_dense = false;
         for (int n : nodes) any_dense |= (N.kind[n] == DENSE);
         if (any_dense) {
-            std::unordered_map<int, double*> XV, WN, L1, R1, CQ;
+            XV.clear();
+            WN.clear();
+            L1.clear();
+            R1.clear();
+            CQ.clear();
             for (int n : nodes) {
                 if (N.kind[n] != DENSE) continue;
                 int t = N.t[n], r = N.s[n];
-                for (int s : G.PT->triples[n]) {
-                    int bx = X.block(t, s), by = Y.block(s, r);
-                    if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.count(bx)) {
+                const auto& tb = G.PT->tri_blocks[n];
+                for (size_t q = 0; q < tb.size(); ++q) {
+                    const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
+                    if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.has(bx)) {
                         double* m = R.dalloc((size_t)T.size[t] * VY.rank[s]);
                         R.job(m, (int)T.size[t], VY.rank[s], (int)T.size[t], 0.0);
                         T_(R, X.N(bx), mv(VY.leaf[s], (int)T.size[s]), (int)T.size[s]);
                         XV[bx] = m;
                     }
-                    if (X.kind(bx) == ADM && Y.kind(by) == DENSE && !WN.count(by)) {
+                    if (X.kind(bx) == ADM && Y.kind(by) == DENSE && !WN.has(by)) {
                         double* m = R.dalloc((size_t)WX.rank[s] * T.size[r]);
                         R.job(m, WX.rank[s], (int)T.size[r], WX.rank[s], 0.0);
                         T_(R, mvT(WX.leaf[s], (int)T.size[s]), Y.N(by), (int)T.size[s]);
@@ -917,14 +960,15 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 L1[n] = R.dalloc((size_t)T.size[t] * WY.rank[r]);
                 R.job(L1[n], (int)T.size[t], WY.rank[r], (int)T.size[t], 0.0);
                 R.term(VX.leaf[t], 0, (int)T.size[t], U1[n], 0, VX.rank[t], VX.rank[t]);
-                for (int s : G.PT->triples[n]) {
-                    int bx = X.block(t, s), by = Y.block(s, r);
+                const auto& tb = G.PT->tri_blocks[n];
+                for (size_t q = 0; q < tb.size(); ++q) {
+                    const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
                     if (X.kind(bx) == DENSE && Y.kind(by) == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
                 }
                 R1[n] = R.dalloc((size_t)VX.rank[t] * T.size[r]);
                 R.job(R1[n], VX.rank[t], (int)T.size[r], VX.rank[t], 0.0);
-                for (int s : G.PT->triples[n]) {
-                    int bx = X.block(t, s), by = Y.block(s, r);
+                for (size_t q = 0; q < tb.size(); ++q) {
+                    const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
                     if (X.kind(bx) == ADM && Y.kind(by) == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
                 }
             }
@@ -945,8 +989,9 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 int bz = Z->st->blocks.find(t, r);
                 bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
                 R.job(G.C[n], mt, mr, mt, zd ? 1.0 : 0.0);
-                for (int s : G.PT->triples[n]) {
-                    int bx = X.block(t, s), by = Y.block(s, r);
+                const auto& tb = G.PT->tri_blocks[n];
+                for (size_t q = 0; q < tb.size(); ++q) {
+                    const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
                     if (X.kind(bx) == DENSE && Y.kind(by) == DENSE) {
                         T_(R, X.N(bx), Y.N(by), (int)T.size[s]);
                         cnt.flops += 2.0 * mt * mr * T.size[s];

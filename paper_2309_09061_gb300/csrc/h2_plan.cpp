@@ -165,12 +165,14 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
     P.nodes.nc = X.nc;
     std::vector<std::pair<int, int>> stack{{0, 0}};
     std::vector<int> ss;
+    std::vector<std::pair<int, int>> bb;
     while (!stack.empty()) {
         auto [t, r] = stack.back();
         stack.pop_back();
         bool split = false;
         bool adm = true;
         ss.clear();
+        bb.clear();
         for (int bx : X.by_row[t]) {
             int s = X.s[bx];
             int by = Y.find(s, r);
@@ -180,11 +182,13 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
                 split = true;
             } else {
                 ss.push_back(s);
+                bb.push_back({bx, by});
                 if (kx != ADM && ky != ADM) adm = false;
             }
         }
         int id = P.nodes.add(t, r, split ? SPLIT : (adm ? ADM : DENSE));
         P.triples.push_back(ss);
+        P.tri_blocks.push_back(bb);
         (void)id;
         if (split) {
             for (int i = 1; i >= 0; --i)
