@@ -262,52 +262,63 @@ def ours_arm(args):
     nclusters = info64["nclusters"]
     d2h = w["n"] * 8 + 3 * nclusters * 8 + 2 * nclusters * 4
 
-    # roofline of the dominant kernel family (FP64 form)
-    fam = np.zeros(12)
-    fam_fl = np.zeros(12)
-    fam_by = np.zeros(12)
-    fam_n = np.zeros(12)
-    for s in st64:
-        fam += np.array(s["fam_ms"])
-        fam_fl += np.array(s["fam_flops"])
-        fam_by += np.array(s["fam_bytes"])
-        fam_n += np.array(s["fam_launches"])
-    top = int(np.argmax(fam))
+    # roofline of the dominant kernel family of each form
     peaks = measured_peaks()
     lib_peaks = library_peaks(torch, dev) if rank == 0 else {}
     names = P.FAMILIES
-    avg_ms = fam[top] / max(1.0, fam_n[top])
-    kernel_of = {0: "k_gemm<double>", 1: "k_gemm<float>", 2: "k_qr<double>", 3: "k_qr<float>", 4: "k_pchol",
-                 5: "k_svd / k_jacobi_cluster<double>", 6: "k_jacobi_pre / k_jacobi_cluster<float>", 7: "k_norm",
-                 8: "k_copy", 9: "k_sumsq / k_finite"}
-    if top in (0, 2, 4, 5, 7):  # FP64 arithmetic: bound by the FP64 pipe
-        achieved = fam_fl[top] / (fam[top] / 1e3) / 1e12
-        roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": achieved, "peak": lib_peaks.get("fp64_tflops"),
-                "unit": "TFLOP/s (FP64)",
-                "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (MEASURED_PEAKS.json has no FP64 figure)"}
-    elif top in (1, 3, 6):
-        achieved = fam_fl[top] / (fam[top] / 1e3) / 1e12
-        roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": achieved, "peak": lib_peaks.get("fp32_tflops"),
-                "unit": "TFLOP/s (FP32)", "peak_source": "cuBLAS SGEMM 8192^3 (no TF32) measured in this run"}
-    else:
-        achieved = fam_by[top] / (fam[top] / 1e3) / 1e9
-        roof = {"kernel": kernel_of[top], "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0),
-                "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
-    roof["traffic"] = None
-    roof["avg_launch_ms"] = avg_ms
-    roof["share_of_step"] = float(fam[top] / max(1e-9, fam.sum()))
+    kernel_of = {0: "k_gemm<double>", 1: "k_gemm_f32<false>", 2: "k_qr<double>", 3: "k_qr<float>", 4: "k_pchol",
+                 5: "k_jacobi64", 6: "k_jacobi_pre / k_jacobi_pre_cluster", 7: "k_norm", 8: "k_copy",
+                 9: "k_sumsq / k_finite", 10: "k_gemm_tc", 11: "k_gemm_f32<true>"}
+
+    def sums(stats):
+        out = {k: np.zeros(12) for k in ("ms", "fl", "by", "n")}
+        for s in stats:
+            out["ms"] += np.array(s["fam_ms"])
+            out["fl"] += np.array(s["fam_flops"])
+            out["by"] += np.array(s["fam_bytes"])
+            out["n"] += np.array(s["fam_launches"])
+        return out
+
+    def roofline(f):
+        top = int(np.argmax(f["ms"]))
+        rate = f["fl"][top] / (f["ms"][top] / 1e3) / 1e12
+        if top in (0, 2, 4, 5, 7):  # FP64 arithmetic: bound by the FP64 pipe
+            roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": rate, "peak": lib_peaks.get("fp64_tflops"),
+                    "unit": "TFLOP/s (FP64)",
+                    "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (MEASURED_PEAKS.json has no FP64 figure)"}
+        elif top in (1, 3, 6):
+            roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": rate, "peak": lib_peaks.get("fp32_tflops"),
+                    "unit": "TFLOP/s (FP32)", "peak_source": "cuBLAS SGEMM 8192^3 (no TF32) measured in this run"}
+        elif top == 11:  # double-float: 12 FP32 operations per multiply-add, i.e. 6 per algorithmic flop
+            roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": 6.0 * rate,
+                    "peak": lib_peaks.get("fp32_tflops"), "unit": "TFLOP/s (FP32 operations executed)",
+                    "algorithmic_fp64_equivalent_tflops": rate,
+                    "peak_source": "cuBLAS SGEMM 8192^3 (no TF32) measured in this run"}
+        elif top == 10:
+            roof = {"kernel": kernel_of[top], "bound": "tensor", "achieved": rate,
+                    "peak": peaks.get("bf16_tflops", 1900.0) / 2.0, "unit": "TFLOP/s (algorithmic, TF32 x6)",
+                    "peak_source": "MEASURED_PEAKS.json bf16 burst x 1/2 (nominal TF32:BF16 ratio)"}
+        else:
+            rate = f["by"][top] / (f["ms"][top] / 1e3) / 1e9
+            roof = {"kernel": kernel_of[top], "bound": "hbm", "achieved": rate, "peak": peaks.get("hbm_gbs", 6800.0),
+                    "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+        roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
+        roof["traffic"] = None
+        roof["avg_launch_ms"] = f["ms"][top] / max(1.0, f["n"][top])
+        roof["share_of_step"] = float(f["ms"][top] / max(1e-9, f["ms"].sum()))
+        return roof
+
+    f64s, fmxs = sums(st64), sums(stmx)
+    roof = roofline(f64s)
     roof["peaks_measured_here"] = lib_peaks
-    fam_report = {names[i]: {"ms_per_step": fam[i] / len(st64), "launches_per_step": fam_n[i] / len(st64),
-                             "gflop_per_step": fam_fl[i] / len(st64) / 1e9, "gb_per_step": fam_by[i] / len(st64) / 1e9}
-                  for i in range(10)}
-    fam_mx = np.zeros(12)
-    fam_mx_fl = np.zeros(12)
-    for s in stmx:
-        fam_mx += np.array(s["fam_ms"])
-        fam_mx_fl += np.array(s["fam_flops"])
-    fam_report_mx = {names[i]: {"ms_per_step": fam_mx[i] / len(stmx), "gflop_per_step": fam_mx_fl[i] / len(stmx) / 1e9}
-                     for i in range(10)}
+    roof_mx = roofline(fmxs)
+    fam_report = {names[i]: {"ms_per_step": f64s["ms"][i] / len(st64), "launches_per_step": f64s["n"][i] / len(st64),
+                             "gflop_per_step": f64s["fl"][i] / len(st64) / 1e9,
+                             "gb_per_step": f64s["by"][i] / len(st64) / 1e9}
+                  for i in range(12) if f64s["n"][i] > 0}
+    fam_report_mx = {names[i]: {"ms_per_step": fmxs["ms"][i] / len(stmx), "launches_per_step": fmxs["n"][i] / len(stmx),
+                                "gflop_per_step": fmxs["fl"][i] / len(stmx) / 1e9}
+                     for i in range(12) if fmxs["n"][i] > 0}
 
     n_all = w["n"] * world
     value = n_all * args.steps / dt64
@@ -322,7 +333,9 @@ def ours_arm(args):
                        "parallelism": f"replicas x{world}"},
             "mixed": {"value": w["n"] * world * args.steps / dtmx, "unit": "rows/s",
                       "ms_per_step": 1e3 * dtmx / args.steps, "speedup_vs_fp64": dt64 / dtmx,
-                      "precision": "FP32 products on CUDA cores, FP64 rank decisions"},
+                      "precision": "FP32 products on CUDA cores; Gram matrices and SVD finishing in "
+                                   "double-float FP32 (FP64-accurate); FP64 rank decisions",
+                      "roofline": roof_mx},
             "tensor_core": {"value": w["n"] * world * args.steps / dttc, "unit": "rows/s",
                             "ms_per_step": 1e3 * dttc / args.steps, "speedup_vs_fp64": dt64 / dttc,
                             "precision": "tcgen05 TF32 three-term products, FP32 accumulation in TMEM, FP64 rank decisions",

@@ -115,6 +115,7 @@ typedef struct {
 #define H2_FAM_COPY 8    /* batched copies, scalings, transpositions */
 #define H2_FAM_OTHER 9   /* block norms, finiteness checks */
 #define H2_FAM_GEMMTC 10 /* batched segmented products on tcgen05 (H2_TC) */
+#define H2_FAM_GEMMDF 11 /* FP64-accurate products of H2_MIXED / H2_TC in double-float FP32 arithmetic */
 
 typedef struct {
     double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */

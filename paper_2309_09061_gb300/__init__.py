@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
 
 
 FAMILIES = ["gemm_fp64", "gemm_fp32", "qr_fp64", "qr_fp32", "pchol", "svd_fp64", "svd_fp32_pre", "norm", "copy", "other",
-            "gemm_tc", ""]
+            "gemm_tc", "gemm_df"]
 
 
 class Opts(ctypes.Structure):

@@ -180,9 +180,12 @@ void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int
 
 void Runner::flush_gemm(int precision_override) {
     if (jobs_.empty()) return;
-    const int pr = precision_override >= 0 ? precision_override : prec_;
+    int pr = precision_override >= 0 ? precision_override : prec_;
+    // FP64 products of the low-precision modes run in double-float arithmetic
+    if (pr == H2_FP64 && prec_ != H2_FP64) pr = kGemmDF;
     const bool tc = (pr == H2_TC);
-    const int tm = tc ? kTcTileM : (pr == H2_MIXED) ? kF32Tile : 32, tn = tc ? kTcTileN : (pr == H2_MIXED) ? kF32Tile : 32;
+    const bool f32 = (pr == H2_MIXED || pr == kGemmDF);
+    const int tm = tc ? kTcTileM : f32 ? kF32Tile : 32, tn = tc ? kTcTileN : f32 ? kF32Tile : 32;
     std::vector<GTile> tiles;
     for (int j = 0; j < (int)jobs_.size(); ++j) {
         GJob& J = jobs_[j];
@@ -205,7 +208,7 @@ void Runner::flush_gemm(int precision_override) {
             }
             by += 8.0 * J.m * J.n * (J.beta != 0.0 ? 2.0 : 1.0);
         }
-        const int fam = tc ? 10 : (pr == H2_MIXED) ? 1 : 0;
+        const int fam = tc ? 10 : (pr == H2_MIXED) ? 1 : (pr == kGemmDF) ? 11 : 0;
         if (tc) ensure_flag();
         begin(fam);
         if (tc)

@@ -255,8 +255,11 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
                  cudaStream_t st);
 // tcgen05 variant: tiles of 128 x 64; *err |= 4 if an MMA wait timed out
 void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st);
-// output tile edge of the batched GEMM in FP32 (H2_MIXED); FP64 uses 32
+// output tile edge of the batched GEMM in FP32 (H2_MIXED) and double-float; FP64 uses 32
 constexpr int kF32Tile = 64;
+// launch_gemm precision tag (not an API value): FP64-accurate products in
+// double-float FP32 arithmetic, used for the FP64 products of H2_MIXED and H2_TC
+constexpr int kGemmDF = 100;
 constexpr int kTcTileM = 128, kTcTileN = 64;
 // precision modes that run the factorisation-side steps in FP32 as well
 inline bool low_precision(int precision) { return precision != H2_FP64; }

@@ -79,15 +79,21 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
         }
 }
 
-// FP32 form (H2_MIXED) on kF32Tile x kF32Tile output tiles: 256 threads,
-// each a 4 x 4 register block.  The (term, K chunk) sequence of a job is
-// pipelined: while one chunk is multiplied from shared memory, the next one
-// is in flight as raw FP64 values in registers, and it is rounded to FP32 (and
-// scaled in FP32) only when it is stored to shared memory.  The term
-// descriptors and their factors are cached in shared memory, 32 at a time.
-constexpr int G32K = 32;
-constexpr int G32E = kF32Tile * G32K / GT;  // staged elements per thread and operand
-constexpr int G32TB = 32;                   // cached term descriptors
+// FP32 forms on kF32Tile x kF32Tile output tiles: 256 threads, each a 4 x 4
+// register block.  The (term, K chunk) sequence of a job is pipelined: while
+// one chunk is multiplied from shared memory, the next one is in flight as raw
+// FP64 values in registers and is converted only when it is stored to shared
+// memory.  The term descriptors and their factors are cached in shared memory,
+// 32 at a time.
+//  DF = false (H2_MIXED products): operands rounded to FP32, FP32 accumulation.
+//  DF = true (FP64-accurate products of the low-precision modes): double-float
+//    arithmetic (Dekker 1971).  Every operand is split as v = hi + lo with two
+//    FP32 values (48 bits); a product contributes hi_a hi_b exactly (the FMA
+//    residual) plus the cross terms hi_a lo_b + lo_a hi_b, and the sum is kept
+//    as an unevaluated pair S + s with an error-free TwoSum (Knuth) per term.
+//    Relative accuracy about 2^-46 per product at ~12 FP32 operations per
+//    multiply-add, against the 1/64-rate FP64 pipe.
+constexpr int G32TB = 32;  // cached term descriptors
 
 // FP64 -> FP32 with round to nearest (ties away from zero) by integer
 // operations on the IEEE 754 encodings, so that the conversion stays off the
@@ -103,32 +109,46 @@ __device__ __forceinline__ float f64_to_f32(double v) {
     return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
-__global__ void __launch_bounds__(GT, 3) k_gemm32(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
-                                               const GTile* __restrict__ tiles) {
-    __shared__ float As[G32K][kF32Tile + 4];
-    __shared__ float Bs[G32K][kF32Tile + 4];
+// exact FP32 -> FP64 widening by integer operations (zero for zero input)
+__device__ __forceinline__ double f32_to_f64(float f, double fallback) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    if (e == 255u) return fallback;
+    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+
+template <bool DF>
+__global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __restrict__ terms,
+                                                              const GJob* __restrict__ jobs,
+                                                              const GTile* __restrict__ tiles) {
+    constexpr int KC = DF ? 16 : 32;            // K chunk
+    constexpr int NE = kF32Tile * KC / GT;      // staged elements per thread and operand
+    constexpr int NP = DF ? 2 : 1;              // FP32 planes per operand
+    __shared__ float As[NP][KC][kF32Tile + 4];
+    __shared__ float Bs[NP][KC][kF32Tile + 4];
     __shared__ GTerm tc[G32TB];
-    __shared__ float tf[G32TB];
+    __shared__ double tf[G32TB];
     __shared__ int tbase;
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float acc[4][4];
+    float acc[4][4], cor[4][4];  // cor: low parts of the double-float sums (DF only)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int b = 0; b < 4; ++b) acc[a][b] = cor[a][b] = 0.f;
     if (threadIdx.x == 0) tbase = -G32TB;
     __syncthreads();
     // term it of the job from the cache (loads the batch holding it; all threads call this together)
-    auto term_at = [&](int it, GTerm& P, float& f) {
+    auto term_at = [&](int it, GTerm& P, double& f) {
         if (it < tbase || it >= tbase + G32TB) {
             __syncthreads();
             const int b0 = it - it % G32TB;
             if (threadIdx.x < G32TB && b0 + (int)threadIdx.x < J.nt) {
                 const GTerm t = terms[J.t0 + b0 + threadIdx.x];
                 tc[threadIdx.x] = t;
-                tf[threadIdx.x] = (float)(t.alpha * (t.scale ? *t.scale : 1.0));
+                tf[threadIdx.x] = t.alpha * (t.scale ? *t.scale : 1.0);
             }
             if (threadIdx.x == 0) tbase = b0;
             __syncthreads();
@@ -137,31 +157,31 @@ __global__ void __launch_bounds__(GT, 3) k_gemm32(const GTerm* __restrict__ term
         f = tf[it - tbase];
     };
     // the chunk after (it, k0), skipping terms with a zero factor or no columns
-    auto advance = [&](int& it, int& k0, GTerm& P, float& f) -> bool {
-        if (it >= 0 && k0 + G32K < P.k) {
-            k0 += G32K;
+    auto advance = [&](int& it, int& k0, GTerm& P, double& f) -> bool {
+        if (it >= 0 && k0 + KC < P.k) {
+            k0 += KC;
             return true;
         }
         for (++it; it < J.nt; ++it) {
             term_at(it, P, f);
-            if (f != 0.f && P.k > 0) {
+            if (f != 0.0 && P.k > 0) {
                 k0 = 0;
                 return true;
             }
         }
         return false;
     };
-    double ra[G32E], rb[G32E];
+    double ra[NE], rb[NE];
     auto fetch = [&](const GTerm& P, int k0) {
 #pragma unroll
-        for (int r = 0; r < G32E; ++r) {
+        for (int r = 0; r < NE; ++r) {
             const int e = threadIdx.x + r * GT;
             int i, kk;
-            if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
+            if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % KC; i = e / KC; }
             int gi = tile.i0 + i, gk = k0 + kk;
             ra[r] = (gi < J.m && gk < P.k) ? (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]) : 0.0;
             int j;
-            if (!P.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
+            if (!P.tb) { kk = e % KC; j = e / KC; } else { j = e % kF32Tile; kk = e / kF32Tile; }
             const int gj = tile.j0 + j;
             gk = k0 + kk;
             rb[r] = (gj < J.n && gk < P.k) ? (P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]) : 0.0;
@@ -171,49 +191,94 @@ __global__ void __launch_bounds__(GT, 3) k_gemm32(const GTerm* __restrict__ term
         float a[4], b[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            a[q] = As[kk][tx + 16 * q];
-            b[q] = Bs[kk][ty + 16 * q];
+            a[q] = As[0][kk][tx + 16 * q];
+            b[q] = Bs[0][kk][ty + 16 * q];
         }
+        if constexpr (!DF) {
 #pragma unroll
-        for (int x = 0; x < 4; ++x)
+            for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        } else {
+            float al[4], bl[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                al[q] = As[NP - 1][kk][tx + 16 * q];
+                bl[q] = Bs[NP - 1][kk][ty + 16 * q];
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const float p = __fmul_rn(a[x], b[y]);
+                    float e = __fmaf_rn(a[x], b[y], -p);  // a_hi b_hi - p exactly
+                    e = __fmaf_rn(a[x], bl[y], e);
+                    e = __fmaf_rn(al[x], b[y], e);
+                    const float S = acc[x][y];
+                    const float t = __fadd_rn(S, p);  // TwoSum(S, p)
+                    const float z = __fsub_rn(t, S);
+                    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(t, z)), __fsub_rn(p, z));
+                    cor[x][y] = __fadd_rn(cor[x][y], __fadd_rn(err, e));
+                    acc[x][y] = t;
+                }
+        }
     };
     int cit = -1, ck0 = 0;
     GTerm CP;
-    float cf = 0.f;
+    double cf = 0.0;
     bool have = advance(cit, ck0, CP, cf);
     if (have) fetch(CP, ck0);
     while (have) {
-        // the chunk in flight goes to shared memory, rounded and scaled in FP32
+        // the chunk in flight goes to shared memory (A scaled by the term's factor)
+        const float cf32 = DF ? 0.f : f64_to_f32(cf);
 #pragma unroll
-        for (int r = 0; r < G32E; ++r) {
+        for (int r = 0; r < NE; ++r) {
             const int e = threadIdx.x + r * GT;
             int i, kk;
-            if (!CP.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % G32K; i = e / G32K; }
-            As[kk][i] = cf * f64_to_f32(ra[r]);
-            int j;
-            if (!CP.tb) { kk = e % G32K; j = e / G32K; } else { j = e % kF32Tile; kk = e / kF32Tile; }
-            Bs[kk][j] = f64_to_f32(rb[r]);
+            if (!CP.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % KC; i = e / KC; }
+            int j, kb;
+            if (!CP.tb) { kb = e % KC; j = e / KC; } else { j = e % kF32Tile; kb = e / kF32Tile; }
+            if constexpr (!DF) {
+                As[0][kk][i] = cf32 * f64_to_f32(ra[r]);
+                Bs[0][kb][j] = f64_to_f32(rb[r]);
+            } else {
+                const double va = ra[r] * cf;  // the factor applied in FP64
+                const float ah = f64_to_f32(va), bh = f64_to_f32(rb[r]);
+                As[0][kk][i] = ah;
+                As[1][kk][i] = f64_to_f32(va - f32_to_f64(ah, va));
+                Bs[0][kb][j] = bh;
+                Bs[1][kb][j] = f64_to_f32(rb[r] - f32_to_f64(bh, rb[r]));
+            }
         }
-        const int kc = min(G32K, CP.k - ck0);
+        const int kc = min(KC, CP.k - ck0);
         int nit = cit, nk0 = ck0;
-        GTerm NP = CP;
-        float nf = cf;
-        const bool more = advance(nit, nk0, NP, nf);  // may sync (term cache)
+        GTerm NP_ = CP;
+        double nf = cf;
+        const bool more = advance(nit, nk0, NP_, nf);  // may sync (term cache)
         __syncthreads();
-        if (more) fetch(NP, nk0);
-        if (kc == G32K) {
+        if (more) fetch(NP_, nk0);
+        if (kc == KC) {
 #pragma unroll
-            for (int kk = 0; kk < G32K; ++kk) mac(kk);
+            for (int kk = 0; kk < KC; ++kk) mac(kk);
         } else {
 #pragma unroll 4
             for (int kk = 0; kk < kc; ++kk) mac(kk);
         }
+        if constexpr (DF) {
+            // renormalise the pairs so that the low parts stay small (Fast2Sum)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const float t = __fadd_rn(acc[x][y], cor[x][y]);
+                    cor[x][y] = __fsub_rn(cor[x][y], __fsub_rn(t, acc[x][y]));
+                    acc[x][y] = t;
+                }
+        }
         __syncthreads();
         cit = nit;
         ck0 = nk0;
-        CP = NP;
+        CP = NP_;
         cf = nf;
         have = more;
     }
@@ -224,7 +289,7 @@ __global__ void __launch_bounds__(GT, 3) k_gemm32(const GTerm* __restrict__ term
             const int gi = tile.i0 + tx + 16 * a, gj = tile.j0 + ty + 16 * b;
             if (gi < J.m && gj < J.n) {
                 double* c = J.C + gi + (size_t)gj * J.ldc;
-                const double v = (double)acc[a][b];
+                const double v = DF ? (double)acc[a][b] + (double)cor[a][b] : (double)acc[a][b];
                 *c = (J.beta == 0.0) ? v : J.beta * *c + v;
                 if (J.sym && tile.i0 != tile.j0) {
                     double* ct = J.C + gj + (size_t)gi * J.ldc;
@@ -238,7 +303,9 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
                  cudaStream_t st) {
     if (ntiles <= 0) return;
     if (precision == H2_MIXED)
-        k_gemm32<<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
+        k_gemm_f32<false><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
+    else if (precision == kGemmDF)
+        k_gemm_f32<true><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
     else
         k_gemm<double><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
 }
