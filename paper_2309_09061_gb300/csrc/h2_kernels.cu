@@ -1301,6 +1301,7 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_
 // Symmetric pivoting on the largest remaining diagonal entry (Higham,
 // "Accuracy and Stability of Numerical Algorithms", Sec. 10.3), stopped when
 // the pivot falls below rel_tol times the largest initial diagonal entry.
+// Only the lower triangle of the working copy is read and updated.
 constexpr int CT = 256;
 constexpr int CMAXK = 1024;
 
@@ -1361,17 +1362,21 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
             break;
         }
         const int p = piv;
-        if (p != j) {  // symmetric swap of rows and columns j and p
+        if (p != j) {  // symmetric swap of j and p (j < p) on the lower triangle
+            auto sw = [&](size_t x, size_t y) {
+                double t = W[x];
+                W[x] = W[y];
+                W[y] = t;
+            };
             for (int c = threadIdx.x; c < k; c += CT) {
-                double t = W[j + (size_t)c * k];
-                W[j + (size_t)c * k] = W[p + (size_t)c * k];
-                W[p + (size_t)c * k] = t;
-            }
-            __syncthreads();
-            for (int r = threadIdx.x; r < k; r += CT) {
-                double t = W[r + (size_t)j * k];
-                W[r + (size_t)j * k] = W[r + (size_t)p * k];
-                W[r + (size_t)p * k] = t;
+                if (c < j)
+                    sw(j + (size_t)c * k, p + (size_t)c * k);  // rows j and p left of column j
+                else if (c > j && c < p)
+                    sw(c + (size_t)j * k, p + (size_t)c * k);  // column j between j and p <-> row p
+                else if (c > p)
+                    sw(c + (size_t)j * k, c + (size_t)p * k);  // columns j and p below row p
+                else if (c == j)
+                    sw(j + (size_t)j * k, p + (size_t)p * k);  // the diagonal entries
             }
             if (threadIdx.x == 0) {
                 int t = perm[j];
@@ -1386,11 +1391,14 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
         for (int i = j + 1 + threadIdx.x; i < k; i += CT) W[i + (size_t)j * k] *= inv;
         if (threadIdx.x == 0) W[j + (size_t)j * k] = d;
         __syncthreads();
-        // trailing update of the whole trailing square (kept symmetric for the swaps)
-        const int rem = k - j - 1;
-        for (int64_t e = threadIdx.x; e < (int64_t)rem * rem; e += CT) {
-            int i = j + 1 + (int)(e % rem), l = j + 1 + (int)(e / rem);
-            W[i + (size_t)l * k] -= W[i + (size_t)j * k] * W[l + (size_t)j * k];
+        // trailing update of the lower triangle (one warp per column)
+        {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            for (int l = j + 1 + warp; l < k; l += CT / 32) {
+                const double wl = W[l + (size_t)j * k];
+                if (wl == 0.0) continue;
+                for (int i = l + lane; i < k; i += 32) W[i + (size_t)l * k] -= W[i + (size_t)j * k] * wl;
+            }
         }
         __syncthreads();
     }
