@@ -235,8 +235,12 @@ def ours_arm(args):
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
             dt = float(t.item())
         info = Zs[-1].info()
+        # eps_2 of the last result (Sec. 7: relative spectral error, 20 power-iteration
+        # steps through H^2 matrix-vector products), outside the timed region
+        eps2 = P.h2_product_error(Zs[-1], G, G, G, steps=20, stream=sptr)[0] if rank == 0 else None
         for Z in Zs:
             Z.free()
+        info["eps2"] = eps2
         return dt, wall, stats, info
 
     sampler = ClockSampler(local)
@@ -345,6 +349,10 @@ def ours_arm(args):
                     "d2h_bytes_per_step": int(d2h),
                     "note": "h2_build_interp from host points + h2_clone + h2_mul_add + h2_get_structure"},
             "gpu_launches": int(sum(s["kernel_launches"] for s in st64)),
+            "accuracy": {"eps": w["eps"], "eps2_fp64": info64["eps2"], "eps2_mixed": infomx["eps2"],
+                         "eps2_tensor_core": infotc["eps2"],
+                         "definition": "||Zr - (Z + X Y)||_2 / ||Z + X Y||_2, 20 power-iteration steps "
+                                       "through H2 matrix-vector products (h2_product_error)"},
             "roofline": roof,
             "kernel_families_fp64": fam_report,
             "kernel_families_mixed": fam_report_mx,

@@ -197,6 +197,21 @@ H2_API int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_d
  * A^* e_i.  Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
 H2_API int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t nvec, int trans, const h2_opts* opts);
 
+/* Relative spectral error of a computed product (the eps_2 of Sec. 7):
+ *   *eps2 = ||Zr - (Z0 + X Y)||_2 / ||Z0 + X Y||_2,   *norm = ||Z0 + X Y||_2,
+ * where Zr is the result of h2_mul_add on a copy of Z0 (for example a clone
+ * taken before the call).  Each spectral norm is estimated by `steps` steps of
+ * power iteration on the normal operator A^* A (Sec. 7 uses 20): x is
+ * normalised, the estimate is ||A x|| of the last unit x, then x <- A^* A x.
+ * Every application of A or A^* runs through h2_matvec of the four operands;
+ * no dense matrix is formed.  x0 (host, n doubles in the ORIGINAL point order)
+ * is the start vector; NULL selects x0_i = 1 + 0.37 i / n.  The estimates are
+ * lower bounds that converge to the norms.  All four handles must share one
+ * structure.  Errors: H2_ERR_ARG (NULL pointers, steps outside 1..100000),
+ * H2_ERR_SHAPE (different structures), H2_ERR_OOM, H2_ERR_CUDA. */
+H2_API int h2_product_error(const h2_matrix* Zr, const h2_matrix* Z0, const h2_matrix* X, const h2_matrix* Y,
+                            const double* x0, int steps, const h2_opts* opts, double* eps2, double* norm);
+
 /* Sizes and structure of a handle.  Errors: H2_ERR_ARG. */
 H2_API int h2_info(const h2_matrix* A, h2_info_t* info);
 

@@ -960,3 +960,39 @@ def mul_add(Z: H2Matrix, X: H2Matrix, Y: H2Matrix, eps: float, eps_induced: floa
     colsB = coarsen_rows(G.transpose(), Z.blocks.transpose(), eps)
     F = final_matrix(G, Z.blocks, rowsB, colsB)
     return ProductResult(F, G, rowsA, colsA, rowsB, colsB, PT)
+
+
+# --------------------------------------------------------------------------
+# Sec. 7: the relative spectral error eps_2 of a computed product
+# --------------------------------------------------------------------------
+
+def power_norm(apply, apply_t, x0: np.ndarray, steps: int) -> float:
+    """Spectral norm of an operator A by power iteration on A^* A (Sec. 7 uses
+    20 steps): x is normalised, the estimate is ||A x||, then x <- A^* A x.
+    Returns the estimate of the last step (a lower bound of ||A||_2)."""
+    x = np.array(x0, dtype=np.float64)
+    nx = float(np.linalg.norm(x))
+    est = 0.0
+    for _ in range(steps):
+        if nx == 0.0:
+            break
+        x = x / nx
+        y = apply(x)
+        est = float(np.linalg.norm(y))
+        if est == 0.0:
+            break
+        x = apply_t(y)
+        nx = float(np.linalg.norm(x))
+    return est
+
+
+def spectral_error(Dr: np.ndarray, D0: np.ndarray, DX: np.ndarray, DY: np.ndarray, x0: np.ndarray,
+                   steps: int = 20) -> tuple[float, float]:
+    """(eps_2, ||P||_2) with P = D0 + DX DY the exact product and eps_2 =
+    ||Dr - P||_2 / ||P||_2, both norms by power_norm from the same start vector
+    (Sec. 7).  P is applied as D0 x + DX (DY x), never formed."""
+    P = lambda x: D0 @ x + DX @ (DY @ x)
+    Pt = lambda y: D0.T @ y + DY.T @ (DX.T @ y)
+    p = power_norm(P, Pt, x0, steps)
+    e = power_norm(lambda x: Dr @ x - P(x), lambda y: Dr.T @ y - Pt(y), x0, steps)
+    return (e / p if p > 0.0 else 0.0), p

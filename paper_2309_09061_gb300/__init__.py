@@ -21,8 +21,8 @@ H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
 H2_FP64, H2_MIXED, H2_TC = 0, 1, 2
 
 EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-            "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_free", "h2_error_string",
-            "h2_last_error_message"]
+            "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error",
+            "h2_free", "h2_error_string", "h2_last_error_message"]
 
 
 class H2Error(RuntimeError):
@@ -89,13 +89,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_to_dense_noalloc.argtypes = [vp, vp, i64, vp]
     lib.h2_matvec.argtypes = [vp, vp, vp, i64, ci, vp]
     lib.h2_mul_add_batched.argtypes = [vp, vp, vp, ci, vp, vp]
+    lib.h2_product_error.argtypes = [vp, vp, vp, vp, vp, ci, vp, vp, vp]
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
     lib.h2_error_string.argtypes = [ci]
     lib.h2_last_error_message.restype = ctypes.c_char_p
     for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-              "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched"):
+              "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -231,6 +232,22 @@ def h2_matvec(A: H2Matrix, x, y, trans: bool = False, stream: int | None = None)
     _check(load().h2_matvec(A.handle, x.data_ptr(), y.data_ptr(), nv, 1 if trans else 0, ctypes.byref(o)),
            "h2_matvec")
     return y
+
+
+def h2_product_error(Zr: H2Matrix, Z0: H2Matrix, X: H2Matrix, Y: H2Matrix, x0=None, steps: int = 20,
+                     stream: int | None = None):
+    """(eps2, norm): relative spectral error ||Zr - (Z0 + X Y)||_2 / ||Z0 + X Y||_2 and
+    ||Z0 + X Y||_2 by power iteration (steps steps each) through H^2 matrix-vector
+    products; x0 is an optional float64 start vector (original point order)."""
+    o = _opts(stream=stream)
+    e, nrm = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    xp = None
+    if x0 is not None:
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        xp = x0.ctypes.data_as(ctypes.c_void_p)
+    _check(load().h2_product_error(Zr.handle, Z0.handle, X.handle, Y.handle, xp, int(steps), ctypes.byref(o),
+                                   ctypes.byref(e), ctypes.byref(nrm)), "h2_product_error")
+    return e.value, nrm.value
 
 
 def h2_rows(A: H2Matrix, idx):

@@ -1581,6 +1581,80 @@ static void matvec(const h2_matrix* M, bool trans, const double* x, double* y, i
     H2_CUDA(cudaStreamSynchronize(st));
 }
 
+// ------------------------------------------------------------------ spectral error of a product
+// eps_2 of Sec. 7: the relative spectral error ||Zr - (Z0 + X Y)||_2 / ||Z0 + X Y||_2
+// of a computed product Zr, both spectral norms by power iteration on the
+// normal operator (x <- A^* A x / ||A^* A x||, estimate ||A x|| for the last
+// unit x), every application through H^2 matrix-vector products of the four
+// operands (no dense matrix is formed).
+static void product_error(const h2_matrix* Zr, const h2_matrix* Z0, const h2_matrix* X, const h2_matrix* Y,
+                          const double* x0_host, int steps, cudaStream_t st, double* eps2, double* normp) {
+    const int64_t n = X->st->tree.n;
+    Runner R(st, H2_FP64);
+    double* x = R.dalloc((size_t)n);
+    double* y = R.dalloc((size_t)n);
+    double* t1 = R.dalloc((size_t)n);
+    double* t2 = R.dalloc((size_t)n);
+    double* acc = R.dalloc(1);
+    std::vector<double> h0((size_t)n);
+    for (int64_t i = 0; i < n; ++i) h0[i] = x0_host ? x0_host[i] : 1.0 + 0.37 * (double)i / (double)n;
+    H2_CUDA(cudaMemcpyAsync(x, h0.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    constexpr int64_t kPart = 65536;  // vector pieces, one CTA each
+    // dst = a src + b dst (b = 0: dst = a src)
+    auto axpby = [&](double* dst, const double* src, double a, double b) {
+        for (int64_t o = 0; o < n; o += kPart) {
+            const int len = (int)std::min(kPart, n - o);
+            R.copy(src + o, len, dst + o, len, len, 1, 0, a, nullptr, b);
+        }
+        R.flush_copy();
+    };
+    auto norm2 = [&](const double* v) {
+        std::vector<SumSqJob> jobs;
+        for (int64_t o = 0; o < n; o += kPart) {
+            const int len = (int)std::min(kPart, n - o);
+            jobs.push_back(SumSqJob{v + o, len, 1, len, 0});
+        }
+        H2_CUDA(cudaMemsetAsync(acc, 0, sizeof(double), st));
+        launch_sumsq(R.upload(jobs), (int)jobs.size(), acc, st);
+        double h = 0.0;
+        H2_CUDA(cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        H2_CUDA(cudaStreamSynchronize(st));
+        return std::sqrt(h);
+    };
+    // out = P in (or P^* in), P = Z0 + X Y; with err: out = Zr in - P in
+    auto apply = [&](bool err, bool trans, const double* in, double* out) {
+        matvec(trans ? X : Y, trans, in, t1, 1, st);
+        matvec(trans ? Y : X, trans, t1, t2, 1, st);
+        matvec(Z0, trans, in, out, 1, st);
+        axpby(out, t2, 1.0, 1.0);
+        if (err) {
+            matvec(Zr, trans, in, t1, 1, st);
+            axpby(out, t1, 1.0, -1.0);
+        }
+    };
+    double* start = R.dalloc((size_t)n);
+    axpby(start, x, 1.0, 0.0);
+    auto power = [&](bool err) {
+        axpby(x, start, 1.0, 0.0);
+        double nx = norm2(x), est = 0.0;
+        for (int it = 0; it < steps && nx > 0.0; ++it) {
+            axpby(x, x, 1.0 / nx, 0.0);
+            apply(err, false, x, y);
+            est = norm2(y);
+            if (est == 0.0) break;
+            apply(err, true, y, x);
+            nx = norm2(x);
+        }
+        return est;
+    };
+    const double p = power(false);
+    const double e = power(true);
+    *normp = p;
+    *eps2 = p > 0.0 ? e / p : 0.0;
+    R.release_all();
+    H2_CUDA(cudaStreamSynchronize(st));
+}
+
 // ------------------------------------------------------------------ driver
 // The product block tree depends only on the two block trees: kept on the
 // structure of X, keyed by the fingerprint of Y's structure.
@@ -1878,6 +1952,24 @@ extern "C" int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t
         h2::matvec(A, trans != 0, x, y, nvec, h2::stream_of(opts));
         return H2_OK;
     } catch (const h2::Error& e) {
+        h2_set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        h2_set_last_error(e.what());
+        return H2_ERR_CUDA;
+    }
+}
+
+extern "C" int h2_product_error(const h2_matrix* Zr, const h2_matrix* Z0, const h2_matrix* X, const h2_matrix* Y,
+                                const double* x0, int steps, const h2_opts* opts, double* eps2, double* norm) {
+    using namespace h2;
+    if (!Zr || !Z0 || !X || !Y || !eps2 || !norm || steps < 1 || steps > 100000) return H2_ERR_ARG;
+    const uint64_t f = X->st->fingerprint;
+    if (Y->st->fingerprint != f || Z0->st->fingerprint != f || Zr->st->fingerprint != f) return H2_ERR_SHAPE;
+    try {
+        product_error(Zr, Z0, X, Y, x0, steps, stream_of(opts), eps2, norm);
+        return H2_OK;
+    } catch (const Error& e) {
         h2_set_last_error(e.what());
         return e.code;
     } catch (const std::exception& e) {
