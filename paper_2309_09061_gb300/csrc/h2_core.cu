@@ -186,6 +186,8 @@ void Runner::flush_gemm(int precision_override) {
     const bool tc = (pr == H2_TC);
     const bool f32 = (pr == H2_MIXED || pr == kGemmDF);
     const int tm = tc ? kTcTileM : f32 ? kF32Tile : 32, tn = tc ? kTcTileN : f32 ? kF32Tile : 32;
+    std::vector<SliceSum> sums;
+    if (!tc) split_k(pr, tm, sums);
     std::vector<GTile> tiles;
     for (int j = 0; j < (int)jobs_.size(); ++j) {
         GJob& J = jobs_[j];
@@ -210,16 +212,93 @@ void Runner::flush_gemm(int precision_override) {
         }
         const int fam = tc ? 10 : (pr == H2_MIXED) ? 1 : (pr == kGemmDF) ? 11 : 0;
         if (tc) ensure_flag();
+        SliceSum* ds = sums.empty() ? nullptr : upload(sums);
+        int max_n = 0;
+        for (const SliceSum& s : sums) max_n = std::max(max_n, s.n);
         begin(fam);
         if (tc)
             launch_gemm_tc(dt, dj, dti, (int)tiles.size(), d_flag_, st_);
         else
             launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
+        launch_slice_sum(ds, (int)sums.size(), max_n, st_);
         end(fam, fl, by);
         ++launches;
     }
     terms_.clear();
     jobs_.clear();
+}
+
+// Split-K: when a launch would not fill the GPU, jobs with long K are cut
+// into segments of their (term, K chunk) sequence; each segment writes its
+// partial product to a slice of scratch, and k_slice_sum adds the slices (in
+// order, deterministic) into C with the job's beta.  Terms that straddle a
+// cut are divided by offsetting their operands along K.
+void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums) {
+    const int kc = (pr == kGemmDF || pr == H2_FP64) ? 16 : 32;  // K chunk of the kernel
+    const int per_sm = (pr == kGemmDF) ? 2 : (pr == H2_MIXED) ? 3 : 4;
+    const int64_t target = 2LL * device_sm_count() * per_sm;
+    int64_t ntiles = 0;
+    for (const GJob& J : jobs_) {
+        const int64_t ti = (int64_t)((J.m + tile - 1) / tile), tj = (int64_t)((J.n + tile - 1) / tile);
+        ntiles += J.sym ? ti * (ti + 1) / 2 : ti * tj;
+    }
+    if (ntiles == 0 || ntiles >= target) return;
+    const int want = (int)std::min<int64_t>(16, (target + ntiles - 1) / ntiles);
+    if (want < 2) return;
+    std::vector<GJob> jobs;
+    std::vector<GTerm> terms;
+    jobs.reserve(jobs_.size());
+    terms.reserve(terms_.size());
+    for (const GJob& J : jobs_) {
+        int64_t chunks = 0;
+        for (int i = 0; i < J.nt; ++i) chunks += (terms_[J.t0 + i].k + kc - 1) / kc;
+        const int S = (int)std::min<int64_t>(want, chunks / 8);
+        if (S < 2) {
+            GJob K = J;
+            K.t0 = (int)terms.size();
+            for (int i = 0; i < J.nt; ++i) terms.push_back(terms_[J.t0 + i]);
+            jobs.push_back(K);
+            continue;
+        }
+        const int64_t mn = (int64_t)J.m * J.n;
+        double* W = dalloc((size_t)(mn * S));
+        sums.push_back(SliceSum{J.C, W, J.m, J.n, J.ldc, S, J.beta});
+        // walk the chunk sequence, starting a new slice job at each cut
+        int s = 0;
+        int64_t done = 0, cut = (chunks * 1) / S;
+        GJob cur{W, J.m, J.n, J.m, (int)terms.size(), 0, 0.0, J.sym};
+        for (int i = 0; i < J.nt; ++i) {
+            const GTerm& T = terms_[J.t0 + i];
+            int k0 = 0;
+            while (k0 < T.k) {
+                const int64_t left = (T.k - k0 + kc - 1) / kc;  // chunks left in this term
+                int64_t take = left;
+                if (s < S - 1 && done + left > cut) take = cut - done;
+                if (take > 0) {
+                    const int k1 = std::min(T.k, k0 + (int)(take * kc));
+                    GTerm P = T;
+                    P.k = k1 - k0;
+                    P.A = T.ta ? T.A + k0 : T.A + (size_t)k0 * T.lda;
+                    P.B = T.tb ? T.B + (size_t)k0 * T.ldb : T.B + k0;
+                    terms.push_back(P);
+                    ++cur.nt;
+                    done += take;
+                    k0 = k1;
+                }
+                if (s < S - 1 && done >= cut) {
+                    jobs.push_back(cur);
+                    ++s;
+                    cur = GJob{W + (size_t)s * mn, J.m, J.n, J.m, (int)terms.size(), 0, 0.0, J.sym};
+                    cut = (chunks * (s + 1)) / S;
+                }
+            }
+        }
+        jobs.push_back(cur);
+        for (++s; s < S; ++s)  // slices that received no chunk (not expected) are zero
+            jobs.push_back(GJob{W + (size_t)s * mn, J.m, J.n, J.m, (int)terms.size(), 0, 0.0, J.sym});
+    }
+    jobs_.swap(jobs);
+    terms_.swap(terms);
 }
 
 void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32,

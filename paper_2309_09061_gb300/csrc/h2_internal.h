@@ -250,9 +250,20 @@ struct CopyJob {
     int rows, cols, lds, ldd, trans;
 };
 
+// C = beta C + sum over `slices` partial products W_s (m x n each, ld m,
+// contiguous) of a split-K job.
+struct SliceSum {
+    double* C;
+    const double* W;
+    int m, n, ldc, slices;
+    double beta;
+};
+
 // Kernel launchers (h2_kernels.cu); job arrays are device pointers.
 void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
                  cudaStream_t st);
+void launch_slice_sum(const SliceSum* jobs, int njobs, int max_n, cudaStream_t st);
+int device_sm_count();
 // tcgen05 variant: tiles of 128 x 64; *err |= 4 if an MMA wait timed out
 void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st);
 // output tile edge of the batched GEMM in FP32 (H2_MIXED) and double-float; FP64 uses 32
@@ -335,6 +346,7 @@ public:
     void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
               const double* scale = nullptr);
     void flush_gemm(int precision_override = -1);
+    void split_k(int precision, int tile, std::vector<SliceSum>& sums);
     void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false,
             int* piv = nullptr);
     void flush_qr();

@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
     constexpr int KC = DF ? 16 : 32;            // K chunk
     constexpr int NE = kF32Tile * KC / GT;      // staged elements per thread and operand
     constexpr int NP = DF ? 2 : 1;              // FP32 planes per operand
-    __shared__ float As[NP][KC][kF32Tile + 4];
-    __shared__ float Bs[NP][KC][kF32Tile + 4];
+    __shared__ float As[NP][KC][kF32Tile + 1];  // odd pitch: conflict-free transposed staging
+    __shared__ float Bs[NP][KC][kF32Tile + 1];
     __shared__ GTerm tc[G32TB];
     __shared__ double tf[G32TB];
     __shared__ int tbase;
@@ -297,6 +297,28 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                 }
             }
         }
+}
+
+// C = beta C + sum_s W_s over the partial products of split-K jobs (slices
+// of m x n, ld m, contiguous), summed in slice order.  One CTA per job and
+// 64-column group.
+__global__ void k_slice_sum(const SliceSum* __restrict__ jobs) {
+    const SliceSum J = jobs[blockIdx.x];
+    const int64_t mn = (int64_t)J.m * J.n;
+    const int64_t c0 = (int64_t)blockIdx.y * 64 * J.m;
+    const int64_t c1 = min(mn, c0 + (int64_t)64 * J.m);
+    for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+        double v = 0.0;
+        for (int s = 0; s < J.slices; ++s) v += J.W[e + (size_t)s * mn];
+        const int i = (int)(e % J.m), j = (int)(e / J.m);
+        double* c = J.C + i + (size_t)j * J.ldc;
+        *c = (J.beta == 0.0) ? v : J.beta * *c + v;
+    }
+}
+
+void launch_slice_sum(const SliceSum* jobs, int njobs, int max_n, cudaStream_t st) {
+    if (njobs <= 0 || max_n <= 0) return;
+    k_slice_sum<<<dim3(njobs, (max_n + 63) / 64), 256, 0, st>>>(jobs);
 }
 
 void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int precision,
@@ -1220,7 +1242,9 @@ __global__ void __launch_bounds__(JT) k_jacobi64(const SVDJob* __restrict__ jobs
     }
 }
 
-static int num_sms() {
+int device_sm_count();
+static int num_sms() { return device_sm_count(); }
+int device_sm_count() {
     static int sms[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);

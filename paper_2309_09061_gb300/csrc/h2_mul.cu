@@ -1678,23 +1678,98 @@ static bool same_col_basis(const h2_matrix* A, const h2_matrix* B) {
     return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint;
 }
 
+// A second stream with its own host thread: the row and column sides of each
+// phase are independent, so the column side runs beside the row side and the
+// host work of one overlaps the device work of the other.  Used in the
+// low-precision forms, whose device work per level is shorter than the host
+// work between the level synchronisations; the FP64 form is bound by the
+// device and runs the sides in order on one stream.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    SideStream() { H2_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)); }
+    ~SideStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+
+// `waiter` runs its later work after everything queued so far on `signaller`
+static void stream_after(cudaStream_t waiter, cudaStream_t signaller) {
+    cudaEvent_t e;
+    H2_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    H2_CUDA(cudaEventRecord(e, signaller));
+    H2_CUDA(cudaStreamWaitEvent(waiter, e, 0));
+    H2_CUDA(cudaEventDestroy(e));
+}
+
+// runs f on a host thread (current device) and joins in join() or the destructor
+class Beside {
+public:
+    template <class F>
+    explicit Beside(F&& f) {
+        int dev = 0;
+        H2_CUDA(cudaGetDevice(&dev));
+        th_ = std::thread([this, dev, f = std::forward<F>(f)]() mutable {
+            try {
+                H2_CUDA(cudaSetDevice(dev));
+                f();
+            } catch (...) {
+                err_ = std::current_exception();
+            }
+        });
+    }
+    void join() {
+        if (th_.joinable()) th_.join();
+        if (err_) {
+            std::exception_ptr e = err_;
+            err_ = nullptr;
+            std::rethrow_exception(e);
+        }
+    }
+    ~Beside() {
+        if (th_.joinable()) th_.join();
+    }
+
+private:
+    std::thread th_;
+    std::exception_ptr err_;
+};
+
 static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, const h2_opts* opts) {
     const double eps = opts ? opts->eps : 1e-6;
     const int prec = opts ? opts->precision : H2_FP64;
     cudaStream_t st = stream_of(opts);
     auto t_host0 = std::chrono::steady_clock::now();
+    SideStream side;
     Runner R(st, prec);
-    PhaseClock clk(st);
-    Counts cnt;
+    Runner R2(side.s, prec);  // column sides; its outputs live until the end of the call
+    const bool beside = low_precision(prec);
+    PhaseClock clk(st), clk2(side.s);
+    Counts cnt, cnt2;
     const OpView X{Xm, false}, Y{Ym, false};
     const Tree& T = X.tree();
     clk.mark();
     // phase A: compressed induced row and column bases (prep included)
-    Induced ra = induced_rows(R, X, Y, eps, cnt);
-    clk.mark();
     const OpView Yt{Ym, true}, Xt{Xm, true};
-    Induced ca = induced_rows(R, Yt, Xt, eps, cnt);
-    clk.mark();
+    Induced ra, ca;
+    if (beside) {
+        stream_after(side.s, st);
+        clk2.mark();
+        Beside col([&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2); });
+        ra = induced_rows(R, X, Y, eps, cnt);
+        clk.mark();
+        col.join();
+    } else {
+        ra = induced_rows(R, X, Y, eps, cnt);
+        clk.mark();
+        stream_after(side.s, st);
+        clk2.mark();
+        ca = induced_rows(R2, Yt, Xt, eps, cnt2);
+    }
+    clk2.mark();
+    stream_after(st, side.s);
     // the intermediate H^2-matrix on T^XY
     Intermediate G;
     G.PT = &cached_product_tree(*Xm->st, *Ym->st);
@@ -1756,10 +1831,23 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
         R.launches += 2;
     }
     GView GR{&G, &T, false}, GC{&G, &T, true};
-    Coarse rb = coarsen_rows(R, GR, cmap, w, w2, eps);
-    clk.mark();
-    Coarse cb = coarsen_rows(R, GC, cmap, w, w2, eps);
-    clk.mark();
+    Coarse rb, cb;
+    if (beside) {
+        stream_after(side.s, st);
+        clk2.mark();
+        Beside col([&] { cb = coarsen_rows(R2, GC, cmap, w, w2, eps); });
+        rb = coarsen_rows(R, GR, cmap, w, w2, eps);
+        clk.mark();
+        col.join();
+    } else {
+        rb = coarsen_rows(R, GR, cmap, w, w2, eps);
+        clk.mark();
+        stream_after(side.s, st);
+        clk2.mark();
+        cb = coarsen_rows(R2, GC, cmap, w, w2, eps);
+    }
+    clk2.mark();
+    stream_after(st, side.s);
     std::vector<double*> Up = final_couplings(R, G, T, cmap, rb, cb, Zb, cnt);
     // assemble the result on Z's block tree in persistent memory
     auto res = std::make_unique<h2_matrix>();
@@ -1801,30 +1889,33 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     R.end(9, 0.0, 8.0 * chunk->len);
     R.launches++;
     clk.mark();
-    int flag = 0;
+    int flag = 0, flag2 = 0;
     H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(&flag2, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     H2_CUDA(cudaGetLastError());
     H2_CUDA(cudaStreamSynchronize(st));
+    flag |= flag2;
     if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
     if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
     if (opts && opts->stats) {
         h2_stats* S = opts->stats;
         S->t_prep_ms = 0.0;
+        // row and column sides run concurrently: their intervals overlap
         S->t_rows_a_ms = clk.ms(0);
-        S->t_cols_a_ms = clk.ms(1);
-        S->t_mat_a_ms = clk.ms(2);
-        S->t_rows_b_ms = clk.ms(3);
-        S->t_cols_b_ms = clk.ms(4);
-        S->t_mat_b_ms = clk.ms(5);
+        S->t_cols_a_ms = clk2.ms(0);
+        S->t_mat_a_ms = clk.ms(1);
+        S->t_rows_b_ms = clk.ms(2);
+        S->t_cols_b_ms = clk2.ms(2);
+        S->t_mat_b_ms = clk.ms(3);
         S->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
-        S->kernel_launches = R.launches;
+        S->kernel_launches = R.launches + R2.launches;
         S->product_nodes = nn;
-        S->triples = cnt.triples;
+        S->triples = cnt.triples + cnt2.triples;
         S->max_rank_a = std::max(ra.Q->max_rank(), ca.Q->max_rank());
         S->max_rank_b = std::max(rb.Qn->max_rank(), cb.Qn->max_rank());
-        S->flops = cnt.flops;
-        S->bytes_moved = cnt.bytes;
+        S->flops = cnt.flops + cnt2.flops;
+        S->bytes_moved = cnt.bytes + cnt2.bytes;
         for (int f = 0; f < 12; ++f) {
             S->fam_ms[f] = 0.0;
             S->fam_launches[f] = 0;
@@ -1832,8 +1923,10 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
             S->fam_bytes[f] = 0.0;
         }
         R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+        R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
     }
     R.release_all();
+    R2.release_all();
     H2_CUDA(cudaStreamSynchronize(st));
     // swap the result into Z (X and Y may alias Z; they are no longer read)
     Zm->V = res->V;
