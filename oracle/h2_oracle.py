@@ -41,6 +41,9 @@ import numpy as np
 # closed-form pins: (1 + x.y)^2 is a polynomial of degree 2 per coordinate,
 # CONST gives the all-ones matrix, DELTA gives the identity for distinct points.
 K_LAPLACE, K_YUKAWA, K_POLY2, K_CONST, K_DELTA = 0, 1, 2, 3, 4
+# Double-layer potential of the Laplace kernel (Sec. 7's second operator, as point
+# collocation): <n(y), x - y> / (4 pi |x - y|^3), 0 on coinciding points.
+K_DLP = 5
 
 TINY = 1e-300
 
@@ -63,6 +66,17 @@ def kernel_matrix(kernel: int, x: np.ndarray, y: np.ndarray) -> np.ndarray:
     else:
         raise ValueError(kernel)
     # The singular kernels are set to 0 on coinciding points ("diagonal 0").
+    return np.where(zero, 0.0, g)
+
+
+def dlp_matrix(x: np.ndarray, y: np.ndarray, ny: np.ndarray) -> np.ndarray:
+    """<n(y_j), x_i - y_j> / (4 pi |x_i - y_j|^3), the normal derivative in y of
+    1 / (4 pi |x - y|); 0 on coinciding points."""
+    diff = x[:, None, :] - y[None, :, :]
+    d = np.sqrt((diff ** 2).sum(axis=2))
+    zero = d == 0.0
+    dd = np.where(zero, 1.0, d)
+    g = (diff * ny[None, :, :]).sum(axis=2) / (4.0 * math.pi * dd ** 3)
     return np.where(zero, 0.0, g)
 
 
@@ -367,6 +381,22 @@ def lagrange_1d(nodes: np.ndarray, x: np.ndarray) -> np.ndarray:
     return out
 
 
+def lagrange_1d_deriv(nodes: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """D[p, i] = l_i'(x_p): the product rule over the factors of l_i."""
+    m = len(nodes)
+    out = np.zeros((len(x), m))
+    for i in range(m):
+        for k in range(m):
+            if k == i:
+                continue
+            term = np.full(len(x), 1.0 / (nodes[i] - nodes[k]))
+            for j in range(m):
+                if j != i and j != k:
+                    term = term * (x - nodes[j]) / (nodes[i] - nodes[j])
+            out[:, i] += term
+    return out
+
+
 def box_nodes(lo, hi, m):
     """Tensor nodes xi_nu, nu = i_x + m i_y + m^2 i_z, as a (m^3 x 3) array."""
     nx, ny, nz = (cheb_nodes_1d(lo[a], hi[a], m) for a in range(3))
@@ -389,6 +419,20 @@ def lagrange_3d(lo, hi, m, x: np.ndarray) -> np.ndarray:
     return out
 
 
+def lagrange_3d_normal(lo, hi, m, x: np.ndarray, nrm: np.ndarray) -> np.ndarray:
+    """grad l_{t,nu}(x_p) . n_p as a (#x x m^3) matrix."""
+    L = [lagrange_1d(cheb_nodes_1d(lo[a], hi[a], m), x[:, a]) for a in range(3)]
+    D = [lagrange_1d_deriv(cheb_nodes_1d(lo[a], hi[a], m), x[:, a]) for a in range(3)]
+    out = np.empty((x.shape[0], m ** 3))
+    for iz in range(m):
+        for iy in range(m):
+            for ix in range(m):
+                out[:, ix + m * iy + m * m * iz] = (D[0][:, ix] * L[1][:, iy] * L[2][:, iz] * nrm[:, 0]
+                                                    + L[0][:, ix] * D[1][:, iy] * L[2][:, iz] * nrm[:, 1]
+                                                    + L[0][:, ix] * L[1][:, iy] * D[2][:, iz] * nrm[:, 2])
+    return out
+
+
 def interp_basis(tree: ClusterTree, points: np.ndarray, m: int) -> Basis:
     """v_{t,i nu} = l_{t,nu}(x_i) on leaves, e_{t',nu' nu} = l_{t,nu}(xi_{t',nu'})."""
     k = m ** 3
@@ -400,6 +444,16 @@ def interp_basis(tree: ClusterTree, points: np.ndarray, m: int) -> Basis:
         if p >= 0:
             transfer[t] = lagrange_3d(tree.lo[p], tree.hi[p], m, box_nodes(tree.lo[t], tree.hi[t], m))
     return Basis(tree, {t: k for t in range(tree.nclusters)}, leaf, transfer)
+
+
+def interp_basis_normal(tree: ClusterTree, points: np.ndarray, normals: np.ndarray, m: int) -> Basis:
+    """Column basis of a double-layer operator: leaf entries d/dn(y_j) l_{s,mu}(y_j);
+    the transfers are those of the Lagrange basis (differentiation is linear and
+    interpolation reproduces the parent's polynomials exactly)."""
+    V = interp_basis(tree, points, m)
+    leaf = {t: lagrange_3d_normal(tree.lo[t], tree.hi[t], m, points[tree.indices(t)], normals[tree.indices(t)])
+            for t in V.leaf}
+    return Basis(tree, dict(V.rank), leaf, dict(V.transfer))
 
 
 @dataclass
@@ -431,6 +485,25 @@ def build_interp(st: Structure, kernel: int) -> H2Matrix:
         elif k == DENSE:
             N[(t, s)] = kernel_matrix(kernel, st.points[tree.indices(t)], st.points[tree.indices(s)])
     return H2Matrix(st.blocks, V, V, S, N)
+
+
+def build_interp_dlp(st: Structure, normals: np.ndarray) -> H2Matrix:
+    """H^2-matrix of the double-layer potential: interpolate 1 / (4 pi |x - y|) in
+    both variables and take the normal derivative in y, so that V is the Lagrange
+    basis, W the normal-derivative basis and S_ts = 1 / (4 pi |xi_t,nu - xi_s,mu|);
+    dense N_ts = <n(x_j), x_i - x_j> / (4 pi |x_i - x_j|^3)."""
+    tree, m = st.tree, st.order
+    V = interp_basis(tree, st.points, m)
+    W = interp_basis_normal(tree, st.points, normals, m)
+    S, N = {}, {}
+    for (t, s), k in st.blocks.kind.items():
+        if k == ADM:
+            S[(t, s)] = kernel_matrix(K_LAPLACE, box_nodes(tree.lo[t], tree.hi[t], m),
+                                      box_nodes(tree.lo[s], tree.hi[s], m))
+        elif k == DENSE:
+            js = tree.indices(s)
+            N[(t, s)] = dlp_matrix(st.points[tree.indices(t)], st.points[js], normals[js])
+    return H2Matrix(st.blocks, V, W, S, N)
 
 
 # --------------------------------------------------------------------------

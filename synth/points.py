@@ -73,6 +73,19 @@ def cube_surface(n: int, seed: int) -> np.ndarray:
     return p
 
 
+def cube_surface_normals(p: np.ndarray) -> np.ndarray:
+    """Outward unit normals of points on the surface of [0,1]^3 (as drawn by
+    cube_surface: exactly one coordinate is 0 or 1): -e_a on the face x_a = 0,
+    +e_a on the face x_a = 1."""
+    nrm = np.zeros_like(p)
+    for i in range(p.shape[0]):
+        for a in range(3):
+            if p[i, a] == 0.0 or p[i, a] == 1.0:
+                nrm[i, a] = 1.0 if p[i, a] == 1.0 else -1.0
+                break
+    return nrm
+
+
 def make_points(geometry: str, n: int, seed: int) -> np.ndarray:
     if geometry == "sphere":
         return sphere(n, seed)
