@@ -446,14 +446,44 @@ def interp_basis(tree: ClusterTree, points: np.ndarray, m: int) -> Basis:
     return Basis(tree, {t: k for t in range(tree.nclusters)}, leaf, transfer)
 
 
-def interp_basis_normal(tree: ClusterTree, points: np.ndarray, normals: np.ndarray, m: int) -> Basis:
-    """Column basis of a double-layer operator: leaf entries d/dn(y_j) l_{s,mu}(y_j);
-    the transfers are those of the Lagrange basis (differentiation is linear and
-    interpolation reproduces the parent's polynomials exactly)."""
-    V = interp_basis(tree, points, m)
-    leaf = {t: lagrange_3d_normal(tree.lo[t], tree.hi[t], m, points[tree.indices(t)], normals[tree.indices(t)])
-            for t in V.leaf}
-    return Basis(tree, dict(V.rank), leaf, dict(V.transfer))
+# Reading: the interpolation boxes of the double-layer operator.  Clusters of a
+# surface are flat (a cube face has zero extent along its normal), and the normal
+# derivative of an interpolant across a vanishing extent is ill-conditioned, so
+# each box extent is widened symmetrically to at least DLP_FAT times the box's
+# largest extent.  Admissibility keeps the bounding boxes.
+DLP_FAT = 0.25
+
+
+def fat_boxes(tree: ClusterTree, rho: float = DLP_FAT):
+    """Bounding boxes with every extent widened to >= rho * (largest extent)."""
+    lo, hi = [], []
+    for t in range(tree.nclusters):
+        l, h = np.array(tree.lo[t], dtype=np.float64), np.array(tree.hi[t], dtype=np.float64)
+        need = rho * float((h - l).max())
+        for a in range(3):
+            if h[a] - l[a] < need:
+                c = 0.5 * (l[a] + h[a])
+                l[a], h[a] = c - 0.5 * need, c + 0.5 * need
+        lo.append(l)
+        hi.append(h)
+    return lo, hi
+
+
+def interp_basis_boxes(tree: ClusterTree, points: np.ndarray, m: int, lo, hi, normals=None) -> Basis:
+    """interp_basis on the given boxes; with normals the leaf entries are
+    d/dn(y_j) l_{s,mu}(y_j) (the transfers are the Lagrange ones: differentiation is
+    linear and interpolation reproduces the parent's polynomials exactly)."""
+    k = m ** 3
+    leaf, transfer = {}, {}
+    for t in range(tree.nclusters):
+        if tree.is_leaf(t):
+            idx = tree.indices(t)
+            leaf[t] = (lagrange_3d(lo[t], hi[t], m, points[idx]) if normals is None
+                       else lagrange_3d_normal(lo[t], hi[t], m, points[idx], normals[idx]))
+        p = tree.parent[t]
+        if p >= 0:
+            transfer[t] = lagrange_3d(lo[p], hi[p], m, box_nodes(lo[t], hi[t], m))
+    return Basis(tree, {t: k for t in range(tree.nclusters)}, leaf, transfer)
 
 
 @dataclass
@@ -489,17 +519,18 @@ def build_interp(st: Structure, kernel: int) -> H2Matrix:
 
 def build_interp_dlp(st: Structure, normals: np.ndarray) -> H2Matrix:
     """H^2-matrix of the double-layer potential: interpolate 1 / (4 pi |x - y|) in
-    both variables and take the normal derivative in y, so that V is the Lagrange
-    basis, W the normal-derivative basis and S_ts = 1 / (4 pi |xi_t,nu - xi_s,mu|);
-    dense N_ts = <n(x_j), x_i - x_j> / (4 pi |x_i - x_j|^3)."""
+    both variables on the widened boxes (fat_boxes) and take the normal derivative
+    in y, so that V is the Lagrange basis, W the normal-derivative basis and
+    S_ts = 1 / (4 pi |xi_t,nu - xi_s,mu|); dense N_ts = <n(x_j), x_i - x_j> /
+    (4 pi |x_i - x_j|^3)."""
     tree, m = st.tree, st.order
-    V = interp_basis(tree, st.points, m)
-    W = interp_basis_normal(tree, st.points, normals, m)
+    lo, hi = fat_boxes(tree)
+    V = interp_basis_boxes(tree, st.points, m, lo, hi)
+    W = interp_basis_boxes(tree, st.points, m, lo, hi, normals)
     S, N = {}, {}
     for (t, s), k in st.blocks.kind.items():
         if k == ADM:
-            S[(t, s)] = kernel_matrix(K_LAPLACE, box_nodes(tree.lo[t], tree.hi[t], m),
-                                      box_nodes(tree.lo[s], tree.hi[s], m))
+            S[(t, s)] = kernel_matrix(K_LAPLACE, box_nodes(lo[t], hi[t], m), box_nodes(lo[s], hi[s], m))
         elif k == DENSE:
             js = tree.indices(s)
             N[(t, s)] = dlp_matrix(st.points[tree.indices(t)], st.points[js], normals[js])
