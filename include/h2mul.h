@@ -50,12 +50,17 @@ extern "C" {
  *   H2_K_YUKAWA   exp(-|x - y|) / |x - y|, 0 on coinciding points
  *   H2_K_POLY2    (1 + x.y)^2      (degree 2 per coordinate: interpolated exactly for order >= 3)
  *   H2_K_CONST    1                (the all-ones matrix)
- *   H2_K_DELTA    1 if x == y else 0 (the identity matrix for distinct points) */
+ *   H2_K_DELTA    1 if x == y else 0 (the identity matrix for distinct points)
+ *   H2_K_DLP      <n(y), x - y> / (4 pi |x - y|^3), 0 on coinciding points: the
+ *                 double-layer potential of the Laplace kernel (the second operator
+ *                 of Sec. 7, as point collocation); needs a normal n(y) per point
+ *                 (h2_build_interp_normals), and gives V != W. */
 #define H2_K_LAPLACE 0
 #define H2_K_YUKAWA 1
 #define H2_K_POLY2 2
 #define H2_K_CONST 3
 #define H2_K_DELTA 4
+#define H2_K_DLP 5
 
 /* Precision of the contractions (products of coupling, transfer, basis and
  * auxiliary matrices).  QR factorisations, singular value decompositions and
@@ -152,9 +157,25 @@ typedef struct {
  *               copied; owned by the caller.
  *   n >= 1, 1 <= leaf_size, 1 <= cheb_order <= 8, eta >= 0, kernel H2_K_*.
  *   out         receives the new handle; untouched on error.
- * Errors: H2_ERR_ARG, H2_ERR_NUMERIC (non-finite point), H2_ERR_OOM, H2_ERR_CUDA. */
+ * Errors: H2_ERR_ARG (H2_K_DLP needs h2_build_interp_normals), H2_ERR_NUMERIC
+ * (non-finite point), H2_ERR_OOM, H2_ERR_CUDA. */
 H2_API int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta,
                     int cheb_order, const h2_opts* opts, h2_matrix** out);
+
+/* h2_build_interp with a unit normal per point (host array, n x 3, row-major,
+ * same order as `points`; read only, copied).  For H2_K_DLP the kernel is
+ * interpolated as the normal derivative in y of 1 / (4 pi |x - y|): V is the
+ * Lagrange basis, W the normal-derivative basis
+ *   W_s[j, mu] = grad l_{s,mu}(y_j) . n(y_j) on leaves, with the Lagrange
+ *   transfer matrices (differentiation is linear and the parent's polynomials
+ *   are interpolated exactly),
+ * S_ts = 1 / (4 pi |xi_{t,nu} - xi_{s,mu}|), dense N_ts[i, j] = g(x_i, x_j).
+ * Other kernels ignore `normals` (it may be NULL for them).
+ * Errors: as h2_build_interp; H2_ERR_ARG if H2_K_DLP and normals == NULL,
+ * H2_ERR_NUMERIC for a non-finite normal. */
+H2_API int h2_build_interp_normals(const double* points, const double* normals, int64_t n, int kernel,
+                                   int leaf_size, double eta, int cheb_order, const h2_opts* opts,
+                                   h2_matrix** out);
 
 /* Z <- Z + X Y (Sec. 1), approximated to the block-relative tolerance
  * opts->eps in both phases (Sec. 5, Sec. 6, Sec. 7).  X, Y and Z must share

@@ -17,11 +17,11 @@ from .build import LIB, build
 H2_OK = 0
 ERRORS = {-1: "H2_ERR_ARG", -2: "H2_ERR_SHAPE", -3: "H2_ERR_OOM", -4: "H2_ERR_NUMERIC",
           -5: "H2_ERR_TIMEOUT", -6: "H2_ERR_UNSUPPORTED", -7: "H2_ERR_CUDA"}
-H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA = 0, 1, 2, 3, 4
+H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA, H2_K_DLP = 0, 1, 2, 3, 4, 5
 H2_FP64, H2_MIXED, H2_TC = 0, 1, 2
 
-EXPORTED = ["h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-            "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error",
+EXPORTED = ["h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
+            "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error",
             "h2_free", "h2_error_string", "h2_last_error_message"]
 
 
@@ -80,6 +80,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.h2_build_interp.argtypes = [vp, i64, ci, ci, cd, ci, vp, ctypes.POINTER(vp)]
+    lib.h2_build_interp_normals.argtypes = [vp, vp, i64, ci, ci, cd, ci, vp, ctypes.POINTER(vp)]
     lib.h2_mul_add.argtypes = [vp, vp, vp, vp]
     lib.h2_to_dense.argtypes = [vp, vp, i64, ci, vp]
     lib.h2_info.argtypes = [vp, vp]
@@ -95,8 +96,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_error_string.restype = ctypes.c_char_p
     lib.h2_error_string.argtypes = [ci]
     lib.h2_last_error_message.restype = ctypes.c_char_p
-    for f in ("h2_build_interp", "h2_mul_add", "h2_to_dense", "h2_info", "h2_get_structure", "h2_clone",
-              "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error"):
+    for f in ("h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
+              "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec",
+              "h2_mul_add_batched", "h2_product_error"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -148,14 +150,24 @@ class H2Matrix:
 
 
 def h2_build_interp(points: np.ndarray, kernel: int, leaf_size: int, eta: float, cheb_order: int,
-                    stream: int | None = None) -> H2Matrix:
+                    stream: int | None = None, normals: np.ndarray | None = None) -> H2Matrix:
+    """Chebyshev H^2-matrix of a kernel; normals (n x 3) are needed for H2_K_DLP
+    (h2_build_interp_normals)."""
     pts = np.ascontiguousarray(points, dtype=np.float64)
     if pts.ndim != 2 or pts.shape[1] != 3:
         raise ValueError("points must be an n x 3 array")
     h = ctypes.c_void_p()
     o = _opts(stream=stream)
-    _check(load().h2_build_interp(pts.ctypes.data, pts.shape[0], kernel, leaf_size, eta, cheb_order,
-                                  ctypes.byref(o), ctypes.byref(h)), "h2_build_interp")
+    if normals is None:
+        _check(load().h2_build_interp(pts.ctypes.data, pts.shape[0], kernel, leaf_size, eta, cheb_order,
+                                      ctypes.byref(o), ctypes.byref(h)), "h2_build_interp")
+    else:
+        nrm = np.ascontiguousarray(normals, dtype=np.float64)
+        if nrm.shape != pts.shape:
+            raise ValueError("normals must be an n x 3 array like points")
+        _check(load().h2_build_interp_normals(pts.ctypes.data, nrm.ctypes.data, pts.shape[0], kernel, leaf_size,
+                                              eta, cheb_order, ctypes.byref(o), ctypes.byref(h)),
+               "h2_build_interp_normals")
     return H2Matrix(h)
 
 

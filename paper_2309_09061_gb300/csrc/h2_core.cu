@@ -513,13 +513,18 @@ const char* h2_error_string(int code) {
 
 const char* h2_last_error_message(void) { return g_last_error.c_str(); }
 
-int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta, int cheb_order,
-                    const h2_opts* opts, h2_matrix** out) {
+// widening of the double-layer interpolation boxes (each extent >= this fraction of the largest)
+constexpr double kDlpFat = 0.25;
+
+static int build_interp(const double* points, const double* normals, int64_t n, int kernel, int leaf_size, double eta,
+                        int cheb_order, const h2_opts* opts, h2_matrix** out) {
     if (!points || !out || n < 1 || leaf_size < 1 || cheb_order < 1 || cheb_order > 8 || !(eta >= 0.0) ||
-        !std::isfinite(eta) || kernel < H2_K_LAPLACE || kernel > H2_K_DELTA)
+        !std::isfinite(eta) || kernel < H2_K_LAPLACE || kernel > H2_K_DLP)
         return H2_ERR_ARG;
+    const bool dlp = (kernel == H2_K_DLP);
+    if (dlp && !normals) return H2_ERR_ARG;
     for (int64_t i = 0; i < 3 * n; ++i)
-        if (!std::isfinite(points[i])) return H2_ERR_NUMERIC;
+        if (!std::isfinite(points[i]) || (dlp && !std::isfinite(normals[i]))) return H2_ERR_NUMERIC;
     return run_guarded([&] {
         cudaStream_t st = stream_of(opts);
         auto M = std::make_unique<h2_matrix>();
@@ -536,8 +541,25 @@ int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, 
         int64_t* d_perm = R.upload(T.perm);
         int64_t* d_off = R.upload(T.off);
         int64_t* d_size = R.upload(T.size);
-        double* d_lo = R.upload(T.lo);
-        double* d_hi = R.upload(T.hi);
+        // interpolation boxes: the bounding boxes, or for the double-layer kernel the
+        // bounding boxes with every extent widened to >= 1/4 of the largest (the normal
+        // derivative across the vanishing extent of a flat surface cluster is ill-conditioned)
+        std::vector<double> blo = T.lo, bhi = T.hi;
+        if (dlp) {
+            for (int c = 0; c < T.nc; ++c) {
+                double* l = &blo[3 * c];
+                double* h = &bhi[3 * c];
+                const double need = kDlpFat * std::max({h[0] - l[0], h[1] - l[1], h[2] - l[2]});
+                for (int a = 0; a < 3; ++a)
+                    if (h[a] - l[a] < need) {
+                        const double mid = 0.5 * (l[a] + h[a]);
+                        l[a] = mid - 0.5 * need;
+                        h[a] = mid + 0.5 * need;
+                    }
+            }
+        }
+        double* d_lo = R.upload(blo);
+        double* d_hi = R.upload(bhi);
         // basis: leaves + transfers in one chunk
         auto V = std::make_shared<Basis>();
         V->rank.assign(T.nc, k);
@@ -566,9 +588,34 @@ int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, 
         }
         double** d_leafp = R.upload(V->leaf);
         double** d_trp = R.upload(V->tr);
-        launch_interp_leaf(d_pts, d_perm, d_off, d_size, d_lo, d_hi, d_leafp, Tree::first(T.L), Tree::count(T.L), m,
-                           max_size, st);
+        launch_interp_leaf(d_pts, nullptr, d_perm, d_off, d_size, d_lo, d_hi, d_leafp, Tree::first(T.L),
+                           Tree::count(T.L), m, max_size, st);
         launch_interp_transfer(d_lo, d_hi, d_trp, T.nc, m, st);
+        // double-layer kernel: the column basis holds the normal derivatives (own leaves and transfers)
+        std::shared_ptr<Basis> W = V;
+        double* d_nrm = nullptr;
+        if (dlp) {
+            d_nrm = R.upload(std::vector<double>(normals, normals + 3 * n));
+            W = std::make_shared<Basis>();
+            W->rank = V->rank;
+            W->leaf.assign(T.nc, nullptr);
+            W->tr.assign(T.nc, nullptr);
+            auto wchunk = std::make_shared<DevBuf>();
+            wchunk->alloc(total);
+            W->chunks.push_back(wchunk);
+            for (int c = 0; c < T.nc; ++c) {
+                if (V->leaf[c]) W->leaf[c] = wchunk->p + (V->leaf[c] - chunk->p);
+                if (V->tr[c]) W->tr[c] = wchunk->p + (V->tr[c] - chunk->p);
+            }
+            launch_interp_leaf(d_pts, d_nrm, d_perm, d_off, d_size, d_lo, d_hi, R.upload(W->leaf), Tree::first(T.L),
+                               Tree::count(T.L), m, max_size, st);
+            launch_interp_transfer(d_lo, d_hi, R.upload(W->tr), T.nc, m, st);
+            uint64_t h = 1469598103934665603ull;  // FNV-1a over the normals' bytes
+            const unsigned char* b = (const unsigned char*)normals;
+            for (size_t i = 0; i < sizeof(double) * 3 * (size_t)n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+            M->wtag = h | 1;
+            M->vtag = 1;
+        }
         // couplings and dense blocks
         size_t stot = 0, ntot = 0;
         int nb = (int)B.kind.size();
@@ -600,15 +647,25 @@ int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, 
             }
         }
         launch_interp_coupling(d_lo, d_hi, R.upload(at), R.upload(as), R.upload(ap), (int)at.size(), m, kernel, st);
-        launch_interp_dense(d_pts, d_perm, d_off, d_size, R.upload(dt), R.upload(ds), R.upload(dp), (int)dt.size(),
-                            kernel, st);
+        launch_interp_dense(d_pts, d_nrm, d_perm, d_off, d_size, R.upload(dt), R.upload(ds), R.upload(dp),
+                            (int)dt.size(), kernel, st);
         M->V = V;
-        M->W = V;
+        M->W = W;
         H2_CUDA(cudaGetLastError());
         R.release_all();
         H2_CUDA(cudaStreamSynchronize(st));
         *out = M.release();
     });
+}
+
+int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta, int cheb_order,
+                    const h2_opts* opts, h2_matrix** out) {
+    return build_interp(points, nullptr, n, kernel, leaf_size, eta, cheb_order, opts, out);
+}
+
+int h2_build_interp_normals(const double* points, const double* normals, int64_t n, int kernel, int leaf_size,
+                            double eta, int cheb_order, const h2_opts* opts, h2_matrix** out) {
+    return build_interp(points, normals, n, kernel, leaf_size, eta, cheb_order, opts, out);
 }
 
 int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, const h2_opts* opts) {
@@ -718,6 +775,8 @@ int h2_clone(const h2_matrix* A, const h2_opts* opts, h2_matrix** out) {
         M->kernel = A->kernel;
         M->order = A->order;
         M->device = A->device;
+        M->vtag = A->vtag;
+        M->wtag = A->wtag;
         // copy every chunk and translate the pointers into it
         std::vector<std::pair<const DevBuf*, DevBuf*>> map;
         auto dup = [&](const std::vector<std::shared_ptr<DevBuf>>& src, std::vector<std::shared_ptr<DevBuf>>& dst) {

@@ -148,6 +148,10 @@ struct h2_matrix {
     int kernel = -1;
     int order = 0;                        // Chebyshev order of the bases, 0 for product results
     int device = 0;
+    uint64_t vtag = 0;                    // Chebyshev row basis: 0 on the bounding boxes, else the
+                                          // widened interpolation boxes of the double-layer kernel
+    uint64_t wtag = 0;                    // Chebyshev column basis: 0 Lagrange, else a hash of the
+                                          // normals of a normal-derivative basis
 };
 
 namespace h2 {
@@ -281,14 +285,17 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_
 void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st);
 void launch_norm(const NormJob* jobs, int njobs, int precision, cudaStream_t st);
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);
-void launch_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
-                        const double* lo, const double* hi, double* const* leafp, int first_leaf, int nleaves, int m,
-                        int64_t max_size, cudaStream_t st);
+// nrm (n x 3, original order) non-null: the normal-derivative basis
+// grad l_nu(x_i) . n_i instead of l_nu(x_i)
+void launch_interp_leaf(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
+                        const int64_t* size, const double* lo, const double* hi, double* const* leafp, int first_leaf,
+                        int nleaves, int m, int64_t max_size, cudaStream_t st);
 void launch_interp_transfer(const double* lo, const double* hi, double* const* trp, int nc, int m, cudaStream_t st);
 void launch_interp_coupling(const double* lo, const double* hi, const int* bt, const int* bs, double* const* bp,
                             int nblocks, int m, int kernel, cudaStream_t st);
-void launch_interp_dense(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
-                         const int* bt, const int* bs, double* const* bp, int nblocks, int kernel, cudaStream_t st);
+void launch_interp_dense(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
+                         const int64_t* size, const int* bt, const int* bs, double* const* bp, int nblocks, int kernel,
+                         cudaStream_t st);
 void launch_scatter_dense(const double* src, int64_t n, const int64_t* perm, double* out, int64_t ld,
                           cudaStream_t st);
 void launch_set_identity(double* A, int m, int n, int lda, cudaStream_t st);

@@ -1560,7 +1560,33 @@ __device__ double lagrange(double a, double b, int m, int i, double x) {
     return v;
 }
 
-__device__ double kernel_eval(int kernel, const double* x, const double* y) {
+// l_i'(x): the product rule over the factors of l_i
+__device__ double lagrange_deriv(double a, double b, int m, int i, double x) {
+    const double xi = cheb_node(a, b, i, m);
+    double sum = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (k == i) continue;
+        const double xk = cheb_node(a, b, k, m);
+        double term = 1.0 / (xi - xk);
+        for (int j = 0; j < m; ++j)
+            if (j != i && j != k) {
+                const double xj = cheb_node(a, b, j, m);
+                term *= (x - xj) / (xi - xj);
+            }
+        sum += term;
+    }
+    return sum;
+}
+
+// ny: the normal at y (H2_K_DLP only)
+__device__ double kernel_eval(int kernel, const double* x, const double* y, const double* ny = nullptr) {
+    if (kernel == H2_K_DLP) {
+        const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        if (r2 == 0.0) return 0.0;
+        const double r = sqrt(r2);
+        return (ny[0] * d0 + ny[1] * d1 + ny[2] * d2) / (4.0 * M_PI * r2 * r);
+    }
     if (kernel == H2_K_POLY2) {
         double d = 1.0 + x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
         return d * d;
@@ -1574,9 +1600,10 @@ __device__ double kernel_eval(int kernel, const double* x, const double* y) {
     return exp(-r) / r;
 }
 
-// leaf bases: one thread per (point, nu)
-__global__ void k_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
-                              const double* lo, const double* hi, double* const* leafp, int first_leaf, int m) {
+// leaf bases: one thread per (point, nu); with normals the normal derivative
+__global__ void k_interp_leaf(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
+                              const int64_t* size, const double* lo, const double* hi, double* const* leafp,
+                              int first_leaf, int m) {
     const int leaf = first_leaf + blockIdx.y;
     const int k = m * m * m;
     const int64_t cnt = size[leaf];
@@ -1585,21 +1612,32 @@ __global__ void k_interp_leaf(const double* pts, const int64_t* perm, const int6
         int64_t i = e % cnt;
         int nu = (int)(e / cnt);
         int ix = nu % m, iy = (nu / m) % m, iz = nu / (m * m);
-        const double* x = pts + 3 * perm[off[leaf] + i];
+        const int64_t p = perm[off[leaf] + i];
+        const double* x = pts + 3 * p;
         const double* l = lo + 3 * leaf;
         const double* h = hi + 3 * leaf;
-        out[i + (size_t)nu * cnt] = lagrange(l[0], h[0], m, ix, x[0]) * lagrange(l[1], h[1], m, iy, x[1]) *
-                                    lagrange(l[2], h[2], m, iz, x[2]);
+        const double lx = lagrange(l[0], h[0], m, ix, x[0]), ly = lagrange(l[1], h[1], m, iy, x[1]),
+                     lz = lagrange(l[2], h[2], m, iz, x[2]);
+        double v;
+        if (nrm) {
+            const double* nv = nrm + 3 * p;
+            v = lagrange_deriv(l[0], h[0], m, ix, x[0]) * ly * lz * nv[0] +
+                lx * lagrange_deriv(l[1], h[1], m, iy, x[1]) * lz * nv[1] +
+                lx * ly * lagrange_deriv(l[2], h[2], m, iz, x[2]) * nv[2];
+        } else {
+            v = lx * ly * lz;
+        }
+        out[i + (size_t)nu * cnt] = v;
     }
 }
 
-void launch_interp_leaf(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
-                        const double* lo, const double* hi, double* const* leafp, int first_leaf, int nleaves, int m,
-                        int64_t max_size, cudaStream_t st) {
+void launch_interp_leaf(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
+                        const int64_t* size, const double* lo, const double* hi, double* const* leafp, int first_leaf,
+                        int nleaves, int m, int64_t max_size, cudaStream_t st) {
     int k = m * m * m;
     int gx = (int)std::min<int64_t>(ceil_div(max_size * k, 128), 1024);
     dim3 grid(gx, nleaves);
-    if (nleaves > 0) k_interp_leaf<<<grid, 128, 0, st>>>(pts, perm, off, size, lo, hi, leafp, first_leaf, m);
+    if (nleaves > 0) k_interp_leaf<<<grid, 128, 0, st>>>(pts, nrm, perm, off, size, lo, hi, leafp, first_leaf, m);
 }
 
 // transfers: E_c[nu', nu] = l_{parent, nu}(xi_{c, nu'}), one block per cluster c >= 1
@@ -1636,7 +1674,8 @@ __global__ void k_interp_coupling(const double* lo, const double* hi, const int*
                        cheb_node(lt[2], ht[2], nu / (m * m), m)};
         double y[3] = {cheb_node(ls[0], hs[0], mu % m, m), cheb_node(ls[1], hs[1], (mu / m) % m, m),
                        cheb_node(ls[2], hs[2], mu / (m * m), m)};
-        out[nu + (size_t)mu * k] = kernel_eval(kernel, x, y);
+        // the double-layer kernel is the normal derivative (carried by W) of the Laplace kernel
+        out[nu + (size_t)mu * k] = kernel_eval(kernel == H2_K_DLP ? H2_K_LAPLACE : kernel, x, y);
     }
 }
 
@@ -1645,21 +1684,23 @@ void launch_interp_coupling(const double* lo, const double* hi, const int* bt, c
     if (nblocks > 0) k_interp_coupling<<<nblocks, 256, 0, st>>>(lo, hi, bt, bs, bp, m, kernel);
 }
 
-// dense blocks: N_ts[i, j] = g(x_i, x_j)
-__global__ void k_interp_dense(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
-                               const int* bt, const int* bs, double* const* bp, int kernel) {
+// dense blocks: N_ts[i, j] = g(x_i, x_j) (normals of the column points for H2_K_DLP)
+__global__ void k_interp_dense(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
+                               const int64_t* size, const int* bt, const int* bs, double* const* bp, int kernel) {
     const int b = blockIdx.x, t = bt[b], s = bs[b];
     const int64_t mt = size[t], ms = size[s];
     double* out = bp[b];
     for (int64_t e = threadIdx.x; e < mt * ms; e += blockDim.x) {
         int64_t i = e % mt, j = e / mt;
-        out[e] = kernel_eval(kernel, pts + 3 * perm[off[t] + i], pts + 3 * perm[off[s] + j]);
+        const int64_t pj = perm[off[s] + j];
+        out[e] = kernel_eval(kernel, pts + 3 * perm[off[t] + i], pts + 3 * pj, nrm ? nrm + 3 * pj : nullptr);
     }
 }
 
-void launch_interp_dense(const double* pts, const int64_t* perm, const int64_t* off, const int64_t* size,
-                         const int* bt, const int* bs, double* const* bp, int nblocks, int kernel, cudaStream_t st) {
-    if (nblocks > 0) k_interp_dense<<<nblocks, 256, 0, st>>>(pts, perm, off, size, bt, bs, bp, kernel);
+void launch_interp_dense(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
+                         const int64_t* size, const int* bt, const int* bs, double* const* bp, int nblocks, int kernel,
+                         cudaStream_t st) {
+    if (nblocks > 0) k_interp_dense<<<nblocks, 256, 0, st>>>(pts, nrm, perm, off, size, bt, bs, bp, kernel);
 }
 
 // ------------------------------------------------------------------ block norms

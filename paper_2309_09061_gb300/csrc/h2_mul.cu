@@ -1671,11 +1671,11 @@ static bool same_row_basis(const h2_matrix* A, const h2_matrix* B) {
     // A's row basis equals B's row basis: the same object, or Chebyshev bases of
     // the same structure and order (they are equal by construction)
     if (A->V == B->V) return true;
-    return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint;
+    return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint && A->vtag == B->vtag;
 }
 static bool same_col_basis(const h2_matrix* A, const h2_matrix* B) {
     if (A->W == B->W) return true;
-    return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint;
+    return A->order > 0 && A->order == B->order && A->st->fingerprint == B->st->fingerprint && A->wtag == B->wtag;
 }
 
 // A second stream with its own host thread: the row and column sides of each

@@ -1,0 +1,107 @@
+"""GPU parity of the double-layer workload (the second operator of Sec. 7 as
+point collocation, <n(y), x - y> / (4 pi |x - y|^3) on the cube surface): a
+non-symmetric operator with V != W.  The interpolation build against the
+oracle element by element, products against the oracle and the dense product
+in every precision, exact mode, mixed operand kinds, the basis relations that
+must be refused, and sampled rows plus eps_2 at the size of the paper's
+49,152-point cube-surface example."""
+import numpy as np
+import pytest
+
+import paper_2309_09061_gb300 as P
+import synth
+from oracle import h2_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.build()
+    return P.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def case(n=700, leaf=16, eta=1.5, order=3, seed=5):
+    pts = synth.cube_surface(n, seed)
+    nrm = synth.cube_surface_normals(pts)
+    st = O.build_structure(pts, leaf, eta, order)
+    return pts, nrm, st
+
+
+def test_dlp_interp_against_oracle():
+    pts, nrm, st = case()
+    K = P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 3, normals=nrm)
+    D = O.build_interp_dlp(st, nrm).to_dense()
+    assert rel(P.h2_to_dense(K), D) <= 1e-12
+    assert np.linalg.norm(D - D.T) > 0.1 * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED, P.H2_TC])
+def test_dlp_product_against_oracle(precision):
+    eps = 1e-5
+    pts, nrm, st = case()
+    K = P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 3, normals=nrm)
+    Ko = O.build_interp_dlp(st, nrm)
+    D = Ko.to_dense()
+    Z = P.h2_clone(K)
+    P.h2_mul_add(Z, K, K, eps, precision)
+    Zg = P.h2_to_dense(Z)
+    assert rel(Zg, O.mul_add(Ko, Ko, Ko, eps).result.to_dense()) <= 10 * eps
+    assert rel(Zg, D + D @ D) <= 2 * eps
+
+
+def test_dlp_exact_mode():
+    pts, nrm, st = case(n=400, order=2)
+    K = P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 2, normals=nrm)
+    D = O.build_interp_dlp(st, nrm).to_dense()
+    Z = P.h2_clone(K)
+    P.h2_mul_add(Z, K, K, 0.0, P.H2_FP64)
+    assert rel(P.h2_to_dense(Z), D + D @ D) <= 1e-12
+
+
+def test_dlp_mixed_operands():
+    """X = DLP (V != W) with Y = Laplace on the same widened boxes is refused
+    (different row bases); the supported relations: Z's row basis is X's and
+    Z's column basis is Y's."""
+    eps = 1e-5
+    pts, nrm, st = case()
+    K = P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 3, normals=nrm)
+    L = P.h2_build_interp(pts, P.H2_K_LAPLACE, 16, 1.5, 3)
+    with pytest.raises(P.H2Error) as e:  # Laplace Z: column basis differs from the DLP's W
+        P.h2_mul_add(P.h2_clone(L), K, K, eps)
+    assert e.value.code == -6
+    with pytest.raises(P.H2Error) as e:  # DLP rows (widened boxes) vs Laplace rows (bounding boxes)
+        P.h2_mul_add(P.h2_clone(K), L, K, eps)
+    assert e.value.code == -6
+    with pytest.raises(P.H2Error) as e:  # the double-layer kernel needs normals
+        P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 3)
+    assert e.value.code == -1
+
+
+def test_dlp_full_size_n49152():
+    """n = 49152 on the cube surface (the size of the paper's DLP example),
+    leaf 64, eta 2, order 4, eps 1e-4: 24 sampled rows of K + K K against the
+    oracle's own H^2 matvec (<= 10 eps), and eps_2 of the FP64 and mixed products."""
+    n, leaf, eta, order, eps = 49152, 64, 2.0, 4, 1e-4
+    pts = synth.cube_surface(n, 2309090615)
+    nrm = synth.cube_surface_normals(pts)
+    K = P.h2_build_interp(pts, P.H2_K_DLP, leaf, eta, order, normals=nrm)
+    rows = np.unique(synth.splitmix64(78, 24) % n).astype(np.int64)
+    Ko = O.build_interp_dlp(O.build_structure(pts, leaf, eta, order), nrm)
+    Rg = Ko.rows_of(rows)
+    ref = Rg + Ko.matvec(Rg.T, trans=True).T
+    for prec in (P.H2_FP64, P.H2_MIXED):
+        Z = P.h2_clone(K)
+        P.h2_mul_add(Z, K, K, eps, prec)
+        got = P.h2_rows(Z, rows).cpu().numpy()
+        assert rel(got, ref) <= 10 * eps
+        e2, nrm2 = P.h2_product_error(Z, K, K, K, steps=20)
+        assert 0.0 < e2 <= 10 * eps and nrm2 > 0.0
+        Z.free()
