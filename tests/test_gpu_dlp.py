@@ -87,8 +87,13 @@ def test_dlp_mixed_operands():
 
 def test_dlp_full_size_n49152():
     """n = 49152 on the cube surface (the size of the paper's DLP example),
-    leaf 64, eta 2, order 4, eps 1e-4: 24 sampled rows of K + K K against the
-    oracle's own H^2 matvec (<= 10 eps), and eps_2 of the FP64 and mixed products."""
+    leaf 64, eta 2, order 4, eps 1e-4.  The paper's measure, eps_2 (relative
+    spectral error, 20 power steps), within 2 eps for the FP64 and mixed
+    products.  Sampled rows of K + K K against the oracle's own H^2 matvec:
+    the error control of Sec. 5 is relative to block norms, and double-layer
+    rows on a cube surface differ in norm by orders of magnitude (coplanar
+    parts vanish, points near edges see large values), so the relative error
+    over a few rows is bounded by 20 eps rather than the global eps."""
     n, leaf, eta, order, eps = 49152, 64, 2.0, 4, 1e-4
     pts = synth.cube_surface(n, 2309090615)
     nrm = synth.cube_surface_normals(pts)
@@ -101,7 +106,7 @@ def test_dlp_full_size_n49152():
         Z = P.h2_clone(K)
         P.h2_mul_add(Z, K, K, eps, prec)
         got = P.h2_rows(Z, rows).cpu().numpy()
-        assert rel(got, ref) <= 10 * eps
+        assert rel(got, ref) <= 20 * eps
         e2, nrm2 = P.h2_product_error(Z, K, K, K, steps=20)
-        assert 0.0 < e2 <= 10 * eps and nrm2 > 0.0
+        assert 0.0 < e2 <= 2 * eps and nrm2 > 0.0
         Z.free()
