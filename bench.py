@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="override n (testing only)")
-    ap.add_argument("--workload", default="sphere32768", choices=["sphere32768", "batched64"],
+    ap.add_argument("--workload", default="sphere32768", choices=["sphere32768", "batched64", "dlp49152"],
                     help="sphere32768: the default line; batched64: 64 independent products in one batched call")
     return ap.parse_args()
 
@@ -433,10 +433,67 @@ def batched_arm(args):
         print(json.dumps(line), flush=True)
 
 
+DLP = dict(n=49152, leaf=64, eta=2.0, order=4, eps=1e-4, seed=2309090615)
+
+
+def dlp_arm(args):
+    """The double-layer workload: K + K K for the collocated double-layer
+    operator on the cube surface (non-symmetric, V != W), n = 49152 (the size of
+    the paper's cube-surface example), FP64 and mixed, with eps_2 of each."""
+    import torch
+
+    import paper_2309_09061_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    P.build()
+    P.load()
+    d = DLP
+    pts = synth.cube_surface(d["n"], d["seed"] + 1000 * rank)
+    nrm = synth.cube_surface_normals(pts)
+    K = P.h2_build_interp(pts, P.H2_K_DLP, d["leaf"], d["eta"], d["order"], stream=sptr, normals=nrm)
+    out = {}
+    for name, prec in (("fp64", P.H2_FP64), ("mixed", P.H2_MIXED)):
+        for _ in range(args.warmup):
+            Zw = P.h2_clone(K, stream=sptr)
+            P.h2_mul_add(Zw, K, K, d["eps"], prec, stream=sptr)
+            Zw.free()
+        Zs = [P.h2_clone(K, stream=sptr) for _ in range(args.steps)]
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for Z in Zs:
+            P.h2_mul_add(Z, K, K, d["eps"], prec, stream=sptr)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        dt = e0.elapsed_time(e1) / 1e3
+        e2 = P.h2_product_error(Zs[-1], K, K, K, steps=20, stream=sptr)[0]
+        for Z in Zs:
+            Z.free()
+        out[name] = {"value": d["n"] * world * args.steps / dt, "unit": "rows/s", "ms_per_step": 1e3 * dt / args.steps,
+                     "eps2": e2}
+    line = {"metric": "H2 Z<-Z+XY rows/s, double-layer operator on the cube surface", "value": out["fp64"]["value"],
+            "unit": "rows/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["fp64"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded points on the cube surface, face normals)",
+            "config": {"workload": "dlp49152", "n": d["n"], "leaf": d["leaf"], "eta": d["eta"], "order": d["order"],
+                       "eps": d["eps"], "X=Y=Z": True},
+            "mixed": out["mixed"], "speedup_mixed_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
+            "accuracy": {"eps2_fp64": out["fp64"]["eps2"], "eps2_mixed": out["mixed"]["eps2"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl != "reference" and args.workload == "batched64":
         batched_arm(args)
+        return
+    if args.impl != "reference" and args.workload == "dlp49152":
+        dlp_arm(args)
         return
     if args.impl == "reference":
         reference_arm(args)
