@@ -367,10 +367,10 @@ void Runner::flush_svd() {
     svd_maxn_ = 0;
 }
 
-void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64) {
+void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64, double* W64) {
     float* W = (float*)dalloc(((size_t)m * n + 1) / 2);
-    float* V = (float*)dalloc(((size_t)n * n + 1) / 2);
-    pres_.push_back(PreJob{B, W, V, V64, nullptr, m, n, ldb});
+    float* V = V64 ? (float*)dalloc(((size_t)n * n + 1) / 2) : nullptr;
+    pres_.push_back(PreJob{B, W, V, V64, W64, nullptr, m, n, ldb});
 }
 
 void Runner::flush_pre() {

@@ -219,8 +219,9 @@ struct SVDJob {
 struct PreJob {
     const double* B;
     float* W;
-    float* V;
-    double* V64;
+    float* V;       // accumulated rotations (n x n), or null: not accumulated
+    double* V64;    // when set: V in FP64
+    double* W64;    // when set: the rotated W in FP64 (m x n, ld m)
     double* flops;  // optional accumulator: executed sweep flops
     int m, n, ldb;
 };
@@ -360,7 +361,7 @@ public:
     void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
              const int* rowperm = nullptr);
     void flush_svd();
-    void jacobi_pre(const double* B, int m, int n, int ldb, double* V64);
+    void jacobi_pre(const double* B, int m, int n, int ldb, double* V64, double* W64 = nullptr);
     void flush_pre();
     void pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol);
     void flush_pchol();

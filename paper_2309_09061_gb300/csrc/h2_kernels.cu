@@ -50,14 +50,21 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
                 Bs[kk][j] = (T)w;
             }
             __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < GK; ++kk) {
+            auto mac = [&](int kk) {
                 T a0 = As[kk][tx], a1 = As[kk][tx + 16];
                 T b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
                 acc[0][0] += a0 * b0;
                 acc[1][0] += a1 * b0;
                 acc[0][1] += a0 * b1;
                 acc[1][1] += a1 * b1;
+            };
+            const int kc = min(GK, P.k - k0);  // the last chunk of a term is partial: skip its zero padding
+            if (kc == GK) {
+#pragma unroll
+                for (int kk = 0; kk < GK; ++kk) mac(kk);
+            } else {
+#pragma unroll 2
+                for (int kk = 0; kk < kc; ++kk) mac(kk);
             }
             __syncthreads();
         }
@@ -826,7 +833,8 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     const bool in_smem = (size_t)m * n * sizeof(float) <= (size_t)smem_bytes;
     float* W = in_smem ? pre_smem : J.W;
     for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) W[e] = (float)J.B[(e % m) + (size_t)(e / m) * J.ldb];
-    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
+    if (J.V)
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
     __syncthreads();
     const int np = n + (n & 1);
     const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
@@ -867,12 +875,14 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
                         ap[i] = c * x - s * y;
                         aq[i] = s * x + c * y;
                     }
-                    float* vp = J.V + (size_t)p * n;
-                    float* vq = J.V + (size_t)q * n;
-                    for (int i = lane; i < n; i += 32) {
-                        float x = vp[i], y = vq[i];
-                        vp[i] = c * x - s * y;
-                        vq[i] = s * x + c * y;
+                    if (J.V) {
+                        float* vp = J.V + (size_t)p * n;
+                        float* vq = J.V + (size_t)q * n;
+                        for (int i = lane; i < n; i += 32) {
+                            float x = vp[i], y = vq[i];
+                            vp[i] = c * x - s * y;
+                            vq[i] = s * x + c * y;
+                        }
                     }
                     if (lane == 0) {
                         rotated = 1;
@@ -885,8 +895,12 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
         converged = (rotated == 0) || (large == 0);
         __syncthreads();
     }
-    for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
-    if (threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
+    if (J.V64)
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
+    if (J.W64)
+        for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) J.W64[e] = (double)W[e];
+    if (threadIdx.x == 0 && J.flops)
+        atomicAdd(J.flops, 12.0 * (m + (J.V ? n : 0)) * (0.5 * n * (n - 1.0)) * sweep);
 }
 
 // ------------------------------------------------------------------ clustered FP32 preconditioning
@@ -917,8 +931,9 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre_cluster(const PreJob* __restr
     float* V = J.V;  // n x n, ld n
     for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)m * n; e += (int64_t)JT * cs)
         __stcg(B + e, (float)J.B[(e % m) + (size_t)(e / m) * J.ldb]);
-    for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
-        __stcg(V + e, ((e % n) == (e / n)) ? 1.f : 0.f);
+    if (V)
+        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
+            __stcg(V + e, ((e % n) == (e / n)) ? 1.f : 0.f);
     cl.sync();
     const int np = n + (n & 1);
     const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
@@ -954,7 +969,7 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre_cluster(const PreJob* __restr
                                                     : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
                     float c = 1.f / sqrtf(1.f + t * t), s = c * t;
                     rot_pair32(ap, aq, m, c, s, lane);
-                    rot_pair32(V + (size_t)p * n, V + (size_t)q * n, n, c, s, lane);
+                    if (V) rot_pair32(V + (size_t)p * n, V + (size_t)q * n, n, c, s, lane);
                     if (lane == 0) {
                         rotated = 1;
                         if (fabsf(ga) > skip * sqrtf(al) * sqrtf(be)) large = 1;
@@ -971,9 +986,14 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre_cluster(const PreJob* __restr
         converged = (any == 0) || (anylarge == 0);
         cl.sync();
     }
-    for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
-        J.V64[e] = (double)__ldcg(V + e);
-    if (cr == 0 && threadIdx.x == 0 && J.flops) atomicAdd(J.flops, 12.0 * (m + n) * (0.5 * n * (n - 1.0)) * sweep);
+    if (J.V64)
+        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)n * n; e += (int64_t)JT * cs)
+            J.V64[e] = (double)__ldcg(V + e);
+    if (J.W64)
+        for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)m * n; e += (int64_t)JT * cs)
+            J.W64[e] = (double)__ldcg(B + e);
+    if (cr == 0 && threadIdx.x == 0 && J.flops)
+        atomicAdd(J.flops, 12.0 * (m + (V ? n : 0)) * (0.5 * n * (n - 1.0)) * sweep);
 }
 
 // ------------------------------------------------------------------ FP64 Jacobi

@@ -424,26 +424,20 @@ public:
         }
         R_.flush_copy();
         if (low_precision(R_.precision())) {
-            // FP32 sweeps accumulate V, then C = B V in FP64 replaces B
-            std::vector<double*> V64(jobs_.size(), nullptr), C(jobs_.size(), nullptr);
+            // FP32 sweeps on B; the FP64 sweeps start from the rotated matrix widened
+            // to FP64.  Its FP32 rounding is of the order of the FP32 products that
+            // formed B, so the FP64 sweeps (rank decision, orthogonality) lose nothing
+            // against starting from B itself.
+            std::vector<double*> C(jobs_.size(), nullptr);
             for (size_t i = 0; i < jobs_.size(); ++i) {
                 Job& j = jobs_[i];
                 if (!j.B) continue;
                 int w = std::min(j.m, j.ncol);
                 if (w < 2) continue;
-                V64[i] = R_.dalloc((size_t)w * w);
-                R_.jacobi_pre(j.B, j.m, w, j.m, V64[i]);
+                C[i] = R_.dalloc((size_t)j.m * w);
+                R_.jacobi_pre(j.B, j.m, w, j.m, nullptr, C[i]);
             }
             R_.flush_pre();
-            for (size_t i = 0; i < jobs_.size(); ++i) {
-                if (!V64[i]) continue;
-                Job& j = jobs_[i];
-                int w = std::min(j.m, j.ncol);
-                C[i] = R_.dalloc((size_t)j.m * w);
-                R_.job(C[i], j.m, w, j.m, 0.0);
-                R_.term(j.B, 0, j.m, V64[i], 0, w, w);
-            }
-            R_.flush_gemm(H2_FP64);
             for (size_t i = 0; i < jobs_.size(); ++i)
                 if (C[i]) jobs_[i].B = C[i];
         }
