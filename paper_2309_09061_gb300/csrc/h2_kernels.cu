@@ -27,11 +27,17 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // warp-uniform halves of the 2 x 2 register block that hold no output of the
+    // job (edge tiles of ranks that are not multiples of 32): their FMAs are skipped
+    const bool row1 = tile.i0 + 16 < J.m;
+    const int wty = (threadIdx.x >> 5) * 2;  // the warp's first column index ty
+    const bool col0 = tile.j0 + wty < J.n, col1 = tile.j0 + wty + 16 < J.n;
     T acc[2][2] = {{0, 0}, {0, 0}};
     for (int it = 0; it < J.nt; ++it) {
         const GTerm P = terms[J.t0 + it];
         const double f = P.alpha * (P.scale ? *P.scale : 1.0);
         if (f == 0.0) continue;
+        const bool scaled = (f != 1.0);
         for (int k0 = 0; k0 < P.k; k0 += GK) {
             // stage op(A)[i0:i0+32, k0:k0+16] and op(B)[k0:k0+16, j0:j0+32]
             for (int e = threadIdx.x; e < GK * GB; e += GT) {
@@ -40,7 +46,7 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
                 int gi = tile.i0 + i, gk = k0 + kk;
                 double v = 0.0;
                 if (gi < J.m && gk < P.k) v = P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda];
-                As[kk][i] = (T)(f * v);
+                As[kk][i] = (T)(scaled ? f * v : v);
                 int j;
                 if (!P.tb) { kk = e % GK; j = e / GK; } else { j = e % GB; kk = e / GB; }
                 int gj = tile.j0 + j;
@@ -53,10 +59,14 @@ __global__ void __launch_bounds__(GT) k_gemm(const GTerm* __restrict__ terms, co
             auto mac = [&](int kk) {
                 T a0 = As[kk][tx], a1 = As[kk][tx + 16];
                 T b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
-                acc[0][0] += a0 * b0;
-                acc[1][0] += a1 * b0;
-                acc[0][1] += a0 * b1;
-                acc[1][1] += a1 * b1;
+                if (col0) {
+                    acc[0][0] += a0 * b0;
+                    if (row1) acc[1][0] += a1 * b0;
+                }
+                if (col1) {
+                    acc[0][1] += a0 * b1;
+                    if (row1) acc[1][1] += a1 * b1;
+                }
             };
             const int kc = min(GK, P.k - k0);  // the last chunk of a term is partial: skip its zero padding
             if (kc == GK) {
