@@ -658,17 +658,32 @@ class InducedRows:
     Q: Basis     # compressed induced row basis (isometric, nested)
     Rbar: dict   # t -> Q_t^* V_{X,t}  (= [R_{X,t}; 0])
     A: dict      # (t, s), s in C_t -> Q_t^* X|_{t x s} V_{Y,s}
+    RbarZ: dict = None  # t -> Q_t^* V_{Z,t} when Z's row basis is preserved as well
 
 
-def induced_rows(X: H2Matrix, Y: H2Matrix, eps: float) -> InducedRows:
-    """Fig. 4: compressed induced row basis of XY, preserving range(V_X)."""
+def same_basis(A: Basis, B: Basis) -> bool:
+    """Equal nested bases (ranks, leaf and transfer matrices)."""
+    if A is B:
+        return True
+    if A.rank != B.rank or set(A.leaf) != set(B.leaf) or set(A.transfer) != set(B.transfer):
+        return False
+    return (all(np.array_equal(A.leaf[t], B.leaf[t]) for t in A.leaf)
+            and all(np.array_equal(A.transfer[t], B.transfer[t]) for t in A.transfer))
+
+
+def induced_rows(X: H2Matrix, Y: H2Matrix, eps: float, VZ: Basis | None = None) -> InducedRows:
+    """Fig. 4: compressed induced row basis of XY, preserving range(V_X).
+    Reading of "+Z" with Z's own row basis: V_Z is preserved with V_X, the
+    preserved block of Eq. (induced_Vtilde) becoming [V_X,t | V_Z,t] (and
+    [Rbar_X E_X | Rbar_Z E_Z] above the leaves), so that Z's couplings are
+    representable in the new basis through Rbar_Z = Q_t^* V_Z,t."""
     tree = X.rows
     PXY = basis_products(X.W, Y.V)
     RW = basis_weights(Y.W)
     Zt = total_weights(Y, RW)
     rowb = X.blocks.row_blocks()
     C = {t: [s for s in rowb[t] if X.blocks.kind[(t, s)] != ADM] for t in rowb}
-    rank, leafm, transfer, Rbar, A = {}, {}, {}, {}, {}
+    rank, leafm, transfer, Rbar, A, RbarZ = {}, {}, {}, {}, {}, {}
 
     def compress(VX, blocks):
         """QR of the preserved block, SVD of the remainder (Eq. induced_Vtilde);
@@ -683,23 +698,27 @@ def induced_rows(X: H2Matrix, Y: H2Matrix, eps: float) -> InducedRows:
     def rec(t):
         if tree.is_leaf(t):
             VX = X.V.leaf[t]
+            VZt = VZ.leaf[t] if VZ is not None else None
             XV = {s: X.N[(t, s)] @ Y.V.leaf[s] for s in C[t]}
             blocks = []
             for s in C[t]:
                 nrm = spectral_norm(XV[s])
                 if nrm > TINY:
                     blocks.append(XV[s] @ Zt[s].T / nrm)  # Eq. induced_V, Sec. 5 scaling
-            Qt = compress(VX, blocks)
+            Qt = compress(VX if VZt is None else np.hstack([VX, VZt]), blocks)
             leafm[t] = Qt
             rank[t] = Qt.shape[1]
             for s in C[t]:
                 A[(t, s)] = Qt.T @ XV[s]
             Rbar[t] = Qt.T @ VX
+            if VZt is not None:
+                RbarZ[t] = Qt.T @ VZt
         else:
             ch = tree.children[t]
             for c in ch:
                 rec(c)
             VXh = np.vstack([Rbar[c] @ X.V.transfer[c] for c in ch])
+            VZh = np.vstack([RbarZ[c] @ VZ.transfer[c] for c in ch]) if VZ is not None else None
             Ahat = {}
             for s in C[t]:
                 rows = []
@@ -718,7 +737,7 @@ def induced_rows(X: H2Matrix, Y: H2Matrix, eps: float) -> InducedRows:
                 nrm = spectral_norm(Ahat[s])
                 if nrm > TINY:
                     blocks.append(Ahat[s] @ Zt[s].T / nrm)  # Eq. induced_Vhat, Sec. 5
-            Qh = compress(VXh, blocks)
+            Qh = compress(VXh if VZh is None else np.hstack([VXh, VZh]), blocks)
             rank[t] = Qh.shape[1]
             o = 0
             for c in ch:  # Eq. compression_nonleaf: split rows into transfers
@@ -727,9 +746,11 @@ def induced_rows(X: H2Matrix, Y: H2Matrix, eps: float) -> InducedRows:
             for s in C[t]:
                 A[(t, s)] = Qh.T @ Ahat[s]
             Rbar[t] = Qh.T @ VXh
+            if VZh is not None:
+                RbarZ[t] = Qh.T @ VZh
 
     rec(0)
-    return InducedRows(Basis(tree, rank, leafm, transfer), Rbar, A)
+    return InducedRows(Basis(tree, rank, leafm, transfer), Rbar, A, RbarZ if VZ is not None else None)
 
 
 # --------------------------------------------------------------------------
@@ -789,7 +810,9 @@ def induced_matrix(X: H2Matrix, Y: H2Matrix, Z: H2Matrix, rowsA: InducedRows, co
     matrices.  Dense leaves of T^XY hold the exact leaf-level products plus the
     expansion of what the ancestors pushed down.  Reading of "+Z": Z's row and
     column bases are X's row and Y's column bases, so S_Z enters the node
-    (t,r) as Rbar_t S_Z Rbar^W_r^* and N_Z enters the dense leaf."""
+    (t,r) as Rbar_t S_Z Rbar^W_r^* and N_Z enters the dense leaf; with bases of
+    its own, V_Z and W_Z were preserved in phase A and S_Z enters as
+    Rbar_Z,t S_Z Rbar^W_Z,r^*."""
     Q, QW = rowsA.Q, colsA.Q
     PXY = basis_products(X.W, Y.V)
     C = {}
@@ -808,7 +831,9 @@ def induced_matrix(X: H2Matrix, Y: H2Matrix, Z: H2Matrix, rowsA: InducedRows, co
             else:
                 raise AssertionError("two inadmissible leaves outside a dense T^XY leaf")
         if Z.blocks.kind.get((t, r)) == ADM:
-            acc += rowsA.Rbar[t] @ Z.S[(t, r)] @ colsA.Rbar[r].T
+            RZ = rowsA.Rbar if rowsA.RbarZ is None else rowsA.RbarZ
+            RWZ = colsA.Rbar if colsA.RbarZ is None else colsA.RbarZ
+            acc += RZ[t] @ Z.S[(t, r)] @ RWZ[r].T
         C[(t, r)] = acc
     S, N = {}, {}
 
@@ -1052,11 +1077,13 @@ def mul_add(Z: H2Matrix, X: H2Matrix, Y: H2Matrix, eps: float, eps_induced: floa
     """Z + X Y: compressed induced bases (Sec. 4-5), the H^2-matrix on T^XY,
     coarsening to Z's block tree (Sec. 6).  Reading: both phases use the same
     tolerance unless eps_induced is given (Sec. 7 uses 1e-4 for both).  The
-    structures of X, Y and Z must share one cluster tree; Z's row basis must be
-    X's row basis and Z's column basis Y's column basis."""
+    structures of X, Y and Z must share one cluster tree; when Z's row (column)
+    basis differs from X's row (Y's column) basis it is preserved as well."""
     epsA = eps if eps_induced is None else eps_induced
-    rowsA = induced_rows(X, Y, epsA)
-    colsA = induced_rows(Y.transpose(), X.transpose(), epsA)
+    VZ = None if same_basis(Z.V, X.V) else Z.V
+    WZ = None if same_basis(Z.W, Y.W) else Z.W
+    rowsA = induced_rows(X, Y, epsA, VZ)
+    colsA = induced_rows(Y.transpose(), X.transpose(), epsA, WZ)
     PT = build_product_tree(X, Y)
     G = induced_matrix(X, Y, Z, rowsA, colsA, PT)
     check_refinement(G, Z.blocks)
