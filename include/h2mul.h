@@ -180,9 +180,11 @@ H2_API int h2_build_interp_normals(const double* points, const double* normals, 
 /* Z <- Z + X Y (Sec. 1), approximated to the block-relative tolerance
  * opts->eps in both phases (Sec. 5, Sec. 6, Sec. 7).  X, Y and Z must share
  * one cluster tree and block tree (built from the same points, leaf size and
- * eta), and Z's row basis must be X's row basis and Z's column basis Y's
- * column basis (same Chebyshev order); otherwise H2_ERR_SHAPE /
- * H2_ERR_UNSUPPORTED.  The same handle may be passed as X, Y and Z.  On
+ * eta); otherwise H2_ERR_SHAPE.  Z's bases are free: when Z's row basis is
+ * not X's row basis (or Z's column basis not Y's column basis), for example
+ * Z from an earlier product or of another Chebyshev order, it is preserved in
+ * phase A beside V_X (W_Y), so that Z's couplings are represented in the new
+ * bases.  The same handle may be passed as X, Y and Z.  On
  * success Z holds new adaptive bases and couplings on its own block tree; on
  * error Z is unchanged (the result is built aside and swapped in at the end).
  * X and Y are only read. */

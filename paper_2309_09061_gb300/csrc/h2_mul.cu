@@ -485,9 +485,13 @@ struct Induced {
     std::shared_ptr<Basis> Q;
     PerCl Rbar;                         // Q_t^* V_{X,t}: rank_Q(t) x rank_VX(t)
     std::unordered_map<int, double*> A; // X block (not admissible) -> Q_t^* X_ts V_{Y,s}: rank_Q(t) x rank_VY(s)
+    bool zpres = false;                 // Z's own basis preserved as well
+    PerCl RbarZ;                        // Q_t^* V_{Z,t}: rank_Q(t) x rank_VZ(t) (zpres)
 };
 
-static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double eps, Counts& cnt) {
+// VZ: a basis preserved beside V_X (Z's own row basis, "+Z" with bases of its own), or null
+static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double eps, Counts& cnt,
+                            const Basis* VZ = nullptr) {
     const Tree& T = X.tree();
     const Basis& VX = X.rowb();
     const Basis& VY = Y.rowb();
@@ -507,12 +511,15 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
     Q.leaf.assign(T.nc, nullptr);
     Q.tr.assign(T.nc, nullptr);
     out.Rbar.init(T.nc);
+    out.zpres = (VZ != nullptr);
+    if (VZ) out.RbarZ.init(T.nc);
+    auto kz = [&](int t) { return VZ ? VZ->rank[t] : 0; };
     for (int l = T.L; l >= 0; --l) {
         const Arena::Mark mkl = R.mark();  // scratch of this level
         const int c0 = Tree::first(l), nl = Tree::count(l);
         const bool leaf = (l == T.L);
         std::vector<int> rows(nl), k1(nl), m2(nl);
-        std::vector<double*> VXh(nl), QX(nl);
+        std::vector<double*> VXh(nl), QX(nl), VZh(nl, nullptr);
         std::vector<std::vector<int>> C(nl);
         std::unordered_map<int, double*> M;
         std::unordered_map<int, double*> inv;
@@ -537,15 +544,24 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
                 rows[i] = (int)T.size[t];
                 VXh[i] = R.dalloc((size_t)rows[i] * VX.rank[t]);
                 R.copy(VX.leaf[t], rows[i], VXh[i], rows[i], rows[i], VX.rank[t], 0);
+                if (VZ) {
+                    VZh[i] = R.dalloc((size_t)std::max(1, rows[i] * kz(t)));
+                    R.copy(VZ->leaf[t], rows[i], VZh[i], rows[i], rows[i], kz(t), 0);
+                }
             } else {
                 int a1 = Tree::child(t, 0), a2 = Tree::child(t, 1);
                 rows[i] = Q.rank[a1] + Q.rank[a2];
                 VXh[i] = R.dalloc((size_t)std::max(1, rows[i] * VX.rank[t]));
+                if (VZ) VZh[i] = R.dalloc((size_t)std::max(1, rows[i] * kz(t)));
                 int o = 0;
                 for (int a : {a1, a2}) {
                     R.job(VXh[i] + o, Q.rank[a], VX.rank[t], rows[i], 0.0);
                     R.term(out.Rbar.p[a], 0, std::max(1, Q.rank[a]), VX.tr[a], 0, std::max(1, VX.rank[a]),
                            VX.rank[a]);
+                    if (VZ) {
+                        R.job(VZh[i] + o, Q.rank[a], kz(t), rows[i], 0.0);
+                        R.term(out.RbarZ.p[a], 0, std::max(1, Q.rank[a]), VZ->tr[a], 0, std::max(1, kz(a)), kz(a));
+                    }
                     o += Q.rank[a];
                 }
                 for (int b : C[i]) {
@@ -608,28 +624,29 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         // complete QR of VX-hat; tall transposed remainder; SVD
         int* d_counts = (int*)R.dalloc(nl);
         H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
-        // With rows <= k_X the complete Q spans all of K^rows, which contains range(VX):
-        // the identity is an equally valid choice and needs no factorisation.
+        // With rows <= k_X (+ k_Z) the complete Q spans all of K^rows, which contains the
+        // preserved range: the identity is an equally valid choice and needs no factorisation.
         int rid = 0;
         for (int i = 0; i < nl; ++i)
-            if (rows[i] > 0 && rows[i] <= VX.rank[c0 + i]) rid = std::max(rid, rows[i]);
+            if (rows[i] > 0 && rows[i] <= VX.rank[c0 + i] + kz(c0 + i)) rid = std::max(rid, rows[i]);
         double* ident = nullptr;
         if (rid > 0) {
             ident = R.dalloc((size_t)rid * rid);
             launch_set_identity(ident, rid, rid, rid, R.stream());
         }
         for (int i = 0; i < nl; ++i) {
-            int t = c0 + i, kx = VX.rank[t];
-            k1[i] = std::min(rows[i], kx);
+            int t = c0 + i, kx = VX.rank[t], kp = kx + kz(t);  // preserved columns [VX-hat | VZ-hat]
+            k1[i] = std::min(rows[i], kp);
             m2[i] = rows[i] - k1[i];
             QX[i] = R.dalloc((size_t)std::max(1, rows[i] * rows[i]));
-            if (rows[i] > 0 && rows[i] <= kx) {
+            if (rows[i] > 0 && rows[i] <= kp) {
                 R.copy(ident, rid, QX[i], rows[i], rows[i], rows[i], 0);
                 continue;
             }
-            double* work = R.dalloc((size_t)std::max(1, rows[i] * kx));
+            double* work = R.dalloc((size_t)std::max(1, rows[i] * kp));
             R.copy(VXh[i], rows[i], work, rows[i], rows[i], kx, 0);
-            R.qr(work, rows[i], kx, rows[i], nullptr, 1, QX[i], rows[i], rows[i]);
+            if (VZ && kz(t) > 0) R.copy(VZh[i], rows[i], work + (size_t)kx * rows[i], rows[i], rows[i], kz(t), 0);
+            R.qr(work, rows[i], kp, rows[i], nullptr, 1, QX[i], rows[i], rows[i]);
         }
         R.flush_copy();
         R.flush_qr();
@@ -721,6 +738,13 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             out.Rbar.p[t] = R.palloc((size_t)std::max(1, kt * VX.rank[t]));
             R.job(out.Rbar.p[t], kt, VX.rank[t], std::max(1, kt), 0.0);
             R.term(Qh[i], 1, rows[i], VXh[i], 0, std::max(1, rows[i]), rows[i]);
+            if (VZ) {  // Rbar_Z,t = Q-hat^* VZ-hat
+                out.RbarZ.rows[t] = kt;
+                out.RbarZ.cols[t] = kz(t);
+                out.RbarZ.p[t] = R.palloc((size_t)std::max(1, kt * kz(t)));
+                R.job(out.RbarZ.p[t], kt, kz(t), std::max(1, kt), 0.0);
+                R.term(Qh[i], 1, rows[i], VZh[i], 0, std::max(1, rows[i]), rows[i]);
+            }
         }
         R.flush_copy();
         R.flush_gemm();
@@ -781,7 +805,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     alloc_cup(0);
     // per-chunk device pointers by node or block (cleared after each chunk)
     Slots PSY(Y.bt().kind.size()), WN(Y.bt().kind.size()), XV(X.bt().kind.size());
-    Slots U1(nn), U2(nn), U3(nn), L1(nn), R1(nn), CQ(nn);
+    Slots U1(nn), U2(nn), U3(nn), L1(nn), R1(nn), CQ(nn), ZR(nn);
     // nodes of a level are processed in chunks that bound the scratch
 #ifndef H2_TMAT_CHUNK
 #define H2_TMAT_CHUNK 16384
@@ -822,10 +846,11 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 o += (size_t)VX.rank[N.t[n]] * WY.rank[N.s[n]];
             }
         }
+        const bool zgen = ra.zpres || ca.zpres;  // Z with bases of its own: enters C below
         for (int n : nodes) {
             int t = N.t[n], r = N.s[n];
             int bz = Z->st->blocks.find(t, r);
-            if (bz >= 0 && Z->st->blocks.kind[bz] == ADM)
+            if (!zgen && bz >= 0 && Z->st->blocks.kind[bz] == ADM)
                 R.copy(ZV.S(bz).p, ZV.S(bz).ld, U1[n], VX.rank[t], VX.rank[t], WY.rank[r], 0);
         }
         R.flush_copy();
@@ -843,9 +868,13 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
             }
         }
         R.flush_gemm();
-        // U2 = Rbar U1 + sum_b A S_Y,  U3 = sum_c S_X B^*  (coupling nodes)
+        // U2 = Rbar U1 + sum_b A S_Y,  U3 = sum_c S_X B^*  (coupling nodes);
+        // Z with bases of its own: ZR = Rbar_Z S_Z
         U2.clear();
         U3.clear();
+        ZR.clear();
+        const PerCl& RZ = ra.zpres ? ra.RbarZ : ra.Rbar;
+        const PerCl& RWZ = ca.zpres ? ca.RbarZ : ca.Rbar;
         for (int n : nodes) {
             if (N.kind[n] == DENSE) continue;
             int t = N.t[n], r = N.s[n];
@@ -859,6 +888,13 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                     T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
                     cnt.flops += 2.0 * Q.rank[t] * WY.rank[r] * VY.rank[s];
                 }
+            }
+            int bz = Z->st->blocks.find(t, r);
+            if (zgen && bz >= 0 && Z->st->blocks.kind[bz] == ADM) {
+                const int kzr = Z->V->rank[t], kzc = Z->W->rank[r];
+                ZR[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * kzc));
+                R.job(ZR[n], Q.rank[t], kzc, std::max(1, Q.rank[t]), 0.0);
+                R.term(RZ.p[t], 0, std::max(1, Q.rank[t]), ZV.S(bz).p, 0, std::max(1, kzr), kzr);
             }
             U3[n] = R.dalloc((size_t)std::max(1, VX.rank[t] * QW.rank[r]));
             R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
@@ -880,6 +916,8 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
             R.job(G.C[n], Q.rank[t], QW.rank[r], std::max(1, Q.rank[t]), 0.0);
             R.term(U2[n], 0, std::max(1, Q.rank[t]), ca.Rbar.p[r], 1, std::max(1, QW.rank[r]), WY.rank[r]);
             R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U3[n], 0, VX.rank[t], VX.rank[t]);
+            if (ZR.has(n))
+                R.term(ZR[n], 0, std::max(1, Q.rank[t]), RWZ.p[r], 1, std::max(1, QW.rank[r]), Z->W->rank[r]);
             cnt.flops += 2.0 * Q.rank[t] * QW.rank[r] * (WY.rank[r] + VX.rank[t]);
         }
         R.flush_gemm();
@@ -946,6 +984,14 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 CQ[n] = R.dalloc((size_t)std::max(1, Q.rank[t]) * T.size[r]);
                 R.job(CQ[n], Q.rank[t], (int)T.size[r], std::max(1, Q.rank[t]), 0.0);
                 R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.leaf[r], 1, (int)T.size[r], QW.rank[r]);
+                // Z with bases of its own, admissible on this dense leaf: ZL = V_Z,t S_Z
+                const int bz = Z->st->blocks.find(t, r);
+                if (zgen && bz >= 0 && Z->st->blocks.kind[bz] == ADM) {
+                    const int kzr = Z->V->rank[t], kzc = Z->W->rank[r];
+                    ZR[n] = R.dalloc((size_t)std::max(1, (int)T.size[t] * kzc));
+                    R.job(ZR[n], (int)T.size[t], kzc, (int)T.size[t], 0.0);
+                    R.term(Z->V->leaf[t], 0, (int)T.size[t], ZV.S(bz).p, 0, std::max(1, kzr), kzr);
+                }
             }
             R.flush_gemm();
             for (int n : nodes) {
@@ -994,6 +1040,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 R.term(L1[n], 0, mt, WY.leaf[r], 1, mr, WY.rank[r]);
                 R.term(VX.leaf[t], 0, mt, R1[n], 0, VX.rank[t], VX.rank[t]);
                 R.term(Q.leaf[t], 0, mt, CQ[n], 0, std::max(1, Q.rank[t]), Q.rank[t]);
+                if (ZR.has(n)) R.term(ZR[n], 0, mt, Z->W->leaf[r], 1, mr, Z->W->rank[r]);
             }
             R.flush_gemm();
         }
@@ -1747,20 +1794,23 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     clk.mark();
     // phase A: compressed induced row and column bases (prep included)
     const OpView Yt{Ym, true}, Xt{Xm, true};
+    // "+Z" with bases of its own: V_Z (W_Z) preserved beside V_X (W_Y) in phase A
+    const Basis* VZ = same_row_basis(Zm, Xm) ? nullptr : Zm->V.get();
+    const Basis* WZ = same_col_basis(Zm, Ym) ? nullptr : Zm->W.get();
     Induced ra, ca;
     if (beside) {
         stream_after(side.s, st);
         clk2.mark();
-        Beside col([&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2); });
-        ra = induced_rows(R, X, Y, eps, cnt);
+        Beside col([&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ); });
+        ra = induced_rows(R, X, Y, eps, cnt, VZ);
         clk.mark();
         col.join();
     } else {
-        ra = induced_rows(R, X, Y, eps, cnt);
+        ra = induced_rows(R, X, Y, eps, cnt, VZ);
         clk.mark();
         stream_after(side.s, st);
         clk2.mark();
-        ca = induced_rows(R2, Yt, Xt, eps, cnt2);
+        ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ);
     }
     clk2.mark();
     stream_after(st, side.s);
@@ -2072,7 +2122,6 @@ extern "C" int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, 
                  (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
         return H2_ERR_ARG;
     if (X->st->fingerprint != Y->st->fingerprint || X->st->fingerprint != Z->st->fingerprint) return H2_ERR_SHAPE;
-    if (!same_row_basis(Z, X) || !same_col_basis(Z, Y)) return H2_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != Z->device) return H2_ERR_ARG;
     return run_guarded_mul(Z, X, Y, opts);

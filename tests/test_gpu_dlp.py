@@ -66,20 +66,22 @@ def test_dlp_exact_mode():
     assert rel(P.h2_to_dense(Z), D + D @ D) <= 1e-12
 
 
-def test_dlp_mixed_operands():
-    """X = DLP (V != W) with Y = Laplace on the same widened boxes is refused
-    (different row bases); the supported relations: Z's row basis is X's and
-    Z's column basis is Y's."""
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED])
+def test_dlp_mixed_operands(precision):
+    """Operands whose bases differ from Z's: a Laplace Z (bounding-box Lagrange
+    bases) plus the product of two double-layer operators, and a DLP Z plus a
+    Laplace-times-DLP product; Z's bases are preserved in phase A."""
     eps = 1e-5
     pts, nrm, st = case()
     K = P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 3, normals=nrm)
     L = P.h2_build_interp(pts, P.H2_K_LAPLACE, 16, 1.5, 3)
-    with pytest.raises(P.H2Error) as e:  # Laplace Z: column basis differs from the DLP's W
-        P.h2_mul_add(P.h2_clone(L), K, K, eps)
-    assert e.value.code == -6
-    with pytest.raises(P.H2Error) as e:  # DLP rows (widened boxes) vs Laplace rows (bounding boxes)
-        P.h2_mul_add(P.h2_clone(K), L, K, eps)
-    assert e.value.code == -6
+    DK, DL = P.h2_to_dense(K), P.h2_to_dense(L)
+    Z = P.h2_clone(L)
+    P.h2_mul_add(Z, K, K, eps, precision)
+    assert rel(P.h2_to_dense(Z), DL + DK @ DK) <= 2 * eps
+    Z = P.h2_clone(K)
+    P.h2_mul_add(Z, L, K, eps, precision)
+    assert rel(P.h2_to_dense(Z), DK + DL @ DK) <= 2 * eps
     with pytest.raises(P.H2Error) as e:  # the double-layer kernel needs normals
         P.h2_build_interp(pts, P.H2_K_DLP, 16, 1.5, 3)
     assert e.value.code == -1
