@@ -1127,3 +1127,49 @@ def spectral_error(Dr: np.ndarray, D0: np.ndarray, DX: np.ndarray, DY: np.ndarra
     p = power_norm(P, Pt, x0, steps)
     e = power_norm(lambda x: Dr @ x - P(x), lambda y: Dr.T @ y - Pt(y), x0, steps)
     return (e / p if p > 0.0 else 0.0), p
+
+
+# --------------------------------------------------------------------------
+# Recompression of an input H^2-matrix (Fig. 1 with the isometric factors, Fig. 7)
+# --------------------------------------------------------------------------
+
+def orthogonalize(B: Basis):
+    """B_t = Q_t R_t with Q nested and isometric (Fig. 1, keeping the Q factors):
+    leaves by a thin QR of B_t, parents by a thin QR of the stacked R_{t'} E_{t'};
+    the rows of that Q-hat split into the children's transfer matrices.
+    Returns (Q, R) with R[t] of size rank_Q(t) x rank_B(t)."""
+    tree = B.tree
+    leaf, transfer, rank, R = {}, {}, {}, {}
+
+    def rec(t):
+        if tree.is_leaf(t):
+            q, r = np.linalg.qr(B.leaf[t])
+            leaf[t], R[t], rank[t] = q, r, q.shape[1]
+            return
+        ch = tree.children[t]
+        for c in ch:
+            rec(c)
+        q, r = np.linalg.qr(np.vstack([R[c] @ B.transfer[c] for c in ch]))
+        R[t], rank[t] = r, q.shape[1]
+        o = 0
+        for c in ch:
+            transfer[c] = q[o:o + rank[c]]
+            o += rank[c]
+
+    rec(0)
+    return Basis(tree, rank, leaf, transfer), R
+
+
+def recompress(A: H2Matrix, eps: float) -> H2Matrix:
+    """Adaptive isometric bases for an input H^2-matrix: orthogonalize both bases,
+    move the couplings into them (S' = R_V S R_W^*), then coarsen with the
+    matrix's own block tree as the tree of the intermediate matrix (Fig. 7) and
+    project (the final couplings of Sec. 6); the block-relative tolerance eps
+    is that of the product's second phase."""
+    QV, RV = orthogonalize(A.V)
+    QW, RW = (QV, RV) if A.W is A.V else orthogonalize(A.W)
+    S = {(t, s): RV[t] @ m @ RW[s].T for (t, s), m in A.S.items()}
+    G = H2Matrix(A.blocks, QV, QW, S, dict(A.N))
+    rowsB = coarsen_rows(G, A.blocks, eps)
+    colsB = coarsen_rows(G.transpose(), A.blocks.transpose(), eps)
+    return final_matrix(G, A.blocks, rowsB, colsB)
