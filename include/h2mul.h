@@ -220,7 +220,19 @@ H2_API int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_d
  * A^* e_i.  Errors: H2_ERR_ARG, H2_ERR_OOM, H2_ERR_CUDA. */
 H2_API int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t nvec, int trans, const h2_opts* opts);
 
-/* Relative spectral error of a computed product (the eps_2 of Sec. 7):
+/* A <- A with adaptive isometric bases (recompression of an input, for
+ * example a Chebyshev matrix whose rank m^3 exceeds what opts->eps needs).
+ * The bases are orthogonalized (the QR factorisations of Fig. 1 with their
+ * isometric factors kept: V = Q R), the couplings are moved into them
+ * (S' = R_V,t S R_W,s^*), and the second phase of the product (Sec. 6:
+ * coarsening, Fig. 7, and the final couplings) runs with A's own block tree
+ * as the intermediate's tree, at the block-relative tolerance opts->eps
+ * (0 keeps every nonzero singular value) and in opts->precision.  On error A
+ * is unchanged.  Errors: H2_ERR_ARG, H2_ERR_NUMERIC, H2_ERR_TIMEOUT, H2_ERR_OOM,
+ * H2_ERR_CUDA. */
+H2_API int h2_recompress(h2_matrix* A, const h2_opts* opts);
+
+/* Relative spectral error of a computed product (the eps_2 of Sec. 7):/* Relative spectral error of a computed product (the eps_2 of Sec. 7):
  *   *eps2 = ||Zr - (Z0 + X Y)||_2 / ||Z0 + X Y||_2,   *norm = ||Z0 + X Y||_2,
  * where Zr is the result of h2_mul_add on a copy of Z0 (for example a clone
  * taken before the call).  Each spectral norm is estimated by `steps` steps of

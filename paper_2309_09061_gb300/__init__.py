@@ -22,7 +22,7 @@ H2_FP64, H2_MIXED, H2_TC = 0, 1, 2
 
 EXPORTED = ["h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
             "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error",
-            "h2_free", "h2_error_string", "h2_last_error_message"]
+            "h2_recompress", "h2_free", "h2_error_string", "h2_last_error_message"]
 
 
 class H2Error(RuntimeError):
@@ -91,6 +91,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_matvec.argtypes = [vp, vp, vp, i64, ci, vp]
     lib.h2_mul_add_batched.argtypes = [vp, vp, vp, ci, vp, vp]
     lib.h2_product_error.argtypes = [vp, vp, vp, vp, vp, ci, vp, vp, vp]
+    lib.h2_recompress.argtypes = [vp, vp]
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
@@ -98,7 +99,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_last_error_message.restype = ctypes.c_char_p
     for f in ("h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
               "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec",
-              "h2_mul_add_batched", "h2_product_error"):
+              "h2_mul_add_batched", "h2_product_error", "h2_recompress"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -244,6 +245,14 @@ def h2_matvec(A: H2Matrix, x, y, trans: bool = False, stream: int | None = None)
     _check(load().h2_matvec(A.handle, x.data_ptr(), y.data_ptr(), nv, 1 if trans else 0, ctypes.byref(o)),
            "h2_matvec")
     return y
+
+
+def h2_recompress(A: H2Matrix, eps: float, precision: int = H2_FP64, stream: int | None = None) -> dict:
+    """A <- A with adaptive isometric bases at tolerance eps (in place); returns statistics."""
+    st = Stats()
+    o = _opts(eps=eps, precision=precision, stream=stream, stats=st)
+    _check(load().h2_recompress(A.handle, ctypes.byref(o)), "h2_recompress")
+    return st.as_dict()
 
 
 def h2_product_error(Zr: H2Matrix, Z0: H2Matrix, X: H2Matrix, Y: H2Matrix, x0=None, steps: int = 20,

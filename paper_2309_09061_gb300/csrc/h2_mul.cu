@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <functional>
 #include <atomic>
 #include <map>
@@ -1778,55 +1779,20 @@ private:
     std::exception_ptr err_;
 };
 
-static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, const h2_opts* opts) {
-    const double eps = opts ? opts->eps : 1e-6;
-    const int prec = opts ? opts->precision : H2_FP64;
-    cudaStream_t st = stream_of(opts);
-    auto t_host0 = std::chrono::steady_clock::now();
-    SideStream side;
-    Runner R(st, prec);
-    Runner R2(side.s, prec);  // column sides; its outputs live until the end of the call
-    const bool beside = low_precision(prec);
-    PhaseClock clk(st), clk2(side.s);
-    Counts cnt, cnt2;
-    const OpView X{Xm, false}, Y{Ym, false};
-    const Tree& T = X.tree();
-    clk.mark();
-    // phase A: compressed induced row and column bases (prep included)
-    const OpView Yt{Ym, true}, Xt{Xm, true};
-    // "+Z" with bases of its own: V_Z (W_Z) preserved beside V_X (W_Y) in phase A
-    const Basis* VZ = same_row_basis(Zm, Xm) ? nullptr : Zm->V.get();
-    const Basis* WZ = same_col_basis(Zm, Ym) ? nullptr : Zm->W.get();
-    Induced ra, ca;
-    if (beside) {
-        stream_after(side.s, st);
-        clk2.mark();
-        Beside col([&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ); });
-        ra = induced_rows(R, X, Y, eps, cnt, VZ);
-        clk.mark();
-        col.join();
-    } else {
-        ra = induced_rows(R, X, Y, eps, cnt, VZ);
-        clk.mark();
-        stream_after(side.s, st);
-        clk2.mark();
-        ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ);
-    }
-    clk2.mark();
-    stream_after(st, side.s);
-    // the intermediate H^2-matrix on T^XY
-    Intermediate G;
-    G.PT = &cached_product_tree(*Xm->st, *Ym->st);
-    G.Q = ra.Q;
-    G.QW = ca.Q;
-    const BlockTree& Zb = Zm->st->blocks;
-    for (int b = 0; b < (int)Zb.kind.size(); ++b) {
-        int n = G.PT->nodes.find(Zb.t[b], Zb.s[b]);
-        if (n < 0 || (Zb.kind[b] == DENSE && G.PT->nodes.kind[n] != DENSE))
-            throw Error(H2_ERR_UNSUPPORTED, "the product block tree does not refine Z's block tree");
-    }
-    induced_matrix(R, X, Y, Zm, ra, ca, G, cnt);
-    clk.mark();
+// Phase B (Sec. 6) and the final couplings for an intermediate H^2-matrix G with
+// isometric bases on a block tree that refines the target block tree Zb:
+// block weights, coarsened row and column bases (Fig. 7, the two sides beside
+// each other in the low-precision forms), final couplings, and the result on Zb
+// in persistent memory.  Used by the product and by the recompression.
+struct PhaseB {
+    std::unique_ptr<h2_matrix> res;
+    Coarse rb, cb;
+    int nodes = 0;
+};
+
+static PhaseB coarsen_and_project(Runner& R, Runner& R2, cudaStream_t st, SideStream& side, bool beside,
+                                  const Tree& T, const BlockTree& Zb, const h2_matrix* Zm, Intermediate& G,
+                                  double eps, Counts& cnt, PhaseClock& clk, PhaseClock& clk2) {
     // phase B: coarsening to Z's block tree
     const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
@@ -1875,7 +1841,9 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
         R.launches += 2;
     }
     GView GR{&G, &T, false}, GC{&G, &T, true};
-    Coarse rb, cb;
+    PhaseB out;
+    Coarse& rb = out.rb;
+    Coarse& cb = out.cb;
     if (beside) {
         stream_after(side.s, st);
         clk2.mark();
@@ -1932,6 +1900,65 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     launch_check_finite(chunk->p, chunk->len, R.svd_flag(), st);
     R.end(9, 0.0, 8.0 * chunk->len);
     R.launches++;
+    out.nodes = nn;
+    out.res = std::move(res);
+    return out;
+}
+
+static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, const h2_opts* opts) {
+    const double eps = opts ? opts->eps : 1e-6;
+    const int prec = opts ? opts->precision : H2_FP64;
+    cudaStream_t st = stream_of(opts);
+    auto t_host0 = std::chrono::steady_clock::now();
+    SideStream side;
+    Runner R(st, prec);
+    Runner R2(side.s, prec);  // column sides; its outputs live until the end of the call
+    const bool beside = low_precision(prec);
+    PhaseClock clk(st), clk2(side.s);
+    Counts cnt, cnt2;
+    const OpView X{Xm, false}, Y{Ym, false};
+    const Tree& T = X.tree();
+    clk.mark();
+    // phase A: compressed induced row and column bases (prep included)
+    const OpView Yt{Ym, true}, Xt{Xm, true};
+    // "+Z" with bases of its own: V_Z (W_Z) preserved beside V_X (W_Y) in phase A
+    const Basis* VZ = same_row_basis(Zm, Xm) ? nullptr : Zm->V.get();
+    const Basis* WZ = same_col_basis(Zm, Ym) ? nullptr : Zm->W.get();
+    Induced ra, ca;
+    if (beside) {
+        stream_after(side.s, st);
+        clk2.mark();
+        Beside col([&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ); });
+        ra = induced_rows(R, X, Y, eps, cnt, VZ);
+        clk.mark();
+        col.join();
+    } else {
+        ra = induced_rows(R, X, Y, eps, cnt, VZ);
+        clk.mark();
+        stream_after(side.s, st);
+        clk2.mark();
+        ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ);
+    }
+    clk2.mark();
+    stream_after(st, side.s);
+    // the intermediate H^2-matrix on T^XY
+    Intermediate G;
+    G.PT = &cached_product_tree(*Xm->st, *Ym->st);
+    G.Q = ra.Q;
+    G.QW = ca.Q;
+    const BlockTree& Zb = Zm->st->blocks;
+    for (int b = 0; b < (int)Zb.kind.size(); ++b) {
+        int n = G.PT->nodes.find(Zb.t[b], Zb.s[b]);
+        if (n < 0 || (Zb.kind[b] == DENSE && G.PT->nodes.kind[n] != DENSE))
+            throw Error(H2_ERR_UNSUPPORTED, "the product block tree does not refine Z's block tree");
+    }
+    induced_matrix(R, X, Y, Zm, ra, ca, G, cnt);
+    clk.mark();
+    PhaseB pb = coarsen_and_project(R, R2, st, side, beside, T, Zb, Zm, G, eps, cnt, clk, clk2);
+    const int nn = pb.nodes;
+    const Coarse& rb = pb.rb;
+    const Coarse& cb = pb.cb;
+    auto& res = pb.res;
     clk.mark();
     int flag = 0, flag2 = 0;
     H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1979,6 +2006,175 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     Zm->chunks = std::move(res->chunks);
     Zm->kernel = -1;
     Zm->order = 0;
+}
+
+// ------------------------------------------------------------------ recompression
+// Fig. 1 with the isometric factors kept: B_t = Q_t R_t with Q nested and
+// isometric.  Leaves: thin QR of B_t with the explicit factor; parents: thin QR
+// of the stacked R_{t'} E_{t'}, whose isometric factor splits row-wise into the
+// children's transfer matrices.  Rf[t] (rank_Q(t) x rank_B(t)) in persistent memory.
+static std::shared_ptr<Basis> orthogonalize(Runner& R, const Tree& T, const Basis& B, PerCl& Rf) {
+    auto Q = std::make_shared<Basis>();
+    Q->rank.assign(T.nc, 0);
+    Q->leaf.assign(T.nc, nullptr);
+    Q->tr.assign(T.nc, nullptr);
+    Rf.init(T.nc);
+    size_t need = 0;
+    for (int c = Tree::first(T.L); c < T.nc; ++c) need += (size_t)T.size[c] * std::min<int64_t>(T.size[c], B.rank[c]);
+    auto lc = std::make_shared<DevBuf>();
+    lc->alloc(std::max<size_t>(need, 1));
+    Q->chunks.push_back(lc);
+    size_t off = 0;
+    for (int c = Tree::first(T.L); c < T.nc; ++c) {
+        const int m = (int)T.size[c], k = B.rank[c], q = std::min(m, k);
+        Q->rank[c] = q;
+        Rf.rows[c] = q;
+        Rf.cols[c] = k;
+        Rf.p[c] = R.palloc((size_t)std::max(1, q * k));
+        if (q == 0) continue;
+        Q->leaf[c] = lc->p + off;
+        off += (size_t)m * q;
+        double* work = R.dalloc((size_t)m * k);
+        R.copy(B.leaf[c], m, work, m, m, k, 0);
+        R.qr(work, m, k, m, Rf.p[c], q, Q->leaf[c], m, q);
+    }
+    R.flush_copy();
+    R.flush_qr();
+    for (int l = T.L - 1; l >= 0; --l) {
+        const int c0 = Tree::first(l), nl = Tree::count(l);
+        std::vector<double*> Qh(nl, nullptr);
+        std::vector<int> rows(nl);
+        for (int i = 0; i < nl; ++i) {
+            const int p = c0 + i, c1 = Tree::child(p, 0), c2 = Tree::child(p, 1), k = B.rank[p];
+            rows[i] = Q->rank[c1] + Q->rank[c2];
+            const int q = std::min(rows[i], k);
+            Q->rank[p] = q;
+            Rf.rows[p] = q;
+            Rf.cols[p] = k;
+            Rf.p[p] = R.palloc((size_t)std::max(1, q * k));
+            if (q == 0) continue;
+            double* st = R.dalloc((size_t)rows[i] * k);
+            int o = 0;
+            for (int c : {c1, c2}) {
+                R.job(st + o, Q->rank[c], k, rows[i], 0.0);
+                R.term(Rf.p[c], 0, std::max(1, Q->rank[c]), B.tr[c], 0, std::max(1, B.rank[c]), B.rank[c]);
+                o += Q->rank[c];
+            }
+            Qh[i] = R.dalloc((size_t)rows[i] * q);
+            R.qr(st, rows[i], k, rows[i], Rf.p[p], q, Qh[i], rows[i], q);
+        }
+        R.flush_gemm(H2_FP64);
+        R.flush_qr();
+        size_t tneed = 0;
+        for (int i = 0; i < nl; ++i) tneed += (size_t)rows[i] * Q->rank[c0 + i];
+        auto tc = std::make_shared<DevBuf>();
+        tc->alloc(std::max<size_t>(tneed, 1));
+        Q->chunks.push_back(tc);
+        size_t to = 0;
+        for (int i = 0; i < nl; ++i) {
+            const int p = c0 + i, q = Q->rank[p];
+            int o = 0;
+            for (int c : {Tree::child(p, 0), Tree::child(p, 1)}) {
+                Q->tr[c] = tc->p + to;
+                to += (size_t)std::max(0, Q->rank[c] * q);
+                if (q > 0 && Q->rank[c] > 0) R.copy(Qh[i] + o, rows[i], Q->tr[c], Q->rank[c], Q->rank[c], q, 0);
+                o += Q->rank[c];
+            }
+        }
+        R.flush_copy();
+    }
+    return Q;
+}
+
+// A <- A with adaptive isometric bases at the block-relative tolerance eps:
+// orthogonalized bases, couplings moved into them (S' = R_V,t S R_W,s^*), then
+// the coarsening and final couplings of the product's second phase with A's own
+// block tree as the tree of the intermediate matrix.
+static void recompress(h2_matrix* A, const h2_opts* opts) {
+    const double eps = opts ? opts->eps : 1e-6;
+    const int prec = opts ? opts->precision : H2_FP64;
+    cudaStream_t st = stream_of(opts);
+    auto t_host0 = std::chrono::steady_clock::now();
+    SideStream side;
+    Runner R(st, prec);
+    Runner R2(side.s, prec);
+    PhaseClock clk(st), clk2(side.s);
+    Counts cnt;
+    const Tree& T = A->st->tree;
+    const BlockTree& B = A->st->blocks;
+    const int nb = (int)B.kind.size();
+    clk.mark();
+    PerCl RV, RW;
+    std::shared_ptr<Basis> QV = orthogonalize(R, T, *A->V, RV);
+    std::shared_ptr<Basis> QW = (A->W == A->V) ? QV : orthogonalize(R, T, *A->W, RW);
+    const PerCl& RWr = (A->W == A->V) ? RV : RW;
+    ProductTree plan;  // the intermediate's tree is A's own block tree
+    plan.nodes = B;
+    plan.triples.assign(nb, {});
+    plan.tri_blocks.assign(nb, {});
+    Intermediate G;
+    G.PT = &plan;
+    G.Q = QV;
+    G.QW = QW;
+    G.C.assign(nb, nullptr);
+    std::vector<double*> tmp(nb, nullptr);
+    for (int b = 0; b < nb; ++b) {
+        if (B.kind[b] == DENSE) G.C[b] = A->blk[b];
+        if (B.kind[b] != ADM) continue;
+        const int t = B.t[b], s = B.s[b], kvt = A->V->rank[t], kws = A->W->rank[s], ks = QW->rank[s];
+        tmp[b] = R.dalloc((size_t)std::max(1, kvt * ks));
+        R.job(tmp[b], kvt, ks, std::max(1, kvt), 0.0);
+        R.term(A->blk[b], 0, std::max(1, kvt), RWr.p[s], 1, std::max(1, ks), kws);
+    }
+    R.flush_gemm(H2_FP64);
+    for (int b = 0; b < nb; ++b) {
+        if (B.kind[b] != ADM) continue;
+        const int t = B.t[b], s = B.s[b], kvt = A->V->rank[t], kt = QV->rank[t], ks = QW->rank[s];
+        G.C[b] = R.palloc((size_t)std::max(1, kt * ks));
+        R.job(G.C[b], kt, ks, std::max(1, kt), 0.0);
+        R.term(RV.p[t], 0, std::max(1, kt), tmp[b], 0, std::max(1, kvt), kvt);
+    }
+    R.flush_gemm(H2_FP64);
+    clk.mark();
+    clk2.mark();
+    clk2.mark();
+    PhaseB pb = coarsen_and_project(R, R2, st, side, low_precision(prec), T, B, A, G, eps, cnt, clk, clk2);
+    clk.mark();
+    int flag = 0, flag2 = 0;
+    H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(&flag2, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    H2_CUDA(cudaGetLastError());
+    H2_CUDA(cudaStreamSynchronize(st));
+    flag |= flag2;
+    if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
+    if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
+    if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
+    if (opts && opts->stats) {
+        h2_stats* S = opts->stats;
+        std::memset(S, 0, sizeof(h2_stats));
+        S->t_rows_a_ms = clk.ms(0);  // orthogonalization and couplings
+        S->t_rows_b_ms = clk.ms(1);
+        S->t_cols_b_ms = clk2.ms(2);
+        S->t_mat_b_ms = clk.ms(2);
+        S->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_host0).count();
+        S->kernel_launches = R.launches + R2.launches;
+        S->product_nodes = nb;
+        S->max_rank_a = std::max(QV->max_rank(), QW->max_rank());
+        S->max_rank_b = std::max(pb.rb.Qn->max_rank(), pb.cb.Qn->max_rank());
+        S->flops = cnt.flops;
+        R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+        R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+    }
+    R.release_all();
+    R2.release_all();
+    H2_CUDA(cudaStreamSynchronize(st));
+    A->V = pb.res->V;
+    A->W = pb.res->W;
+    A->blk = std::move(pb.res->blk);
+    A->chunks = std::move(pb.res->chunks);
+    A->kernel = -1;
+    A->order = 0;
+    A->vtag = A->wtag = 0;
 }
 
 }  // namespace h2
@@ -2105,6 +2301,26 @@ extern "C" int h2_product_error(const h2_matrix* Zr, const h2_matrix* Z0, const 
     if (Y->st->fingerprint != f || Z0->st->fingerprint != f || Zr->st->fingerprint != f) return H2_ERR_SHAPE;
     try {
         product_error(Zr, Z0, X, Y, x0, steps, stream_of(opts), eps2, norm);
+        return H2_OK;
+    } catch (const Error& e) {
+        h2_set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        h2_set_last_error(e.what());
+        return H2_ERR_CUDA;
+    }
+}
+
+extern "C" int h2_recompress(h2_matrix* A, const h2_opts* opts) {
+    using namespace h2;
+    if (!A) return H2_ERR_ARG;
+    if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
+                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
+        return H2_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != A->device) return H2_ERR_ARG;
+    try {
+        recompress(A, opts);
         return H2_OK;
     } catch (const Error& e) {
         h2_set_last_error(e.what());
