@@ -126,13 +126,28 @@ __device__ __forceinline__ float f64_to_f32(double v) {
     return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
-// exact FP32 -> FP64 widening by integer operations (zero for zero input)
-__device__ __forceinline__ double f32_to_f64(float f, double fallback) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u) return 0.0;
-    if (e == 255u) return fallback;
-    return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+// v = hi + lo with hi = v rounded to FP32 (f64_to_f32) and lo = the remainder
+// v - hi (exact in FP64) rounded to FP32, without the FP64 pipe: the remainder
+// is R 2^(e-1075) with R the 29 mantissa bits that hi drops, less 2^29 where hi
+// rounded up (|R| <= 2^28), converted to FP32 and scaled by powers of two.
+// lo is zero where hi is zero or infinite.
+__device__ __forceinline__ void split_f64(double v, float& hi, float& lo) {
+    const unsigned h = (unsigned)__double2hiint(v), l = (unsigned)__double2loint(v);
+    const unsigned e = (h >> 20) & 0x7ffu;
+    hi = f64_to_f32(v);
+    const int R = (int)(l & 0x1fffffffu) - (int)(l & 0x10000000u) * 2;
+    const unsigned c = (e < 1011u) ? 64u : 0u;  // keeps the first scale factor normal
+    const float s1 = __uint_as_float((h & 0x80000000u) | ((e + c - 948u) << 23));  // +-2^(e-1075+c)
+    const float s2 = __uint_as_float((127u - c) << 23);                              // 2^-c
+    lo = (e < 897u || e > 1150u) ? 0.f : __fmul_rn(__fmul_rn(__int2float_rn(R), s1), s2);
+}
+
+// the 4 values of a 16-byte shared-memory load whose elements are permuted by c -> c ^ Q
+template <int Q>
+__device__ __forceinline__ void unpack4(const float4 v, float* o) {
+    const float w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[c] = w[c ^ Q];
 }
 
 template <bool DF>
@@ -142,14 +157,20 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
     constexpr int KC = DF ? 16 : 32;            // K chunk
     constexpr int NE = kF32Tile * KC / GT;      // staged elements per thread and operand
     constexpr int NP = DF ? 2 : 1;              // FP32 planes per operand
-    __shared__ float As[NP][KC][kF32Tile + 1];  // odd pitch: conflict-free transposed staging
-    __shared__ float Bs[NP][KC][kF32Tile + 1];
+    // Row kk of a staged tile holds 64 values in 16 groups of 4: group g sits
+    // at g ^ sh(kk) and element c of a group at c ^ sq(kk).  Staging along a
+    // row and along a column is then free of bank conflicts, and each thread
+    // reads its 4 values of a row as one 16-byte load (2 wavefronts a warp).
+    __shared__ __align__(16) float As[NP][KC][kF32Tile];
+    __shared__ __align__(16) float Bs[NP][KC][kF32Tile];
     __shared__ GTerm tc[G32TB];
     __shared__ double tf[G32TB];
     __shared__ int tbase;
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // rows 4 tx + x, columns 4 ty + y
+    auto sh = [](int kk) { return DF ? (kk >> 1) & 7 : (kk >> 2) & 7; };
+    auto sidx = [&](int kk, int i) { return (((i >> 2) ^ sh(kk)) << 2) | ((i & 3) ^ (DF ? (kk & 1) << 1 : kk & 3)); };
     float acc[4][4], cor[4][4];  // cor: low parts of the double-float sums (DF only)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -204,13 +225,14 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
             rb[r] = (gj < J.n && gk < P.k) ? (P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]) : 0.0;
         }
     };
-    auto mac = [&](int kk) {
+    // one k step; D = kk mod 4, known at compile time, fixes the in-group order
+    auto mac = [&](int kk, auto D) {
+        constexpr int q = DF ? (decltype(D)::value & 1) << 1 : decltype(D)::value;
         float a[4], b[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            a[q] = As[0][kk][tx + 16 * q];
-            b[q] = Bs[0][kk][ty + 16 * q];
-        }
+        const float4 va = *reinterpret_cast<const float4*>(&As[0][kk][(tx ^ sh(kk)) << 2]);
+        const float4 vb = *reinterpret_cast<const float4*>(&Bs[0][kk][(ty ^ sh(kk)) << 2]);
+        unpack4<q>(va, a);
+        unpack4<q>(vb, b);
         if constexpr (!DF) {
 #pragma unroll
             for (int x = 0; x < 4; ++x)
@@ -218,11 +240,8 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                 for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
         } else {
             float al[4], bl[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                al[q] = As[NP - 1][kk][tx + 16 * q];
-                bl[q] = Bs[NP - 1][kk][ty + 16 * q];
-            }
+            unpack4<q>(*reinterpret_cast<const float4*>(&As[NP - 1][kk][(tx ^ sh(kk)) << 2]), al);
+            unpack4<q>(*reinterpret_cast<const float4*>(&Bs[NP - 1][kk][(ty ^ sh(kk)) << 2]), bl);
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -248,6 +267,8 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
     while (have) {
         // the chunk in flight goes to shared memory (A scaled by the term's factor)
         const float cf32 = DF ? 0.f : f64_to_f32(cf);
+        const bool unit = (cf == 1.0 || cf == -1.0);  // the same for the whole block
+        const float sgn = (cf < 0.0) ? -1.f : 1.f;
 #pragma unroll
         for (int r = 0; r < NE; ++r) {
             const int e = threadIdx.x + r * GT;
@@ -255,16 +276,24 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
             if (!CP.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % KC; i = e / KC; }
             int j, kb;
             if (!CP.tb) { kb = e % KC; j = e / KC; } else { j = e % kF32Tile; kb = e / kF32Tile; }
+            const int pa = sidx(kk, i), pb = sidx(kb, j);
             if constexpr (!DF) {
-                As[0][kk][i] = cf32 * f64_to_f32(ra[r]);
-                Bs[0][kb][j] = f64_to_f32(rb[r]);
+                As[0][kk][pa] = cf32 * f64_to_f32(ra[r]);
+                Bs[0][kb][pb] = f64_to_f32(rb[r]);
             } else {
-                const double va = ra[r] * cf;  // the factor applied in FP64
-                const float ah = f64_to_f32(va), bh = f64_to_f32(rb[r]);
-                As[0][kk][i] = ah;
-                As[1][kk][i] = f64_to_f32(va - f32_to_f64(ah, va));
-                Bs[0][kb][j] = bh;
-                Bs[1][kb][j] = f64_to_f32(rb[r] - f32_to_f64(bh, rb[r]));
+                float ah, al, bh, bl;
+                if (unit) {  // factor +-1: applied to the split exactly
+                    split_f64(ra[r], ah, al);
+                    ah *= sgn;
+                    al *= sgn;
+                } else {
+                    split_f64(ra[r] * cf, ah, al);  // the factor applied in FP64
+                }
+                split_f64(rb[r], bh, bl);
+                As[0][kk][pa] = ah;
+                As[1][kk][pa] = al;
+                Bs[0][kb][pb] = bh;
+                Bs[1][kb][pb] = bl;
             }
         }
         const int kc = min(KC, CP.k - ck0);
@@ -274,12 +303,27 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         const bool more = advance(nit, nk0, NP_, nf);  // may sync (term cache)
         __syncthreads();
         if (more) fetch(NP_, nk0);
-        if (kc == KC) {
+        // rows kc .. KC-1 hold zeros, so a partial chunk may run to a multiple of 4
+        constexpr std::integral_constant<int, 0> d0;
+        constexpr std::integral_constant<int, 1> d1;
+        constexpr std::integral_constant<int, 2> d2;
+        constexpr std::integral_constant<int, 3> d3;
+        if (!DF && kc == KC) {  // (the double-float step is long: its loop stays rolled for the instruction cache)
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) mac(kk);
+            for (int kk = 0; kk < KC; kk += 4) {
+                mac(kk, d0);
+                mac(kk + 1, d1);
+                mac(kk + 2, d2);
+                mac(kk + 3, d3);
+            }
         } else {
-#pragma unroll 4
-            for (int kk = 0; kk < kc; ++kk) mac(kk);
+#pragma unroll 1
+            for (int kk = 0; kk < kc; kk += 4) {
+                mac(kk, d0);
+                mac(kk + 1, d1);
+                mac(kk + 2, d2);
+                mac(kk + 3, d3);
+            }
         }
         if constexpr (DF) {
             // renormalise the pairs so that the low parts stay small (Fast2Sum)
@@ -303,7 +347,7 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int gi = tile.i0 + tx + 16 * a, gj = tile.j0 + ty + 16 * b;
+            const int gi = tile.i0 + 4 * tx + a, gj = tile.j0 + 4 * ty + b;
             if (gi < J.m && gj < J.n) {
                 double* c = J.C + gi + (size_t)gj * J.ldc;
                 const double v = DF ? (double)acc[a][b] + (double)cor[a][b] : (double)acc[a][b];
