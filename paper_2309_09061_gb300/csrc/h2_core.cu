@@ -2,6 +2,8 @@
 // entry points h2_build_interp, h2_to_dense, h2_info, h2_get_structure,
 // h2_free, h2_error_string.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -77,14 +79,17 @@ void Runner::begin(int fam) {
     H2_CUDA(cudaEventRecord(cur_, st_));
 }
 
-void Runner::end(int fam, double flops, double bytes) {
+void Runner::end(int fam, double flops, double bytes, int64_t units) {
     cudaEvent_t b = get_event();
     H2_CUDA(cudaEventRecord(b, st_));
-    marks_.push_back(Mark{fam, cur_, b, flops, bytes, nullptr});
+    marks_.push_back(Mark{fam, cur_, b, flops, bytes, nullptr, units});
     cur_ = nullptr;
 }
 
+// With H2_TRACE set in the environment, every launch is also printed to
+// stderr as "h2trace <family> <units> <GFLOP> <MB> <ms>" in launch order.
 void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes) {
+    static const bool trace = std::getenv("H2_TRACE") != nullptr;
     for (auto& m : marks_) {
         float f = 0.f;
         cudaEventElapsedTime(&f, m.a, m.b);
@@ -94,6 +99,9 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
         if (launches) launches[m.fam] += 1;
         if (flops) flops[m.fam] += m.flops + df;
         if (bytes) bytes[m.fam] += m.bytes;
+        if (trace)
+            std::fprintf(stderr, "h2trace %d %lld %.6f %.3f %.6f\n", m.fam, (long long)m.units, (m.flops + df) * 1e-9,
+                         m.bytes * 1e-6, f);
         pool_.push_back(m.a);
         pool_.push_back(m.b);
     }
@@ -221,7 +229,7 @@ void Runner::flush_gemm(int precision_override) {
         else
             launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
         launch_slice_sum(ds, (int)sums.size(), max_n, st_);
-        end(fam, fl, by);
+        end(fam, fl, by, (int64_t)tiles.size());
         ++launches;
     }
     terms_.clear();

@@ -376,7 +376,7 @@ public:
 
     // per-family device time: events around every launch (collected after a sync)
     void begin(int fam);
-    void end(int fam, double flops, double bytes);
+    void end(int fam, double flops, double bytes, int64_t units = 0);
     void collect(double* ms, int64_t* launches, double* flops, double* bytes);
 
     // device scratch from the stream-ordered pool
@@ -410,6 +410,7 @@ private:
         cudaEvent_t a, b;
         double flops, bytes;
         double* dflops;  // device-side flop count of the launch, read at collect()
+        int64_t units;   // CTAs of the launch (tiles for the products)
     };
     double* dev_counter();
     std::vector<Mark> marks_;
