@@ -322,6 +322,16 @@ void Runner::qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q,
     }
 }
 
+void Runner::qr_wy(double* A, int m, int n, int lda, double* V, double* T) {
+    if (m <= 0 || n <= 0) return;
+    if (std::min(m, n) > kQRPivMax) throw Error(H2_ERR_UNSUPPORTED, "WY form of a QR with more than 2048 reflectors");
+    double* tau = dalloc(std::min(m, n));
+    QRJob j{A, nullptr, nullptr, tau, nullptr, m, n, lda, 1, 1, 0, nullptr};
+    j.V = V;
+    j.T = T;
+    qrs_.push_back(j);
+}
+
 void Runner::flush_qr() {
     if (!qrs32_.empty()) {
         QRJob* d = upload(qrs32_);
@@ -342,8 +352,9 @@ void Runner::flush_qr() {
     double fl = 0.0, by = 0.0;
     for (auto& j : qrs_) {
         double m = j.m, n = j.n, p = std::min(j.m, j.n);
-        fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p + (j.Q ? 4.0 * m * j.q * p : 0.0);
-        by += 8.0 * (2.0 * m * n + (j.R ? p * n : 0.0) + (j.Q ? m * j.q : 0.0));
+        fl += 4.0 * m * n * p - 2.0 * (m + n) * p * p + 4.0 / 3.0 * p * p * p + (j.Q ? 4.0 * m * j.q * p : 0.0) +
+              (j.V ? m * p * p - p * p * p / 3.0 : 0.0);
+        by += 8.0 * (2.0 * m * n + (j.R ? p * n : 0.0) + (j.Q ? m * j.q : 0.0) + (j.V ? m * p + p * p : 0.0));
     }
     begin(2);
     launch_qr(d, (int)qrs_.size(), st_);

@@ -193,6 +193,10 @@ struct QRJob {
     int m, n, lda, ldr, ldq, q;
     int* piv;     // when set (n <= kQRPivMax): column pivoting, A P = Q R with
                   // column j of A P = column piv[j] of A
+    double* V;    // when set (FP64, no pivoting, min(m,n) <= kQRPivMax): instead of Q,
+    double* T;    // the compact WY form H_0 ... H_{p-1} = I - V T V^T: V (m x p, ld m)
+                  // the Householder vectors with unit diagonal and zeros above it,
+                  // T (p x p, ld p) upper triangular
 };
 
 // widest matrix the column-pivoted QR takes (its norms live in shared memory)
@@ -357,6 +361,9 @@ public:
     void split_k(int precision, int tile, std::vector<SliceSum>& sums);
     void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false,
             int* piv = nullptr);
+    // FP64 QR of A (m x n, in place) returning the compact WY form of its Q:
+    // Q = I - V T V^T with V (m x p) and T (p x p), p = min(m, n)
+    void qr_wy(double* A, int m, int n, int lda, double* V, double* T);
     void flush_qr();
     void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
              const int* rowperm = nullptr);

@@ -666,7 +666,10 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
     __shared__ double red[QT / 32];
     __shared__ int redi[QT / 32];
     __shared__ float redf[QT / 32];
-    __shared__ float vn1[kQRPivMax], vn2[kQRPivMax];  // remaining / last recomputed column norms
+    // remaining / last recomputed column norms (pivoting); V^T v_j (WY form)
+    __shared__ __align__(8) float vnbuf[2 * kQRPivMax];
+    float* vn1 = vnbuf;
+    float* vn2 = vnbuf + kQRPivMax;
     const QRJob J = jobs[blockIdx.x];
     const int m = J.m, n = J.n, p = m < n ? m : n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = QT / 32;
@@ -816,6 +819,40 @@ __global__ void __launch_bounds__(QT) k_qr(const QRJob* __restrict__ jobs) {
         for (int e = threadIdx.x; e < p * n; e += QT) {
             int i = e % p, c = e / p;
             J.R[i + (size_t)c * J.ldr] = (i <= c) ? (double)A[i + (size_t)c * lda] : 0.0;
+        }
+    }
+    if (sizeof(T) == 8 && J.V && p <= kQRPivMax) {
+        // compact WY form (forward, column by column): T_jj = tau_j and
+        // T(0:j, j) = -tau_j T(0:j, 0:j) y with y_l = v_l^T v_j (l < j); v_j is
+        // zero above row j and one at row j
+        for (int e = threadIdx.x; e < m * p; e += QT) {
+            const int i = e % m, c = e / m;
+            J.V[e] = (i < c) ? 0.0 : (i == c) ? 1.0 : (double)A[i + (size_t)c * lda];
+        }
+        double* y = reinterpret_cast<double*>(vnbuf);
+        for (int j = 0; j < p; ++j) {
+            const T* vj = A + (size_t)j * lda;
+            for (int l = warp; l < j; l += nw) {
+                const T* vl = A + (size_t)l * lda;
+                double s = 0.0;
+                for (int r = j + 1 + lane; r < m; r += 32) s += (double)vl[r] * (double)vj[r];
+                s = warp_sum(s);
+                if (lane == 0) y[l] = s + (double)vl[j];
+            }
+            __syncthreads();
+            const double tau = J.tau[j];
+            for (int i = threadIdx.x; i < p; i += QT) {
+                double v = 0.0;
+                if (i < j) {
+                    double s = 0.0;
+                    for (int l = i; l < j; ++l) s += J.T[i + (size_t)l * p] * y[l];
+                    v = -tau * s;
+                } else if (i == j) {
+                    v = tau;
+                }
+                J.T[i + (size_t)j * p] = v;
+            }
+            __syncthreads();
         }
     }
     if (sizeof(T) == 8 && J.Q) {

@@ -627,30 +627,49 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
         // With rows <= k_X (+ k_Z) the complete Q spans all of K^rows, which contains the
         // preserved range: the identity is an equally valid choice and needs no factorisation.
+        // Otherwise Q_X = I - V T V^T from the compact WY form of the Householder QR,
+        // expanded by two batched FP64-accurate products (W = T V^T, Q_X = I - V W).
         int rid = 0;
-        for (int i = 0; i < nl; ++i)
-            if (rows[i] > 0 && rows[i] <= VX.rank[c0 + i] + kz(c0 + i)) rid = std::max(rid, rows[i]);
+        for (int i = 0; i < nl; ++i) rid = std::max(rid, rows[i]);
         double* ident = nullptr;
         if (rid > 0) {
             ident = R.dalloc((size_t)rid * rid);
             launch_set_identity(ident, rid, rid, rid, R.stream());
         }
+        std::vector<double*> Vq(nl, nullptr), Tq(nl, nullptr);
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i, kx = VX.rank[t], kp = kx + kz(t);  // preserved columns [VX-hat | VZ-hat]
             k1[i] = std::min(rows[i], kp);
             m2[i] = rows[i] - k1[i];
             QX[i] = R.dalloc((size_t)std::max(1, rows[i] * rows[i]));
-            if (rows[i] > 0 && rows[i] <= kp) {
-                R.copy(ident, rid, QX[i], rows[i], rows[i], rows[i], 0);
-                continue;
-            }
+            if (rows[i] <= 0) continue;
+            R.copy(ident, rid, QX[i], rows[i], rows[i], rows[i], 0);
+            if (rows[i] <= kp) continue;
             double* work = R.dalloc((size_t)std::max(1, rows[i] * kp));
             R.copy(VXh[i], rows[i], work, rows[i], rows[i], kx, 0);
             if (VZ && kz(t) > 0) R.copy(VZh[i], rows[i], work + (size_t)kx * rows[i], rows[i], rows[i], kz(t), 0);
-            R.qr(work, rows[i], kp, rows[i], nullptr, 1, QX[i], rows[i], rows[i]);
+            Vq[i] = R.dalloc((size_t)rows[i] * kp);
+            Tq[i] = R.dalloc((size_t)kp * kp);
+            R.qr_wy(work, rows[i], kp, rows[i], Vq[i], Tq[i]);
         }
         R.flush_copy();
         R.flush_qr();
+        {
+            std::vector<double*> Wq(nl, nullptr);
+            for (int i = 0; i < nl; ++i) {
+                if (!Vq[i]) continue;
+                Wq[i] = R.dalloc((size_t)k1[i] * rows[i]);
+                R.job(Wq[i], k1[i], rows[i], k1[i], 0.0);
+                R.term(Tq[i], 0, k1[i], Vq[i], 1, rows[i], k1[i]);
+            }
+            R.flush_gemm(H2_FP64);
+            for (int i = 0; i < nl; ++i) {
+                if (!Vq[i]) continue;
+                R.job(QX[i], rows[i], rows[i], rows[i], 1.0);
+                R.term(Vq[i], 0, rows[i], Wq[i], 0, k1[i], k1[i], -1.0);
+            }
+            R.flush_gemm(H2_FP64);
+        }
         std::vector<double*> Vts(nl, nullptr), Tts(nl, nullptr);
         std::vector<int> ncols(nl, 0);
         for (int i = 0; i < nl; ++i) {
