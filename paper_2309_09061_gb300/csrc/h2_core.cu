@@ -87,10 +87,14 @@ void Runner::end(int fam, double flops, double bytes, int64_t units) {
 }
 
 // With H2_TRACE set in the environment, every launch is also printed to
-// stderr as "h2trace <family> <units> <GFLOP> <MB> <ms>" in launch order.
-void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes) {
+// stderr as "h2trace <family> <units> <GFLOP> <MB> <ms> <start ms> <stream>" in
+// launch order (start relative to ref, else to the first launch collected here).
+void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes, cudaEvent_t ref) {
     static const bool trace = std::getenv("H2_TRACE") != nullptr;
+    if (!ref && !marks_.empty()) ref = marks_.front().a;
     for (auto& m : marks_) {
+        float t0 = 0.f;
+        if (trace) cudaEventElapsedTime(&t0, ref, m.a);
         float f = 0.f;
         cudaEventElapsedTime(&f, m.a, m.b);
         double df = 0.0;
@@ -100,8 +104,8 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
         if (flops) flops[m.fam] += m.flops + df;
         if (bytes) bytes[m.fam] += m.bytes;
         if (trace)
-            std::fprintf(stderr, "h2trace %d %lld %.6f %.3f %.6f\n", m.fam, (long long)m.units, (m.flops + df) * 1e-9,
-                         m.bytes * 1e-6, f);
+            std::fprintf(stderr, "h2trace %d %lld %.6f %.3f %.6f %.3f %p\n", m.fam, (long long)m.units,
+                         (m.flops + df) * 1e-9, m.bytes * 1e-6, f, t0, (void*)st_);
         pool_.push_back(m.a);
         pool_.push_back(m.b);
     }
@@ -150,11 +154,57 @@ void Arena::release_all() {
     left_ = 0;
 }
 
+namespace {
+std::mutex g_pinned_mu;
+std::vector<Runner::Pinned> g_pinned_free;
+constexpr size_t kPinnedChunk = size_t(32) << 20;
+}  // namespace
+
+const void* Runner::stage(const void* src, size_t bytes) {
+    const size_t need = (bytes + 255) & ~size_t(255);
+    if (pinned_.empty() || pinned_used_ + need > pinned_.back().size) {
+        Pinned c{nullptr, 0, nullptr};
+        {
+            std::lock_guard<std::mutex> lk(g_pinned_mu);
+            for (size_t i = 0; i < g_pinned_free.size(); ++i)
+                if (g_pinned_free[i].size >= need) {
+                    c = g_pinned_free[i];
+                    g_pinned_free.erase(g_pinned_free.begin() + i);
+                    break;
+                }
+        }
+        if (c.p) {
+            H2_CUDA(cudaEventSynchronize(c.done));  // its previous copies have ended
+        } else {
+            c.size = std::max(need, kPinnedChunk);
+            H2_CUDA(cudaHostAlloc((void**)&c.p, c.size, cudaHostAllocDefault));
+            H2_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+        }
+        pinned_.push_back(c);
+        pinned_used_ = 0;
+    }
+    char* h = pinned_.back().p + pinned_used_;
+    pinned_used_ += need;
+    std::memcpy(h, src, bytes);
+    return h;
+}
+
+void Runner::release_pinned() {
+    if (pinned_.empty()) return;
+    for (Pinned& c : pinned_) cudaEventRecord(c.done, st_);
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    for (Pinned& c : pinned_) g_pinned_free.push_back(c);
+    pinned_.clear();
+    pinned_used_ = 0;
+}
+
 template <class T>
 T* Runner::upload(const std::vector<T>& v) {
     size_t bytes = std::max<size_t>(v.size() * sizeof(T), 8);
     double* d = dalloc((bytes + 7) / 8);
-    if (!v.empty()) H2_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
+    if (!v.empty())
+        H2_CUDA(cudaMemcpyAsync(d, stage(v.data(), v.size() * sizeof(T)), v.size() * sizeof(T),
+                                cudaMemcpyHostToDevice, st_));
     return (T*)d;
 }
 template int* Runner::upload<int>(const std::vector<int>&);
@@ -163,6 +213,7 @@ template double* Runner::upload<double>(const std::vector<double>&);
 template double** Runner::upload<double*>(const std::vector<double*>&);
 
 void Runner::release_all() {
+    release_pinned();
     scratch_.release_all();
     persist_.release_all();
     d_flag_ = nullptr;

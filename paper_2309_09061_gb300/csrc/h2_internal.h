@@ -384,7 +384,8 @@ public:
     // per-family device time: events around every launch (collected after a sync)
     void begin(int fam);
     void end(int fam, double flops, double bytes, int64_t units = 0);
-    void collect(double* ms, int64_t* launches, double* flops, double* bytes);
+    void collect(double* ms, int64_t* launches, double* flops, double* bytes, cudaEvent_t ref = nullptr);
+    cudaEvent_t first_event() const { return marks_.empty() ? nullptr : marks_.front().a; }
 
     // device scratch from the stream-ordered pool
     double* dalloc(size_t n) { return scratch_.alloc(n); }
@@ -424,6 +425,22 @@ private:
     std::vector<cudaEvent_t> pool_;
     cudaEvent_t cur_ = nullptr;
     cudaEvent_t get_event();
+public:
+    // Pinned host staging of the uploaded descriptors: from pageable memory an
+    // asynchronous copy may wait for the stream, and the host could not run
+    // ahead of the GPU.  Chunks return to a process-wide pool on release, with
+    // an event that marks the end of their last copy.
+    struct Pinned {
+        char* p;
+        size_t size;
+        cudaEvent_t done;
+    };
+
+private:
+    std::vector<Pinned> pinned_;
+    size_t pinned_used_ = 0;
+    const void* stage(const void* src, size_t bytes);
+    void release_pinned();
 };
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -2012,8 +2012,11 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
             S->fam_flops[f] = 0.0;
             S->fam_bytes[f] = 0.0;
         }
-        R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
-        R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+        {
+            cudaEvent_t ref = R.first_event();
+            R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+            R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes, ref);
+        }
     }
     R.release_all();
     R2.release_all();
@@ -2181,8 +2184,11 @@ static void recompress(h2_matrix* A, const h2_opts* opts) {
         S->max_rank_a = std::max(QV->max_rank(), QW->max_rank());
         S->max_rank_b = std::max(pb.rb.Qn->max_rank(), pb.cb.Qn->max_rank());
         S->flops = cnt.flops;
-        R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
-        R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+        {
+            cudaEvent_t ref = R.first_event();
+            R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
+            R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes, ref);
+        }
     }
     R.release_all();
     R2.release_all();
