@@ -227,14 +227,22 @@ void Runner::ensure_flag() {
 }
 
 void Runner::job(double* C, int m, int n, int ldc, double beta, bool sym) {
-    jobs_.push_back(GJob{C, m, n, ldc, (int)terms_.size(), 0, beta, (sym && m == n) ? 1 : 0});
+    const int sy = (sym && m == n) ? 1 : 0;
+    jobs_.push_back(GJob{C, m, n, ldc, (int)terms_.size(), 0, beta, sy});
+    pend_bytes_ += 8.0 * m * n * (beta != 0.0 ? 2.0 : 1.0);
+    const int64_t a32 = (m + 31) / 32, b32 = (n + 31) / 32, a64 = (m + 63) / 64, b64 = (n + 63) / 64;
+    pend_tiles32_ += sy ? a32 * (a32 + 1) / 2 : a32 * b32;
+    pend_tiles64_ += sy ? a64 * (a64 + 1) / 2 : a64 * b64;
 }
 
 void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha,
                   const double* scale) {
     if (k <= 0 || jobs_.empty()) return;
     terms_.push_back(GTerm{A, B, scale, alpha, k, lda, ldb, ta, tb});
-    jobs_.back().nt++;
+    GJob& J = jobs_.back();
+    J.nt++;
+    pend_flops_ += (J.sym ? (double)J.m * (J.m + 1) : 2.0 * J.m * J.n) * k;
+    pend_bytes_ += 8.0 * ((double)J.m * k + (double)k * J.n);
 }
 
 void Runner::flush_gemm(int precision_override) {
@@ -245,9 +253,16 @@ void Runner::flush_gemm(int precision_override) {
     const bool tc = (pr == H2_TC);
     const bool f32 = (pr == H2_MIXED || pr == kGemmDF);
     const int tm = tc ? kTcTileM : f32 ? kF32Tile : 32, tn = tc ? kTcTileN : f32 ? kF32Tile : 32;
+    // algorithmic work of the batch: every operand read once, every output written once
+    const double fl = pend_flops_, by = pend_bytes_;
+    const int64_t nt_est = (tm == 32 && tn == 32) ? pend_tiles32_ : (tm == 64 && tn == 64) ? pend_tiles64_ : -1;
+    pend_flops_ = pend_bytes_ = 0.0;
+    pend_tiles32_ = pend_tiles64_ = 0;
     std::vector<SliceSum> sums;
-    if (!tc) split_k(pr, tm, sums);
-    std::vector<GTile> tiles;
+    if (!tc) split_k(pr, tm, sums, nt_est);
+    std::vector<GTile>& tiles = tiles_;
+    tiles.clear();
+    if (nt_est > 0) tiles.reserve((size_t)nt_est);
     for (int j = 0; j < (int)jobs_.size(); ++j) {
         GJob& J = jobs_[j];
         if (tm != tn) J.sym = 0;  // symmetric jobs need a square tile grid
@@ -259,16 +274,6 @@ void Runner::flush_gemm(int precision_override) {
         GTerm* dt = upload(terms_);
         GJob* dj = upload(jobs_);
         GTile* dti = upload(tiles);
-        // algorithmic work: every operand read once, every output written once
-        double fl = 0.0, by = 0.0;
-        for (const GJob& J : jobs_) {
-            for (int i = 0; i < J.nt; ++i) {
-                const GTerm& T = terms_[J.t0 + i];
-                fl += (J.sym ? (double)J.m * (J.m + 1) : 2.0 * J.m * J.n) * T.k;
-                by += 8.0 * ((double)J.m * T.k + (double)T.k * J.n);
-            }
-            by += 8.0 * J.m * J.n * (J.beta != 0.0 ? 2.0 : 1.0);
-        }
         const int fam = tc ? 10 : (pr == H2_MIXED) ? 1 : (pr == kGemmDF) ? 11 : 0;
         if (tc) ensure_flag();
         SliceSum* ds = sums.empty() ? nullptr : upload(sums);
@@ -292,14 +297,16 @@ void Runner::flush_gemm(int precision_override) {
 // partial product to a slice of scratch, and k_slice_sum adds the slices (in
 // order, deterministic) into C with the job's beta.  Terms that straddle a
 // cut are divided by offsetting their operands along K.
-void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums) {
+void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles) {
     const int kc = (pr == kGemmDF || pr == H2_FP64) ? 16 : 32;  // K chunk of the kernel
     const int per_sm = (pr == kGemmDF) ? 2 : (pr == H2_MIXED) ? 3 : 4;
     const int64_t target = 2LL * device_sm_count() * per_sm;
-    int64_t ntiles = 0;
-    for (const GJob& J : jobs_) {
-        const int64_t ti = (int64_t)((J.m + tile - 1) / tile), tj = (int64_t)((J.n + tile - 1) / tile);
-        ntiles += J.sym ? ti * (ti + 1) / 2 : ti * tj;
+    if (ntiles < 0) {  // tiles of the batch, unless counted while it was built
+        ntiles = 0;
+        for (const GJob& J : jobs_) {
+            const int64_t ti = (int64_t)((J.m + tile - 1) / tile), tj = (int64_t)((J.n + tile - 1) / tile);
+            ntiles += J.sym ? ti * (ti + 1) / 2 : ti * tj;
+        }
     }
     if (ntiles == 0 || ntiles >= target) return;
     const int want = (int)std::min<int64_t>(16, (target + ntiles - 1) / ntiles);

@@ -10,6 +10,7 @@
 #include <stdexcept>
 #include <string>
 #include <unordered_map>
+#include <array>
 #include <vector>
 
 #include "../../include/h2mul.h"
@@ -89,6 +90,8 @@ struct ProductTree {
     BlockTree nodes;                       // kind ADM / DENSE / SPLIT
     std::vector<std::vector<int>> triples; // per node: list of s
     std::vector<std::vector<std::pair<int, int>>> tri_blocks;  // per node and triple: blocks (t,s) of X, (s,r) of Y
+    std::vector<std::vector<std::pair<int8_t, int8_t>>> tri_kinds;  // per node and triple: kinds of the two blocks
+    std::vector<std::array<int, 4>> kids;  // SPLIT node: node (child(t,i), child(r,j)) at 2 i + j
 };
 ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y);
 
@@ -358,7 +361,7 @@ public:
     void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
               const double* scale = nullptr);
     void flush_gemm(int precision_override = -1);
-    void split_k(int precision, int tile, std::vector<SliceSum>& sums);
+    void split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles = -1);
     void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false,
             int* piv = nullptr);
     // FP64 QR of A (m x n, in place) returning the compact WY form of its Q:
@@ -402,6 +405,11 @@ private:
     int prec_;
     std::vector<GTerm> terms_;
     std::vector<GJob> jobs_;
+    std::vector<GTile> tiles_;
+    // accumulated while the batch is built: algorithmic flops and bytes, and
+    // its tiles at 32 x 32 and 64 x 64
+    double pend_flops_ = 0.0, pend_bytes_ = 0.0;
+    int64_t pend_tiles32_ = 0, pend_tiles64_ = 0;
     std::vector<QRJob> qrs_;
     std::vector<SVDJob> svds_;
     std::vector<PreJob> pres_;

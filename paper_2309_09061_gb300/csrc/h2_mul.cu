@@ -485,7 +485,7 @@ static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
 struct Induced {
     std::shared_ptr<Basis> Q;
     PerCl Rbar;                         // Q_t^* V_{X,t}: rank_Q(t) x rank_VX(t)
-    std::unordered_map<int, double*> A; // X block (not admissible) -> Q_t^* X_ts V_{Y,s}: rank_Q(t) x rank_VY(s)
+    std::vector<double*> A;             // X block (not admissible) -> Q_t^* X_ts V_{Y,s}: rank_Q(t) x rank_VY(s)
     bool zpres = false;                 // Z's own basis preserved as well
     PerCl RbarZ;                        // Q_t^* V_{Z,t}: rank_Q(t) x rank_VZ(t) (zpres)
 };
@@ -506,6 +506,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         Zt = total_weights(R, Y, RW);
     }
     Induced out;
+    out.A.assign(X.bt().kind.size(), nullptr);
     out.Q = std::make_shared<Basis>();
     Basis& Q = *out.Q;
     Q.rank.assign(T.nc, 0);
@@ -807,6 +808,8 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
     std::vector<std::vector<int>> lv(T.L + 1);
     for (int n = 0; n < nn; ++n) lv[Tree::level(N.t[n])].push_back(n);
     G.C.assign(nn, nullptr);
+    std::vector<int> zbk(nn);  // block of Z on each node, or -1
+    for (int n = 0; n < nn; ++n) zbk[n] = Z->st->blocks.find(N.t[n], N.s[n]);
     // couplings pushed down from the ancestors live in two alternating arenas
     Arena pp0(R.stream()), pp1(R.stream());
     Arena* pp[2] = {&pp0, &pp1};
@@ -842,9 +845,10 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         for (int n : nodes) {
             int t = N.t[n], r = N.s[n];
             const auto& tb = G.PT->tri_blocks[n];
+            const auto& tk = G.PT->tri_kinds[n];
             for (size_t q = 0; q < tb.size(); ++q) {
                 const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                if (X.kind(bx) != ADM || Y.kind(by) != ADM || PSY.has(by)) continue;
+                if (tk[q].first != ADM || tk[q].second != ADM || PSY.has(by)) continue;
                 double* m = R.dalloc((size_t)WX.rank[s] * WY.rank[r]);
                 R.job(m, WX.rank[s], WY.rank[r], WX.rank[s], 0.0);
                 T_(R, mv(P.p[s], std::max(1, P.rows[s])), Y.S(by), VY.rank[s]);
@@ -869,7 +873,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
         const bool zgen = ra.zpres || ca.zpres;  // Z with bases of its own: enters C below
         for (int n : nodes) {
             int t = N.t[n], r = N.s[n];
-            int bz = Z->st->blocks.find(t, r);
+            int bz = zbk[n];
             if (!zgen && bz >= 0 && Z->st->blocks.kind[bz] == ADM)
                 R.copy(ZV.S(bz).p, ZV.S(bz).ld, U1[n], VX.rank[t], VX.rank[t], WY.rank[r], 0);
         }
@@ -878,9 +882,10 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
             int t = N.t[n], r = N.s[n];
             R.job(U1[n], VX.rank[t], WY.rank[r], VX.rank[t], 1.0);
             const auto& tb = G.PT->tri_blocks[n];
+            const auto& tk = G.PT->tri_kinds[n];
             for (size_t q = 0; q < tb.size(); ++q) {
                 const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                if (X.kind(bx) == ADM && Y.kind(by) == ADM) {
+                if (tk[q].first == ADM && tk[q].second == ADM) {
                     T_(R, X.S(bx), mv(PSY[by], WX.rank[s]), WX.rank[s]);
                     cnt.flops += 2.0 * VX.rank[t] * WY.rank[r] * WX.rank[s];
                 }
@@ -902,14 +907,15 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
             R.job(U2[n], Q.rank[t], WY.rank[r], std::max(1, Q.rank[t]), 0.0);
             R.term(ra.Rbar.p[t], 0, std::max(1, Q.rank[t]), U1[n], 0, VX.rank[t], VX.rank[t]);
             const auto& tb = G.PT->tri_blocks[n];
+            const auto& tk = G.PT->tri_kinds[n];
             for (size_t q = 0; q < tb.size(); ++q) {
                 const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                if (X.kind(bx) != ADM && Y.kind(by) == ADM) {
-                    T_(R, mv(ra.A.at(bx), std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
+                if (tk[q].first != ADM && tk[q].second == ADM) {
+                    T_(R, mv(ra.A[bx], std::max(1, Q.rank[t])), Y.S(by), VY.rank[s]);
                     cnt.flops += 2.0 * Q.rank[t] * WY.rank[r] * VY.rank[s];
                 }
             }
-            int bz = Z->st->blocks.find(t, r);
+            int bz = zbk[n];
             if (zgen && bz >= 0 && Z->st->blocks.kind[bz] == ADM) {
                 const int kzr = Z->V->rank[t], kzc = Z->W->rank[r];
                 ZR[n] = R.dalloc((size_t)std::max(1, Q.rank[t] * kzc));
@@ -920,8 +926,8 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
             R.job(U3[n], VX.rank[t], QW.rank[r], VX.rank[t], 0.0);
             for (size_t q = 0; q < tb.size(); ++q) {
                 const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                if (X.kind(bx) == ADM && Y.kind(by) != ADM) {
-                    T_(R, X.S(bx), mvT(ca.A.at(by), std::max(1, QW.rank[r])), WX.rank[s]);
+                if (tk[q].first == ADM && tk[q].second != ADM) {
+                    T_(R, X.S(bx), mvT(ca.A[by], std::max(1, QW.rank[r])), WX.rank[s]);
                     cnt.flops += 2.0 * VX.rank[t] * QW.rank[r] * WX.rank[s];
                 }
             }
@@ -953,7 +959,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                     R.job(m, Q.rank[t], QW.rank[b], std::max(1, Q.rank[t]), 0.0);
                     R.term(G.C[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
                     R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
-                    for (int i = 0; i < 2; ++i) tmp.push_back({N.find(Tree::child(t, i), b), m});
+                    for (int i = 0; i < 2; ++i) tmp.push_back({G.PT->kids[n][2 * i + j], m});
                 }
             }
             R.flush_gemm();
@@ -986,15 +992,16 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 if (N.kind[n] != DENSE) continue;
                 int t = N.t[n], r = N.s[n];
                 const auto& tb = G.PT->tri_blocks[n];
+                const auto& tk = G.PT->tri_kinds[n];
                 for (size_t q = 0; q < tb.size(); ++q) {
                     const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                    if (X.kind(bx) == DENSE && Y.kind(by) == ADM && !XV.has(bx)) {
+                    if (tk[q].first == DENSE && tk[q].second == ADM && !XV.has(bx)) {
                         double* m = R.dalloc((size_t)T.size[t] * VY.rank[s]);
                         R.job(m, (int)T.size[t], VY.rank[s], (int)T.size[t], 0.0);
                         T_(R, X.N(bx), mv(VY.leaf[s], (int)T.size[s]), (int)T.size[s]);
                         XV[bx] = m;
                     }
-                    if (X.kind(bx) == ADM && Y.kind(by) == DENSE && !WN.has(by)) {
+                    if (tk[q].first == ADM && tk[q].second == DENSE && !WN.has(by)) {
                         double* m = R.dalloc((size_t)WX.rank[s] * T.size[r]);
                         R.job(m, WX.rank[s], (int)T.size[r], WX.rank[s], 0.0);
                         T_(R, mvT(WX.leaf[s], (int)T.size[s]), Y.N(by), (int)T.size[s]);
@@ -1005,7 +1012,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 R.job(CQ[n], Q.rank[t], (int)T.size[r], std::max(1, Q.rank[t]), 0.0);
                 R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.leaf[r], 1, (int)T.size[r], QW.rank[r]);
                 // Z with bases of its own, admissible on this dense leaf: ZL = V_Z,t S_Z
-                const int bz = Z->st->blocks.find(t, r);
+                const int bz = zbk[n];
                 if (zgen && bz >= 0 && Z->st->blocks.kind[bz] == ADM) {
                     const int kzr = Z->V->rank[t], kzc = Z->W->rank[r];
                     ZR[n] = R.dalloc((size_t)std::max(1, (int)T.size[t] * kzc));
@@ -1021,15 +1028,16 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 R.job(L1[n], (int)T.size[t], WY.rank[r], (int)T.size[t], 0.0);
                 R.term(VX.leaf[t], 0, (int)T.size[t], U1[n], 0, VX.rank[t], VX.rank[t]);
                 const auto& tb = G.PT->tri_blocks[n];
+                const auto& tk = G.PT->tri_kinds[n];
                 for (size_t q = 0; q < tb.size(); ++q) {
                     const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                    if (X.kind(bx) == DENSE && Y.kind(by) == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
+                    if (tk[q].first == DENSE && tk[q].second == ADM) T_(R, mv(XV[bx], (int)T.size[t]), Y.S(by), VY.rank[s]);
                 }
                 R1[n] = R.dalloc((size_t)VX.rank[t] * T.size[r]);
                 R.job(R1[n], VX.rank[t], (int)T.size[r], VX.rank[t], 0.0);
                 for (size_t q = 0; q < tb.size(); ++q) {
                     const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                    if (X.kind(bx) == ADM && Y.kind(by) == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
+                    if (tk[q].first == ADM && tk[q].second == DENSE) T_(R, X.S(bx), mv(WN[by], WX.rank[s]), WX.rank[s]);
                 }
             }
             R.flush_gemm();
@@ -1038,7 +1046,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 int t = N.t[n], r = N.s[n];
                 int mt = (int)T.size[t], mr = (int)T.size[r];
                 G.C[n] = R.palloc((size_t)mt * mr);
-                int bz = Z->st->blocks.find(t, r);
+                int bz = zbk[n];
                 if (bz >= 0 && Z->st->blocks.kind[bz] == DENSE) R.copy(ZV.N(bz).p, ZV.N(bz).ld, G.C[n], mt, mt, mr, 0);
             }
             R.flush_copy();
@@ -1046,13 +1054,14 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                 if (N.kind[n] != DENSE) continue;
                 int t = N.t[n], r = N.s[n];
                 int mt = (int)T.size[t], mr = (int)T.size[r];
-                int bz = Z->st->blocks.find(t, r);
+                int bz = zbk[n];
                 bool zd = bz >= 0 && Z->st->blocks.kind[bz] == DENSE;
                 R.job(G.C[n], mt, mr, mt, zd ? 1.0 : 0.0);
                 const auto& tb = G.PT->tri_blocks[n];
+                const auto& tk = G.PT->tri_kinds[n];
                 for (size_t q = 0; q < tb.size(); ++q) {
                     const int s = G.PT->triples[n][q], bx = tb[q].first, by = tb[q].second;
-                    if (X.kind(bx) == DENSE && Y.kind(by) == DENSE) {
+                    if (tk[q].first == DENSE && tk[q].second == DENSE) {
                         T_(R, X.N(bx), Y.N(by), (int)T.size[s]);
                         cnt.flops += 2.0 * mt * mr * T.size[s];
                     }
@@ -1503,7 +1512,7 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
     const Basis& Wn = *cb.Qn;
     const Basis& Q = *G.Q;
     const Basis& QW = *G.QW;
-    std::vector<double*> Up(nn, nullptr);
+    std::vector<double*> Up(nn, nullptr), m1v(nn, nullptr);
     Arena pp0(R.stream()), pp1(R.stream());  // Up of two consecutive levels
     Arena* pp[2] = {&pp0, &pp1};
     for (int l = T.L; l >= 0; --l) {
@@ -1511,7 +1520,7 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
         std::vector<int> lv;
         for (int n = 0; n < nn; ++n)
             if (cmap[n] >= 0 && Tree::level(N.t[n]) == l) lv.push_back(n);
-        std::unordered_map<int, double*> m1;  // ADM/DENSE: node -> first factor; SPLIT: child -> Up F'
+        std::vector<double*>& m1 = m1v;  // ADM/DENSE: node -> first factor; SPLIT: child -> Up F'
         for (int n : lv) {
             int t = N.t[n], r = N.s[n];
             int kt = Qn.rank[t], kr = Wn.rank[r];
@@ -1531,7 +1540,7 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 2; ++j) {
                         int a = Tree::child(t, i), b = Tree::child(r, j);
-                        int c = N.find(a, b);
+                        int c = G.PT->kids[n][2 * i + j];
                         double* m = R.dalloc((size_t)std::max(1, Qn.rank[a] * kr));
                         R.job(m, Qn.rank[a], kr, std::max(1, Qn.rank[a]), 0.0);
                         R.term(Up[c], 0, std::max(1, Qn.rank[a]), Wn.tr[b], 0, std::max(1, Wn.rank[b]), Wn.rank[b]);
@@ -1558,7 +1567,7 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 2; ++j) {
                         int a = Tree::child(t, i), b = Tree::child(r, j);
-                        int c = N.find(a, b);
+                        int c = G.PT->kids[n][2 * i + j];
                         R.term(Qn.tr[a], 1, std::max(1, Qn.rank[a]), m1[c], 0, std::max(1, Qn.rank[a]), Qn.rank[a]);
                         cnt.flops += 2.0 * kt * kr * Qn.rank[a];
                     }

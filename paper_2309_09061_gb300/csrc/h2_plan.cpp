@@ -166,6 +166,7 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
     std::vector<std::pair<int, int>> stack{{0, 0}};
     std::vector<int> ss;
     std::vector<std::pair<int, int>> bb;
+    std::vector<std::pair<int8_t, int8_t>> kk;
     while (!stack.empty()) {
         auto [t, r] = stack.back();
         stack.pop_back();
@@ -173,6 +174,7 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
         bool adm = true;
         ss.clear();
         bb.clear();
+        kk.clear();
         for (int bx : X.by_row[t]) {
             int s = X.s[bx];
             int by = Y.find(s, r);
@@ -183,12 +185,14 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
             } else {
                 ss.push_back(s);
                 bb.push_back({bx, by});
+                kk.push_back({kx, ky});
                 if (kx != ADM && ky != ADM) adm = false;
             }
         }
         int id = P.nodes.add(t, r, split ? SPLIT : (adm ? ADM : DENSE));
         P.triples.push_back(ss);
         P.tri_blocks.push_back(bb);
+        P.tri_kinds.push_back(kk);
         (void)id;
         if (split) {
             for (int i = 1; i >= 0; --i)
@@ -196,6 +200,12 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
         }
     }
     P.nodes.finish();
+    P.kids.assign(P.nodes.t.size(), std::array<int, 4>{-1, -1, -1, -1});
+    for (size_t n = 0; n < P.nodes.t.size(); ++n)
+        if (P.nodes.kind[n] == SPLIT)
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j)
+                    P.kids[n][2 * i + j] = P.nodes.find(Tree::child(P.nodes.t[n], i), Tree::child(P.nodes.s[n], j));
     return P;
 }
 
