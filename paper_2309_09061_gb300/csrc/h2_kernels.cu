@@ -126,6 +126,17 @@ __device__ __forceinline__ float f64_to_f32(double v) {
     return __uint_as_float((hi & 0x80000000u) | mag);
 }
 
+// exact FP32 -> FP64 widening by integer operations (FP32 subnormals give
+// zero, infinities and NaN keep their class)
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned sgn = u & 0x80000000u;
+    if (e == 0u) return __hiloint2double((int)sgn, 0);
+    const unsigned eh = (e == 255u) ? 0x7ff00000u : ((e + 896u) << 20);
+    return __hiloint2double((int)(sgn | eh | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+
 // v = hi + lo with hi = v rounded to FP32 (f64_to_f32) and lo = the remainder
 // v - hi (exact in FP64) rounded to FP32, without the FP64 pipe: the remainder
 // is R 2^(e-1075) with R the 29 mantissa bits that hi drops, less 2^29 where hi
@@ -202,27 +213,44 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         }
         for (++it; it < J.nt; ++it) {
             term_at(it, P, f);
-            if (f != 0.0 && P.k > 0) {
+            if ((__double_as_longlong(f) << 1) != 0 && P.k > 0) {  // nonzero factor (an integer test)
                 k0 = 0;
                 return true;
             }
         }
         return false;
     };
+    // Element r of a thread (e = threadIdx.x + r GT) lies in one of two
+    // families: "N" at (row, k) = (e mod 64, e / 64) = (n_i, n_k + (GT/64) r)
+    // and "T" at (k, row) = (e mod KC, e / KC) = (t_k, t_i + (GT/KC) r).  A
+    // plain A and a transposed B use N, the others T; addresses and staged
+    // offsets are a base plus a compile-time step per r (the swizzle adds an
+    // XOR: r << 2 or r << 3 for N, r << 3 or r << 4 for T).
+    const int n_i = threadIdx.x % kF32Tile, n_k = threadIdx.x / kF32Tile;
+    const int t_k = threadIdx.x % KC, t_i = threadIdx.x / KC;
+    const int offN = n_k * kF32Tile + sidx(n_k, n_i), offT = t_k * kF32Tile + sidx(t_k, t_i);
+    auto soff = [&](bool tfam, int r) {
+        return tfam ? (offT ^ (r << (DF ? 4 : 3))) : ((offN ^ (r << (DF ? 3 : 2))) + r * (GT / kF32Tile) * kF32Tile);
+    };
     double ra[NE], rb[NE];
     auto fetch = [&](const GTerm& P, int k0) {
+        {  // A (m x k): N when plain, T when transposed
+            const bool tf_ = P.ta;
+            const int row = tile.i0 + (tf_ ? t_i : n_i), rs = tf_ ? GT / KC : 0;
+            const int kq = k0 + (tf_ ? t_k : n_k), ks = tf_ ? 0 : GT / kF32Tile;
+            const double* a = tf_ ? P.A + kq + (size_t)row * P.lda : P.A + row + (size_t)kq * P.lda;
+            const size_t as = (size_t)(tf_ ? rs : ks) * P.lda;
 #pragma unroll
-        for (int r = 0; r < NE; ++r) {
-            const int e = threadIdx.x + r * GT;
-            int i, kk;
-            if (!P.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % KC; i = e / KC; }
-            int gi = tile.i0 + i, gk = k0 + kk;
-            ra[r] = (gi < J.m && gk < P.k) ? (P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]) : 0.0;
-            int j;
-            if (!P.tb) { kk = e % KC; j = e / KC; } else { j = e % kF32Tile; kk = e / kF32Tile; }
-            const int gj = tile.j0 + j;
-            gk = k0 + kk;
-            rb[r] = (gj < J.n && gk < P.k) ? (P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]) : 0.0;
+            for (int r = 0; r < NE; ++r) ra[r] = (row + rs * r < J.m && kq + ks * r < P.k) ? a[r * as] : 0.0;
+        }
+        {  // B (k x n): T when plain, N when transposed
+            const bool tf_ = !P.tb;
+            const int col = tile.j0 + (tf_ ? t_i : n_i), cs = tf_ ? GT / KC : 0;
+            const int kq = k0 + (tf_ ? t_k : n_k), ks = tf_ ? 0 : GT / kF32Tile;
+            const double* b = tf_ ? P.B + kq + (size_t)col * P.ldb : P.B + col + (size_t)kq * P.ldb;
+            const size_t bs = (size_t)(tf_ ? cs : ks) * P.ldb;
+#pragma unroll
+            for (int r = 0; r < NE; ++r) rb[r] = (col + cs * r < J.n && kq + ks * r < P.k) ? b[r * bs] : 0.0;
         }
     };
     // one k step; D = kk mod 4, known at compile time, fixes the in-group order
@@ -269,17 +297,15 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         const float cf32 = DF ? 0.f : f64_to_f32(cf);
         const bool unit = (cf == 1.0 || cf == -1.0);  // the same for the whole block
         const float sgn = (cf < 0.0) ? -1.f : 1.f;
+        float* const as0 = &As[0][0][0];
+        float* const bs0 = &Bs[0][0][0];
+        constexpr int PL = KC * kF32Tile;  // floats per plane
 #pragma unroll
         for (int r = 0; r < NE; ++r) {
-            const int e = threadIdx.x + r * GT;
-            int i, kk;
-            if (!CP.ta) { i = e % kF32Tile; kk = e / kF32Tile; } else { kk = e % KC; i = e / KC; }
-            int j, kb;
-            if (!CP.tb) { kb = e % KC; j = e / KC; } else { j = e % kF32Tile; kb = e / kF32Tile; }
-            const int pa = sidx(kk, i), pb = sidx(kb, j);
+            const int pa = soff(CP.ta != 0, r), pb = soff(CP.tb == 0, r);
             if constexpr (!DF) {
-                As[0][kk][pa] = cf32 * f64_to_f32(ra[r]);
-                Bs[0][kb][pb] = f64_to_f32(rb[r]);
+                as0[pa] = cf32 * f64_to_f32(ra[r]);
+                bs0[pb] = f64_to_f32(rb[r]);
             } else {
                 float ah, al, bh, bl;
                 if (unit) {  // factor +-1: applied to the split exactly
@@ -290,10 +316,10 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                     split_f64(ra[r] * cf, ah, al);  // the factor applied in FP64
                 }
                 split_f64(rb[r], bh, bl);
-                As[0][kk][pa] = ah;
-                As[1][kk][pa] = al;
-                Bs[0][kb][pb] = bh;
-                Bs[1][kb][pb] = bl;
+                as0[pa] = ah;
+                as0[PL + pa] = al;
+                bs0[pb] = bh;
+                bs0[PL + pb] = bl;
             }
         }
         const int kc = min(KC, CP.k - ck0);
@@ -343,6 +369,8 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         cf = nf;
         have = more;
     }
+    const bool beta0 = (__double_as_longlong(J.beta) << 1) == 0;  // (integer tests keep the
+    const bool mirror = J.sym && tile.i0 != tile.j0;                 //  FP64 pipe for the sums)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -350,11 +378,11 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
             const int gi = tile.i0 + 4 * tx + a, gj = tile.j0 + 4 * ty + b;
             if (gi < J.m && gj < J.n) {
                 double* c = J.C + gi + (size_t)gj * J.ldc;
-                const double v = DF ? (double)acc[a][b] + (double)cor[a][b] : (double)acc[a][b];
-                *c = (J.beta == 0.0) ? v : J.beta * *c + v;
-                if (J.sym && tile.i0 != tile.j0) {
+                const double v = DF ? (double)acc[a][b] + (double)cor[a][b] : f32_to_f64(acc[a][b]);
+                *c = beta0 ? v : J.beta * *c + v;
+                if (mirror) {
                     double* ct = J.C + gj + (size_t)gi * J.ldc;
-                    *ct = (J.beta == 0.0) ? v : J.beta * *ct + v;
+                    *ct = beta0 ? v : J.beta * *ct + v;
                 }
             }
         }
