@@ -1090,6 +1090,8 @@ struct GView {
     const Basis& rowb() const { return T ? *G->QW : *G->Q; }
     const Basis& colb() const { return T ? *G->Q : *G->QW; }
     int node(int t, int r) const { return T ? nodes().find(r, t) : nodes().find(t, r); }
+    // child (child(t, i), child(r, j)) of split node n in view coordinates
+    int kid(int n, int i, int j) const { return T ? G->PT->kids[n][2 * j + i] : G->PT->kids[n][2 * i + j]; }
     const std::vector<int>& row_list(int t) const { return T ? nodes().by_col[t] : nodes().by_row[t]; }
     int other(int n) const { return T ? nodes().t[n] : nodes().s[n]; }
     int8_t kind(int n) const { return nodes().kind[n]; }
@@ -1115,38 +1117,47 @@ struct Coarse {
 };
 
 // One chain X0 F1 F2 ... written to dst; no factors means a copy.
+// src F_1 ... F_nf written to dst; the factors F and their column counts sit in a
+// pool shared by the chains of one level (entries f0 .. f0 + nf - 1)
 struct Chain {
     Mv src;
     int rows, cols0;
-    std::vector<Mv> f;
-    std::vector<int> fcols;
+    int f0, nf;
     double* dst;
     int ldd;
 };
+struct ChainPool {
+    std::vector<Mv> f;
+    std::vector<int> fcols;
+    void clear() {
+        f.clear();
+        fcols.clear();
+    }
+};
 
-static void run_chains(Runner& R, std::vector<Chain>& items) {
-    size_t maxlen = 0;
-    for (auto& c : items) maxlen = std::max(maxlen, c.f.size());
+static void run_chains(Runner& R, std::vector<Chain>& items, const ChainPool& pool) {
+    int maxlen = 0;
+    for (auto& c : items) maxlen = std::max(maxlen, c.nf);
     std::vector<Mv> cur(items.size());
     std::vector<int> curc(items.size());
     for (size_t i = 0; i < items.size(); ++i) {
         cur[i] = items[i].src;
         curc[i] = items[i].cols0;
-        if (items[i].f.empty())
+        if (items[i].nf == 0)
             R.copy(items[i].src.p, items[i].src.ld, items[i].dst, items[i].ldd, items[i].rows, items[i].cols0,
                    items[i].src.tr);
     }
     R.flush_copy();
-    for (size_t st = 0; st < maxlen; ++st) {
+    for (int st = 0; st < maxlen; ++st) {
         for (size_t i = 0; i < items.size(); ++i) {
             Chain& c = items[i];
-            if (st >= c.f.size()) continue;
-            bool last = (st + 1 == c.f.size());
-            int nc = c.fcols[st];
+            if (st >= c.nf) continue;
+            bool last = (st + 1 == c.nf);
+            int nc = pool.fcols[c.f0 + st];
             double* d = last ? c.dst : R.dalloc((size_t)std::max(1, c.rows * nc));
             int ldd = last ? c.ldd : std::max(1, c.rows);
             R.job(d, c.rows, nc, ldd, 0.0);
-            T_(R, cur[i], c.f[st], curc[i]);
+            T_(R, cur[i], pool.f[c.f0 + st], curc[i]);
             cur[i] = mv(d, ldd);
             curc[i] = nc;
         }
@@ -1257,7 +1268,12 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
         R.flush_copy();
         R.flush_qr();
     }
-    std::unordered_map<int, Rep> A;  // node -> representation
+    std::vector<Rep> A(G.nodes().kind.size());     // node -> representation
+    std::vector<Rep> Ahat(G.nodes().kind.size());  // split node -> A-hat before the projection (per level)
+    std::vector<Chain> chains;
+    ChainPool pool;
+    std::vector<std::pair<int, bool>> target;  // cluster -> admissible (all reps agree)
+    std::vector<int> path;
     for (int l = T.L; l >= 0; --l) {
         const Arena::Mark mkl = R.mark();
         const int c0 = Tree::first(l), nl = Tree::count(l);
@@ -1265,8 +1281,8 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
         std::vector<int> rows(nl);
         std::vector<double*> Vh(nl, nullptr);
         std::vector<std::vector<int>> nodes(nl);   // dense (leaf) or split (non-leaf) coarse-admissible nodes
-        std::unordered_map<int, Rep> Ahat;          // split node -> A-hat before the projection
-        std::vector<Chain> chains;
+        chains.clear();
+        pool.clear();
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i;
             for (int n : G.row_list(t))
@@ -1287,17 +1303,25 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             // A-hat for every split coarse-admissible node (Eq. ct_nonleaf with match_column)
             for (int n : nodes[i]) {
                 int r = G.other(n);
-                std::map<int, bool> target;  // cluster -> admissible (all reps agree)
-                for (int a : {a1, a2})
+                target.clear();
+                auto slot = [&](int c) -> std::pair<int, bool>* {
+                    for (auto& x : target)
+                        if (x.first == c) return &x;
+                    return nullptr;
+                };
+                for (int ia = 0; ia < 2; ++ia)
                     for (int j = 0; j < 2; ++j) {
                         int b = Tree::child(r, j);
-                        int nb = G.node(a, b);
+                        int nb = G.kid(n, ia, j);
                         if (G.kind(nb) == ADM) {
-                            if (!target.count(b)) target[b] = true;
+                            if (!slot(b)) target.push_back({b, true});
                         } else {
-                            for (auto& lf : A.at(nb).leaves) {
-                                auto it = target.find(lf.c);
-                                target[lf.c] = (it == target.end() ? true : it->second) && lf.adm;
+                            for (auto& lf : A[nb].leaves) {
+                                auto* x = slot(lf.c);
+                                if (x)
+                                    x->second = x->second && lf.adm;
+                                else
+                                    target.push_back({lf.c, lf.adm});
                             }
                         }
                     }
@@ -1318,25 +1342,28 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                 rep.ld = std::max(1, rows[i]);
                 rep.p = R.dalloc((size_t)rep.ld * std::max(1, cols));
                 int ro = 0;
-                for (int a : {a1, a2}) {
+                for (int ia = 0; ia < 2; ++ia) {
+                    const int a = ia ? a2 : a1;
                     for (auto& lf : rep.leaves) {
-                        int b = is_desc(Tree::child(r, 0), lf.c) ? Tree::child(r, 0) : Tree::child(r, 1);
-                        int nb = G.node(a, b);
+                        const int jb = is_desc(Tree::child(r, 0), lf.c) ? 0 : 1;
+                        int b = Tree::child(r, jb);
+                        int nb = G.kid(n, ia, jb);
                         Chain ch;
                         ch.rows = Qn.rank[a];
                         ch.dst = rep.p + ro + (size_t)lf.col * rep.ld;
                         ch.ldd = rep.ld;
+                        ch.f0 = (int)pool.f.size();
                         int src_c;
                         bool src_adm;
                         if (G.kind(nb) == ADM) {
                             ch.src = mv(out.Rt.p[a], std::max(1, Qn.rank[a]));
                             ch.cols0 = Q.rank[a];
-                            ch.f.push_back(G.C(nb));
-                            ch.fcols.push_back(QW.rank[b]);
+                            pool.f.push_back(G.C(nb));
+                            pool.fcols.push_back(QW.rank[b]);
                             src_c = b;
                             src_adm = true;
                         } else {
-                            const Rep& cr = A.at(nb);
+                            const Rep& cr = A[nb];
                             const Rep::Leaf* sl = nullptr;
                             for (auto& x : cr.leaves)
                                 if (is_desc(x.c, lf.c)) sl = &x;
@@ -1347,26 +1374,32 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                             src_adm = sl->adm;
                         }
                         // split admissible representations down to the target leaf: A F^*
-                        std::vector<int> path;
+                        path.clear();
                         for (int c = lf.c; c != src_c; c = Tree::parent(c)) path.push_back(c);
                         std::reverse(path.begin(), path.end());
                         for (int c : path) {
-                            ch.f.push_back(mvT(QW.tr[c], std::max(1, QW.rank[c])));
-                            ch.fcols.push_back(QW.rank[c]);
+                            pool.f.push_back(mvT(QW.tr[c], std::max(1, QW.rank[c])));
+                            pool.fcols.push_back(QW.rank[c]);
                         }
                         if (src_adm && !lf.adm) {  // expand with the leaf basis: A W^*
-                            ch.f.push_back(mvT(QW.leaf[lf.c], (int)T.size[lf.c]));
-                            ch.fcols.push_back((int)T.size[lf.c]);
+                            pool.f.push_back(mvT(QW.leaf[lf.c], (int)T.size[lf.c]));
+                            pool.fcols.push_back((int)T.size[lf.c]);
                         }
-                        if (ch.rows > 0) chains.push_back(ch);
+                        ch.nf = (int)pool.f.size() - ch.f0;
+                        if (ch.rows > 0) {
+                            chains.push_back(ch);
+                        } else {  // an empty chain leaves its factors unused
+                            pool.f.resize(ch.f0);
+                            pool.fcols.resize(ch.f0);
+                        }
                     }
                     ro += Qn.rank[a];
                 }
-                Ahat[n] = rep;
+                Ahat[n] = std::move(rep);
             }
         }
         R.flush_gemm();
-        run_chains(R, chains);
+        run_chains(R, chains, pool);
         // condensed matrices (transposed): [Z_t V^*; w G_tr^* ...]; SVD
         int* d_counts = (int*)R.dalloc(nl);
         H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
@@ -1378,7 +1411,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             for (int n : nodes[i]) {
                 if (leaf) ncol += (int)T.size[G.other(n)];
                 else {
-                    auto& rp = Ahat.at(n);
+                    auto& rp = Ahat[n];
                     for (auto& lf : rp.leaves) ncol += lf.width;
                 }
             }
@@ -1403,7 +1436,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                     R.copy(d.p, d.ld, Ct + o, ncol, (int)T.size[r], rows[i], d.tr ^ 1, 1.0, w + cmap[n]);
                     o += (int)T.size[r];
                 } else {
-                    auto& rp = Ahat.at(n);
+                    auto& rp = Ahat[n];
                     int wdt = 0;
                     for (auto& lf : rp.leaves) wdt += lf.width;
                     R.copy(rp.p, rp.ld, Ct + o, ncol, wdt, rows[i], 1, 1.0, w + cmap[n]);
@@ -1474,22 +1507,23 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
                     R.job(rep.p, kt, (int)T.size[r], rep.ld, 0.0);
                     if (kt > 0) T_(R, mvT(U, ldu), G.D(n), rows[i]);
                 } else {
-                    const Rep& ah = Ahat.at(n);
-                    rep.leaves = ah.leaves;
+                    Rep& ah = Ahat[n];
                     int cols = 0;
                     for (auto& lf : ah.leaves) cols += lf.width;
+                    rep.leaves = std::move(ah.leaves);
                     rep.p = pp[l & 1]->alloc((size_t)rep.ld * std::max(1, cols));
                     R.job(rep.p, kt, cols, rep.ld, 0.0);
                     if (kt > 0) R.term(U, 1, ldu, ah.p, 0, ah.ld, rows[i]);
+                    ah = Rep{};
                 }
-                A[n] = rep;
+                A[n] = std::move(rep);
             }
         }
         R.flush_gemm();
         // the representations of the level below are consumed
         if (l < T.L) {
             for (int c = Tree::first(l + 1); c < Tree::first(l + 1) + Tree::count(l + 1); ++c)
-                for (int n : G.row_list(c)) A.erase(n);
+                for (int n : G.row_list(c)) A[n] = Rep{};
             pp[(l + 1) & 1]->release_all();
         }
         R.release(mkl);
