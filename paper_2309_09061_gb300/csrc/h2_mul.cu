@@ -481,6 +481,37 @@ static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
     return h;
 }
 
+// Transfer matrices of the children of the nl clusters from c0 (ranks known):
+// one device chunk per level, carved at 256-byte boundaries, not one allocation
+// per cluster (each device allocation is a driver call).
+static size_t carve_size(size_t n) { return (std::max<size_t>(n, 1) + 31) & ~size_t(31); }
+static size_t transfer_need(const Basis& B, int c0, int nl) {
+    size_t need = 0;
+    for (int i = 0; i < nl; ++i)
+        for (int j = 0; j < 2; ++j) need += carve_size((size_t)B.rank[Tree::child(c0 + i, j)] * B.rank[c0 + i]);
+    return need;
+}
+struct Carve {
+    double* p = nullptr;
+    size_t left = 0;
+    Carve(Basis& B, size_t need) {
+        if (need == 0) return;
+        auto ch = std::make_shared<DevBuf>();
+        ch->alloc(need);
+        B.chunks.push_back(ch);
+        p = ch->p;
+        left = need;
+    }
+    double* take(size_t n) {
+        const size_t m = carve_size(n);
+        if (m > left) throw Error(H2_ERR_UNSUPPORTED, "transfer chunk too small");
+        double* q = p;
+        p += m;
+        left -= m;
+        return q;
+    }
+};
+
 // ------------------------------------------------------------------ phase A (Fig. 4)
 struct Induced {
     std::shared_ptr<Basis> Q;
@@ -729,6 +760,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         }
         R.flush_copy();
         R.flush_gemm();
+        Carve trc(Q, leaf ? 0 : transfer_need(Q, c0, nl));  // the children's transfers of this level
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i, kt = Q.rank[t];
             if (leaf) {
@@ -737,11 +769,9 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
                 // split rows into the children's transfers (stored with ld = rank of the child)
                 int o = 0;
                 for (int a : {Tree::child(t, 0), Tree::child(t, 1)}) {
-                    auto ch = std::make_shared<DevBuf>();
-                    ch->alloc(std::max<size_t>((size_t)Q.rank[a] * kt, 1));
-                    Q.chunks.push_back(ch);
-                    R.copy(Qh[i] + o, rows[i], ch->p, std::max(1, Q.rank[a]), Q.rank[a], kt, 0);
-                    Q.tr[a] = ch->p;
+                    double* tp = trc.take((size_t)Q.rank[a] * kt);
+                    R.copy(Qh[i] + o, rows[i], tp, std::max(1, Q.rank[a]), Q.rank[a], kt, 0);
+                    Q.tr[a] = tp;
                     o += Q.rank[a];
                 }
             }
@@ -1456,6 +1486,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
         chunk->alloc(std::max<size_t>(need, 1));
         Qn.chunks.push_back(chunk);
         size_t off = 0;
+        Carve trc(Qn, leaf ? 0 : transfer_need(Qn, c0, nl));  // the children's transfers of this level
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i, kt = Qn.rank[t];
             double* q = chunk->p + off;
@@ -1466,11 +1497,9 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             } else {
                 int o = 0;
                 for (int a : {Tree::child(t, 0), Tree::child(t, 1)}) {
-                    auto ch = std::make_shared<DevBuf>();
-                    ch->alloc(std::max<size_t>((size_t)Qn.rank[a] * kt, 1));
-                    Qn.chunks.push_back(ch);
-                    Qn.tr[a] = ch->p;
-                    if (kt > 0) R.copy(so[i].U + o, so[i].ldu, ch->p, std::max(1, Qn.rank[a]), Qn.rank[a], kt, 0);
+                    double* tp = trc.take((size_t)Qn.rank[a] * kt);
+                    Qn.tr[a] = tp;
+                    if (kt > 0) R.copy(so[i].U + o, so[i].ldu, tp, std::max(1, Qn.rank[a]), Qn.rank[a], kt, 0);
                     o += Qn.rank[a];
                 }
             }
