@@ -2,6 +2,7 @@
 // entry points h2_build_interp, h2_to_dense, h2_info, h2_get_structure,
 // h2_free, h2_error_string.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
@@ -31,16 +32,33 @@ static cudaMemPool_t lib_pool(int dev) {
     return pools[dev];
 }
 
+// With H2_TRACE set, host calls that may block print "h2wait <call> <ms> <bytes>"
+// when they take longer than 0.2 ms.
+struct HostWait {
+    const char* what;
+    size_t bytes;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    HostWait(const char* w, size_t b) : what(w), bytes(b) {}
+    ~HostWait() {
+        static const bool trace = std::getenv("H2_TRACE") != nullptr;
+        if (!trace) return;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > 0.2) std::fprintf(stderr, "h2wait %s %.3f %zu\n", what, ms, bytes);
+    }
+};
+
 void DevBuf::alloc(size_t n) {
     reset();
     if (n == 0) return;
     void* p2 = nullptr;
+    HostWait hw("cudaMalloc", n * sizeof(double));
     H2_CUDA(cudaMalloc(&p2, n * sizeof(double)));
     p = (double*)p2;
     len = n;
 }
 
 void DevBuf::reset() {
+    HostWait hw("cudaFree", len * sizeof(double));
     if (p) cudaFree(p);
     p = nullptr;
     len = 0;
@@ -127,6 +145,7 @@ double* Arena::alloc(size_t n) {
         int dev = 0;
         H2_CUDA(cudaGetDevice(&dev));
         void* p = nullptr;
+        HostWait hw("pool_alloc", sz);
         H2_CUDA(cudaMallocFromPoolAsync(&p, sz, lib_pool(dev), st_));
         chunks_.push_back(p);
         cur_ = (char*)p;
@@ -163,7 +182,7 @@ constexpr size_t kPinnedChunk = size_t(32) << 20;
 const void* Runner::stage(const void* src, size_t bytes) {
     const size_t need = (bytes + 255) & ~size_t(255);
     if (pinned_.empty() || pinned_used_ + need > pinned_.back().size) {
-        Pinned c{nullptr, 0, nullptr};
+        Pinned c{nullptr, nullptr, 0, nullptr};
         {
             std::lock_guard<std::mutex> lk(g_pinned_mu);
             for (size_t i = 0; i < g_pinned_free.size(); ++i)
@@ -174,19 +193,23 @@ const void* Runner::stage(const void* src, size_t bytes) {
                 }
         }
         if (c.p) {
+            HostWait hw("pinned_reuse", c.size);
             H2_CUDA(cudaEventSynchronize(c.done));  // its previous copies have ended
         } else {
             c.size = std::max(need, kPinnedChunk);
-            H2_CUDA(cudaHostAlloc((void**)&c.p, c.size, cudaHostAllocDefault));
+            HostWait hw("cudaHostAlloc", c.size);
+            H2_CUDA(cudaHostAlloc((void**)&c.p, c.size, cudaHostAllocMapped | cudaHostAllocPortable));
+            H2_CUDA(cudaHostGetDevicePointer((void**)&c.dp, c.p, 0));
             H2_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
         }
         pinned_.push_back(c);
         pinned_used_ = 0;
     }
     char* h = pinned_.back().p + pinned_used_;
+    char* dh = pinned_.back().dp + pinned_used_;
     pinned_used_ += need;
     std::memcpy(h, src, bytes);
-    return h;
+    return dh;
 }
 
 void Runner::release_pinned() {
@@ -198,14 +221,35 @@ void Runner::release_pinned() {
     pinned_used_ = 0;
 }
 
+// Uploads: staged in mapped pinned memory (256-byte granules) and pulled into
+// the arena (256-byte granules) by k_pull on this stream.
 template <class T>
 T* Runner::upload(const std::vector<T>& v) {
     size_t bytes = std::max<size_t>(v.size() * sizeof(T), 8);
     double* d = dalloc((bytes + 7) / 8);
-    if (!v.empty())
-        H2_CUDA(cudaMemcpyAsync(d, stage(v.data(), v.size() * sizeof(T)), v.size() * sizeof(T),
-                                cudaMemcpyHostToDevice, st_));
+    if (!v.empty()) {
+        PullBatch b{};
+        b.seg[0] = PullSeg{stage(v.data(), v.size() * sizeof(T)), d, v.size() * sizeof(T)};
+        b.n = 1;
+        launch_pull(b, st_);
+    }
     return (T*)d;
+}
+
+template <class A, class B, class C>
+void Runner::upload3(const std::vector<A>& a, A*& da, const std::vector<B>& b, B*& db, const std::vector<C>& c,
+                     C*& dc) {
+    PullBatch pb{};
+    auto one = [&](const void* src, size_t n, size_t esz) -> double* {
+        const size_t bytes = std::max<size_t>(n * esz, 8);
+        double* d = dalloc((bytes + 7) / 8);
+        if (n) pb.seg[pb.n++] = PullSeg{stage(src, n * esz), d, n * esz};
+        return d;
+    };
+    da = (A*)one(a.data(), a.size(), sizeof(A));
+    db = (B*)one(b.data(), b.size(), sizeof(B));
+    dc = (C*)one(c.data(), c.size(), sizeof(C));
+    if (pb.n) launch_pull(pb, st_);
 }
 template int* Runner::upload<int>(const std::vector<int>&);
 template int64_t* Runner::upload<int64_t>(const std::vector<int64_t>&);
@@ -271,19 +315,22 @@ void Runner::flush_gemm(int precision_override) {
                 if (!J.sym || i0 <= j0) tiles.push_back(GTile{j, i0, j0});
     }
     if (!tiles.empty()) {
-        GTerm* dt = upload(terms_);
-        GJob* dj = upload(jobs_);
-        GTile* dti = upload(tiles);
+        GTerm* dt;
+        GJob* dj;
+        GTile* dti;
+        upload3(terms_, dt, jobs_, dj, tiles, dti);
         const int fam = tc ? 10 : (pr == H2_MIXED) ? 1 : (pr == kGemmDF) ? 11 : 0;
         if (tc) ensure_flag();
         SliceSum* ds = sums.empty() ? nullptr : upload(sums);
         int max_n = 0;
         for (const SliceSum& s : sums) max_n = std::max(max_n, s.n);
         begin(fam);
-        if (tc)
+        if (tc) {
             launch_gemm_tc(dt, dj, dti, (int)tiles.size(), d_flag_, st_);
-        else
+        } else {
+            HostWait hw("launch_gemm", tiles.size());
             launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
+        }
         launch_slice_sum(ds, (int)sums.size(), max_n, st_);
         end(fam, fl, by, (int64_t)tiles.size());
         ++launches;

@@ -293,6 +293,18 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_
 void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st);
 void launch_norm(const NormJob* jobs, int njobs, int precision, cudaStream_t st);
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);
+// Stream-ordered pull of up to 4 buffers from mapped pinned host memory into
+// device memory (16-byte words; both sides 16-byte aligned), as one kernel.
+struct PullSeg {
+    const void* src;  // device-visible address of the pinned source
+    void* dst;
+    size_t bytes;     // rounded up to 16 by the kernel: both buffers must hold it
+};
+struct PullBatch {
+    PullSeg seg[4];
+    int n;
+};
+void launch_pull(const PullBatch& b, cudaStream_t st);
 // nrm (n x 3, original order) non-null: the normal-derivative basis
 // grad l_nu(x_i) . n_i instead of l_nu(x_i)
 void launch_interp_leaf(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
@@ -434,12 +446,15 @@ private:
     cudaEvent_t cur_ = nullptr;
     cudaEvent_t get_event();
 public:
-    // Pinned host staging of the uploaded descriptors: from pageable memory an
-    // asynchronous copy may wait for the stream, and the host could not run
-    // ahead of the GPU.  Chunks return to a process-wide pool on release, with
-    // an event that marks the end of their last copy.
+    // Uploads are staged in mapped pinned host memory and pulled into device
+    // memory by a kernel on the Runner's stream (k_pull).  A copy-engine copy
+    // could queue behind the copies of another stream, and those behind that
+    // stream's kernels; a pageable source could make the copy wait for the
+    // stream.  Chunks return to a process-wide pool on release, with an event
+    // that marks the end of their last pull.
     struct Pinned {
         char* p;
+        char* dp;  // the same memory as seen by the device (mapped)
         size_t size;
         cudaEvent_t done;
     };
@@ -447,7 +462,9 @@ public:
 private:
     std::vector<Pinned> pinned_;
     size_t pinned_used_ = 0;
-    const void* stage(const void* src, size_t bytes);
+    const void* stage(const void* src, size_t bytes);  // returns the device-visible copy
+    template <class A, class B, class C>
+    void upload3(const std::vector<A>& a, A*& da, const std::vector<B>& b, B*& db, const std::vector<C>& c, C*& dc);
     void release_pinned();
 };
 

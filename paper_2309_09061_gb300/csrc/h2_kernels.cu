@@ -1653,6 +1653,27 @@ __global__ void k_copy(const CopyJob* __restrict__ jobs) {
     }
 }
 
+// Copy of the descriptor arrays of a launch from mapped pinned host memory, in
+// stream order on the SMs: no copy engine, so the uploads of one stream never
+// queue behind the copies of another.
+__global__ void k_pull(PullBatch b) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int s = 0; s < b.n; ++s) {
+        const uint4* src = (const uint4*)b.seg[s].src;
+        uint4* dst = (uint4*)b.seg[s].dst;
+        const size_t n = (b.seg[s].bytes + 15) / 16;
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+    }
+}
+
+void launch_pull(const PullBatch& b, cudaStream_t st) {
+    size_t words = 0;
+    for (int s = 0; s < b.n; ++s) words = std::max(words, (b.seg[s].bytes + 15) / 16);
+    if (words == 0) return;
+    const int grid = (int)std::min<size_t>((words + 255) / 256, (size_t)2 * device_sm_count());
+    k_pull<<<grid, 256, 0, st>>>(b);
+}
+
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st) {
     if (njobs > 0) k_copy<<<njobs, 256, 0, st>>>(jobs);
 }
