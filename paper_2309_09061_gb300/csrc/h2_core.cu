@@ -232,6 +232,7 @@ T* Runner::upload(const std::vector<T>& v) {
         b.seg[0] = PullSeg{stage(v.data(), v.size() * sizeof(T)), d, v.size() * sizeof(T)};
         b.n = 1;
         launch_pull(b, st_);
+        ++launches;
     }
     return (T*)d;
 }
@@ -249,7 +250,10 @@ void Runner::upload3(const std::vector<A>& a, A*& da, const std::vector<B>& b, B
     da = (A*)one(a.data(), a.size(), sizeof(A));
     db = (B*)one(b.data(), b.size(), sizeof(B));
     dc = (C*)one(c.data(), c.size(), sizeof(C));
-    if (pb.n) launch_pull(pb, st_);
+    if (pb.n) {
+        launch_pull(pb, st_);
+        ++launches;
+    }
 }
 template int* Runner::upload<int>(const std::vector<int>&);
 template int64_t* Runner::upload<int64_t>(const std::vector<int64_t>&);
@@ -332,6 +336,7 @@ void Runner::flush_gemm(int precision_override) {
             launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
         }
         launch_slice_sum(ds, (int)sums.size(), max_n, st_);
+        if (!sums.empty()) ++launches;
         end(fam, fl, by, (int64_t)tiles.size());
         ++launches;
     }

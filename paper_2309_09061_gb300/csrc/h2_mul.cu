@@ -667,6 +667,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         if (rid > 0) {
             ident = R.dalloc((size_t)rid * rid);
             launch_set_identity(ident, rid, rid, rid, R.stream());
+            ++R.launches;
         }
         std::vector<double*> Vq(nl, nullptr), Tq(nl, nullptr);
         for (int i = 0; i < nl; ++i) {
