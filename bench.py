@@ -283,6 +283,13 @@ def ours_arm(args):
             out["n"] += np.array(s["fam_launches"])
         return out
 
+    # DRAM traffic of k_gemm<double> from one ncu capture (sphere n=8192, the 61st
+    # launch of the kernel; profiles/k_gemm_sphere-n8192_fp64.md): 45.77 MB of
+    # dram__bytes_read.sum + dram__bytes_write.sum for 0.629 GFLOP of executed FP64 work
+    # (314.6 M DFMA), scaled to the average launch here by its flops.  The kernel has not
+    # changed since the capture.
+    gemm64_capture = {"dram_bytes": 45.77e6, "flops": 0.629e9}
+
     def roofline(f):
         top = int(np.argmax(f["ms"]))
         rate = f["fl"][top] / (f["ms"][top] / 1e3) / 1e12
@@ -313,6 +320,13 @@ def ours_arm(args):
                     "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
         roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
         roof["traffic"] = None
+        if top == 0 and f["n"][top] > 0:
+            per_launch = f["fl"][top] / f["n"][top]
+            roof["traffic"] = gemm64_capture["dram_bytes"] * per_launch / gemm64_capture["flops"]
+            roof["traffic_unit"] = "bytes per launch"
+            roof["traffic_source"] = ("ncu capture at n=8192 (45.77 MB for 0.629 GFLOP executed), "
+                                      "scaled by the average launch's flops")
+            roof["algorithmic_bytes_per_launch"] = f["by"][top] / f["n"][top]
         roof["avg_launch_ms"] = f["ms"][top] / max(1.0, f["n"][top])
         roof["share_of_step"] = float(f["ms"][top] / max(1e-9, f["ms"].sum()))
         return roof
