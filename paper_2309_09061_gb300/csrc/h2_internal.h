@@ -64,6 +64,7 @@ struct BlockTree {
     std::unordered_map<int64_t, int> id;     // t * nc + s -> block index
     std::vector<std::vector<int>> by_row;    // t -> blocks of row t, by increasing s
     std::vector<std::vector<int>> by_col;    // s -> blocks of column s, by increasing t
+    std::vector<std::array<int, 4>> kids;    // SPLIT block: block (child(t,i), child(s,j)) at 2 i + j
     int find(int a, int b) const {
         auto it = id.find((int64_t)a * nc + b);
         return it == id.end() ? -1 : it->second;
@@ -76,7 +77,7 @@ struct BlockTree {
         id[(int64_t)a * nc + b] = i;
         return i;
     }
-    void finish();  // fills by_row / by_col
+    void finish();  // fills by_row / by_col / kids
     int64_t count(int8_t k) const {
         int64_t c = 0;
         for (auto x : kind) c += (x == k);
@@ -91,7 +92,6 @@ struct ProductTree {
     std::vector<std::vector<int>> triples; // per node: list of s
     std::vector<std::vector<std::pair<int, int>>> tri_blocks;  // per node and triple: blocks (t,s) of X, (s,r) of Y
     std::vector<std::vector<std::pair<int8_t, int8_t>>> tri_kinds;  // per node and triple: kinds of the two blocks
-    std::vector<std::array<int, 4>> kids;  // SPLIT node: node (child(t,i), child(r,j)) at 2 i + j
 };
 ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y);
 

@@ -43,6 +43,8 @@ struct OpView {
     const Basis& rowb() const { return T ? *M->W : *M->V; }
     const Basis& colb() const { return T ? *M->V : *M->W; }
     int block(int t, int s) const { return T ? bt().find(s, t) : bt().find(t, s); }
+    // child (child(t, i), child(s, j)) of split block b in view coordinates
+    int kid(int b, int i, int j) const { return T ? bt().kids[b][2 * j + i] : bt().kids[b][2 * i + j]; }
     int8_t kind(int b) const { return bt().kind[b]; }
     const std::vector<int>& row_list(int t) const { return T ? bt().by_col[t] : bt().by_row[t]; }
     int other(int b) const { return T ? bt().t[b] : bt().s[b]; }  // column cluster of block b in the view
@@ -547,6 +549,8 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
     out.zpres = (VZ != nullptr);
     if (VZ) out.RbarZ.init(T.nc);
     auto kz = [&](int t) { return VZ ? VZ->rank[t] : 0; };
+    // per block of X (entries are set and used within the level of the block)
+    std::vector<double*> M(X.bt().kind.size(), nullptr), inv(M.size(), nullptr), SPE(M.size(), nullptr);
     for (int l = T.L; l >= 0; --l) {
         const Arena::Mark mkl = R.mark();  // scratch of this level
         const int c0 = Tree::first(l), nl = Tree::count(l);
@@ -554,8 +558,6 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         std::vector<int> rows(nl), k1(nl), m2(nl);
         std::vector<double*> VXh(nl), QX(nl), VZh(nl, nullptr);
         std::vector<std::vector<int>> C(nl);
-        std::unordered_map<int, double*> M;
-        std::unordered_map<int, double*> inv;
         // PE_{s'} = P_{s'} E_{Y,s'} for the children level
         std::vector<double*> PE(T.nc, nullptr);
         if (!leaf) {
@@ -568,7 +570,6 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             R.flush_gemm();
         }
         // VX-hat and the admissible-child chains S_X(a,b) PE_b
-        std::unordered_map<int, double*> SPE;
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i;
             for (int b : X.row_list(t))
@@ -599,10 +600,11 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
                 }
                 for (int b : C[i]) {
                     int s = X.other(b);
-                    for (int a : {a1, a2})
+                    for (int ia = 0; ia < 2; ++ia)
                         for (int j = 0; j < 2; ++j) {
+                            const int a = ia ? a2 : a1;
                             int sj = Tree::child(s, j);
-                            int bb = X.block(a, sj);
+                            int bb = X.kid(b, ia, j);
                             if (X.kind(bb) != ADM) continue;
                             double* m = R.dalloc((size_t)std::max(1, VX.rank[a] * VY.rank[s]));
                             R.job(m, VX.rank[a], VY.rank[s], std::max(1, VX.rank[a]), 0.0);
@@ -629,11 +631,12 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
                     cnt.flops += 2.0 * rows[i] * ky * T.size[s];
                 } else {
                     int o = 0;
-                    for (int a : {Tree::child(t, 0), Tree::child(t, 1)}) {
+                    for (int ia = 0; ia < 2; ++ia) {
+                        const int a = Tree::child(t, ia);
                         R.job(m + o, Q.rank[a], ky, rows[i], 0.0);
                         for (int j = 0; j < 2; ++j) {
                             int sj = Tree::child(s, j);
-                            int bb = X.block(a, sj);
+                            int bb = X.kid(b, ia, j);
                             if (X.kind(bb) == ADM) {
                                 R.term(out.Rbar.p[a], 0, std::max(1, Q.rank[a]), SPE[bb], 0,
                                        std::max(1, VX.rank[a]), VX.rank[a]);
@@ -990,7 +993,7 @@ static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2
                     R.job(m, Q.rank[t], QW.rank[b], std::max(1, Q.rank[t]), 0.0);
                     R.term(G.C[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
                     R.term(Cup[n], 0, std::max(1, Q.rank[t]), QW.tr[b], 1, std::max(1, QW.rank[b]), QW.rank[r]);
-                    for (int i = 0; i < 2; ++i) tmp.push_back({G.PT->kids[n][2 * i + j], m});
+                    for (int i = 0; i < 2; ++i) tmp.push_back({G.PT->nodes.kids[n][2 * i + j], m});
                 }
             }
             R.flush_gemm();
@@ -1122,7 +1125,7 @@ struct GView {
     const Basis& colb() const { return T ? *G->Q : *G->QW; }
     int node(int t, int r) const { return T ? nodes().find(r, t) : nodes().find(t, r); }
     // child (child(t, i), child(r, j)) of split node n in view coordinates
-    int kid(int n, int i, int j) const { return T ? G->PT->kids[n][2 * j + i] : G->PT->kids[n][2 * i + j]; }
+    int kid(int n, int i, int j) const { return T ? G->PT->nodes.kids[n][2 * j + i] : G->PT->nodes.kids[n][2 * i + j]; }
     const std::vector<int>& row_list(int t) const { return T ? nodes().by_col[t] : nodes().by_row[t]; }
     int other(int n) const { return T ? nodes().t[n] : nodes().s[n]; }
     int8_t kind(int n) const { return nodes().kind[n]; }
@@ -1604,7 +1607,7 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 2; ++j) {
                         int a = Tree::child(t, i), b = Tree::child(r, j);
-                        int c = G.PT->kids[n][2 * i + j];
+                        int c = G.PT->nodes.kids[n][2 * i + j];
                         double* m = R.dalloc((size_t)std::max(1, Qn.rank[a] * kr));
                         R.job(m, Qn.rank[a], kr, std::max(1, Qn.rank[a]), 0.0);
                         R.term(Up[c], 0, std::max(1, Qn.rank[a]), Wn.tr[b], 0, std::max(1, Wn.rank[b]), Wn.rank[b]);
@@ -1631,7 +1634,7 @@ static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, co
                 for (int i = 0; i < 2; ++i)
                     for (int j = 0; j < 2; ++j) {
                         int a = Tree::child(t, i), b = Tree::child(r, j);
-                        int c = G.PT->kids[n][2 * i + j];
+                        int c = G.PT->nodes.kids[n][2 * i + j];
                         R.term(Qn.tr[a], 1, std::max(1, Qn.rank[a]), m1[c], 0, std::max(1, Qn.rank[a]), Qn.rank[a]);
                         cnt.flops += 2.0 * kt * kr * Qn.rank[a];
                     }

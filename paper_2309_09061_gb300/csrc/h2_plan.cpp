@@ -18,6 +18,11 @@ void BlockTree::finish() {
     }
     for (auto& v : by_row) std::sort(v.begin(), v.end(), [&](int a, int b) { return s[a] < s[b]; });
     for (auto& v : by_col) std::sort(v.begin(), v.end(), [&](int a, int b) { return t[a] < t[b]; });
+    kids.assign(t.size(), std::array<int, 4>{-1, -1, -1, -1});
+    for (size_t b = 0; b < t.size(); ++b)
+        if (kind[b] == SPLIT)
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) kids[b][2 * i + j] = find(Tree::child(t[b], i), Tree::child(s[b], j));
 }
 
 // Depth L: the smallest depth with ceil(n / 2^L) <= leaf, so that every
@@ -200,12 +205,6 @@ ProductTree build_product_tree(const BlockTree& X, const BlockTree& Y) {
         }
     }
     P.nodes.finish();
-    P.kids.assign(P.nodes.t.size(), std::array<int, 4>{-1, -1, -1, -1});
-    for (size_t n = 0; n < P.nodes.t.size(); ++n)
-        if (P.nodes.kind[n] == SPLIT)
-            for (int i = 0; i < 2; ++i)
-                for (int j = 0; j < 2; ++j)
-                    P.kids[n][2 * i + j] = P.nodes.find(Tree::child(P.nodes.t[n], i), Tree::child(P.nodes.s[n], j));
     return P;
 }
 
