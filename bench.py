@@ -59,6 +59,22 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(seed, rank):
+    """Seed of rank `rank`'s points: every rank runs an independent product."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, world, tdist, device):
+    """The largest x of all ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -202,7 +218,7 @@ def ours_arm(args):
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     # each rank: its own independent product (seed offset by rank)
-    pts = synth.make_points(w["geometry"], w["n"], w["seed"] + 1000 * rank)
+    pts = synth.make_points(w["geometry"], w["n"], rank_seed(w["seed"], rank))
     G = P.h2_build_interp(pts, w["kernel"], w["leaf"], w["eta"], w["order"], stream=sptr)
 
     def barrier():
@@ -229,11 +245,7 @@ def ours_arm(args):
         barrier()
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
-        dt = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, tdist, dev)
         info = Zs[-1].info()
         # eps_2 of the last result (Sec. 7: relative spectral error, 20 power-iteration
         # steps through H^2 matrix-vector products), outside the timed region
@@ -471,7 +483,7 @@ def dlp_arm(args):
     P.build()
     P.load()
     d = DLP
-    pts = synth.cube_surface(d["n"], d["seed"] + 1000 * rank)
+    pts = synth.cube_surface(d["n"], rank_seed(d["seed"], rank))
     nrm = synth.cube_surface_normals(pts)
     K = P.h2_build_interp(pts, P.H2_K_DLP, d["leaf"], d["eta"], d["order"], stream=sptr, normals=nrm)
     out = {}
