@@ -194,7 +194,7 @@ const void* Runner::stage(const void* src, size_t bytes) {
         }
         if (c.p) {
             HostWait hw("pinned_reuse", c.size);
-            H2_CUDA(cudaEventSynchronize(c.done));  // its previous copies have ended
+            H2_CUDA(cudaEventSynchronize(c.done));  // its previous pulls have ended
         } else {
             c.size = std::max(need, kPinnedChunk);
             HostWait hw("cudaHostAlloc", c.size);
