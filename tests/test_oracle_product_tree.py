@@ -2,7 +2,8 @@
 oracle: its leaves tile I x K exactly once, and for every leaf (t, r) the
 triples (a, s, b) met on the way from the root to (t, r), restricted to t x r,
 add up to the dense product (XY)|t x r.  A dropped or doubled triple breaks
-the sum."""
+the sum.  The map from T^XY nodes to the admissible target blocks of phase B
+is checked against containment of index ranges."""
 import numpy as np
 import pytest
 
@@ -69,3 +70,30 @@ def test_dropped_triple_is_detected():
            if not np.allclose(acc, XY[_rng(X.rows, k[0]), _rng(Y.cols, k[1])], rtol=1e-12,
                               atol=1e-12 * np.abs(XY).max())]
     assert bad
+
+
+@pytest.mark.parametrize("geometry,n,leaf", [("cube", 300, 16), ("sphere", 257, 20)])
+def test_coarse_map_by_index_ranges(geometry, n, leaf):
+    """Every T^XY node inside an admissible target block of T_IK maps to exactly
+    that block (containment of index ranges), and no other node is mapped."""
+    pts = synth.make_points(geometry, n, 2309090633)
+    st = O.build_structure(pts, leaf, 2.0, 3)
+    X = O.build_interp(st, O.K_LAPLACE)
+    res = O.mul_add(O.build_interp(st, O.K_LAPLACE), X, O.build_interp(st, O.K_YUKAWA), 1e-4)
+    G = res.induced
+    cmap = O.coarse_map(G, st.blocks)
+    tree = st.tree
+    targets = [b for b, k in st.blocks.kind.items() if k == O.ADM]
+
+    def inside(node, blk):
+        (t, r), (bt, br) = node, blk
+        return (tree.off[bt] <= tree.off[t] and tree.off[t] + tree.size[t] <= tree.off[bt] + tree.size[bt]
+                and tree.off[br] <= tree.off[r] and tree.off[r] + tree.size[r] <= tree.off[br] + tree.size[br])
+
+    for node in G.blocks.kind:
+        holders = [b for b in targets if inside(node, b)]
+        assert len(holders) <= 1  # admissible target blocks are disjoint
+        if holders:
+            assert cmap.get(node) == holders[0]
+        else:
+            assert node not in cmap
