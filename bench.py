@@ -4,11 +4,16 @@ One step = one h2_mul_add call (the whole hot path: basis products, weights,
 compressed induced bases, the couplings on T^XY, coarsening, final
 couplings) on the n = 32768 unit-sphere workload: Laplace kernel, leaf 64,
 eta 2, Chebyshev order 4 (rank 64), X = Y = Z, eps = 1e-6.  The metric is
-rows per second (n / time).  The line's `value` is the FP64 GPU form (the
-workload's stated precision); the mixed-precision form of the same workload
-is reported beside it.
+rows per second (n / time).  The line's `value` is the fast form (H2_AUTO,
+which at eps = 1e-6 runs the FP32-class products on the tcgen05 tensor cores
+in three-term TF32 pieces and keeps QR/SVD/ranks in FP64); the plain FP64 GPU
+form of the same workload is timed beside it with the same steps, and the
+other workloads (n = 2048 sphere, n = 131072 cube at eps 1e-4 and 1e-6, the
+64-product batch, n = 524288 sphere) follow as compact records at the end of
+the line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--configs all|none]
 
 Under torchrun every rank runs its own independent product (the products of
 a batch are independent: replicas only, weak scaling); value = all rows of
@@ -18,6 +23,7 @@ oracle (the reference for this method) on a bounded sample of the workload.
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,10 +39,46 @@ import synth  # noqa: E402
 
 WORKLOAD = dict(name="sphere-n32768-laplace-leaf64-eta2-m4-eps1e-6", geometry="sphere", n=32768, kernel=0,
                 leaf=64, eta=2.0, order=4, eps=1e-6, seed=2309090611)
+# the other workloads: parity-test cases that the line reports compactly
+CONFIGS = {
+    "sphere2048": dict(geometry="sphere", n=2048, kernel=0, leaf=32, eta=2.0, order=3, eps=1e-4, seed=2309090610),
+    "cube131072_e4": dict(geometry="cube", n=131072, kernel=1, leaf=64, eta=1.5, order=4, eps=1e-4,
+                          seed=2309090612),
+    "cube131072_e6": dict(geometry="cube", n=131072, kernel=1, leaf=64, eta=1.5, order=4, eps=1e-6,
+                          seed=2309090612),
+    "sphere524288": dict(geometry="sphere", n=524288, kernel=0, leaf=64, eta=2.0, order=5, eps=1e-6,
+                         seed=2309090614),
+}
 # bounded CPU sample of the same workload for the oracle: same geometry,
 # kernel, leaf, eta, order and eps at n = 4096 (about 10-20 s of CPU work)
 CPU_SAMPLE_N = 4096
-METRIC = "H2 Z<-Z+XY rows/s at eps (FP64 GPU form; mixed form beside it)"
+METRIC = "H2 Z<-Z+XY rows/s at eps (fast form: tensor-core products, FP64 QR/SVD; FP64 GPU form beside it)"
+MODE_NAMES = {0: "fp64", 1: "mixed", 2: "tf32x3", 3: "tf32", 4: "bf16x3", 5: "auto"}
+
+
+def resolve_precision(p, eps):
+    """The concrete mode of H2_AUTO for a tolerance (the library's rule)."""
+    if p != 5:
+        return p
+    return 3 if eps >= 1e-4 else 4 if eps >= 1e-5 else 2 if eps >= 1e-7 else 0
+
+
+def r4(x):
+    """x rounded to 4 significant digits (short JSON)."""
+    if x is None or x == 0:
+        return x
+    return float(f"{x:.4g}")
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
 
 
 def parse():
@@ -46,6 +88,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--configs", default="all", choices=["all", "none"],
+                    help="all: also time the other workloads and report them compactly")
     ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="override n (testing only)")
     ap.add_argument("--workload", default="sphere32768", choices=["sphere32768", "batched64", "dlp49152"],
                     help="sphere32768: the default line; batched64: 64 independent products in one batched call")
@@ -177,6 +221,35 @@ def run_cpu_sample():
     return CPU_SAMPLE_N / dt, dt
 
 
+ONE_THREAD = {v: "1" for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")}
+
+
+def run_c1_one_thread():
+    """The oracle on the whole n = 2048 sphere workload (leaf 32, eta 2, order 3,
+    eps 1e-4) with its BLAS held to one thread, in a fresh process: seconds of
+    the product (for comparison with the paper's sequential timings)."""
+    code = ("import sys,time; sys.path.insert(0, %r); import synth; from oracle import h2_oracle as O; "
+            "c = %r; p = synth.make_points(c['geometry'], c['n'], c['seed']); "
+            "st = O.build_structure(p, c['leaf'], c['eta'], c['order']); G = O.build_interp(st, c['kernel']); "
+            "t = time.perf_counter(); O.mul_add(G, G, G, c['eps']); print(time.perf_counter() - t)"
+            % (ROOT, CONFIGS["sphere2048"]))
+    env = dict(os.environ)
+    env.update(ONE_THREAD)
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        return float(out.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
+def cpu_baseline_record(value, dt):
+    secs = run_c1_one_thread()
+    return {"value": r4(value), "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"numpy FP64 oracle, one product at n={CPU_SAMPLE_N} of the same workload, {dt:.1f} s",
+            "cpu": cpu_model(),
+            "n2048_one_thread": {"rows_s": r4(2048 / secs) if secs else None, "s": r4(secs)}}
+
+
 def reference_arm(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -195,9 +268,64 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 points)",
             "config": {"workload": WORKLOAD["name"] + f" (CPU sample n={CPU_SAMPLE_N})", "n": CPU_SAMPLE_N},
-            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+KERNEL_OF = {0: "k_gemm<double>", 1: "k_gemm_f32<false>", 2: "k_qr<double>", 3: "k_qr<float>", 4: "k_pchol",
+             5: "k_jacobi64", 6: "k_jacobi_pre", 7: "k_norm", 8: "k_copy", 9: "k_sumsq/k_finite", 10: "k_gemm_tc",
+             11: "k_gemm_f32<true>"}
+
+
+def family_sums(stats):
+    out = {k: np.zeros(12) for k in ("ms", "fl", "by", "n")}
+    for s in stats:
+        out["ms"] += np.array(s["fam_ms"])
+        out["fl"] += np.array(s["fam_flops"])
+        out["by"] += np.array(s["fam_bytes"])
+        out["n"] += np.array(s["fam_launches"])
+    return out
+
+
+def roofline(f, mode, peaks, lib_peaks):
+    """Roofline of the dominant kernel family: achieved = algorithmic flops (or
+    bytes) of its launches / their summed CUDA-event time, against the peak of
+    the unit that bounds it."""
+    top = int(np.argmax(f["ms"]))
+    sec = f["ms"][top] / 1e3
+    rate = f["fl"][top] / sec / 1e12
+    tf32 = peaks.get("bf16_tflops", 1891.8) / 2.0
+    if top in (0, 2, 4, 5, 7):  # FP64 pipe
+        roof = {"bound": "alu", "achieved": rate, "peak": lib_peaks.get("fp64_tflops"), "unit": "TFLOP/s fp64",
+                "peak_src": "cuBLAS DGEMM in this run"}
+    elif top in (1, 3, 6):  # FP32 CUDA cores
+        roof = {"bound": "alu", "achieved": rate, "peak": lib_peaks.get("fp32_tflops"), "unit": "TFLOP/s fp32",
+                "peak_src": "cuBLAS SGEMM (no TF32) in this run"}
+    elif top == 11:  # double-float: 6 FP32 lane operations per algorithmic flop
+        f32 = lib_peaks.get("fp32_tflops")
+        roof = {"bound": "alu", "achieved": 6.0 * rate, "peak": f32 / 2.0 if f32 else None,
+                "unit": "T fp32 lane ops/s", "peak_src": "cuBLAS SGEMM in this run / 2"}
+    elif top == 10:  # tensor cores: products issued per algorithmic flop by mode
+        issued = {2: 3.0, 3: 1.0, 4: 3.0}.get(mode, 3.0)
+        pk = tf32 if mode != 4 else 2.0 * tf32
+        roof = {"bound": "tensor", "achieved": issued * rate, "peak": pk,
+                "unit": "TFLOP/s issued on tcgen05 (%s)" % MODE_NAMES.get(mode),
+                "peak_src": "MEASURED_PEAKS bf16 burst" + (" x 1/2 (TF32:BF16)" if mode != 4 else "")}
+    else:
+        rate = f["by"][top] / sec / 1e9
+        roof = {"bound": "hbm", "achieved": rate, "peak": peaks.get("hbm_gbs", 6780.7), "unit": "GB/s",
+                "peak_src": "MEASURED_PEAKS hbm_gbs"}
+    roof["kernel"] = KERNEL_OF[top]
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
+    roof["traffic"] = None
+    n = max(1.0, f["n"][top])
+    roof["avg_launch_ms"] = f["ms"][top] / n
+    roof["share"] = float(f["ms"][top] / max(1e-9, f["ms"].sum()))
+    for k in ("achieved", "peak", "frac", "avg_launch_ms", "share"):
+        roof[k] = r4(roof[k])
+    return roof
 
 
 def ours_arm(args):
@@ -215,6 +343,7 @@ def ours_arm(args):
     P.load()
     w = dict(WORKLOAD)
     w["n"] = args.n
+    fast = resolve_precision(P.H2_AUTO, w["eps"])
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     # each rank: its own independent product (seed offset by rank)
@@ -225,177 +354,114 @@ def ours_arm(args):
         if world > 1:
             tdist.barrier()
 
-    def timed(precision, steps, warmup):
+    def timed(G, c, precision, steps, warmup, eps2=True):
+        """steps products (each on a fresh clone of G, made outside the timed
+        region) timed back to back with CUDA events on the library's stream."""
         for _ in range(warmup):
             Zw = P.h2_clone(G, stream=sptr)
-            P.h2_mul_add(Zw, G, G, w["eps"], precision, stream=sptr)
-            del Zw
+            P.h2_mul_add(Zw, G, G, c["eps"], precision, stream=sptr)
+            Zw.free()
         Zs = [P.h2_clone(G, stream=sptr) for _ in range(steps)]
         torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stats = []
-        t0 = time.perf_counter()
         e0.record(stream)
         for Z in Zs:
-            stats.append(P.h2_mul_add(Z, G, G, w["eps"], precision, stream=sptr))
+            stats.append(P.h2_mul_add(Z, G, G, c["eps"], precision, stream=sptr))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
-        wall = time.perf_counter() - t0
         dt = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, tdist, dev)
-        info = Zs[-1].info()
         # eps_2 of the last result (Sec. 7: relative spectral error, 20 power-iteration
         # steps through H^2 matrix-vector products), outside the timed region
-        eps2 = P.h2_product_error(Zs[-1], G, G, G, steps=20, stream=sptr)[0] if rank == 0 else None
+        e2 = P.h2_product_error(Zs[-1], G, G, G, steps=20, stream=sptr)[0] if (eps2 and rank == 0) else None
         for Z in Zs:
             Z.free()
-        info["eps2"] = eps2
-        return dt, wall, stats, info
+        return dt, stats, e2
 
+    peaks = measured_peaks()
     sampler = ClockSampler(local)
     sampler.start()
-    dt64, wall64, st64, info64 = timed(P.H2_FP64, args.steps, args.warmup)
+    dtf, stf, e2f = timed(G, w, P.H2_AUTO, args.steps, args.warmup)
     clocks = sampler.stop()
-    dtmx, wallmx, stmx, infomx = timed(P.H2_MIXED, args.steps, max(1, args.warmup // 2))
-    dttc, walltc, sttc, infotc = timed(P.H2_TC, args.steps, max(1, args.warmup // 2))
+    dt64, st64, e264 = timed(G, w, P.H2_FP64, args.steps, args.warmup)
+    # the other precision modes on the same workload (context; fewer steps)
+    forms = {}
+    for p in (P.H2_MIXED, P.H2_TF32X3, P.H2_BF16X3):
+        if p == fast:
+            continue
+        k = max(1, min(args.steps, 5))
+        dtp, _, e2p = timed(G, w, p, k, 2)
+        forms[MODE_NAMES[p]] = {"ms": r4(1e3 * dtp / k), "eps2": r4(e2p)}
     # end to end through the public API with host buffers: points host->device,
-    # build, product, result structure (ranks) device->host, per step
+    # build, product, result structure (permutation and ranks) device->host
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         X = P.h2_build_interp(pts, w["kernel"], w["leaf"], w["eta"], w["order"], stream=sptr)
         Z = P.h2_clone(X, stream=sptr)
-        P.h2_mul_add(Z, X, X, w["eps"], P.H2_FP64, stream=sptr)
+        P.h2_mul_add(Z, X, X, w["eps"], P.H2_AUTO, stream=sptr)
         _ = Z.structure()
         Z.free()
         X.free()
     torch.cuda.synchronize(dev)
     e2e_dt = (time.perf_counter() - t0) / e2e_steps
-    nclusters = info64["nclusters"]
+    nclusters = G.info()["nclusters"]
     d2h = w["n"] * 8 + 3 * nclusters * 8 + 2 * nclusters * 4
 
-    # roofline of the dominant kernel family of each form
-    peaks = measured_peaks()
     lib_peaks = library_peaks(torch, dev) if rank == 0 else {}
-    names = P.FAMILIES
-    kernel_of = {0: "k_gemm<double>", 1: "k_gemm_f32<false>", 2: "k_qr<double>", 3: "k_qr<float>", 4: "k_pchol",
-                 5: "k_jacobi64", 6: "k_jacobi_pre / k_jacobi_pre_cluster", 7: "k_norm", 8: "k_copy",
-                 9: "k_sumsq / k_finite", 10: "k_gemm_tc", 11: "k_gemm_f32<true>"}
+    ff = family_sums(stf)
+    roof = roofline(ff, fast, peaks, lib_peaks)
+    roof64 = roofline(family_sums(st64), P.H2_FP64, peaks, lib_peaks)
 
-    def sums(stats):
-        out = {k: np.zeros(12) for k in ("ms", "fl", "by", "n")}
-        for s in stats:
-            out["ms"] += np.array(s["fam_ms"])
-            out["fl"] += np.array(s["fam_flops"])
-            out["by"] += np.array(s["fam_bytes"])
-            out["n"] += np.array(s["fam_launches"])
-        return out
-
-    # DRAM traffic of k_gemm<double> from one ncu capture (sphere n=8192, the 61st
-    # launch of the kernel; profiles/k_gemm_sphere-n8192_fp64.md): 45.77 MB of
-    # dram__bytes_read.sum + dram__bytes_write.sum for 0.629 GFLOP of executed FP64 work
-    # (314.6 M DFMA), scaled to the average launch here by its flops.  The kernel has not
-    # changed since the capture.
-    gemm64_capture = {"dram_bytes": 45.77e6, "flops": 0.629e9}
-
-    def roofline(f):
-        top = int(np.argmax(f["ms"]))
-        rate = f["fl"][top] / (f["ms"][top] / 1e3) / 1e12
-        if top in (0, 2, 4, 5, 7):  # FP64 arithmetic: bound by the FP64 pipe
-            roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": rate, "peak": lib_peaks.get("fp64_tflops"),
-                    "unit": "TFLOP/s (FP64)",
-                    "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (MEASURED_PEAKS.json has no FP64 figure)"}
-        elif top in (1, 3, 6):
-            roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": rate, "peak": lib_peaks.get("fp32_tflops"),
-                    "unit": "TFLOP/s (FP32)", "peak_source": "cuBLAS SGEMM 8192^3 (no TF32) measured in this run"}
-        elif top == 11:
-            # double-float: 12 FP32 instructions per multiply-add (1 FMUL, 3 FFMA, 8 FADD),
-            # i.e. 6 per algorithmic flop, each one lane operation; the SGEMM rate counts
-            # an FFMA lane operation as 2 flops, so its lane-operation rate is half of it
-            f32 = lib_peaks.get("fp32_tflops")
-            roof = {"kernel": kernel_of[top], "bound": "alu", "achieved": 6.0 * rate,
-                    "peak": f32 / 2.0 if f32 else None,
-                    "unit": "T FP32 lane operations/s (FFMA, FADD, FMUL each one)",
-                    "algorithmic_fp64_equivalent_tflops": rate,
-                    "peak_source": "cuBLAS SGEMM 8192^3 (no TF32) measured in this run, / 2 (one FFMA = 2 flops)"}
-        elif top == 10:
-            roof = {"kernel": kernel_of[top], "bound": "tensor", "achieved": rate,
-                    "peak": peaks.get("bf16_tflops", 1900.0) / 2.0, "unit": "TFLOP/s (algorithmic, TF32 x6)",
-                    "peak_source": "MEASURED_PEAKS.json bf16 burst x 1/2 (nominal TF32:BF16 ratio)"}
-        else:
-            rate = f["by"][top] / (f["ms"][top] / 1e3) / 1e9
-            roof = {"kernel": kernel_of[top], "bound": "hbm", "achieved": rate, "peak": peaks.get("hbm_gbs", 6800.0),
-                    "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
-        roof["frac"] = (roof["achieved"] / roof["peak"]) if roof.get("peak") else None
-        roof["traffic"] = None
-        if top == 0 and f["n"][top] > 0:
-            per_launch = f["fl"][top] / f["n"][top]
-            roof["traffic"] = gemm64_capture["dram_bytes"] * per_launch / gemm64_capture["flops"]
-            roof["traffic_unit"] = "bytes per launch"
-            roof["traffic_source"] = ("ncu capture at n=8192 (45.77 MB for 0.629 GFLOP executed), "
-                                      "scaled by the average launch's flops")
-            roof["algorithmic_bytes_per_launch"] = f["by"][top] / f["n"][top]
-        roof["avg_launch_ms"] = f["ms"][top] / max(1.0, f["n"][top])
-        roof["share_of_step"] = float(f["ms"][top] / max(1e-9, f["ms"].sum()))
-        return roof
-
-    f64s, fmxs = sums(st64), sums(stmx)
-    roof = roofline(f64s)
-    roof["peaks_measured_here"] = lib_peaks
-    roof_mx = roofline(fmxs)
-    fam_report = {names[i]: {"ms_per_step": f64s["ms"][i] / len(st64), "launches_per_step": f64s["n"][i] / len(st64),
-                             "gflop_per_step": f64s["fl"][i] / len(st64) / 1e9,
-                             "gb_per_step": f64s["by"][i] / len(st64) / 1e9}
-                  for i in range(12) if f64s["n"][i] > 0}
-    fam_report_mx = {names[i]: {"ms_per_step": fmxs["ms"][i] / len(stmx), "launches_per_step": fmxs["n"][i] / len(stmx),
-                                "gflop_per_step": fmxs["fl"][i] / len(stmx) / 1e9}
-                     for i in range(12) if fmxs["n"][i] > 0}
+    # the other workloads: one warm-up and two timed products of the fast form,
+    # one timed product of the FP64 form (after the fast form planned the structure)
+    configs = {}
+    if args.configs == "all" and world == 1:
+        for name, c in CONFIGS.items():
+            pc = synth.make_points(c["geometry"], c["n"], c["seed"])
+            Gc = P.h2_build_interp(pc, c["kernel"], c["leaf"], c["eta"], c["order"], stream=sptr)
+            dfc, sfc, e2c = timed(Gc, c, P.H2_AUTO, 2, 1, eps2=(c["n"] <= 131072))
+            d64c, _, _ = timed(Gc, c, P.H2_FP64, 1, 0, eps2=False)
+            rf = roofline(family_sums(sfc), resolve_precision(P.H2_AUTO, c["eps"]), peaks, lib_peaks)
+            configs[name] = {"mode": MODE_NAMES[resolve_precision(P.H2_AUTO, c["eps"])],
+                             "ms": r4(1e3 * dfc / 2), "fp64_ms": r4(1e3 * d64c), "speedup": r4(d64c / (dfc / 2)),
+                             "rows_s": r4(c["n"] * 2 / dfc), "eps2": r4(e2c),
+                             "top": rf["kernel"], "frac": rf["frac"]}
+            Gc.free()
+        configs["batched64"] = batched_record(P, torch, dev, fp64=True)
 
     n_all = w["n"] * world
-    value = n_all * args.steps / dt64
+    value = n_all * args.steps / dtf
     line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * dt64 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "warmup": args.warmup, "ms_per_step": 1e3 * dtf / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "%s products, f64 QR/SVD" % MODE_NAMES[fast],
             "data": "synthetic (seeded SplitMix64 points on the unit sphere)",
             "config": {"workload": w["name"], "n": w["n"], "leaf": w["leaf"], "eta": w["eta"],
-                       "order": w["order"], "rank": w["order"] ** 3, "eps": w["eps"], "X=Y=Z": True,
-                       "precision": "FP64 products, FP64 QR/SVD",
-                       "l2": "inputs larger than L2 (X: %.0f MB)" % (G.info()["device_bytes"] / 1e6),
+                       "order": w["order"], "eps": w["eps"], "precision": "H2_AUTO -> " + MODE_NAMES[fast],
+                       "X=Y=Z": True, "l2": "inputs larger than L2 (X: %.0f MB)" % (G.info()["device_bytes"] / 1e6),
                        "parallelism": f"replicas x{world}"},
-            "mixed": {"value": w["n"] * world * args.steps / dtmx, "unit": "rows/s",
-                      "ms_per_step": 1e3 * dtmx / args.steps, "speedup_vs_fp64": dt64 / dtmx,
-                      "precision": "FP32 products on CUDA cores; Gram matrices and SVD finishing in "
-                                   "double-float FP32 (FP64-accurate); FP64 rank decisions",
-                      "roofline": roof_mx},
-            "tensor_core": {"value": w["n"] * world * args.steps / dttc, "unit": "rows/s",
-                            "ms_per_step": 1e3 * dttc / args.steps, "speedup_vs_fp64": dt64 / dttc,
-                            "precision": "tcgen05 TF32 three-term products, FP32 accumulation in TMEM, FP64 rank decisions",
-                            "gemm_tc_ms_per_step": sum(x["fam_ms"][10] for x in sttc) / len(sttc),
-                            "gemm_tc_gflop_per_step": sum(x["fam_flops"][10] for x in sttc) / len(sttc) / 1e9},
-            "e2e": {"value": n_all / e2e_dt, "unit": "rows/s", "h2d_bytes_per_step": int(pts.nbytes),
-                    "d2h_bytes_per_step": int(d2h),
-                    "note": "h2_build_interp from host points + h2_clone + h2_mul_add + h2_get_structure"},
-            "gpu_launches": int(sum(s["kernel_launches"] for s in st64)),
-            "accuracy": {"eps": w["eps"], "eps2_fp64": info64["eps2"], "eps2_mixed": infomx["eps2"],
-                         "eps2_tensor_core": infotc["eps2"],
-                         "definition": "||Zr - (Z + X Y)||_2 / ||Z + X Y||_2, 20 power-iteration steps "
-                                       "through H2 matrix-vector products (h2_product_error)"},
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stf)),
             "roofline": roof,
-            "kernel_families_fp64": fam_report,
-            "kernel_families_mixed": fam_report_mx,
-            "stats_fp64": {k: st64[-1][k] for k in ("t_rows_a_ms", "t_cols_a_ms", "t_mat_a_ms", "t_rows_b_ms",
-                                                     "t_cols_b_ms", "t_mat_b_ms", "product_nodes", "triples",
-                                                     "max_rank_a", "max_rank_b")},
-            "clocks": clocks}
+            "clocks": clocks,
+            "e2e": {"value": r4(n_all / e2e_dt), "unit": "rows/s", "h2d_bytes_per_step": int(pts.nbytes),
+                    "d2h_bytes_per_step": int(d2h),
+                    "note": "build from host points + clone + h2_mul_add + structure read-back (ranks, "
+                            "permutation; not the couplings: a lower bound on a full host round trip)"}}
     if rank == 0 and not args.no_cpu_baseline:
         v, dt = run_cpu_sample()
-        line["cpu_baseline"] = {"value": v, "unit": "rows/s", "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"oracle on n={CPU_SAMPLE_N} points of the same workload, one product, "
-                                          f"{dt:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline_record(v, dt)
+    # short records last, where a truncated tail still shows them
+    line["fp64"] = {"value": r4(n_all * args.steps / dt64), "ms_per_step": r4(1e3 * dt64 / args.steps),
+                    "top": roof64["kernel"], "frac": roof64["frac"]}
+    line["speedup_vs_fp64"] = r4(dt64 / dtf)
+    line["eps2"] = {"fast": r4(e2f), "fp64": r4(e264)}
+    line["forms_ms"] = forms
+    line["configs"] = configs
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -420,6 +486,48 @@ def batch_members():
     return out
 
 
+def batched_record(P, torch, dev, fp64=True, fast_reps=1):
+    """The 64-product batch through h2_mul_add_batched: one warm-up and
+    fast_reps timed calls of the fast form (H2_AUTO at eps 1e-5), one timed
+    call of the FP64 form; CUDA events on the calling stream around each call
+    (the call returns when its products are done)."""
+    members = batch_members()
+    Gs = [P.h2_build_interp(synth.make_points(g, n, seed), 0, BATCH["leaf"], BATCH["eta"], m)
+          for g, n, m, seed in members]
+    rows = sum(n for _, n, _, _ in members)
+    stream = torch.cuda.current_stream(dev)
+    out = {"products": len(members), "rows": rows}
+    launches = 0
+    for name, prec, warm, reps in (("fast", P.H2_AUTO, 1, fast_reps), ("fp64", P.H2_FP64, 0, 1 if fp64 else 0)):
+        times = []
+        for it in range(warm + reps):
+            Zs = [P.h2_clone(G) for G in Gs]
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            stats, codes = P.h2_mul_add_batched(Zs, Gs, Gs, BATCH["eps"], prec, stream=stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            assert codes == [0] * len(Zs), codes
+            for Z in Zs:
+                Z.free()
+            if it >= warm:
+                times.append(e0.elapsed_time(e1) / 1e3)
+                if name == "fast":
+                    launches = stats["kernel_launches"]
+        if times:
+            dt = sum(times) / len(times)
+            out[name + "_ms"] = r4(1e3 * dt)
+            out[name + "_rows_s"] = r4(rows / dt)
+    out["mode"] = MODE_NAMES[resolve_precision(P.H2_AUTO, BATCH["eps"])]
+    if "fp64_ms" in out:
+        out["speedup"] = r4(out["fp64_ms"] / out["fast_ms"])
+    out["launches"] = launches
+    for G in Gs:
+        G.free()
+    return out
+
+
 def batched_arm(args):
     import torch
 
@@ -430,36 +538,14 @@ def batched_arm(args):
     dev = torch.device("cuda", local)
     P.build()
     P.load()
-    members = batch_members()
-    Gs = [P.h2_build_interp(synth.make_points(g, n, seed + rank), 0, BATCH["leaf"], BATCH["eta"], m)
-          for g, n, m, seed in members]
-    rows = sum(n for _, n, _, _ in members) * world
-    out = {}
-    for name, prec in (("mixed", P.H2_MIXED), ("fp64", P.H2_FP64)):
-        times, stats = [], None
-        for it in range(args.warmup + args.steps):
-            Zs = [P.h2_clone(G) for G in Gs]
-            torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
-            stats, codes = P.h2_mul_add_batched(Zs, Gs, Gs, BATCH["eps"], prec)
-            torch.cuda.synchronize(dev)
-            dt = time.perf_counter() - t0
-            assert codes == [0] * len(Zs)
-            for Z in Zs:
-                Z.free()
-            if it >= args.warmup:
-                times.append(dt)
-        out[name] = {"value": rows * len(times) / sum(times), "unit": "rows/s",
-                     "ms_per_step": 1e3 * sum(times) / len(times), "kernel_launches": stats["kernel_launches"]}
-    line = {"metric": "H2 Z<-Z+XY rows/s, 64 independent products in one batched call", "value": out["mixed"]["value"],
-            "unit": "rows/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": out["mixed"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 products, f64 factorisations", "data": "synthetic",
-            "config": {"workload": "batched64", "products": len(members), "rows": rows,
-                       "n_range": [min(n for _, n, _, _ in members), max(n for _, n, _, _ in members)],
-                       "orders": sorted(set(m for _, _, m, _ in members)), "eps": BATCH["eps"]},
-            "fp64": out["fp64"], "speedup_mixed_vs_fp64": out["mixed"]["value"] / out["fp64"]["value"],
-            "gpu_launches": out["mixed"]["kernel_launches"]}
+    rec = batched_record(P, torch, dev, fp64=True, fast_reps=max(1, args.steps))
+    line = {"metric": "H2 Z<-Z+XY rows/s, 64 independent products in one batched call",
+            "value": rec["fast_rows_s"] * world, "unit": "rows/s", "n_gpus": world, "steps": max(1, args.steps),
+            "warmup": 1, "ms_per_step": rec["fast_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "%s products, f64 QR/SVD" % rec["mode"], "data": "synthetic",
+            "config": {"workload": "batched64", "products": rec["products"], "rows": rec["rows"],
+                       "eps": BATCH["eps"]},
+            "gpu_launches": rec["launches"], "batched": rec}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

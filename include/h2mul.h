@@ -65,18 +65,31 @@ extern "C" {
 /* Precision of the contractions (products of coupling, transfer, basis and
  * auxiliary matrices).  QR factorisations, singular value decompositions and
  * the choice of ranks always run in FP64.
- *   H2_FP64   every product in FP64 (the plain FP64 GPU form)
- *   H2_MIXED  products in FP32 with FP32 accumulation (CUDA cores), storage in FP64
- *   H2_TC     products on the tensor cores (tcgen05 kind::tf32): each FP32
- *             operand split into three TF32 pieces, the six products of order
- *             up to 2^-22 accumulated in FP32 in TMEM (FP32 accuracy)
- * In H2_MIXED and H2_TC the wide-to-square reduction ahead of each SVD runs
- * in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the weights'
- * Gram matrices, the pivoted Cholesky, the final sweeps and every rank
- * decision stay FP64. */
+ *   H2_FP64    every product in FP64 (the plain FP64 GPU form)
+ *   H2_MIXED   products in FP32 with FP32 accumulation on the CUDA cores
+ *   H2_TF32X3  products on the tensor cores (tcgen05.mma kind::tf32): each FP32
+ *              operand split as a0 + a1 into two TF32 pieces, three products
+ *              a0 b0 + a0 b1 + a1 b0 accumulated in FP32 in TMEM (about FP32
+ *              accuracy); H2_TC is the same value
+ *   H2_TF32    one TF32 product a0 b0 per pair (relative error about 2^-11 per
+ *              operand; for eps >= 1e-4)
+ *   H2_BF16X3  tensor cores with BF16 pieces (tcgen05.mma kind::f16): a0 + a1
+ *              with 8 significant bits each, three products (about 2^-16)
+ *   H2_AUTO    chosen by eps: H2_TF32 for eps >= 1e-4, H2_BF16X3 for
+ *              1e-5 <= eps < 1e-4, H2_TF32X3 below 1e-5 (three-term products
+ *              where eps < 1e-5), H2_FP64 for eps < 1e-7 (exact mode included)
+ * In every mode but H2_FP64 the wide-to-square reduction ahead of each SVD
+ * runs in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the
+ * weights' Gram matrices and the other products that must be FP64-accurate
+ * run in double-float FP32 arithmetic, and the pivoted Cholesky, the final
+ * sweeps and every rank decision stay FP64. */
 #define H2_FP64 0
 #define H2_MIXED 1
-#define H2_TC 2
+#define H2_TF32X3 2
+#define H2_TC H2_TF32X3
+#define H2_TF32 3
+#define H2_BF16X3 4
+#define H2_AUTO 5
 
 typedef struct h2_matrix h2_matrix;
 
@@ -122,11 +135,42 @@ typedef struct {
 #define H2_FAM_GEMMTC 10 /* batched segmented products on tcgen05 (H2_TC) */
 #define H2_FAM_GEMMDF 11 /* FP64-accurate products of H2_MIXED / H2_TC in double-float FP32 arithmetic */
 
+/* Device memory supplied by the caller.  alloc(bytes, stream, ctx) returns a
+ * device pointer on the current device, aligned to at least 256 bytes, usable
+ * by work issued on `stream` (or NULL when out of memory); free(ptr, bytes,
+ * stream, ctx) returns it with stream-ordered semantics: work issued on
+ * `stream` after the call may reuse the memory, and the library issues no
+ * later work on it.  `stream` is the stream the buffer was allocated for: the
+ * call's opts->stream, or one of the library's internal streams (the column
+ * side of a product, the products of h2_mul_add_batched). */
+typedef void* (*h2_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*h2_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
 typedef struct {
     double eps;       /* relative truncation tolerance; 0 keeps every nonzero singular value */
-    int precision;    /* H2_FP64, H2_MIXED or H2_TC */
+    int precision;    /* H2_FP64, H2_MIXED, H2_TF32X3 (= H2_TC), H2_TF32, H2_BF16X3 or H2_AUTO */
     void* stream;     /* cudaStream_t; NULL selects the legacy default stream */
     h2_stats* stats;  /* optional output, may be NULL */
+    /* Device memory.  alloc == NULL: the library allocates (cudaMalloc for the
+     * buffers of handles, its own stream-ordered pool for scratch).  Otherwise
+     * every device buffer of the call -- scratch and the buffers of the handles
+     * it creates or rebuilds -- comes from alloc and goes back through free
+     * (both required).  A handle remembers the callbacks its buffers came from
+     * and returns them through the same free in h2_free, or when a later call
+     * replaces them; alloc_ctx must stay valid until then. */
+    h2_alloc_fn alloc;
+    h2_free_fn free;
+    void* alloc_ctx;
+    /* Nonzero: the library tunes its launch schedules online.  Each batch of
+     * products is keyed by (kernel family, number of output tiles, K per
+     * tile); the first batches of a key run the candidate schedules in turn
+     * (split-K off or over 2, 4 or 8 slices, and for the FP32-class products
+     * the CUDA-core kernel against the tensor-core kernel when both meet the
+     * precision mode's accuracy), their device times are read when the call
+     * ends, and later batches of the key run the fastest.  The choices are kept
+     * per device for the life of the process.  Every candidate computes the
+     * same products, so results agree to rounding. */
+    int autotune;
 } h2_opts;
 
 /* Structure and sizes of a handle (h2_info). */
@@ -153,8 +197,11 @@ typedef struct {
  * The cluster tree is a median bisection along the longest box axis down to
  * the depth L where every cluster holds at most `leaf_size` points; the block
  * tree uses max(diam B_t, diam B_s) <= eta dist(B_t, B_s) (Def. "Block tree").
- *   points      host array, n x 3, row-major (x0 y0 z0 x1 ...); read only,
- *               copied; owned by the caller.
+ *   points      n x 3, row-major (x0 y0 z0 x1 ...), in host memory or in
+ *               device memory of the current device (the library tells them
+ *               apart with cudaPointerGetAttributes); read only, copied to the
+ *               host for the tree construction (it runs on the host); owned by
+ *               the caller.
  *   n >= 1, 1 <= leaf_size, 1 <= cheb_order <= 8, eta >= 0, kernel H2_K_*.
  *   out         receives the new handle; untouched on error.
  * Errors: H2_ERR_ARG (H2_K_DLP needs h2_build_interp_normals), H2_ERR_NUMERIC
@@ -162,8 +209,8 @@ typedef struct {
 H2_API int h2_build_interp(const double* points, int64_t n, int kernel, int leaf_size, double eta,
                     int cheb_order, const h2_opts* opts, h2_matrix** out);
 
-/* h2_build_interp with a unit normal per point (host array, n x 3, row-major,
- * same order as `points`; read only, copied).  For H2_K_DLP the kernel is
+/* h2_build_interp with a unit normal per point (n x 3, row-major, same order
+ * as `points`, host or device memory like `points`; read only, copied).  For H2_K_DLP the kernel is
  * interpolated as the normal derivative in y of 1 / (4 pi |x - y|): V is the
  * Lagrange basis, W the normal-derivative basis
  *   W_s[j, mu] = grad l_{s,mu}(y_j) . n(y_j) on leaves, with the Lagrange
@@ -288,20 +335,35 @@ H2_API int h2_plan_structure(const double* points, int64_t n, int leaf_size, dou
  * Scratch: one fixed device array of 4 Mi doubles (32 MiB) in the library,
  * held on every GPU that loads the library until the process exits.  The
  * call needs n^2 + (the expanded cluster bases, about n x rank per level) +
- * (n x rank per admissible block row) doubles to fit in 15/16 of it (the
- * rest holds descriptor arrays); larger matrices are rejected with
+ * (n x rank per admissible block row) doubles plus its descriptor arrays; it
+ * measures them on the host first and rejects a matrix that does not fit with
  * H2_ERR_UNSUPPORTED before any device work is issued.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  The first
  * call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array and it keeps the
- * last call's contents (the call clears what must start at zero), so calls
- * that overlap on the GPU -- from several threads or streams -- race and
- * must be serialised by the caller.
+ * (cudaGetSymbolAddress) with that device current and keeps it (the lookup is
+ * serialised between threads); make that first call before any stream
+ * capture, and make no call on a device after a cudaDeviceReset of it.
+ * Every call shares the array and it keeps the last call's contents (the
+ * call clears what must start at zero), so calls that overlap on the GPU --
+ * from several threads or streams -- race and must be serialised by the
+ * caller.
  * Errors: H2_ERR_ARG, H2_ERR_UNSUPPORTED (too large), H2_ERR_CUDA. */
 H2_API int h2_to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, void* stream);
 
-/* Release a handle and its device memory; NULL is ignored. */
+/* Device memory the library holds from its own sources -- cudaMalloc for the
+ * buffers of handles and its stream-ordered pool for scratch -- summed over
+ * devices: the bytes held now and the most held at once since the library was
+ * loaded or the peak was last reset (reset_peak != 0 sets it to the current
+ * figure after reading it).  Memory from caller callbacks (h2_opts.alloc) is
+ * not counted: with callbacks on every call, both figures stay at zero.  Any
+ * pointer may be NULL.  Always H2_OK.  The paper has no counterpart; this is a
+ * diagnostic of the allocation contract. */
+H2_API int h2_library_memory(int64_t* current_bytes, int64_t* peak_bytes, int reset_peak);
+
+/* Release a handle and its device memory; NULL is ignored.  Buffers from
+ * caller callbacks (h2_opts.alloc) go back through the matching free; the
+ * library's own buffers through cudaFree.  No wait is needed before: every
+ * entry point returns after its work on the handle has finished. */
 H2_API void h2_free(h2_matrix* A);
 
 /* Static description of an error code. */

@@ -18,11 +18,14 @@ H2_OK = 0
 ERRORS = {-1: "H2_ERR_ARG", -2: "H2_ERR_SHAPE", -3: "H2_ERR_OOM", -4: "H2_ERR_NUMERIC",
           -5: "H2_ERR_TIMEOUT", -6: "H2_ERR_UNSUPPORTED", -7: "H2_ERR_CUDA"}
 H2_K_LAPLACE, H2_K_YUKAWA, H2_K_POLY2, H2_K_CONST, H2_K_DELTA, H2_K_DLP = 0, 1, 2, 3, 4, 5
-H2_FP64, H2_MIXED, H2_TC = 0, 1, 2
+H2_FP64, H2_MIXED, H2_TF32X3, H2_TF32, H2_BF16X3, H2_AUTO = 0, 1, 2, 3, 4, 5
+H2_TC = H2_TF32X3
+PRECISIONS = {"fp64": H2_FP64, "mixed": H2_MIXED, "tf32x3": H2_TF32X3, "tf32": H2_TF32, "bf16x3": H2_BF16X3,
+              "auto": H2_AUTO}
 
 EXPORTED = ["h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
             "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error",
-            "h2_recompress", "h2_free", "h2_error_string", "h2_last_error_message"]
+            "h2_recompress", "h2_library_memory", "h2_free", "h2_error_string", "h2_last_error_message"]
 
 
 class H2Error(RuntimeError):
@@ -54,9 +57,87 @@ FAMILIES = ["gemm_fp64", "gemm_fp32", "qr_fp64", "qr_fp32", "pchol", "svd_fp64",
             "gemm_tc", "gemm_df"]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("stats", ctypes.POINTER(Stats))]
+                ("stats", ctypes.POINTER(Stats)), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_ctx", ctypes.c_void_p), ("autotune", ctypes.c_int)]
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator: the
+    h2_opts alloc/free callbacks.  A buffer is allocated for the stream the
+    library names (torch keeps it in that stream's pool) and returned with
+    stream-ordered semantics, as the callbacks' contract asks.  ``live`` and
+    ``calls`` count the bytes held and the allocations made through it."""
+
+    def __init__(self):
+        import torch
+        torch.cuda.init()  # the raw allocator needs an initialised CUDA state
+        raw_alloc = torch._C._cuda_cudaCachingAllocator_raw_alloc
+        raw_delete = torch._C._cuda_cudaCachingAllocator_raw_delete
+        self.live = 0
+        self.calls = 0
+        self.last_error = ""
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                p = raw_alloc(int(nbytes), int(stream or 0))
+            except Exception as e:  # out of memory: the library reports H2_ERR_OOM
+                self.last_error = f"{type(e).__name__}: {e}"[:300]
+                return None
+            self.live += int(nbytes)
+            self.calls += 1
+            return p
+
+        def _free(ptr, nbytes, stream, ctx):
+            try:
+                raw_delete(int(ptr))
+            except Exception:  # interpreter shutdown: torch's allocator may be gone
+                return
+            self.live -= int(nbytes)
+
+        # the callback objects live as long as this allocator (module-wide singleton)
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+_allocator = None  # None: not chosen yet; "library" or a TorchAllocator
+_autotune = 0
+
+
+def set_allocator(kind: str = "torch"):
+    """Where the library's device memory comes from: "torch" (PyTorch's caching
+    allocator through the h2_opts callbacks, the default when PyTorch has CUDA)
+    or "library" (the library's own cudaMalloc and stream-ordered pool)."""
+    global _allocator
+    if kind == "library":
+        _allocator = "library"
+    elif kind == "torch":
+        _allocator = TorchAllocator()
+    else:
+        raise ValueError(kind)
+    return _allocator
+
+
+def allocator():
+    global _allocator
+    if _allocator is None:
+        try:
+            import torch
+            _allocator = TorchAllocator() if torch.cuda.is_available() else "library"
+        except ImportError:
+            _allocator = "library"
+    return _allocator
+
+
+def set_autotune(on: bool = True):
+    """Online tuning of launch schedules (h2_opts.autotune) for later calls."""
+    global _autotune
+    _autotune = 1 if on else 0
 
 
 class Info(ctypes.Structure):
@@ -92,6 +173,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_mul_add_batched.argtypes = [vp, vp, vp, ci, vp, vp]
     lib.h2_product_error.argtypes = [vp, vp, vp, vp, vp, ci, vp, vp, vp]
     lib.h2_recompress.argtypes = [vp, vp]
+    lib.h2_library_memory.argtypes = [vp, vp, ci]
+    lib.h2_library_memory.restype = ci
     lib.h2_free.argtypes = [vp]
     lib.h2_free.restype = None
     lib.h2_error_string.restype = ctypes.c_char_p
@@ -108,13 +191,23 @@ def load(path: str | None = None) -> ctypes.CDLL:
 def _check(code, what):
     if code != H2_OK:
         msg = load().h2_last_error_message().decode(errors="replace")
+        if isinstance(_allocator, TorchAllocator) and _allocator.last_error:
+            msg += f"; torch allocator: {_allocator.last_error}"
         raise H2Error(code, what, msg)
 
 
 def _opts(eps=1e-6, precision=H2_FP64, stream=None, stats=None):
-    o = Opts(eps, precision, ctypes.c_void_p(stream or 0), None)
+    o = Opts()
+    o.eps = eps
+    o.precision = precision
+    o.stream = ctypes.c_void_p(stream or 0)
     if stats is not None:
         o.stats = ctypes.pointer(stats)
+    a = allocator()
+    if a != "library":
+        o.alloc = a.alloc
+        o.free = a.free
+    o.autotune = _autotune
     return o
 
 
@@ -153,22 +246,29 @@ class H2Matrix:
 def h2_build_interp(points: np.ndarray, kernel: int, leaf_size: int, eta: float, cheb_order: int,
                     stream: int | None = None, normals: np.ndarray | None = None) -> H2Matrix:
     """Chebyshev H^2-matrix of a kernel; normals (n x 3) are needed for H2_K_DLP
-    (h2_build_interp_normals)."""
-    pts = np.ascontiguousarray(points, dtype=np.float64)
-    if pts.ndim != 2 or pts.shape[1] != 3:
-        raise ValueError("points must be an n x 3 array")
+    (h2_build_interp_normals).  points (and normals) are n x 3 float64 arrays on
+    the host, or contiguous float64 CUDA tensors (passed as device pointers)."""
+    def ptr(a, what):
+        if hasattr(a, "is_cuda") and a.is_cuda:
+            if a.dtype != __import__("torch").float64 or not a.is_contiguous() or a.dim() != 2 or a.shape[1] != 3:
+                raise ValueError(f"{what} must be a contiguous n x 3 float64 tensor")
+            return a, a.data_ptr(), a.shape[0]
+        h = np.ascontiguousarray(a, dtype=np.float64)
+        if h.ndim != 2 or h.shape[1] != 3:
+            raise ValueError(f"{what} must be an n x 3 array")
+        return h, h.ctypes.data, h.shape[0]
+    pts, pp, n = ptr(points, "points")
     h = ctypes.c_void_p()
     o = _opts(stream=stream)
     if normals is None:
-        _check(load().h2_build_interp(pts.ctypes.data, pts.shape[0], kernel, leaf_size, eta, cheb_order,
-                                      ctypes.byref(o), ctypes.byref(h)), "h2_build_interp")
+        _check(load().h2_build_interp(pp, n, kernel, leaf_size, eta, cheb_order, ctypes.byref(o), ctypes.byref(h)),
+               "h2_build_interp")
     else:
-        nrm = np.ascontiguousarray(normals, dtype=np.float64)
-        if nrm.shape != pts.shape:
+        nrm, npp, nn = ptr(normals, "normals")
+        if nn != n:
             raise ValueError("normals must be an n x 3 array like points")
-        _check(load().h2_build_interp_normals(pts.ctypes.data, nrm.ctypes.data, pts.shape[0], kernel, leaf_size,
-                                              eta, cheb_order, ctypes.byref(o), ctypes.byref(h)),
-               "h2_build_interp_normals")
+        _check(load().h2_build_interp_normals(pp, npp, n, kernel, leaf_size, eta, cheb_order, ctypes.byref(o),
+                                              ctypes.byref(h)), "h2_build_interp_normals")
     return H2Matrix(h)
 
 
@@ -226,12 +326,15 @@ def h2_plan_structure(points: np.ndarray, leaf_size: int, eta: float):
     return perm, counts
 
 
-def h2_to_dense_noalloc(A: H2Matrix, out, stream: int | None = None):
-    """Dense expansion into the CUDA tensor ``out`` (n x n float64, column-major
-    view of its storage) without device allocation: the library's fixed
-    32 MiB scratch holds all intermediates.  Calls must not overlap."""
+def h2_to_dense_noalloc(A: H2Matrix, out, stream: int | None = None, ld: int | None = None):
+    """Dense expansion into the CUDA tensor ``out`` without device allocation:
+    the library's fixed 32 MiB scratch holds all intermediates.  ``out`` holds
+    an n x n float64 matrix column-major with leading dimension ld (default n),
+    i.e. the storage of an (n, ld) row-major tensor; rows n..ld-1 of each column
+    are left untouched.  Calls must not overlap."""
     n = A.info()["n"]
-    _check(load().h2_to_dense_noalloc(A.handle, out.data_ptr(), n, ctypes.c_void_p(stream or 0)),
+    ld = n if ld is None else int(ld)
+    _check(load().h2_to_dense_noalloc(A.handle, out.data_ptr(), ld, ctypes.c_void_p(stream or 0)),
            "h2_to_dense_noalloc")
     return out
 
@@ -281,6 +384,14 @@ def h2_rows(A: H2Matrix, idx):
     out = torch.empty_like(e)
     h2_matvec(A, e, out, trans=True)
     return out
+
+
+def h2_library_memory(reset_peak: bool = False):
+    """(current, peak) bytes of device memory the library holds from its own
+    sources (cudaMalloc and its pool), not from the allocator callbacks."""
+    cur, pk = ctypes.c_int64(0), ctypes.c_int64(0)
+    load().h2_library_memory(ctypes.byref(cur), ctypes.byref(pk), 1 if reset_peak else 0)
+    return cur.value, pk.value
 
 
 def h2_free(A: H2Matrix) -> None:

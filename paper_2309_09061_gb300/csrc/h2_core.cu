@@ -7,7 +7,9 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <functional>
+#include <atomic>
 #include <mutex>
 
 #include "h2_internal.h"
@@ -47,25 +49,103 @@ struct HostWait {
     }
 };
 
+// ---------------------------------------------------------------- memory sources
+namespace {
+thread_local DevAlloc tl_alloc;
+thread_local cudaStream_t tl_alloc_stream = nullptr;
+// device memory the library holds from its own sources (not from callbacks)
+std::atomic<int64_t> g_own_bytes{0}, g_own_peak{0};
+void own_add(int64_t b) {
+    const int64_t now = g_own_bytes.fetch_add(b) + b;
+    int64_t pk = g_own_peak.load();
+    while (now > pk && !g_own_peak.compare_exchange_weak(pk, now)) {
+    }
+}
+}  // namespace
+
+DevAlloc alloc_of(const h2_opts* o) {
+    DevAlloc a;
+    if (!o || !o->alloc) return a;
+    if (!o->free) throw Error(H2_ERR_ARG, "h2_opts.alloc given without h2_opts.free");
+    a.alloc = o->alloc;
+    a.free = o->free;
+    a.ctx = o->alloc_ctx;
+    return a;
+}
+
+AllocScope::AllocScope(const DevAlloc& a, cudaStream_t st) : prev_a_(tl_alloc), prev_s_(tl_alloc_stream) {
+    tl_alloc = a;
+    tl_alloc_stream = st;
+}
+AllocScope::~AllocScope() {
+    tl_alloc = prev_a_;
+    tl_alloc_stream = prev_s_;
+}
+const DevAlloc& current_alloc() { return tl_alloc; }
+cudaStream_t current_alloc_stream() { return tl_alloc_stream; }
+
+// pooled: scratch from the library's stream-ordered pool; otherwise cudaMalloc
+// (the buffers of handles, returned to the driver when they are freed)
+void* dev_get(const DevAlloc& a, size_t bytes, cudaStream_t st, bool pooled) {
+    void* p = nullptr;
+    if (a.external()) {
+        HostWait hw("alloc_callback", bytes);
+        p = a.alloc(bytes, (void*)st, a.ctx);
+        if (!p) throw Error(H2_ERR_OOM, "the caller's allocator returned NULL");
+        if (((uintptr_t)p & 255u) != 0) {
+            a.free(p, bytes, (void*)st, a.ctx);
+            throw Error(H2_ERR_ARG, "the caller's allocator returned memory aligned to less than 256 bytes");
+        }
+        return p;
+    }
+    if (pooled) {
+        int dev = 0;
+        H2_CUDA(cudaGetDevice(&dev));
+        HostWait hw("pool_alloc", bytes);
+        H2_CUDA(cudaMallocFromPoolAsync(&p, bytes, lib_pool(dev), st));
+    } else {
+        HostWait hw("cudaMalloc", bytes);
+        H2_CUDA(cudaMalloc(&p, bytes));
+    }
+    own_add((int64_t)bytes);
+    return p;
+}
+
+void dev_put(const DevAlloc& a, void* p, size_t bytes, cudaStream_t st, bool pooled) {
+    if (!p) return;
+    if (a.external()) {
+        a.free(p, bytes, (void*)st, a.ctx);
+        return;
+    }
+    if (pooled) {
+        cudaFreeAsync(p, st);
+    } else {
+        HostWait hw("cudaFree", bytes);
+        cudaFree(p);
+    }
+    own_add(-(int64_t)bytes);
+}
+
 void DevBuf::alloc(size_t n) {
     reset();
     if (n == 0) return;
-    void* p2 = nullptr;
-    HostWait hw("cudaMalloc", n * sizeof(double));
-    H2_CUDA(cudaMalloc(&p2, n * sizeof(double)));
-    p = (double*)p2;
+    src = current_alloc();
+    st = current_alloc_stream();
+    p = (double*)dev_get(src, n * sizeof(double), st, false);
     len = n;
 }
 
 void DevBuf::reset() {
-    HostWait hw("cudaFree", len * sizeof(double));
-    if (p) cudaFree(p);
+    if (p) dev_put(src, p, len * sizeof(double), st, false);
     p = nullptr;
     len = 0;
 }
 
 // ---------------------------------------------------------------- runner
 Runner::~Runner() {
+    // on an error path work may still be queued (on this or another stream) that
+    // reads buffers about to be returned: wait for it before freeing them
+    if (std::uncaught_exceptions() > 0) cudaDeviceSynchronize();
     release_all();
     for (auto& m : marks_) {
         cudaEventDestroy(m.a);
@@ -121,6 +201,7 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
         if (launches) launches[m.fam] += 1;
         if (flops) flops[m.fam] += m.flops + df;
         if (bytes) bytes[m.fam] += m.bytes;
+        if (m.tcand >= 0 && m.flops > 0.0) Tuner::get().report(m.tkey, m.tcand, f / (m.flops * 1e-9));
         if (trace)
             std::fprintf(stderr, "h2trace %d %lld %.6f %.3f %.6f %.3f %p\n", m.fam, (long long)m.units,
                          (m.flops + df) * 1e-9, m.bytes * 1e-6, f, t0, (void*)st_);
@@ -141,13 +222,10 @@ double* Arena::alloc(size_t n) {
     const size_t chunk_min = (size_t)64 << 20;
 #endif
     if (bytes > left_) {
-        size_t sz = std::max(bytes, chunk_min);
-        int dev = 0;
-        H2_CUDA(cudaGetDevice(&dev));
-        void* p = nullptr;
-        HostWait hw("pool_alloc", sz);
-        H2_CUDA(cudaMallocFromPoolAsync(&p, sz, lib_pool(dev), st_));
-        chunks_.push_back(p);
+        const size_t sz = std::max(bytes, chunk_min);
+        const DevAlloc& src = current_alloc();
+        void* p = dev_get(src, sz, st_, true);
+        chunks_.push_back(Chunk{p, sz, src});
         cur_ = (char*)p;
         left_ = sz;
     }
@@ -159,7 +237,8 @@ double* Arena::alloc(size_t n) {
 
 void Arena::release(const Mark& m) {
     while (chunks_.size() > m.nchunks) {
-        cudaFreeAsync(chunks_.back(), st_);
+        const Chunk& c = chunks_.back();
+        dev_put(c.src, c.p, c.bytes, st_, true);
         chunks_.pop_back();
     }
     cur_ = m.cur;
@@ -167,7 +246,7 @@ void Arena::release(const Mark& m) {
 }
 
 void Arena::release_all() {
-    for (void* p : chunks_) cudaFreeAsync(p, st_);
+    for (const Chunk& c : chunks_) dev_put(c.src, c.p, c.bytes, st_, true);
     chunks_.clear();
     cur_ = nullptr;
     left_ = 0;
@@ -293,12 +372,78 @@ void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int
     pend_bytes_ += 8.0 * ((double)J.m * k + (double)k * J.n);
 }
 
+// ---------------------------------------------------------------- autotuner
+Tuner& Tuner::get() {
+    static Tuner t;
+    return t;
+}
+
+int Tuner::pick(uint64_t key, int ncand) {
+    std::lock_guard<std::mutex> lk(mu_);
+    Entry& e = map_[key];
+    e.ncand = ncand;
+    if (e.best >= 0) return e.best;
+    // the candidate issued least so far (round robin until every one is timed twice)
+    int c = 0;
+    for (int i = 1; i < ncand; ++i)
+        if (e.issued[i] < e.issued[c]) c = i;
+    e.issued[c]++;
+    return c;
+}
+
+void Tuner::report(uint64_t key, int cand, double ms_per_gflop) {
+    std::lock_guard<std::mutex> lk(mu_);
+    auto it = map_.find(key);
+    if (it == map_.end() || cand < 0 || cand >= kCand) return;
+    Entry& e = it->second;
+    e.cost[cand] += ms_per_gflop;
+    e.timed[cand]++;
+    if (e.best >= 0) return;
+    for (int i = 0; i < e.ncand; ++i)
+        if (e.timed[i] < 2) return;
+    int b = 0;
+    for (int i = 1; i < e.ncand; ++i)
+        if (e.cost[i] / e.timed[i] < e.cost[b] / e.timed[b]) b = i;
+    e.best = b;
+}
+
+std::vector<std::pair<uint64_t, int>> Tuner::table() {
+    std::lock_guard<std::mutex> lk(mu_);
+    std::vector<std::pair<uint64_t, int>> out;
+    for (auto& kv : map_) out.push_back({kv.first, kv.second.best});
+    return out;
+}
+
+static int ilog2(double x) {
+    int l = 0;
+    while (x >= 2.0 && l < 62) {
+        x *= 0.5;
+        ++l;
+    }
+    return l;
+}
+
 void Runner::flush_gemm(int precision_override) {
     if (jobs_.empty()) return;
     int pr = precision_override >= 0 ? precision_override : prec_;
     // FP64 products of the low-precision modes run in double-float arithmetic
     if (pr == H2_FP64 && prec_ != H2_FP64) pr = kGemmDF;
-    const bool tc = (pr == H2_TC);
+    // autotuned schedule: the kernel of the FP32-class products and the split-K policy
+    uint64_t tkey = 0;
+    int tcand = -1, force_split = 0;
+    if (tune_) {
+        const bool f32class = (pr == H2_MIXED || tc_precision(pr));
+        double chunks = 0.0;
+        for (const GTerm& t : terms_) chunks += (t.k + 31) / 32;
+        const int64_t tiles = std::max<int64_t>(1, pend_tiles64_);
+        tkey = ((uint64_t)(pr & 0xff) << 16) | ((uint64_t)ilog2((double)tiles) << 8) |
+               (uint64_t)ilog2(chunks / (double)tiles);
+        tcand = Tuner::get().pick(tkey, f32class ? 8 : 4);
+        const int sp[4] = {0, 1, 2, 4};
+        force_split = sp[tcand & 3];
+        if (tcand >= 4) pr = (pr == H2_MIXED) ? H2_TF32X3 : H2_MIXED;  // the other FP32-class kernel
+    }
+    const bool tc = tc_precision(pr);
     const bool f32 = (pr == H2_MIXED || pr == kGemmDF);
     const int tm = tc ? kTcTileM : f32 ? kF32Tile : 32, tn = tc ? kTcTileN : f32 ? kF32Tile : 32;
     // algorithmic work of the batch: every operand read once, every output written once
@@ -306,8 +451,25 @@ void Runner::flush_gemm(int precision_override) {
     const int64_t nt_est = (tm == 32 && tn == 32) ? pend_tiles32_ : (tm == 64 && tn == 64) ? pend_tiles64_ : -1;
     pend_flops_ = pend_bytes_ = 0.0;
     pend_tiles32_ = pend_tiles64_ = 0;
+    static const bool trace = std::getenv("H2_TRACE") != nullptr;
+    if (trace) {  // "h2gemm <prec> <jobs> <terms> <mean m> <mean n> <mean K per job> <jobs with m,n <= 64> <max m> <max n>"
+        double sm = 0, sn = 0, sk = 0;
+        int64_t small = 0;
+        int mm = 0, mn = 0;
+        for (const GJob& J : jobs_) {
+            sm += J.m;
+            sn += J.n;
+            for (int i = 0; i < J.nt; ++i) sk += terms_[J.t0 + i].k;
+            small += (J.m <= 64 && J.n <= 64);
+            mm = std::max(mm, J.m);
+            mn = std::max(mn, J.n);
+        }
+        const double nj = (double)jobs_.size();
+        std::fprintf(stderr, "h2gemm %d %zu %zu %.1f %.1f %.1f %lld %d %d\n", pr, jobs_.size(), terms_.size(), sm / nj,
+                     sn / nj, sk / nj, (long long)small, mm, mn);
+    }
     std::vector<SliceSum> sums;
-    if (!tc) split_k(pr, tm, sums, nt_est);
+    if (!tc || force_split >= 2) split_k(pr, tm, sums, nt_est, force_split);
     std::vector<GTile>& tiles = tiles_;
     tiles.clear();
     if (nt_est > 0) tiles.reserve((size_t)nt_est);
@@ -330,7 +492,7 @@ void Runner::flush_gemm(int precision_override) {
         for (const SliceSum& s : sums) max_n = std::max(max_n, s.n);
         begin(fam);
         if (tc) {
-            launch_gemm_tc(dt, dj, dti, (int)tiles.size(), d_flag_, st_);
+            launch_gemm_tc(dt, dj, dti, (int)tiles.size(), pr, d_flag_, st_);
         } else {
             HostWait hw("launch_gemm", tiles.size());
             launch_gemm(dt, dj, dti, (int)tiles.size(), pr, st_);
@@ -338,6 +500,8 @@ void Runner::flush_gemm(int precision_override) {
         launch_slice_sum(ds, (int)sums.size(), max_n, st_);
         if (!sums.empty()) ++launches;
         end(fam, fl, by, (int64_t)tiles.size());
+        marks_.back().tkey = tkey;
+        marks_.back().tcand = tcand;
         ++launches;
     }
     terms_.clear();
@@ -349,7 +513,8 @@ void Runner::flush_gemm(int precision_override) {
 // partial product to a slice of scratch, and k_slice_sum adds the slices (in
 // order, deterministic) into C with the job's beta.  Terms that straddle a
 // cut are divided by offsetting their operands along K.
-void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles) {
+void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles, int force) {
+    if (force == 1) return;
     const int kc = (pr == kGemmDF || pr == H2_FP64) ? 16 : 32;  // K chunk of the kernel
     const int per_sm = (pr == kGemmDF) ? 2 : (pr == H2_MIXED) ? 3 : 4;
     const int64_t target = 2LL * device_sm_count() * per_sm;
@@ -360,8 +525,13 @@ void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntil
             ntiles += J.sym ? ti * (ti + 1) / 2 : ti * tj;
         }
     }
-    if (ntiles == 0 || ntiles >= target) return;
-    const int want = (int)std::min<int64_t>(16, (target + ntiles - 1) / ntiles);
+    int want = 0;
+    if (force >= 2) {
+        want = force;
+    } else {
+        if (ntiles == 0 || ntiles >= target) return;
+        want = (int)std::min<int64_t>(16, (target + ntiles - 1) / ntiles);
+    }
     if (want < 2) return;
     std::vector<GJob> jobs;
     std::vector<GTerm> terms;
@@ -370,7 +540,7 @@ void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntil
     for (const GJob& J : jobs_) {
         int64_t chunks = 0;
         for (int i = 0; i < J.nt; ++i) chunks += (terms_[J.t0 + i].k + kc - 1) / kc;
-        const int S = (int)std::min<int64_t>(want, chunks / 8);
+        const int S = (int)std::min<int64_t>(want, chunks / (force >= 2 ? 4 : 8));
         if (S < 2) {
             GJob K = J;
             K.t0 = (int)terms.size();
@@ -645,17 +815,40 @@ const char* h2_last_error_message(void) { return g_last_error.c_str(); }
 // widening of the double-layer interpolation boxes (each extent >= this fraction of the largest)
 constexpr double kDlpFat = 0.25;
 
-static int build_interp(const double* points, const double* normals, int64_t n, int kernel, int leaf_size, double eta,
-                        int cheb_order, const h2_opts* opts, h2_matrix** out) {
-    if (!points || !out || n < 1 || leaf_size < 1 || cheb_order < 1 || cheb_order > 8 || !(eta >= 0.0) ||
+// A host view of n x 3 doubles given in host memory or in device memory of the
+// current device (copied to `buf` in the latter case).
+static const double* host_view(const double* p, int64_t n, std::vector<double>& buf) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // plain host memory on older drivers
+        return p;
+    }
+    if (at.type != cudaMemoryTypeDevice) return p;  // host, registered or managed memory
+    buf.resize((size_t)3 * n);
+    H2_CUDA(cudaMemcpy(buf.data(), p, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost));
+    return buf.data();
+}
+
+static int build_interp(const double* points_in, const double* normals_in, int64_t n, int kernel, int leaf_size,
+                        double eta, int cheb_order, const h2_opts* opts, h2_matrix** out) {
+    if (!points_in || !out || n < 1 || leaf_size < 1 || cheb_order < 1 || cheb_order > 8 || !(eta >= 0.0) ||
         !std::isfinite(eta) || kernel < H2_K_LAPLACE || kernel > H2_K_DLP)
         return H2_ERR_ARG;
     const bool dlp = (kernel == H2_K_DLP);
-    if (dlp && !normals) return H2_ERR_ARG;
+    if (dlp && !normals_in) return H2_ERR_ARG;
+    std::vector<double> pbuf, nbuf;
+    const double* points = points_in;
+    const double* normals = normals_in;
+    int rc = run_guarded([&] {
+        points = host_view(points_in, n, pbuf);
+        if (dlp) normals = host_view(normals_in, n, nbuf);
+    });
+    if (rc != H2_OK) return rc;
     for (int64_t i = 0; i < 3 * n; ++i)
         if (!std::isfinite(points[i]) || (dlp && !std::isfinite(normals[i]))) return H2_ERR_NUMERIC;
     return run_guarded([&] {
         cudaStream_t st = stream_of(opts);
+        AllocScope scope(alloc_of(opts), st);
         auto M = std::make_unique<h2_matrix>();
         H2_CUDA(cudaGetDevice(&M->device));
         M->st = build_structure(points, n, leaf_size, eta);
@@ -801,6 +994,7 @@ int h2_to_dense(const h2_matrix* A, double* out, int64_t ld, int out_on_device, 
     if (!A || !out || ld < A->st->tree.n) return H2_ERR_ARG;
     return run_guarded([&] {
         cudaStream_t st = stream_of(opts);
+        AllocScope scope(alloc_of(opts), st);
         const Tree& T = A->st->tree;
         const BlockTree& B = A->st->blocks;
         const int64_t n = T.n;
@@ -899,6 +1093,7 @@ int h2_clone(const h2_matrix* A, const h2_opts* opts, h2_matrix** out) {
     if (!A || !out) return H2_ERR_ARG;
     return run_guarded([&] {
         cudaStream_t st = stream_of(opts);
+        AllocScope scope(alloc_of(opts), st);
         auto M = std::make_unique<h2_matrix>();
         M->st = A->st;
         M->kernel = A->kernel;
@@ -963,9 +1158,17 @@ int h2_plan_structure(const double* points, int64_t n, int leaf_size, double eta
     });
 }
 
+int h2_library_memory(int64_t* current_bytes, int64_t* peak_bytes, int reset_peak) {
+    if (current_bytes) *current_bytes = g_own_bytes.load();
+    if (peak_bytes) *peak_bytes = g_own_peak.load();
+    if (reset_peak) g_own_peak.store(g_own_bytes.load());
+    return H2_OK;
+}
+
+// Every entry point returns after its work on the handle has finished, so the
+// buffers are free to go without waiting for the device.
 void h2_free(h2_matrix* A) {
     if (!A) return;
-    cudaDeviceSynchronize();
     delete A;
 }
 

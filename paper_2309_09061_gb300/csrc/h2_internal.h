@@ -109,10 +109,42 @@ struct Structure {
 
 std::shared_ptr<Structure> build_structure(const double* pts, int64_t n, int leaf, double eta);
 
+// ---------------------------------------------------------------- device memory
+// Source of device memory: the caller's callbacks (h2_opts alloc/free/alloc_ctx)
+// or, when alloc is null, the library itself.
+struct DevAlloc {
+    h2_alloc_fn alloc = nullptr;
+    h2_free_fn free = nullptr;
+    void* ctx = nullptr;
+    bool external() const { return alloc != nullptr; }
+};
+DevAlloc alloc_of(const h2_opts* o);  // throws H2_ERR_ARG for alloc without free
+// The device-memory source and stream of the API call running on this thread;
+// every device buffer a call makes comes from it.  Set for the duration of a
+// call (and in its helper threads) by AllocScope.
+struct AllocScope {
+    AllocScope(const DevAlloc& a, cudaStream_t st);
+    ~AllocScope();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+
+private:
+    DevAlloc prev_a_;
+    cudaStream_t prev_s_;
+};
+const DevAlloc& current_alloc();
+cudaStream_t current_alloc_stream();
+// one buffer of `bytes` from the current source, for work on `st`
+void* dev_get(const DevAlloc& a, size_t bytes, cudaStream_t st, bool pooled);
+void dev_put(const DevAlloc& a, void* p, size_t bytes, cudaStream_t st, bool pooled);
+
 // ---------------------------------------------------------------- device storage
+// A device buffer of a handle; it remembers where its memory came from.
 struct DevBuf {
     double* p = nullptr;
     size_t len = 0;  // doubles
+    DevAlloc src;
+    cudaStream_t st = nullptr;
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
@@ -276,8 +308,10 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
                  cudaStream_t st);
 void launch_slice_sum(const SliceSum* jobs, int njobs, int max_n, cudaStream_t st);
 int device_sm_count();
-// tcgen05 variant: tiles of 128 x 64; *err |= 4 if an MMA wait timed out
-void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st);
+// tcgen05 variant (mode H2_TF32X3, H2_TF32 or H2_BF16X3): tiles of 128 x 64;
+// *err |= 4 if a wait timed out
+void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int mode, int* err,
+                    cudaStream_t st);
 // output tile edge of the batched GEMM in FP32 (H2_MIXED) and double-float; FP64 uses 32
 constexpr int kF32Tile = 64;
 // launch_gemm precision tag (not an API value): FP64-accurate products in
@@ -286,6 +320,20 @@ constexpr int kGemmDF = 100;
 constexpr int kTcTileM = 128, kTcTileN = 64;
 // precision modes that run the factorisation-side steps in FP32 as well
 inline bool low_precision(int precision) { return precision != H2_FP64; }
+inline bool valid_precision(int p) { return p >= H2_FP64 && p <= H2_AUTO; }
+// the FP32-class products run on the tensor cores
+inline bool tc_precision(int p) { return p == H2_TF32X3 || p == H2_TF32 || p == H2_BF16X3; }
+// H2_AUTO by tolerance: one TF32 product where its 2^-11 operand rounding stays
+// an order below eps, BF16 pieces (2^-16) down to 1e-5, three-term TF32 products
+// (about FP32 accuracy) below that, and FP64 where a Gram matrix in FP32-class
+// arithmetic could no longer resolve the singular values the tolerance keeps
+inline int resolve_precision(int p, double eps) {
+    if (p != H2_AUTO) return p;
+    if (eps >= 1e-4) return H2_TF32;
+    if (eps >= 1e-5) return H2_BF16X3;
+    if (eps >= 1e-7) return H2_TF32X3;
+    return H2_FP64;
+}
 void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);
@@ -353,16 +401,51 @@ public:
     void release_all();
 
 private:
+    struct Chunk {
+        void* p;
+        size_t bytes;
+        DevAlloc src;
+    };
     cudaStream_t st_;
-    std::vector<void*> chunks_;
+    std::vector<Chunk> chunks_;
     char* cur_ = nullptr;
     size_t left_ = 0;
+};
+
+// Online tuner of GEMM launch schedules (h2_opts.autotune), process-wide.  A
+// batch is keyed by its kernel family and the logarithms of its tile count and
+// of its K chunks per tile.  The candidates of a key run in turn until each
+// has been timed twice (the times arrive when a call collects its launch
+// events); from then on the cheapest, in device milliseconds per GFLOP, runs.
+// Candidates: split-K by the default rule, off, or over 2 or 4 slices; for the
+// FP32-class products also the other kernel (CUDA-core FP32 against the
+// tensor-core mode), whose accuracy is at least the mode's.
+class Tuner {
+public:
+    static constexpr int kCand = 8;  // (kernel: own, other) x (split: default, off, 2, 4)
+    static Tuner& get();
+    int pick(uint64_t key, int ncand);
+    void report(uint64_t key, int cand, double ms_per_gflop);
+    // choices made so far (for tests and traces): key -> best candidate or -1
+    std::vector<std::pair<uint64_t, int>> table();
+
+private:
+    struct Entry {
+        double cost[kCand] = {};
+        int timed[kCand] = {};
+        int issued[kCand] = {};
+        int best = -1;
+        int ncand = 0;
+    };
+    std::mutex mu_;
+    std::unordered_map<uint64_t, Entry> map_;
 };
 
 // Host-side driver of batched ops: collects jobs, uploads, launches.
 class Runner {
 public:
     explicit Runner(cudaStream_t st, int precision) : st_(st), prec_(precision), scratch_(st), persist_(st) {}
+    void set_autotune(bool on) { tune_ = on; }
     ~Runner();
     cudaStream_t stream() const { return st_; }
     int precision() const { return prec_; }
@@ -373,7 +456,9 @@ public:
     void term(const double* A, int ta, int lda, const double* B, int tb, int ldb, int k, double alpha = 1.0,
               const double* scale = nullptr);
     void flush_gemm(int precision_override = -1);
-    void split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles = -1);
+    // force: 0 the default rule (when the batch would not fill the GPU), 1 never,
+    // S >= 2 every job with enough K into S slices
+    void split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles = -1, int force = 0);
     void qr(double* A, int m, int n, int lda, double* R, int ldr, double* Q, int ldq, int q, bool fp32 = false,
             int* piv = nullptr);
     // FP64 QR of A (m x n, in place) returning the compact WY form of its Q:
@@ -439,7 +524,10 @@ private:
         double flops, bytes;
         double* dflops;  // device-side flop count of the launch, read at collect()
         int64_t units;   // CTAs of the launch (tiles for the products)
+        uint64_t tkey = 0;  // autotuned batch: its key and candidate
+        int tcand = -1;
     };
+    bool tune_ = false;
     double* dev_counter();
     std::vector<Mark> marks_;
     std::vector<cudaEvent_t> pool_;

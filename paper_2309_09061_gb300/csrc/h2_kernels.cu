@@ -4,9 +4,11 @@
 // blocks of one tree level at once.  Each batched kernel reads a device array
 // of job descriptors built by the host executor.
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "h2_internal.h"
 
@@ -421,224 +423,453 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
         k_gemm<double><<<ntiles, GT, 0, st>>>(terms, jobs, tiles);
 }
 
-// ------------------------------------------------------------------ GEMM on tcgen05 (H2_TC)
-// Same contract as k_gemm on the 5th-generation tensor cores.  One CTA of 128
-// threads computes a 128 x 64 output tile.  The operands of each K chunk are
-// rounded to FP32 and staged in shared memory as three TF32 pieces x = x0 + x1
-// + x2 (each rna of the remainder; together they hold the 24 bits of the FP32
-// value exactly) in the K-major core-matrix layout (8 rows x 16 bytes per core
-// matrix).  One thread issues tcgen05.mma.kind::tf32: a0 b0 into accumulator
-// D0 and the five correction products of order 2^-11 .. 2^-22 (a0 b1, a1 b0,
-// a0 b2, a1 b1, a2 b0) into D1 (two 128-lane x 64-column FP32 accumulators in
-// TMEM).  The tensor cores' FP32 accumulation rounds toward zero, so the
-// accumulators only live for one chunk: after each chunk tcgen05.ld moves them
-// into registers, where a compensated (Kahan) FP32 sum carries the result.
-// Waits on the MMA completion barrier are bounded: on timeout the kernel
-// records the error, frees its TMEM and returns.
-constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 128;
-constexpr int TC_A = TC_M * TC_K, TC_B = TC_N * TC_K;  // elements per operand tile
-constexpr int TC_PIECES = 3;
-constexpr int TC_COLS = 2 * TC_N;  // two accumulators
-constexpr size_t TC_SMEM = TC_PIECES * (size_t)(TC_A + TC_B) * 4 + 64;
+// ------------------------------------------------------------------ GEMM on tcgen05
+// Same contract as k_gemm on the 5th-generation tensor cores, for the FP32-class
+// products of the tensor-core modes.  One CTA computes a 128 x 64 output tile
+// of one job and is warp-specialised:
+//   warps 0-3  producers: each K chunk of 32 (term, k) pairs is read from the
+//              FP64 operands, rounded to FP32 (integer operations), split into
+//              pieces and stored in shared memory in the K-major core-matrix
+//              layout (8 rows x 16 bytes per core matrix, the cores of a row
+//              group contiguous along K), two stages deep;
+//   warp 4     one lane issues tcgen05.mma for every ready stage and commits
+//              the stage and the accumulator groups to mbarriers;
+//   warps 0-3  again, as the epilogue: tcgen05.ld of the accumulators (warp w
+//              owns TMEM lanes 32w..32w+31, i.e. tile rows 32w..32w+31).
+// Pieces and products per mode:
+//   TF32X3  x = a0 + a1 (two TF32 values, each rounded to nearest);
+//           a0 b0 into D0, a0 b1 + a1 b0 into D1
+//   TF32    a0 b0 into D0
+//   BF16X3  x = a0 + a1 (two BF16 values); a0 b0 into D0, a0 b1 + a1 b0 into D1
+// The tensor cores' FP32 accumulation rounds toward zero, so its error is a
+// bias that grows with the number of accumulation steps.  In the three-term
+// modes D0 (the leading product) therefore holds one chunk at a time: two D0
+// buffers alternate, and while the MMAs fill one, the producers add the other
+// into FP32 registers with round to nearest.  D1 is 2^-11 (TF32) or 2^-8
+// (BF16) smaller, so its bias is negligible and it accumulates over the whole
+// job; so does D0 in the one-product mode, whose operand rounding (2^-11) is far
+// above that bias.  Every wait is bounded (about a second): on timeout the CTA
+// sets bit 4 of *err, stops, drains its MMAs and frees its TMEM.
+constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 160;  // 4 producer warps + 1 MMA warp
+constexpr int TC_PRODUCERS = 128;
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
+template <int MODE>
+struct TcCfg {
+    static constexpr bool bf16 = (MODE == H2_BF16X3);
+    static constexpr bool three = (MODE != H2_TF32);
+    static constexpr int esize = bf16 ? 2 : 4;         // bytes per element
+    static constexpr int ke = 16 / esize;              // elements per 16-byte core row
+    static constexpr int cores_k = TC_K / ke;          // core matrices along K per row group
+    static constexpr int a_piece = TC_M * TC_K * esize;  // bytes of one piece of A
+    static constexpr int b_piece = TC_N * TC_K * esize;
+    static constexpr int pieces = three ? 2 : 1;
+    static constexpr int stage = pieces * (a_piece + b_piece);
+    static constexpr int flush = three ? 1 : (1 << 30);  // chunks per D0 group
+    static constexpr int kstep = bf16 ? 16 : 8;          // K of one MMA
+    static constexpr int cols = three ? 256 : 128;       // TMEM columns: D0 x 2 (+ D1)
+    // shared memory: two stages, then the barriers and the stage flags; at least
+    // 80 KB, so that at most two CTAs share an SM (their TMEM columns always fit)
+    static constexpr int bar_off = 2 * stage;
+    static constexpr int smem = (2 * stage + 256) > 80 * 1024 ? (2 * stage + 256) : 80 * 1024;
+    // instruction descriptor: D FP32, A and B TF32 (kind::tf32) or BF16 (kind::f16),
+    // both K-major, N = 64, M = 128
+    static constexpr uint32_t idesc = (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) |
+                                      ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+};
+
+// shared memory descriptor, K-major without swizzle: LBO = 128 B (next core
+// matrix along K), SBO = cores_k * 128 B (next 8-row group)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, int cores_k) {
+    const uint64_t lbo = 128, sbo = (uint64_t)cores_k * 128;
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+template <int MODE>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    if constexpr (MODE == H2_BF16X3) {
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                     "l"(a), "l"(b), "r"(TcCfg<MODE>::idesc), "r"(acc));
+    } else {
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                     "l"(a), "l"(b), "r"(TcCfg<MODE>::idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t* u = (uint32_t*)v;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
+          "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
+          "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait for the phase of the given parity: false when the CTA was
+// aborted, or about a second passed (then the CTA is aborted and *err flagged).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t spin = 1;; ++spin) {
+        if (mbar_try(bar, parity)) return true;
+        if ((spin & 63u) == 0) {
+            // another CTA of this or an earlier launch of the call timed out: give up too
+            if (*abort_flag || (err && (*(volatile int*)err & 4))) {
+                *abort_flag = 1;
+                return false;
+            }
+            if (global_ns() - t0 > 1000000000ull) {
+                *abort_flag = 1;
+                if (err) atomicOr(err, 4);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return r;
 }
 
-// element (row r, k) of a K-major tile with TC_K columns
-__device__ __forceinline__ int core_index(int r, int k) {
-    return ((r >> 3) * (TC_K / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t* w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
 }
 
-// shared memory descriptor: K-major, no swizzle; LBO = 128 B (next core in K),
-// SBO = (TC_K / 4) * 128 B (next 8-row group)
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    const uint64_t lbo = 128, sbo = (TC_K / 4) * 128;
-    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | ((uint64_t)1 << 46);
+// One operand tile of a K chunk into shared memory (producer warps).  Item
+// (row r, K group q) is the 16 bytes of row r in core matrix q of its row group
+// (ke consecutive k); a warp stores 8 rows x 4 K groups, i.e. 4 consecutive
+// 128-byte cores: conflict-free 16-byte stores.  Element (r, k) of the tile is
+// base[r * ld + k] (kcontig) or base[r + k * ld]; rows >= rows_valid are not
+// written (they were zeroed once), k >= kvalid is stored as zero.  The second
+// piece (three-term modes) goes to dst + pstride.  Four items are loaded before
+// any is converted, to keep loads in flight.
+template <int MODE>
+__device__ __forceinline__ void tc_stage(uint32_t dst, uint32_t pstride, const double* base, int ld, bool kcontig,
+                                         int rows_valid, int kvalid, int nrows, float scale, int warp, int lane) {
+    using C = TcCfg<MODE>;
+    constexpr int KE = C::ke, QW = C::cores_k / 4;  // K groups of 4 cores per row group
+    const int ngroups = (nrows / 8) * QW;           // warp items of the tile
+    for (int g0 = warp; g0 < ngroups; g0 += 16) {
+        double v[4][KE];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int g = g0 + 4 * h;
+            const int r = (g / QW) * 8 + (lane & 7), q = (g % QW) * 4 + (lane >> 3);
+#pragma unroll
+            for (int e = 0; e < KE; ++e) {
+                const int k = q * KE + e;
+                const bool in = g < ngroups && r < rows_valid && k < kvalid;
+                v[h][e] = in ? (kcontig ? base[(size_t)r * ld + k] : base[r + (size_t)k * ld]) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int g = g0 + 4 * h;
+            const int r8 = g / QW, q = (g % QW) * 4 + (lane >> 3);
+            if (g >= ngroups || r8 * 8 >= rows_valid) continue;
+            const uint32_t addr = dst + (uint32_t)((r8 * C::cores_k + q) * 128 + (lane & 7) * 16);
+            uint32_t w0[4], w1[4];
+            if constexpr (C::bf16) {
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    const float x0 = scale * f64_to_f32(v[h][e]), x1 = scale * f64_to_f32(v[h][e + 1]);
+                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                    w0[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                    w1[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float x = scale * f64_to_f32(v[h][e]);
+                    w0[e] = tf32_rn(x);
+                    w1[e] = C::three ? tf32_rn(x - __uint_as_float(w0[e])) : 0u;
+                }
+            }
+            st_shared_v4(addr, w0);
+            if constexpr (C::three) st_shared_v4(addr + pstride, w1);
+        }
+    }
 }
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128
-constexpr uint32_t TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                              ((uint32_t)(TC_M >> 4) << 24);
-
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
-    uint32_t* u = (uint32_t*)v;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
-        "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
-          "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]),
-          "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]),
-          "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31]),
-          "=r"(u[32]), "=r"(u[33]), "=r"(u[34]), "=r"(u[35]), "=r"(u[36]), "=r"(u[37]), "=r"(u[38]), "=r"(u[39]),
-          "=r"(u[40]), "=r"(u[41]), "=r"(u[42]), "=r"(u[43]), "=r"(u[44]), "=r"(u[45]), "=r"(u[46]), "=r"(u[47]),
-          "=r"(u[48]), "=r"(u[49]), "=r"(u[50]), "=r"(u[51]), "=r"(u[52]), "=r"(u[53]), "=r"(u[54]), "=r"(u[55]),
-          "=r"(u[56]), "=r"(u[57]), "=r"(u[58]), "=r"(u[59]), "=r"(u[60]), "=r"(u[61]), "=r"(u[62]), "=r"(u[63])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                 "l"(a), "l"(b), "r"(TC_IDESC), "r"(acc));
-}
-
-__global__ void __launch_bounds__(TC_T) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
-                                                  const GTile* __restrict__ tiles, int* err) {
+// Stage flags (one int per stage, written by producer 0 before the producers
+// arrive on the stage's barrier): bit 0 a chunk is present, bit 1 it opens a D0
+// group, bit 2 it closes one, bit 3 it is the job's last chunk.
+template <int MODE>
+__global__ void __launch_bounds__(TC_T, 2) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
+                                                     const GTile* __restrict__ tiles, int* err) {
+    using C = TcCfg<MODE>;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
-    uint32_t* as = (uint32_t*)tc_smem;     // pieces 0..2 of A, TC_A elements each
-    uint32_t* bs = as + TC_PIECES * TC_A;  // pieces 0..2 of B, TC_B elements each
-    uint64_t* mbar = (uint64_t*)(bs + TC_PIECES * TC_B);
-    uint32_t* tmem_slot = (uint32_t*)(mbar + 1);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tc_smem);
+    // barriers: full[2] 0..1, empty[2] 2..3, accf[2] 4..5, acce[2] 6..7, drain 8
+    const uint32_t bar0 = sbase + C::bar_off;
+    volatile int* sflag = (volatile int*)(tc_smem + C::bar_off + 80);  // [2]
+    volatile int* abort_flag = sflag + 2;
+    uint32_t* tmem_slot = (uint32_t*)(tc_smem + C::bar_off + 96);
+    auto full = [&](int s) { return bar0 + 8u * s; };
+    auto empty = [&](int s) { return bar0 + 16u + 8u * s; };
+    auto accf = [&](int b) { return bar0 + 32u + 8u * b; };
+    auto acce = [&](int b) { return bar0 + 48u + 8u * b; };
+    const uint32_t drain = bar0 + 64u;
+    // after a timeout anywhere in the call, later CTAs do nothing (one read, shared by the CTA)
+    __shared__ int skip;
+    if (threadIdx.x == 0) skip = err ? (*(volatile int*)err & 4) : 0;
+    __syncthreads();
+    if (skip) return;
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(mbar);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(tmem_slot)),
-                     "r"(TC_COLS));
+                     "r"(C::cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar_s));
+    if (threadIdx.x == 32) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(full(s), TC_PRODUCERS);
+            mbar_init(empty(s), 1);
+            mbar_init(accf(s), 1);
+            mbar_init(acce(s), TC_PRODUCERS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    // rows of A and B beyond the job stay zero in both stages
+    const int mrows = min(TC_M, J.m - tile.i0), ncols = min(TC_N, J.n - tile.j0);
+    for (int s = 0; s < 2; ++s)
+        for (int p = 0; p < C::pieces; ++p) {
+            uint4* a = (uint4*)(tc_smem + s * C::stage + p * C::a_piece);
+            uint4* b = (uint4*)(tc_smem + s * C::stage + C::pieces * C::a_piece + p * C::b_piece);
+            for (int e = threadIdx.x; e < C::a_piece / 16; e += TC_T)
+                if ((e / (8 * C::cores_k)) * 8 + (e & 7) >= mrows) a[e] = make_uint4(0, 0, 0, 0);
+            for (int e = threadIdx.x; e < C::b_piece / 16; e += TC_T)
+                if ((e / (8 * C::cores_k)) * 8 + (e & 7) >= ncols) b[e] = make_uint4(0, 0, 0, 0);
+        }
+    asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    float sum[TC_N], comp[TC_N], v[TC_N];
-#pragma unroll
-    for (int c = 0; c < TC_N; ++c) sum[c] = comp[c] = 0.f;
-    uint32_t phase = 0;
-    bool failed = false;
-    for (int it = 0; it < J.nt && !failed; ++it) {
-        const GTerm P = terms[J.t0 + it];
-        const double f = P.alpha * (P.scale ? *P.scale : 1.0);
-        if (f == 0.0) continue;
-        const float ff = (float)f;
-        for (int k0 = 0; k0 < P.k && !failed; k0 += TC_K) {
-            // stage op(A)[i0:i0+128, k0:k0+32] and op(B)^T[j0:j0+64, k0:k0+32]
-            for (int e = threadIdx.x; e < TC_A; e += TC_T) {
-                int r, kk;
-                if (!P.ta) { r = e % TC_M; kk = e / TC_M; } else { kk = e % TC_K; r = e / TC_K; }
-                int gi = tile.i0 + r, gk = k0 + kk;
-                float x = 0.f;
-                if (gi < J.m && gk < P.k)
-                    x = ff * (float)(P.ta ? P.A[gk + (size_t)gi * P.lda] : P.A[gi + (size_t)gk * P.lda]);
-                const int ci = core_index(r, kk);
-                const uint32_t p0 = tf32_rna(x);
-                const float r1 = x - __uint_as_float(p0);
-                const uint32_t p1 = tf32_rna(r1);
-                as[ci] = p0;
-                as[TC_A + ci] = p1;
-                as[2 * TC_A + ci] = tf32_rna(r1 - __uint_as_float(p1));
-            }
-            for (int e = threadIdx.x; e < TC_B; e += TC_T) {
-                int c, kk;
-                if (!P.tb) { kk = e % TC_K; c = e / TC_K; } else { c = e % TC_N; kk = e / TC_N; }
-                int gj = tile.j0 + c, gk = k0 + kk;
-                float x = 0.f;
-                if (gj < J.n && gk < P.k) x = (float)(P.tb ? P.B[gj + (size_t)gk * P.ldb] : P.B[gk + (size_t)gj * P.ldb]);
-                const int ci = core_index(c, kk);
-                const uint32_t p0 = tf32_rna(x);
-                const float r1 = x - __uint_as_float(p0);
-                const uint32_t p1 = tf32_rna(r1);
-                bs[ci] = p0;
-                bs[TC_B + ci] = p1;
-                bs[2 * TC_B + ci] = tf32_rna(r1 - __uint_as_float(p1));
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (threadIdx.x == 0) {
+
+    if (warp == 4) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            bool d1_started = false;
+            int g = 0;  // D0 group index
+            for (int c = 0;; ++c) {
+                const int s = c & 1;
+                if (!mbar_wait(full(s), (uint32_t)((c >> 1) & 1), abort_flag, err)) break;
+                const int f = sflag[s];
+                if (!(f & 1)) break;
+                const int b = g & 1;
+                if ((f & 2) && g >= 2 && !mbar_wait(acce(b), (uint32_t)(((g - 2) >> 1) & 1), abort_flag, err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(as);
-                const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(bs);
-                constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
-                constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+                const uint32_t sa = sbase + s * C::stage, sb = sa + C::pieces * C::a_piece;
+                const uint32_t d0 = tmem + (uint32_t)(b * TC_N), d1 = tmem + 2u * TC_N;
 #pragma unroll
-                for (int ks = 0; ks < TC_K / 8; ++ks) {
-                    const uint32_t off = ks * 2 * 128;  // two core matrices of K per MMA
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const uint64_t da = smem_desc(a0 + (uint32_t)(pa[q] * TC_A * 4) + off);
-                        const uint64_t db = smem_desc(b0 + (uint32_t)(pb[q] * TC_B * 4) + off);
-                        // D0 (columns 0..63) takes a0 b0, D1 (columns 64..127) the corrections;
-                        // each starts afresh in every chunk
-                        const uint32_t d = (q == 0) ? tmem : tmem + TC_N;
-                        const uint32_t acc = (ks > 0 || q > 1) ? 1u : 0u;
-                        tc_mma(d, da, db, acc);
+                for (int ks = 0; ks < TC_K / C::kstep; ++ks) {
+                    const uint32_t off = ks * 256;  // two core matrices along K per MMA
+                    const uint64_t a0 = tc_desc(sa + off, C::cores_k), b0 = tc_desc(sb + off, C::cores_k);
+                    tc_mma<MODE>(d0, a0, b0, ((f & 2) && ks == 0) ? 0u : 1u);
+                    if constexpr (C::three) {
+                        const uint64_t a1 = tc_desc(sa + C::a_piece + off, C::cores_k);
+                        const uint64_t b1 = tc_desc(sb + C::b_piece + off, C::cores_k);
+                        tc_mma<MODE>(d1, a0, b1, d1_started ? 1u : 0u);
+                        d1_started = true;
+                        tc_mma<MODE>(d1, a1, b0, 1u);
                     }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    mbar_s));
-            }
-            // bounded wait for the MMAs of this chunk
-            uint32_t done = 0;
-            for (long spin = 0; spin < (1L << 24) && !done; ++spin) {
-                asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
-                             : "=r"(done)
-                             : "r"(mbar_s), "r"(phase));
-            }
-            // one decision for the whole CTA (the barriers above and below must match)
-            failed = __syncthreads_or(done ? 0 : 1) != 0;
-            if (failed && threadIdx.x == 0 && err) atomicOr(err, 4);
-            phase ^= 1;
-            if (!failed) {
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                // move both accumulators into the compensated register sums
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    tmem_ld64(tmem + lane_base + (uint32_t)(half * TC_N), v);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-                    for (int c = 0; c < TC_N; ++c) {
-                        const float y = v[c] - comp[c];
-                        const float t = sum[c] + y;
-                        comp[c] = (t - sum[c]) - y;
-                        sum[c] = t;
-                    }
+                tc_commit(empty(s));  // the stage may be refilled once these MMAs are done
+                if (f & 4) {
+                    tc_commit(accf(b));
+                    ++g;
                 }
-                // the next chunk's MMAs overwrite the accumulators only after these loads
-                asm volatile("tcgen05.fence::before_thread_sync;");
-                __syncthreads();
+                if (f & 8) break;
+            }
+            // drain: every MMA issued has completed before TMEM is freed
+            tc_commit(drain);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try(drain, 0u) && global_ns() - t0 < 1000000000ull) {
             }
         }
-    }
-    if (!failed) {
-        const int gi = tile.i0 + warp * 32 + lane;
-        if (gi < J.m) {
+        __syncwarp();
+    } else {
+        // ---------------- producers, then the epilogue (warp w: tile rows 32 w .. 32 w + 31)
+        float acc[TC_N];
 #pragma unroll
-            for (int c = 0; c < TC_N; ++c) {
-                const int gj = tile.j0 + c;
-                if (gj < J.n) {
-                    double* cp = J.C + gi + (size_t)gj * J.ldc;
-                    const double val = (double)sum[c] - (double)comp[c];
-                    *cp = (J.beta == 0.0) ? val : J.beta * *cp + val;
+        for (int j = 0; j < TC_N; ++j) acc[j] = 0.f;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        // adds D0 group g into acc; its MMAs are complete once accf(g & 1) fires
+        auto read_group = [&](int g) -> bool {
+            const int b = g & 1;
+            // one decision per warp: tcgen05.ld needs the whole warp
+            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), (uint32_t)((g >> 1) & 1), abort_flag, err))) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            float v[32];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                tmem_ld32(tmem + lane_base + (uint32_t)(b * TC_N + 32 * h), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[32 * h + j] += v[j];
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(acce(b));
+            return true;
+        };
+        // chunk sequence: (term it, k0) over the job's terms, skipping zero factors
+        int it = -1, k0 = 0;
+        GTerm P{};
+        double fct = 0.0;
+        auto advance = [&]() -> bool {
+            if (it >= 0 && k0 + TC_K < P.k) {
+                k0 += TC_K;
+                return true;
+            }
+            for (++it; it < J.nt; ++it) {
+                P = terms[J.t0 + it];
+                fct = P.alpha * (P.scale ? *P.scale : 1.0);
+                if (fct != 0.0 && P.k > 0) {
+                    k0 = 0;
+                    return true;
+                }
+            }
+            return false;
+        };
+        bool ok = true;
+        bool have = advance();
+        int c = 0, in_group = 0, g = 0;
+        if (!have) {  // no chunk: tell the MMA warp
+            if (threadIdx.x == 0) sflag[0] = 0;
+            mbar_arrive(full(0));
+        }
+        while (have) {
+            const int s = c & 1;
+            const GTerm Q = P;
+            const int q0 = k0;
+            const float fs = f64_to_f32(fct);
+            const bool more = advance();
+            if (c >= 2 &&
+                !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)(((c >> 1) + 1) & 1), abort_flag, err))) {
+                ok = false;
+                break;
+            }
+            const uint32_t sa = sbase + s * C::stage, sb = sa + C::pieces * C::a_piece;
+            const int kvalid = min(TC_K, Q.k - q0);
+            // A (m x k) rows i0.., k q0..: plain A[i + k lda], transposed A[k + i lda]
+            const double* ab = Q.ta ? Q.A + q0 + (size_t)tile.i0 * Q.lda : Q.A + tile.i0 + (size_t)q0 * Q.lda;
+            tc_stage<MODE>(sa, C::a_piece, ab, Q.lda, Q.ta != 0, mrows, kvalid, TC_M, fs, warp, lane);
+            // B (k x n) as rows j0.. of B^T: plain B[k + j ldb], transposed B[j + k ldb]
+            const double* bb = Q.tb ? Q.B + tile.j0 + (size_t)q0 * Q.ldb : Q.B + q0 + (size_t)tile.j0 * Q.ldb;
+            tc_stage<MODE>(sb, C::b_piece, bb, Q.ldb, Q.tb == 0, ncols, kvalid, TC_N, 1.f, warp, lane);
+            const bool opens = (in_group == 0);
+            const bool closes = (in_group + 1 == C::flush) || !more;
+            if (threadIdx.x == 0) sflag[s] = 1 | (opens ? 2 : 0) | (closes ? 4 : 0) | (more ? 0 : 8);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full(s));
+            // the group before this one is complete: add it up while the MMAs run
+            if (opens && g >= 1 && !read_group(g - 1)) {
+                ok = false;
+                break;
+            }
+            in_group = closes ? 0 : in_group + 1;
+            if (closes) ++g;
+            ++c;
+            have = more;
+        }
+        if (ok && c > 0) ok = read_group(g - 1);
+        if (ok && c > 0 && C::three) {  // D1 (complete with the last group)
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            float v[32];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                tmem_ld32(tmem + lane_base + (uint32_t)(2 * TC_N + 32 * h), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[32 * h + j] += v[j];
+            }
+        }
+        if (ok && !*abort_flag) {
+            const int row = tile.i0 + warp * 32 + lane;
+            if (row < J.m) {
+                const bool beta0 = (__double_as_longlong(J.beta) << 1) == 0;
+#pragma unroll
+                for (int j = 0; j < TC_N; ++j) {
+                    if (j < ncols) {
+                        double* cp = J.C + row + (size_t)(tile.j0 + j) * J.ldc;
+                        const double val = f32_to_f64(acc[j]);
+                        *cp = beta0 ? val : J.beta * *cp + val;
+                    }
                 }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::cols));
 }
 
-void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st) {
-    if (ntiles <= 0) return;
+template <int MODE>
+static void launch_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int* err, cudaStream_t st) {
     static bool attr_set[64] = {};
+    static std::mutex mu;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
-        attr_set[dev] = true;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<MODE>::smem);
+            attr_set[dev] = true;
+        }
     }
-    k_gemm_tc<<<ntiles, TC_T, TC_SMEM, st>>>(terms, jobs, tiles, err);
+    k_gemm_tc<MODE><<<ntiles, TC_T, TcCfg<MODE>::smem, st>>>(terms, jobs, tiles, err);
+}
+
+void launch_gemm_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, int ntiles, int mode, int* err,
+                    cudaStream_t st) {
+    if (ntiles <= 0) return;
+    if (mode == H2_TF32)
+        launch_tc<H2_TF32>(terms, jobs, tiles, ntiles, err, st);
+    else if (mode == H2_BF16X3)
+        launch_tc<H2_BF16X3>(terms, jobs, tiles, ntiles, err, st);
+    else
+        launch_tc<H2_TF32X3>(terms, jobs, tiles, ntiles, err, st);
 }
 
 // ------------------------------------------------------------------ reductions

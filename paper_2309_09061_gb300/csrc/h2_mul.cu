@@ -479,6 +479,7 @@ static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
             H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, R.stream()));
         H2_CUDA(cudaStreamSynchronize(R.stream()));
         if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
+        if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     }
     return h;
 }
@@ -1841,16 +1842,19 @@ static void stream_after(cudaStream_t waiter, cudaStream_t signaller) {
     H2_CUDA(cudaEventDestroy(e));
 }
 
-// runs f on a host thread (current device) and joins in join() or the destructor
+// runs f on a host thread (current device, the caller's device-memory source
+// with stream st) and joins in join() or the destructor
 class Beside {
 public:
     template <class F>
-    explicit Beside(F&& f) {
+    Beside(cudaStream_t st, F&& f) {
         int dev = 0;
         H2_CUDA(cudaGetDevice(&dev));
-        th_ = std::thread([this, dev, f = std::forward<F>(f)]() mutable {
+        const DevAlloc src = current_alloc();
+        th_ = std::thread([this, dev, src, st, f = std::forward<F>(f)]() mutable {
             try {
                 H2_CUDA(cudaSetDevice(dev));
+                AllocScope scope(src, st);
                 f();
             } catch (...) {
                 err_ = std::current_exception();
@@ -1942,7 +1946,7 @@ static PhaseB coarsen_and_project(Runner& R, Runner& R2, cudaStream_t st, SideSt
     if (beside) {
         stream_after(side.s, st);
         clk2.mark();
-        Beside col([&] { cb = coarsen_rows(R2, GC, cmap, w, w2, eps); });
+        Beside col(R2.stream(), [&] { cb = coarsen_rows(R2, GC, cmap, w, w2, eps); });
         rb = coarsen_rows(R, GR, cmap, w, w2, eps);
         clk.mark();
         col.join();
@@ -2002,12 +2006,16 @@ static PhaseB coarsen_and_project(Runner& R, Runner& R2, cudaStream_t st, SideSt
 
 static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, const h2_opts* opts) {
     const double eps = opts ? opts->eps : 1e-6;
-    const int prec = opts ? opts->precision : H2_FP64;
+    const int prec = resolve_precision(opts ? opts->precision : H2_FP64, eps);
     cudaStream_t st = stream_of(opts);
+    AllocScope scope(alloc_of(opts), st);
     auto t_host0 = std::chrono::steady_clock::now();
     SideStream side;
     Runner R(st, prec);
     Runner R2(side.s, prec);  // column sides; its outputs live until the end of the call
+    const bool tune = opts && opts->autotune;
+    R.set_autotune(tune);
+    R2.set_autotune(tune);
     const bool beside = low_precision(prec);
     PhaseClock clk(st), clk2(side.s);
     Counts cnt, cnt2;
@@ -2023,7 +2031,7 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     if (beside) {
         stream_after(side.s, st);
         clk2.mark();
-        Beside col([&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ); });
+        Beside col(R2.stream(), [&] { ca = induced_rows(R2, Yt, Xt, eps, cnt2, WZ); });
         ra = induced_rows(R, X, Y, eps, cnt, VZ);
         clk.mark();
         col.join();
@@ -2093,6 +2101,9 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
             R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
             R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes, ref);
         }
+    } else if (opts && opts->autotune) {  // the tuner learns from the launch times
+        R.collect(nullptr, nullptr, nullptr, nullptr);
+        R2.collect(nullptr, nullptr, nullptr, nullptr);
     }
     R.release_all();
     R2.release_all();
@@ -2190,12 +2201,15 @@ static std::shared_ptr<Basis> orthogonalize(Runner& R, const Tree& T, const Basi
 // block tree as the tree of the intermediate matrix.
 static void recompress(h2_matrix* A, const h2_opts* opts) {
     const double eps = opts ? opts->eps : 1e-6;
-    const int prec = opts ? opts->precision : H2_FP64;
+    const int prec = resolve_precision(opts ? opts->precision : H2_FP64, eps);
+    AllocScope scope(alloc_of(opts), stream_of(opts));
     cudaStream_t st = stream_of(opts);
     auto t_host0 = std::chrono::steady_clock::now();
     SideStream side;
     Runner R(st, prec);
     Runner R2(side.s, prec);
+    R.set_autotune(opts && opts->autotune);
+    R2.set_autotune(opts && opts->autotune);
     PhaseClock clk(st), clk2(side.s);
     Counts cnt;
     const Tree& T = A->st->tree;
@@ -2265,6 +2279,9 @@ static void recompress(h2_matrix* A, const h2_opts* opts) {
             R.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes);
             R2.collect(S->fam_ms, S->fam_launches, S->fam_flops, S->fam_bytes, ref);
         }
+    } else if (opts && opts->autotune) {  // the tuner learns from the launch times
+        R.collect(nullptr, nullptr, nullptr, nullptr);
+        R2.collect(nullptr, nullptr, nullptr, nullptr);
     }
     R.release_all();
     R2.release_all();
@@ -2308,7 +2325,7 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
     for (int i = 0; i < count; ++i)
         if (!Z[i] || !X[i] || !Y[i]) return H2_ERR_ARG;
     if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
-                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
+                 !valid_precision(opts->precision)))
         return H2_ERR_ARG;
     // a Z may not appear twice, nor as an operand of another product (its swap would race)
     for (int i = 0; i < count; ++i)
@@ -2333,7 +2350,13 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
         }
         cudaStreamWaitEvent(st, start, 0);
         for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
-            h2_opts o = opts ? *opts : h2_opts{1e-6, H2_FP64, nullptr, nullptr};
+            h2_opts o{};
+            if (opts) {
+                o = *opts;
+            } else {
+                o.eps = 1e-6;
+                o.precision = H2_FP64;
+            }
             o.stream = st;
             o.stats = opts && opts->stats ? &stats[i] : nullptr;
             codes[i] = h2_mul_add(Z[i], X[i], Y[i], &o);
@@ -2383,6 +2406,7 @@ extern "C" int h2_matvec(const h2_matrix* A, const double* x, double* y, int64_t
                          const h2_opts* opts) {
     if (!A || !x || !y || nvec < 1 || nvec > (1 << 20) || (trans != 0 && trans != 1)) return H2_ERR_ARG;
     try {
+        h2::AllocScope scope(h2::alloc_of(opts), h2::stream_of(opts));
         h2::matvec(A, trans != 0, x, y, nvec, h2::stream_of(opts));
         return H2_OK;
     } catch (const h2::Error& e) {
@@ -2401,6 +2425,7 @@ extern "C" int h2_product_error(const h2_matrix* Zr, const h2_matrix* Z0, const 
     const uint64_t f = X->st->fingerprint;
     if (Y->st->fingerprint != f || Z0->st->fingerprint != f || Zr->st->fingerprint != f) return H2_ERR_SHAPE;
     try {
+        AllocScope scope(alloc_of(opts), stream_of(opts));
         product_error(Zr, Z0, X, Y, x0, steps, stream_of(opts), eps2, norm);
         return H2_OK;
     } catch (const Error& e) {
@@ -2416,7 +2441,7 @@ extern "C" int h2_recompress(h2_matrix* A, const h2_opts* opts) {
     using namespace h2;
     if (!A) return H2_ERR_ARG;
     if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
-                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
+                 !valid_precision(opts->precision)))
         return H2_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != A->device) return H2_ERR_ARG;
@@ -2436,7 +2461,7 @@ extern "C" int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, 
     using namespace h2;
     if (!Z || !X || !Y) return H2_ERR_ARG;
     if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) ||
-                 (opts->precision != H2_FP64 && opts->precision != H2_MIXED && opts->precision != H2_TC)))
+                 !valid_precision(opts->precision)))
         return H2_ERR_ARG;
     if (X->st->fingerprint != Y->st->fingerprint || X->st->fingerprint != Z->st->fingerprint) return H2_ERR_SHAPE;
     int dev = 0;

@@ -3,6 +3,7 @@
 // matrix in tree order) comes from one file-scope device array.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "h2_internal.h"
@@ -15,10 +16,15 @@ constexpr size_t kNoAllocScratchDoubles = (size_t)4 << 20;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 // Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is not a device address).
+// device current (the host-side symbol is not a device address).  The lookup
+// is serialised, so concurrent first calls from several threads are safe.  A
+// device reset (cudaDeviceReset) invalidates the cached address: a process
+// that resets a device must not call h2_to_dense_noalloc on it afterwards.
 static double* noalloc_scratch_ptr(int dev) {
     static double* ptrs[64] = {};
+    static std::mutex mu;
     if (dev < 0 || dev >= 64) throw Error(H2_ERR_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lk(mu);
     if (!ptrs[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -28,22 +34,28 @@ static double* noalloc_scratch_ptr(int dev) {
     return ptrs[dev];
 }
 
-// Bump allocation inside the fixed scratch; exceeding it is an error.
+// Bump allocation inside the fixed scratch.  A dry arena (base null) only
+// counts: the expansion first runs dry, issuing no device work, so that a
+// matrix whose buffers and descriptor arrays do not fit is rejected before
+// anything is queued.
 class FixedArena {
 public:
     FixedArena(double* base, size_t cap) : base_(base), cap_(cap) {}
+    bool dry() const { return base_ == nullptr; }
+    size_t used() const { return used_; }
     double* take(size_t n) {
         size_t aligned = (std::max<size_t>(n, 1) + 31) & ~(size_t)31;  // 256-byte steps
-        if (used_ + aligned > cap_)
+        if (!dry() && used_ + aligned > cap_)
             throw Error(H2_ERR_UNSUPPORTED, "matrix too large for the fixed scratch of h2_to_dense_noalloc");
-        double* p = base_ + used_;
+        double* p = dry() ? nullptr : base_ + used_;
         used_ += aligned;
         return p;
     }
     template <class T>
     T* put(const std::vector<T>& v, cudaStream_t st) {
         T* d = (T*)take((v.size() * sizeof(T) + 7) / 8);
-        if (!v.empty()) H2_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+        if (!dry() && !v.empty())
+            H2_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
         return d;
     }
 
@@ -71,33 +83,17 @@ struct GemmList {
         GTerm* dt = ar.put(terms, st);
         GJob* dj = ar.put(jobs, st);
         GTile* dti = ar.put(tiles, st);
-        launch_gemm(dt, dj, dti, (int)tiles.size(), H2_FP64, st);
+        if (!ar.dry()) launch_gemm(dt, dj, dti, (int)tiles.size(), H2_FP64, st);
         terms.clear();
         jobs.clear();
     }
 };
 
-static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaStream_t st) {
-    int dev = 0;
-    H2_CUDA(cudaGetDevice(&dev));
+// The expansion into `ar`; with a dry arena it only measures the scratch it needs.
+static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaStream_t st, FixedArena& ar) {
     const Tree& T = A->st->tree;
     const BlockTree& B = A->st->blocks;
     const int64_t n = T.n;
-    // size check before any device work: data buffers must fit with a
-    // sixteenth of the array left for the descriptor arrays
-    {
-        auto pad = [](size_t x) { return (std::max<size_t>(x, 1) + 31) & ~(size_t)31; };
-        size_t need = pad((size_t)n * n);
-        for (int c = 0; c < T.nc; ++c) {
-            need += pad((size_t)T.size[c] * std::max(1, A->V->rank[c]));
-            if (A->W != A->V) need += pad((size_t)T.size[c] * std::max(1, A->W->rank[c]));
-        }
-        for (int b = 0; b < (int)B.kind.size(); ++b)
-            if (B.kind[b] == ADM) need += pad((size_t)T.size[B.t[b]] * std::max(1, A->W->rank[B.s[b]]));
-        if (need > kNoAllocScratchDoubles - kNoAllocScratchDoubles / 16)
-            throw Error(H2_ERR_UNSUPPORTED, "matrix too large for the fixed scratch of h2_to_dense_noalloc");
-    }
-    FixedArena ar(noalloc_scratch_ptr(dev), kNoAllocScratchDoubles);
     // expanded bases: rows of the cluster x rank, level by level from the leaves
     auto expand = [&](const Basis& b) {
         std::vector<double*> ex(T.nc, nullptr);
@@ -107,7 +103,10 @@ static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaSt
             if (b.rank[c] > 0)
                 cp.push_back(CopyJob{b.leaf[c], ex[c], nullptr, 1.0, 0.0, (int)T.size[c], b.rank[c], (int)T.size[c],
                                      (int)T.size[c], 0});
-        if (!cp.empty()) launch_copy(ar.put(cp, st), (int)cp.size(), st);
+        if (!cp.empty()) {
+            CopyJob* d = ar.put(cp, st);
+            if (!ar.dry()) launch_copy(d, (int)cp.size(), st);
+        }
         GemmList g;
         for (int l = T.L - 1; l >= 0; --l) {
             for (int c = Tree::first(l); c < Tree::first(l) + Tree::count(l); ++c)
@@ -124,7 +123,7 @@ static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaSt
     auto ew = (A->W == A->V) ? ev : expand(*A->W);
     // the matrix in tree order; cleared because the scratch keeps the last call's contents
     double* dense = ar.take((size_t)n * n);
-    H2_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * n * n, st));
+    if (!ar.dry()) H2_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * n * n, st));
     GemmList g;
     std::vector<CopyJob> cp;
     std::vector<double*> tmp(B.kind.size(), nullptr);
@@ -140,7 +139,10 @@ static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaSt
         }
     }
     g.run(ar, st);
-    if (!cp.empty()) launch_copy(ar.put(cp, st), (int)cp.size(), st);
+    if (!cp.empty()) {
+        CopyJob* d = ar.put(cp, st);
+        if (!ar.dry()) launch_copy(d, (int)cp.size(), st);
+    }
     for (int b = 0; b < (int)B.kind.size(); ++b) {
         int t = B.t[b], s = B.s[b];
         if (B.kind[b] != ADM) continue;
@@ -149,9 +151,21 @@ static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaSt
     }
     g.run(ar, st);
     int64_t* d_perm = ar.put(T.perm, st);
+    if (ar.dry()) return;
     launch_scatter_dense(dense, n, d_perm, out, ld, st);
     H2_CUDA(cudaGetLastError());
     H2_CUDA(cudaStreamSynchronize(st));
+}
+
+static void to_dense_noalloc(const h2_matrix* A, double* out, int64_t ld, cudaStream_t st) {
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    FixedArena probe(nullptr, 0);  // every buffer and descriptor array, measured on the host
+    to_dense_noalloc(A, out, ld, st, probe);
+    if (probe.used() > kNoAllocScratchDoubles)
+        throw Error(H2_ERR_UNSUPPORTED, "matrix too large for the fixed scratch of h2_to_dense_noalloc");
+    FixedArena ar(noalloc_scratch_ptr(dev), kNoAllocScratchDoubles);
+    to_dense_noalloc(A, out, ld, st, ar);
 }
 
 }  // namespace h2

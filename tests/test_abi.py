@@ -86,3 +86,58 @@ def test_product_tree_counts_against_oracle(lib):
     pk = list(PT.kind.values())
     assert counts[4:7].tolist() == [pk.count(O.ADM), pk.count(O.DENSE), pk.count(O.SPLIT)]
     assert counts[7] == sum(len(v) for v in PT.triples.values())
+
+
+def _c_layout(tmp_path):
+    """sizeof/offsetof of the public structs and the enum values, from a C
+    program compiled against include/h2mul.h."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text('''#include <stddef.h>
+#include <stdio.h>
+#include "h2mul.h"
+int main(void) {
+  printf("opts %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(h2_opts), offsetof(h2_opts, eps),
+         offsetof(h2_opts, precision), offsetof(h2_opts, stream), offsetof(h2_opts, stats),
+         offsetof(h2_opts, alloc), offsetof(h2_opts, free), offsetof(h2_opts, alloc_ctx),
+         offsetof(h2_opts, autotune));
+  printf("stats %zu\\n", sizeof(h2_stats));
+  printf("info %zu\\n", sizeof(h2_info_t));
+  printf("prec %d %d %d %d %d %d %d\\n", H2_FP64, H2_MIXED, H2_TF32X3, H2_TC, H2_TF32, H2_BF16X3, H2_AUTO);
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    r = subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("no C compiler: " + r.stderr[:200])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    return {ln.split()[0]: [int(x) for x in ln.split()[1:]] for ln in out if ln.strip()}
+
+
+def test_binding_structs_match_header(tmp_path):
+    """The ctypes mirrors of h2_opts, h2_stats and h2_info_t have the C layout,
+    and the precision constants are the header's."""
+    c = _c_layout(tmp_path)
+    O_ = P.Opts
+    assert c["opts"] == [ctypes.sizeof(O_)] + [getattr(O_, f).offset for f, _ in O_._fields_]
+    assert c["stats"] == [ctypes.sizeof(P.Stats)]
+    assert c["info"] == [ctypes.sizeof(P.Info)]
+    assert c["prec"] == [P.H2_FP64, P.H2_MIXED, P.H2_TF32X3, P.H2_TC, P.H2_TF32, P.H2_BF16X3, P.H2_AUTO]
+
+
+def test_precision_and_allocator_validation_without_device(lib):
+    """An unknown precision and alloc without free are rejected before any
+    device work (H2_ERR_ARG)."""
+    o = P.Opts()
+    o.eps = 1e-6
+    o.precision = 17
+    dummy = ctypes.c_void_p(1)
+    assert lib.h2_mul_add(dummy, dummy, dummy, ctypes.byref(o)) in (-1, -2)
+    o.precision = P.H2_AUTO
+    o.alloc = P.ALLOC_FN(lambda n, s, c: None)
+    pts = np.random.default_rng(0).random((64, 3))
+    h = ctypes.c_void_p()
+    # alloc given, free missing: refused (the check runs before the device is touched)
+    assert lib.h2_build_interp(pts.ctypes.data, 64, 0, 16, 2.0, 2, ctypes.byref(o), ctypes.byref(h)) == -1

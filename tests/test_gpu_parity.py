@@ -46,7 +46,14 @@ def run_pair(pts, leaf, eta, order, eps, kx, ky, kz, precision):
     return Z, stats, st, (Xo, Yo, Zo), ref
 
 
-@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED, P.H2_TC])
+# the tolerance each precision mode is meant for: one TF32 product for eps >= 1e-4,
+# BF16 pieces for eps >= 1e-5, the others for every eps >= 1e-6
+MIN_EPS = {P.H2_FP64: 0.0, P.H2_MIXED: 1e-6, P.H2_TF32X3: 1e-6, P.H2_TF32: 1e-4, P.H2_BF16X3: 1e-5,
+           P.H2_AUTO: 0.0}
+ALL = [P.H2_FP64, P.H2_MIXED, P.H2_TF32X3, P.H2_TF32, P.H2_BF16X3, P.H2_AUTO]
+
+
+@pytest.mark.parametrize("precision", ALL)
 def test_c1_sphere_against_oracle(precision):
     """n = 2048 on the sphere, Laplace, leaf 32, eta 2, order 3, X = Y = Z, eps 1e-4."""
     eps = 1e-4
@@ -71,13 +78,16 @@ def test_exact_mode(precision, tol):
     assert rel(P.h2_to_dense(Z), ref) <= tol
 
 
-@pytest.mark.parametrize("geometry,n,leaf,eta,order,eps,kernels", [
+SHAPES = [
     ("cube_surface", 600, 16, 1.5, 2, 1e-5, (0, 0, 0)),
     ("cube", 1024, 32, 1.5, 3, 1e-4, (1, 1, 1)),
     ("cube", 1024, 32, 1.5, 3, 1e-6, (1, 0, 1)),
     ("sphere", 1000, 20, 2.0, 3, 1e-6, (0, 1, 0)),   # ragged leaves (sizes 15 and 16)
-])
-@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_MIXED, P.H2_TC])
+]
+
+
+@pytest.mark.parametrize("geometry,n,leaf,eta,order,eps,kernels,precision",
+                         [s + (p,) for s in SHAPES for p in ALL if s[5] >= MIN_EPS[p]])
 def test_workload_shapes_against_oracle(geometry, n, leaf, eta, order, eps, kernels, precision):
     pts = synth.make_points(geometry, n, 5)
     Z, stats, st, (Xo, Yo, Zo), ref = run_pair(pts, leaf, eta, order, eps, *kernels, precision)

@@ -59,3 +59,49 @@ def test_noalloc_rejects_too_large():
     with pytest.raises(P.H2Error) as e:
         P.h2_to_dense_noalloc(A, out)
     assert e.value.code == -6
+
+
+def _product_matrix(n=1024):
+    pts = synth.sphere(n, 31)
+    A = P.h2_build_interp(pts, P.H2_K_LAPLACE, 32, 2.0, 3)
+    Y = P.h2_build_interp(pts, P.H2_K_YUKAWA, 32, 2.0, 3)
+    P.h2_mul_add(A, A, Y, 1e-6)
+    return A
+
+
+def test_noalloc_leading_dimension_and_stream():
+    """ld = n + 7 on a non-default stream: rows 0..n-1 of every column equal
+    h2_to_dense, the padding rows n..ld-1 keep their NaN, two calls in a row."""
+    import torch
+    n = 1024
+    ld = n + 7
+    A = _product_matrix(n)
+    ref = torch.empty((n, n), dtype=torch.float64, device="cuda:0")
+    P.h2_to_dense(A, ref)
+    s = torch.cuda.Stream()
+    for _ in range(2):
+        out = torch.full((n, ld), float("nan"), dtype=torch.float64, device="cuda:0")  # column j = out[j]
+        torch.cuda.synchronize()
+        P.h2_to_dense_noalloc(A, out, stream=s.cuda_stream, ld=ld)
+        torch.cuda.synchronize()
+        assert bool(torch.isnan(out[:, n:]).all())
+        err = float(torch.linalg.norm(out[:, :n] - ref) / torch.linalg.norm(ref))
+        assert err <= 1e-14, err
+
+
+def test_noalloc_allocates_nothing():
+    """Free device memory is the same before and after warmed-up calls: the
+    call takes nothing from the driver, the library's pool or torch."""
+    import torch
+    n = 1024
+    A = _product_matrix(n)
+    out = torch.empty((n, n), dtype=torch.float64, device="cuda:0")
+    P.h2_to_dense_noalloc(A, out)  # warm-up: module load, symbol lookup
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(3):
+        P.h2_to_dense_noalloc(A, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
