@@ -71,13 +71,15 @@ extern "C" {
  *              operand split as a0 + a1 into two TF32 pieces, three products
  *              a0 b0 + a0 b1 + a1 b0 accumulated in FP32 in TMEM (about FP32
  *              accuracy); H2_TC is the same value
- *   H2_TF32    one TF32 product a0 b0 per pair (relative error about 2^-11 per
- *              operand; for eps >= 1e-4)
+ *   H2_TF32    one TF32 product a0 b0 per pair (operand rounding 2^-12: the
+ *              products are off by about 5e-4 relative; for eps >= 1e-3)
  *   H2_BF16X3  tensor cores with BF16 pieces (tcgen05.mma kind::f16): a0 + a1
- *              with 8 significant bits each, three products (about 2^-16)
- *   H2_AUTO    chosen by eps: H2_TF32 for eps >= 1e-4, H2_BF16X3 for
- *              1e-5 <= eps < 1e-4, H2_TF32X3 below 1e-5 (three-term products
- *              where eps < 1e-5), H2_FP64 for eps < 1e-7 (exact mode included)
+ *              with 8 significant bits each, three products (about 2^-17 on
+ *              the whole, single blocks up to 3e-5; for eps >= 1e-4)
+ *   H2_AUTO    chosen by eps: H2_TF32 for eps >= 1e-3, H2_BF16X3 for
+ *              1e-4 <= eps < 1e-3, H2_TF32X3 below 1e-4 (three-term products
+ *              wherever eps < 1e-5), H2_FP64 for eps < 1e-7 (exact mode
+ *              included)
  * In every mode but H2_FP64 the wide-to-square reduction ahead of each SVD
  * runs in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the
  * weights' Gram matrices and the other products that must be FP64-accurate
@@ -164,12 +166,13 @@ typedef struct {
     /* Nonzero: the library tunes its launch schedules online.  Each batch of
      * products is keyed by (kernel family, number of output tiles, K per
      * tile); the first batches of a key run the candidate schedules in turn
-     * (split-K off or over 2, 4 or 8 slices, and for the FP32-class products
-     * the CUDA-core kernel against the tensor-core kernel when both meet the
-     * precision mode's accuracy), their device times are read when the call
-     * ends, and later batches of the key run the fastest.  The choices are kept
-     * per device for the life of the process.  Every candidate computes the
-     * same products, so results agree to rounding. */
+     * (for the FP32-class products the mode's kernel or the other one --
+     * CUDA-core FP32 against the tensor cores, at least as accurate -- with
+     * split-K by the default rule or off; for the others split-K by the
+     * default rule, off, or over 2 or 4 slices), their device times are read
+     * when the call ends, and later batches of the key run the fastest.  The
+     * choices are kept per device for the life of the process.  Every
+     * candidate computes the same products, so results agree to rounding. */
     int autotune;
 } h2_opts;
 

@@ -223,11 +223,21 @@ double* Arena::alloc(size_t n) {
 #endif
     if (bytes > left_) {
         const size_t sz = std::max(bytes, chunk_min);
-        const DevAlloc& src = current_alloc();
-        void* p = dev_get(src, sz, st_, true);
-        chunks_.push_back(Chunk{p, sz, src});
-        cur_ = (char*)p;
-        left_ = sz;
+        // a chunk released earlier in the call is reused first: work on this stream
+        // that used it is ordered before any later work
+        int pick = -1;
+        for (int i = 0; i < (int)spare_.size(); ++i)
+            if (spare_[i].bytes >= sz && (pick < 0 || spare_[i].bytes < spare_[pick].bytes)) pick = i;
+        if (pick >= 0) {
+            chunks_.push_back(spare_[pick]);
+            spare_.erase(spare_.begin() + pick);
+        } else {
+            const DevAlloc& src = current_alloc();
+            void* p = dev_get(src, sz, st_, true);
+            chunks_.push_back(Chunk{p, sz, src});
+        }
+        cur_ = (char*)chunks_.back().p;
+        left_ = chunks_.back().bytes;
     }
     double* out = (double*)cur_;
     cur_ += bytes;
@@ -236,9 +246,18 @@ double* Arena::alloc(size_t n) {
 }
 
 void Arena::release(const Mark& m) {
+    // keep up to 1 GiB of released chunks for reuse (fewer allocator calls per
+    // level); the rest goes back to its source, where other arenas can use it
+    size_t kept = 0;
+    for (const Chunk& c : spare_) kept += c.bytes;
     while (chunks_.size() > m.nchunks) {
         const Chunk& c = chunks_.back();
-        dev_put(c.src, c.p, c.bytes, st_, true);
+        if (kept + c.bytes <= ((size_t)1 << 30)) {
+            kept += c.bytes;
+            spare_.push_back(c);
+        } else {
+            dev_put(c.src, c.p, c.bytes, st_, true);
+        }
         chunks_.pop_back();
     }
     cur_ = m.cur;
@@ -247,7 +266,9 @@ void Arena::release(const Mark& m) {
 
 void Arena::release_all() {
     for (const Chunk& c : chunks_) dev_put(c.src, c.p, c.bytes, st_, true);
+    for (const Chunk& c : spare_) dev_put(c.src, c.p, c.bytes, st_, true);
     chunks_.clear();
+    spare_.clear();
     cur_ = nullptr;
     left_ = 0;
 }
@@ -400,7 +421,7 @@ void Tuner::report(uint64_t key, int cand, double ms_per_gflop) {
     e.timed[cand]++;
     if (e.best >= 0) return;
     for (int i = 0; i < e.ncand; ++i)
-        if (e.timed[i] < 2) return;
+        if (e.timed[i] < 1) return;
     int b = 0;
     for (int i = 1; i < e.ncand; ++i)
         if (e.cost[i] / e.timed[i] < e.cost[b] / e.timed[b]) b = i;
@@ -438,10 +459,14 @@ void Runner::flush_gemm(int precision_override) {
         const int64_t tiles = std::max<int64_t>(1, pend_tiles64_);
         tkey = ((uint64_t)(pr & 0xff) << 16) | ((uint64_t)ilog2((double)tiles) << 8) |
                (uint64_t)ilog2(chunks / (double)tiles);
-        tcand = Tuner::get().pick(tkey, f32class ? 8 : 4);
-        const int sp[4] = {0, 1, 2, 4};
-        force_split = sp[tcand & 3];
-        if (tcand >= 4) pr = (pr == H2_MIXED) ? H2_TF32X3 : H2_MIXED;  // the other FP32-class kernel
+        tcand = Tuner::get().pick(tkey, 4);
+        if (f32class) {  // (kernel: own, other) x (split-K: default rule, off)
+            force_split = (tcand & 1) ? 1 : 0;
+            if (tcand >= 2) pr = (pr == H2_MIXED) ? H2_TF32X3 : H2_MIXED;  // the other FP32-class kernel
+        } else {  // split-K: default rule, off, 2 or 4 slices
+            const int sp[4] = {0, 1, 2, 4};
+            force_split = sp[tcand];
+        }
     }
     const bool tc = tc_precision(pr);
     const bool f32 = (pr == H2_MIXED || pr == kGemmDF);
@@ -469,7 +494,12 @@ void Runner::flush_gemm(int precision_override) {
                      sn / nj, sk / nj, (long long)small, mm, mn);
     }
     std::vector<SliceSum> sums;
-    if (!tc || force_split >= 2) split_k(pr, tm, sums, nt_est, force_split);
+    int64_t nt_all = nt_est;
+    if (nt_all < 0) {  // rectangular tiles (tensor cores): count them
+        nt_all = 0;
+        for (const GJob& J : jobs_) nt_all += (int64_t)((J.m + tm - 1) / tm) * ((J.n + tn - 1) / tn);
+    }
+    split_k(pr, tm, sums, nt_all, force_split);
     std::vector<GTile>& tiles = tiles_;
     tiles.clear();
     if (nt_est > 0) tiles.reserve((size_t)nt_est);
@@ -516,7 +546,7 @@ void Runner::flush_gemm(int precision_override) {
 void Runner::split_k(int pr, int tile, std::vector<SliceSum>& sums, int64_t ntiles, int force) {
     if (force == 1) return;
     const int kc = (pr == kGemmDF || pr == H2_FP64) ? 16 : 32;  // K chunk of the kernel
-    const int per_sm = (pr == kGemmDF) ? 2 : (pr == H2_MIXED) ? 3 : 4;
+    const int per_sm = (pr == kGemmDF || tc_precision(pr)) ? 2 : (pr == H2_MIXED) ? 3 : 4;  // resident CTAs
     const int64_t target = 2LL * device_sm_count() * per_sm;
     if (ntiles < 0) {  // tiles of the batch, unless counted while it was built
         ntiles = 0;

@@ -323,14 +323,16 @@ inline bool low_precision(int precision) { return precision != H2_FP64; }
 inline bool valid_precision(int p) { return p >= H2_FP64 && p <= H2_AUTO; }
 // the FP32-class products run on the tensor cores
 inline bool tc_precision(int p) { return p == H2_TF32X3 || p == H2_TF32 || p == H2_BF16X3; }
-// H2_AUTO by tolerance: one TF32 product where its 2^-11 operand rounding stays
-// an order below eps, BF16 pieces (2^-16) down to 1e-5, three-term TF32 products
-// (about FP32 accuracy) below that, and FP64 where a Gram matrix in FP32-class
-// arithmetic could no longer resolve the singular values the tolerance keeps
+// H2_AUTO by tolerance: one TF32 product (operand rounding 2^-12, products off
+// by about 5e-4) only from eps = 1e-3 up, BF16 pieces (about 2^-17, single
+// blocks off by up to 3e-5) down to 1e-4, three-term TF32 products (about FP32
+// accuracy) below that, and FP64
+// where a Gram matrix in FP32-class arithmetic could no longer resolve the
+// singular values the tolerance keeps
 inline int resolve_precision(int p, double eps) {
     if (p != H2_AUTO) return p;
-    if (eps >= 1e-4) return H2_TF32;
-    if (eps >= 1e-5) return H2_BF16X3;
+    if (eps >= 1e-3) return H2_TF32;
+    if (eps >= 1e-4) return H2_BF16X3;
     if (eps >= 1e-7) return H2_TF32X3;
     return H2_FP64;
 }
@@ -408,6 +410,7 @@ private:
     };
     cudaStream_t st_;
     std::vector<Chunk> chunks_;
+    std::vector<Chunk> spare_;  // released chunks, reused by later allocations of the call
     char* cur_ = nullptr;
     size_t left_ = 0;
 };
@@ -415,14 +418,15 @@ private:
 // Online tuner of GEMM launch schedules (h2_opts.autotune), process-wide.  A
 // batch is keyed by its kernel family and the logarithms of its tile count and
 // of its K chunks per tile.  The candidates of a key run in turn until each
-// has been timed twice (the times arrive when a call collects its launch
-// events); from then on the cheapest, in device milliseconds per GFLOP, runs.
-// Candidates: split-K by the default rule, off, or over 2 or 4 slices; for the
-// FP32-class products also the other kernel (CUDA-core FP32 against the
-// tensor-core mode), whose accuracy is at least the mode's.
+// has been timed (the times arrive when a call collects its launch events);
+// from then on the cheapest, in device milliseconds per GFLOP, runs.
+// Candidates: for the FP32-class products the mode's kernel or the other one
+// (CUDA-core FP32 against the tensor-core mode, at least as accurate), each
+// with split-K by the default rule or off; for the others split-K by the
+// default rule, off, or over 2 or 4 slices.
 class Tuner {
 public:
-    static constexpr int kCand = 8;  // (kernel: own, other) x (split: default, off, 2, 4)
+    static constexpr int kCand = 4;
     static Tuner& get();
     int pick(uint64_t key, int ncand);
     void report(uint64_t key, int cand, double ms_per_gflop);

@@ -425,17 +425,18 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
 
 // ------------------------------------------------------------------ GEMM on tcgen05
 // Same contract as k_gemm on the 5th-generation tensor cores, for the FP32-class
-// products of the tensor-core modes.  One CTA computes a 128 x 64 output tile
-// of one job and is warp-specialised:
-//   warps 0-3  producers: each K chunk of 32 (term, k) pairs is read from the
-//              FP64 operands, rounded to FP32 (integer operations), split into
-//              pieces and stored in shared memory in the K-major core-matrix
-//              layout (8 rows x 16 bytes per core matrix, the cores of a row
-//              group contiguous along K), two stages deep;
-//   warp 4     one lane issues tcgen05.mma for every ready stage and commits
-//              the stage and the accumulator groups to mbarriers;
-//   warps 0-3  again, as the epilogue: tcgen05.ld of the accumulators (warp w
-//              owns TMEM lanes 32w..32w+31, i.e. tile rows 32w..32w+31).
+// products of the tensor-core modes.  One CTA of 8 warps computes a 128 x 64
+// output tile of one job:
+//   - every warp stages its share of each K chunk of 32 (term, k) pairs: the
+//     FP64 operands are read, rounded to FP32 (integer operations), split into
+//     pieces and stored in shared memory in the K-major core-matrix layout
+//     (8 rows x 16 bytes per core matrix, the cores of a row group contiguous
+//     along K), two stages deep;
+//   - thread 0 issues tcgen05.mma for each staged chunk and commits the stage
+//     and the accumulator groups to mbarriers;
+//   - every warp adds finished accumulator groups into registers and writes the
+//     tile at the end: tcgen05.ld of TMEM lanes 32 (w mod 4) .. + 31 (those tile
+//     rows) and columns 32 (w / 4) .. + 31.
 // Pieces and products per mode:
 //   TF32X3  x = a0 + a1 (two TF32 values, each rounded to nearest);
 //           a0 b0 into D0, a0 b1 + a1 b0 into D1
@@ -443,15 +444,16 @@ void launch_gemm(const GTerm* terms, const GJob* jobs, const GTile* tiles, int n
 //   BF16X3  x = a0 + a1 (two BF16 values); a0 b0 into D0, a0 b1 + a1 b0 into D1
 // The tensor cores' FP32 accumulation rounds toward zero, so its error is a
 // bias that grows with the number of accumulation steps.  In the three-term
-// modes D0 (the leading product) therefore holds one chunk at a time: two D0
-// buffers alternate, and while the MMAs fill one, the producers add the other
-// into FP32 registers with round to nearest.  D1 is 2^-11 (TF32) or 2^-8
+// modes D0 (the leading product) therefore holds one chunk at a time: three D0
+// buffers rotate, and while the MMAs fill one, the producers add the one two
+// chunks back into FP32 registers with round to nearest.  D1 is 2^-11 (TF32) or 2^-8
 // (BF16) smaller, so its bias is negligible and it accumulates over the whole
 // job; so does D0 in the one-product mode, whose operand rounding (2^-11) is far
 // above that bias.  Every wait is bounded (about a second): on timeout the CTA
 // sets bit 4 of *err, stops, drains its MMAs and frees its TMEM.
-constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 160;  // 4 producer warps + 1 MMA warp
-constexpr int TC_PRODUCERS = 128;
+constexpr int TC_M = 128, TC_N = 64, TC_K = 32, TC_T = 256;  // 8 warps, all producers
+constexpr int TC_PRODUCERS = 256, TC_PW = TC_PRODUCERS / 32;
+constexpr int TC_TCACHE = 64;  // term descriptors cached in shared memory
 
 template <int MODE>
 struct TcCfg {
@@ -466,7 +468,7 @@ struct TcCfg {
     static constexpr int stage = pieces * (a_piece + b_piece);
     static constexpr int flush = three ? 1 : (1 << 30);  // chunks per D0 group
     static constexpr int kstep = bf16 ? 16 : 8;          // K of one MMA
-    static constexpr int cols = three ? 256 : 128;       // TMEM columns: D0 x 2 (+ D1)
+    static constexpr int cols = 256;                     // TMEM columns: D0 x 3 (+ D1)
     // shared memory: two stages, then the barriers and the stage flags; at least
     // 80 KB, so that at most two CTAs share an SM (their TMEM columns always fit)
     static constexpr int bar_off = 2 * stage;
@@ -570,85 +572,101 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, const uint32_t* w) {
                  : "memory");
 }
 
-// One operand tile of a K chunk into shared memory (producer warps).  Item
+// Staging of one operand tile of a K chunk (producer warps), in two steps so
+// that the loads of both operands are in flight together: tc_load reads this
+// thread's items from global memory, tc_store converts and stores them.  Item
 // (row r, K group q) is the 16 bytes of row r in core matrix q of its row group
 // (ke consecutive k); a warp stores 8 rows x 4 K groups, i.e. 4 consecutive
 // 128-byte cores: conflict-free 16-byte stores.  Element (r, k) of the tile is
 // base[r * ld + k] (kcontig) or base[r + k * ld]; rows >= rows_valid are not
 // written (they were zeroed once), k >= kvalid is stored as zero.  The second
-// piece (three-term modes) goes to dst + pstride.  Four items are loaded before
-// any is converted, to keep loads in flight.
-template <int MODE>
-__device__ __forceinline__ void tc_stage(uint32_t dst, uint32_t pstride, const double* base, int ld, bool kcontig,
-                                         int rows_valid, int kvalid, int nrows, float scale, int warp, int lane) {
-    using C = TcCfg<MODE>;
-    constexpr int KE = C::ke, QW = C::cores_k / 4;  // K groups of 4 cores per row group
-    const int ngroups = (nrows / 8) * QW;           // warp items of the tile
-    for (int g0 = warp; g0 < ngroups; g0 += 16) {
-        double v[4][KE];
+// piece (three-term modes) goes to dst + pstride.  Warp w takes the row groups
+// w, w + 8, ... (NI items per thread).
+template <int MODE, int NROWS>
+struct TcOp {
+    static constexpr int QW = TcCfg<MODE>::cores_k / 4;  // K groups of 4 cores per row group
+    static constexpr int NI = (NROWS / 8) * QW / TC_PW;   // items per producer thread
+    static constexpr int KE = TcCfg<MODE>::ke;
+};
+
+template <int MODE, int NROWS>
+__device__ __forceinline__ void tc_load(double (&v)[TcOp<MODE, NROWS>::NI][TcOp<MODE, NROWS>::KE], const double* base,
+                                        int ld, bool kcontig, int rows_valid, int kvalid, int warp, int lane) {
+    using O = TcOp<MODE, NROWS>;
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int g = g0 + 4 * h;
-            const int r = (g / QW) * 8 + (lane & 7), q = (g % QW) * 4 + (lane >> 3);
+    for (int h = 0; h < O::NI; ++h) {
+        const int g = warp + TC_PW * h;
+        const int r = (g / O::QW) * 8 + (lane & 7), q = (g % O::QW) * 4 + (lane >> 3);
 #pragma unroll
-            for (int e = 0; e < KE; ++e) {
-                const int k = q * KE + e;
-                const bool in = g < ngroups && r < rows_valid && k < kvalid;
-                v[h][e] = in ? (kcontig ? base[(size_t)r * ld + k] : base[r + (size_t)k * ld]) : 0.0;
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            const int g = g0 + 4 * h;
-            const int r8 = g / QW, q = (g % QW) * 4 + (lane >> 3);
-            if (g >= ngroups || r8 * 8 >= rows_valid) continue;
-            const uint32_t addr = dst + (uint32_t)((r8 * C::cores_k + q) * 128 + (lane & 7) * 16);
-            uint32_t w0[4], w1[4];
-            if constexpr (C::bf16) {
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    const float x0 = scale * f64_to_f32(v[h][e]), x1 = scale * f64_to_f32(v[h][e + 1]);
-                    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-                    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-                    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-                    w0[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                    w1[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float x = scale * f64_to_f32(v[h][e]);
-                    w0[e] = tf32_rn(x);
-                    w1[e] = C::three ? tf32_rn(x - __uint_as_float(w0[e])) : 0u;
-                }
-            }
-            st_shared_v4(addr, w0);
-            if constexpr (C::three) st_shared_v4(addr + pstride, w1);
+        for (int e = 0; e < O::KE; ++e) {
+            const int k = q * O::KE + e;
+            const bool in = r < rows_valid && k < kvalid;
+            v[h][e] = in ? (kcontig ? base[(size_t)r * ld + k] : base[r + (size_t)k * ld]) : 0.0;
         }
     }
 }
 
-// Stage flags (one int per stage, written by producer 0 before the producers
-// arrive on the stage's barrier): bit 0 a chunk is present, bit 1 it opens a D0
-// group, bit 2 it closes one, bit 3 it is the job's last chunk.
+template <int MODE, int NROWS>
+__device__ __forceinline__ void tc_store(const double (&v)[TcOp<MODE, NROWS>::NI][TcOp<MODE, NROWS>::KE], uint32_t dst,
+                                         uint32_t pstride, int rows_valid, float scale, int warp, int lane) {
+    using C = TcCfg<MODE>;
+    using O = TcOp<MODE, NROWS>;
+#pragma unroll
+    for (int h = 0; h < O::NI; ++h) {
+        const int g = warp + TC_PW * h;
+        const int r8 = g / O::QW, q = (g % O::QW) * 4 + (lane >> 3);
+        if (r8 * 8 >= rows_valid) continue;
+        const uint32_t addr = dst + (uint32_t)((r8 * C::cores_k + q) * 128 + (lane & 7) * 16);
+        uint32_t w0[4], w1[4];
+        if constexpr (C::bf16) {
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                const float x0 = scale * f64_to_f32(v[h][e]), x1 = scale * f64_to_f32(v[h][e + 1]);
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+                w0[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                w1[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = (scale == 1.f) ? f64_to_f32(v[h][e]) : scale * f64_to_f32(v[h][e]);
+                w0[e] = tf32_rn(x);
+                w1[e] = C::three ? tf32_rn(x - __uint_as_float(w0[e])) : 0u;
+            }
+        }
+        st_shared_v4(addr, w0);
+        if constexpr (C::three) st_shared_v4(addr + pstride, w1);
+    }
+}
+
+// One CTA per output tile; its 8 warps stage the K chunks (all of them), and
+// thread 0 also issues the MMAs: after arriving on a stage's barrier it waits
+// for the other warps' arrivals (their shared-memory stores are then visible),
+// issues the stage's MMAs and commits them to the stage's "empty" barrier and,
+// at the end of a D0 group, to the group's "full" barrier.  Two CTAs share an
+// SM (16 warps, 4 per SM sub-partition: at most 128 registers a thread), so one
+// CTA's epilogue and prologue overlap the other's main loop.
 template <int MODE>
-__global__ void __launch_bounds__(TC_T, 2) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
-                                                     const GTile* __restrict__ tiles, int* err) {
+__global__ void __maxnreg__(128) k_gemm_tc(const GTerm* __restrict__ terms, const GJob* __restrict__ jobs,
+                                           const GTile* __restrict__ tiles, int* err) {
     using C = TcCfg<MODE>;
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tc_smem);
-    // barriers: full[2] 0..1, empty[2] 2..3, accf[2] 4..5, acce[2] 6..7, drain 8
+    // barriers: full[2] 0..1, empty[2] 2..3, accf[3] 4..6, acce[3] 7..9, drain 10
     const uint32_t bar0 = sbase + C::bar_off;
-    volatile int* sflag = (volatile int*)(tc_smem + C::bar_off + 80);  // [2]
-    volatile int* abort_flag = sflag + 2;
-    uint32_t* tmem_slot = (uint32_t*)(tc_smem + C::bar_off + 96);
+    volatile int* abort_flag = (volatile int*)(tc_smem + C::bar_off + 96);
+    uint32_t* tmem_slot = (uint32_t*)(tc_smem + C::bar_off + 112);
     auto full = [&](int s) { return bar0 + 8u * s; };
     auto empty = [&](int s) { return bar0 + 16u + 8u * s; };
     auto accf = [&](int b) { return bar0 + 32u + 8u * b; };
-    auto acce = [&](int b) { return bar0 + 48u + 8u * b; };
-    const uint32_t drain = bar0 + 64u;
+    auto acce = [&](int b) { return bar0 + 56u + 8u * b; };
+    const uint32_t drain = bar0 + 80u;
     // after a timeout anywhere in the call, later CTAs do nothing (one read, shared by the CTA)
     __shared__ int skip;
+    __shared__ GTerm tcache[TC_TCACHE];
+    __shared__ float tfact[TC_TCACHE];
     if (threadIdx.x == 0) skip = err ? (*(volatile int*)err & 4) : 0;
     __syncthreads();
     if (skip) return;
@@ -665,12 +683,21 @@ __global__ void __launch_bounds__(TC_T, 2) k_gemm_tc(const GTerm* __restrict__ t
         for (int s = 0; s < 2; ++s) {
             mbar_init(full(s), TC_PRODUCERS);
             mbar_init(empty(s), 1);
-            mbar_init(accf(s), 1);
-            mbar_init(acce(s), TC_PRODUCERS);
+        }
+        for (int b = 0; b < 3; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), TC_PRODUCERS);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // the job's first term descriptors, with their factors in FP32 (0: skipped)
+    for (int q = threadIdx.x; q < min(J.nt, TC_TCACHE); q += TC_T) {
+        const GTerm t = terms[J.t0 + q];
+        const double f = t.alpha * (t.scale ? *t.scale : 1.0);
+        tcache[q] = t;
+        tfact[q] = (f != 0.0 && t.k > 0) ? f64_to_f32(f) : 0.f;
     }
     // rows of A and B beyond the job stay zero in both stages
     const int mrows = min(TC_M, J.m - tile.i0), ncols = min(TC_N, J.n - tile.j0);
@@ -689,26 +716,104 @@ __global__ void __launch_bounds__(TC_T, 2) k_gemm_tc(const GTerm* __restrict__ t
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            bool d1_started = false;
-            int g = 0;  // D0 group index
-            for (int c = 0;; ++c) {
-                const int s = c & 1;
-                if (!mbar_wait(full(s), (uint32_t)((c >> 1) & 1), abort_flag, err)) break;
-                const int f = sflag[s];
-                if (!(f & 1)) break;
-                const int b = g & 1;
-                if ((f & 2) && g >= 2 && !mbar_wait(acce(b), (uint32_t)(((g - 2) >> 1) & 1), abort_flag, err)) break;
+    // accumulators: warp w reads tile rows 32 (w mod 4) .. + 31 (its TMEM lanes)
+    // and columns 32 (w / 4) .. + 31
+    float acc[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+    const int quarter = warp & 3, chalf = warp >> 2;
+    const uint32_t lane_base = ((uint32_t)(quarter * 32) << 16) + (uint32_t)(chalf * 32);
+    // adds D0 group g into acc; its MMAs are complete once accf(g mod 3) fires
+    auto read_group = [&](int g) -> bool {
+        const int b = g % 3;
+        // one decision per warp: tcgen05.ld needs the whole warp
+        if (!__all_sync(0xffffffffu, mbar_wait(accf(b), (uint32_t)((g / 3) & 1), abort_flag, err))) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(b * TC_N), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] += v[j];
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(acce(b));
+        return true;
+    };
+    // chunk sequence: (term it, k0) over the job's terms, skipping zero factors.
+    // The first TC_TCACHE term descriptors and their FP32 factors were staged
+    // in shared memory above (a branch on a descriptor fresh from global memory
+    // would stall the warp for a full load latency); later terms of long jobs
+    // are read from global memory.
+    int it = -1, k0 = 0;
+    GTerm P{};
+    float fs = 0.f;
+    auto term_at = [&](int i) {
+        if (i < TC_TCACHE) {
+            P = tcache[i];
+            fs = tfact[i];
+        } else {
+            P = terms[J.t0 + i];
+            const double f = P.alpha * (P.scale ? *P.scale : 1.0);
+            fs = (f != 0.0 && P.k > 0) ? f64_to_f32(f) : 0.f;
+        }
+    };
+    auto advance = [&]() -> bool {
+        if (it >= 0 && k0 + TC_K < P.k) {
+            k0 += TC_K;
+            return true;
+        }
+        for (++it; it < J.nt; ++it) {
+            term_at(it);
+            if (fs != 0.f) {
+                k0 = 0;
+                return true;
+            }
+        }
+        return false;
+    };
+    bool ok = true, d1_started = false;
+    bool have = advance();
+    int c = 0, in_group = 0, g = 0, g_read = 0;
+    while (have) {
+        const int s = c & 1;
+        const GTerm Q = P;
+        const int q0 = k0;
+        const float qs = fs;
+        const bool more = advance();
+        const int kvalid = min(TC_K, Q.k - q0);
+        // A (m x k) rows i0.., k q0..: plain A[i + k lda], transposed A[k + i lda]
+        const double* ab = Q.ta ? Q.A + q0 + (size_t)tile.i0 * Q.lda : Q.A + tile.i0 + (size_t)q0 * Q.lda;
+        // B (k x n) as rows j0.. of B^T: plain B[k + j ldb], transposed B[j + k ldb]
+        const double* bb = Q.tb ? Q.B + tile.j0 + (size_t)q0 * Q.ldb : Q.B + q0 + (size_t)tile.j0 * Q.ldb;
+        double va[TcOp<MODE, TC_M>::NI][TcOp<MODE, TC_M>::KE], vb[TcOp<MODE, TC_N>::NI][TcOp<MODE, TC_N>::KE];
+        tc_load<MODE, TC_M>(va, ab, Q.lda, Q.ta != 0, mrows, kvalid, warp, lane);
+        tc_load<MODE, TC_N>(vb, bb, Q.ldb, Q.tb == 0, ncols, kvalid, warp, lane);
+        // the stage's previous chunk (c - 2) must be consumed before it is overwritten
+        if (c >= 2 &&
+            !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)(((c >> 1) + 1) & 1), abort_flag, err))) {
+            ok = false;
+            break;
+        }
+        const uint32_t sa = sbase + s * C::stage, sb = sa + C::pieces * C::a_piece;
+        tc_store<MODE, TC_M>(va, sa, C::a_piece, mrows, qs, warp, lane);
+        tc_store<MODE, TC_N>(vb, sb, C::b_piece, ncols, 1.f, warp, lane);
+        const bool opens = (in_group == 0);
+        const bool closes = (in_group + 1 == C::flush) || !more;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(full(s));
+        if (threadIdx.x == 0) {
+            // the MMAs of this chunk, once every warp has staged it; D0 group g uses
+            // buffer g mod 3, whose last use (group g - 3) was read out before
+            // the warps arrived on this stage
+            const int b = g % 3;
+            bool go = mbar_wait(full(s), (uint32_t)((c >> 1) & 1), abort_flag, err);
+            if (go && opens && g >= 3) go = mbar_wait(acce(b), (uint32_t)((g / 3 - 1) & 1), abort_flag, err);
+            if (go) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t sa = sbase + s * C::stage, sb = sa + C::pieces * C::a_piece;
-                const uint32_t d0 = tmem + (uint32_t)(b * TC_N), d1 = tmem + 2u * TC_N;
+                const uint32_t d0 = tmem + (uint32_t)(b * TC_N), d1 = tmem + 3u * TC_N;
 #pragma unroll
                 for (int ks = 0; ks < TC_K / C::kstep; ++ks) {
                     const uint32_t off = ks * 256;  // two core matrices along K per MMA
                     const uint64_t a0 = tc_desc(sa + off, C::cores_k), b0 = tc_desc(sb + off, C::cores_k);
-                    tc_mma<MODE>(d0, a0, b0, ((f & 2) && ks == 0) ? 0u : 1u);
+                    tc_mma<MODE>(d0, a0, b0, (opens && ks == 0) ? 0u : 1u);
                     if constexpr (C::three) {
                         const uint64_t a1 = tc_desc(sa + C::a_piece + off, C::cores_k);
                         const uint64_t b1 = tc_desc(sb + C::b_piece + off, C::cores_k);
@@ -718,126 +823,50 @@ __global__ void __launch_bounds__(TC_T, 2) k_gemm_tc(const GTerm* __restrict__ t
                     }
                 }
                 tc_commit(empty(s));  // the stage may be refilled once these MMAs are done
-                if (f & 4) {
-                    tc_commit(accf(b));
-                    ++g;
-                }
-                if (f & 8) break;
-            }
-            // drain: every MMA issued has completed before TMEM is freed
-            tc_commit(drain);
-            const uint64_t t0 = global_ns();
-            while (!mbar_try(drain, 0u) && global_ns() - t0 < 1000000000ull) {
+                if (closes) tc_commit(accf(b));
             }
         }
         __syncwarp();
-    } else {
-        // ---------------- producers, then the epilogue (warp w: tile rows 32 w .. 32 w + 31)
-        float acc[TC_N];
-#pragma unroll
-        for (int j = 0; j < TC_N; ++j) acc[j] = 0.f;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        // adds D0 group g into acc; its MMAs are complete once accf(g & 1) fires
-        auto read_group = [&](int g) -> bool {
-            const int b = g & 1;
-            // one decision per warp: tcgen05.ld needs the whole warp
-            if (!__all_sync(0xffffffffu, mbar_wait(accf(b), (uint32_t)((g >> 1) & 1), abort_flag, err))) return false;
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            float v[32];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                tmem_ld32(tmem + lane_base + (uint32_t)(b * TC_N + 32 * h), v);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) acc[32 * h + j] += v[j];
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(acce(b));
-            return true;
-        };
-        // chunk sequence: (term it, k0) over the job's terms, skipping zero factors
-        int it = -1, k0 = 0;
-        GTerm P{};
-        double fct = 0.0;
-        auto advance = [&]() -> bool {
-            if (it >= 0 && k0 + TC_K < P.k) {
-                k0 += TC_K;
-                return true;
-            }
-            for (++it; it < J.nt; ++it) {
-                P = terms[J.t0 + it];
-                fct = P.alpha * (P.scale ? *P.scale : 1.0);
-                if (fct != 0.0 && P.k > 0) {
-                    k0 = 0;
-                    return true;
-                }
-            }
-            return false;
-        };
-        bool ok = true;
-        bool have = advance();
-        int c = 0, in_group = 0, g = 0;
-        if (!have) {  // no chunk: tell the MMA warp
-            if (threadIdx.x == 0) sflag[0] = 0;
-            mbar_arrive(full(0));
-        }
-        while (have) {
-            const int s = c & 1;
-            const GTerm Q = P;
-            const int q0 = k0;
-            const float fs = f64_to_f32(fct);
-            const bool more = advance();
-            if (c >= 2 &&
-                !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)(((c >> 1) + 1) & 1), abort_flag, err))) {
+        // the group two before this one is long complete: add it up while the MMAs run
+        if (opens && g >= 2 && g_read <= g - 2) {
+            if (!read_group(g_read)) {
                 ok = false;
                 break;
             }
-            const uint32_t sa = sbase + s * C::stage, sb = sa + C::pieces * C::a_piece;
-            const int kvalid = min(TC_K, Q.k - q0);
-            // A (m x k) rows i0.., k q0..: plain A[i + k lda], transposed A[k + i lda]
-            const double* ab = Q.ta ? Q.A + q0 + (size_t)tile.i0 * Q.lda : Q.A + tile.i0 + (size_t)q0 * Q.lda;
-            tc_stage<MODE>(sa, C::a_piece, ab, Q.lda, Q.ta != 0, mrows, kvalid, TC_M, fs, warp, lane);
-            // B (k x n) as rows j0.. of B^T: plain B[k + j ldb], transposed B[j + k ldb]
-            const double* bb = Q.tb ? Q.B + tile.j0 + (size_t)q0 * Q.ldb : Q.B + q0 + (size_t)tile.j0 * Q.ldb;
-            tc_stage<MODE>(sb, C::b_piece, bb, Q.ldb, Q.tb == 0, ncols, kvalid, TC_N, 1.f, warp, lane);
-            const bool opens = (in_group == 0);
-            const bool closes = (in_group + 1 == C::flush) || !more;
-            if (threadIdx.x == 0) sflag[s] = 1 | (opens ? 2 : 0) | (closes ? 4 : 0) | (more ? 0 : 8);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(full(s));
-            // the group before this one is complete: add it up while the MMAs run
-            if (opens && g >= 1 && !read_group(g - 1)) {
-                ok = false;
-                break;
-            }
-            in_group = closes ? 0 : in_group + 1;
-            if (closes) ++g;
-            ++c;
-            have = more;
+            ++g_read;
         }
-        if (ok && c > 0) ok = read_group(g - 1);
-        if (ok && c > 0 && C::three) {  // D1 (complete with the last group)
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            float v[32];
+        in_group = closes ? 0 : in_group + 1;
+        if (closes) ++g;
+        ++c;
+        have = more;
+    }
+    while (ok && g_read < g) ok = read_group(g_read++);
+    if (ok && c > 0 && C::three) {  // D1 (complete with the last group)
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        float v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(3 * TC_N), v);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                tmem_ld32(tmem + lane_base + (uint32_t)(2 * TC_N + 32 * h), v);
+        for (int j = 0; j < 32; ++j) acc[j] += v[j];
+    }
+    if (ok && !*abort_flag) {
+        const int row = tile.i0 + quarter * 32 + lane;
+        if (row < J.m) {
+            const bool beta0 = (__double_as_longlong(J.beta) << 1) == 0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) acc[32 * h + j] += v[j];
-            }
-        }
-        if (ok && !*abort_flag) {
-            const int row = tile.i0 + warp * 32 + lane;
-            if (row < J.m) {
-                const bool beta0 = (__double_as_longlong(J.beta) << 1) == 0;
-#pragma unroll
-                for (int j = 0; j < TC_N; ++j) {
-                    if (j < ncols) {
-                        double* cp = J.C + row + (size_t)(tile.j0 + j) * J.ldc;
-                        const double val = f32_to_f64(acc[j]);
-                        *cp = beta0 ? val : J.beta * *cp + val;
-                    }
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = chalf * 32 + jj;
+                if (j < ncols) {
+                    double* cp = J.C + row + (size_t)(tile.j0 + j) * J.ldc;
+                    const double val = f32_to_f64(acc[jj]);
+                    *cp = beta0 ? val : J.beta * *cp + val;
                 }
             }
+        }
+    }
+    if (threadIdx.x == 0 && c > 0) {  // drain: every MMA issued has completed before TMEM is freed
+        tc_commit(drain);
+        const uint64_t t0 = global_ns();
+        while (!mbar_try(drain, 0u) && global_ns() - t0 < 1000000000ull) {
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -855,6 +884,9 @@ static void launch_tc(const GTerm* terms, const GJob* jobs, const GTile* tiles, 
         std::lock_guard<std::mutex> lk(mu);
         if (dev >= 0 && dev < 64 && !attr_set[dev]) {
             cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<MODE>::smem);
+            // all of the unified L1/shared storage as shared memory: two CTAs per SM
+            cudaFuncSetAttribute(k_gemm_tc<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
             attr_set[dev] = true;
         }
     }

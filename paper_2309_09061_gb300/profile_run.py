@@ -1,11 +1,13 @@
 """Run products of the unit-sphere workload once, for profilers.
 
-    python -m paper_2309_09061_gb300.profile_run [--n 8192] [--precision fp64|mixed|tc] [--reps 1]
+    python -m paper_2309_09061_gb300.profile_run [--n 8192] [--precision fp64|mixed|tf32x3|tf32|bf16x3|auto]
+        [--eps 1e-6] [--order 4] [--reps 1] [--autotune]
 
 Builds the Laplace H^2-matrix (leaf 64, eta 2, Chebyshev order 4) of n seeded
 points on the unit sphere and computes Z <- Z + G G at eps (default 1e-6) on
-cuda:0, printing the call's statistics as JSON.  Under a profiler, pick the
-kernels with ncu's -k / -s / -c and end the program with --kill.
+cuda:0, reps times, printing the last call's statistics as JSON.  With
+--autotune the library's online tuner is on (the first products settle it).
+Under a profiler, pick the kernels with ncu's -k / -s / -c.
 """
 import argparse
 import json
@@ -21,16 +23,18 @@ import synth  # noqa: E402
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=8192)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "tc"])
+    ap.add_argument("--precision", default="fp64", choices=sorted(P.PRECISIONS) + ["tc"])
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--order", type=int, default=4)
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--autotune", action="store_true")
     a = ap.parse_args()
     P.build()
     P.load()
     pts = synth.sphere(a.n, 2309090611)
     G = P.h2_build_interp(pts, P.H2_K_LAPLACE, 64, 2.0, a.order)
-    prec = {"fp64": P.H2_FP64, "mixed": P.H2_MIXED, "tc": P.H2_TC}[a.precision]
+    prec = P.H2_TC if a.precision == "tc" else P.PRECISIONS[a.precision]
+    P.set_autotune(a.autotune)
     for _ in range(a.reps):
         Z = P.h2_clone(G)
         st = P.h2_mul_add(Z, G, G, a.eps, prec)

@@ -6,7 +6,9 @@ transformation matvec; the GPU result's rows come from the library's
 h2_matvec.  The bound is 10 eps in relative Frobenius norm over the sampled
 rows.  The n = 32768 sphere case runs in the benchmark's launch path (fresh
 clone of Z, one h2_mul_add); the cube-volume and the n = 524288 sphere cases
-run in the precision their workloads state."""
+run in the plain FP64 form, the CUDA-core FP32 form and the fast form
+(H2_AUTO); the cases are ordered so that those of one geometry follow each
+other and share the oracle's matrix."""
 import numpy as np
 import pytest
 
@@ -20,10 +22,16 @@ CASES = {
     # name: geometry, n, kernel, leaf, eta, order, eps, precision, seed
     "sphere-n32768-fp64": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_FP64, 2309090611),
     "sphere-n32768-mixed": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_MIXED, 2309090611),
-    "sphere-n32768-tc": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_TC, 2309090611),
+    "sphere-n32768-auto": ("sphere", 32768, O.K_LAPLACE, 64, 2.0, 4, 1e-6, P.H2_AUTO, 2309090611),
     "cube-n131072-yukawa-mixed-1e-4": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-4, P.H2_MIXED, 2309090612),
     "cube-n131072-yukawa-mixed-1e-6": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-6, P.H2_MIXED, 2309090612),
+    "cube-n131072-yukawa-auto-1e-4": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-4, P.H2_AUTO, 2309090612),
+    "cube-n131072-yukawa-auto-1e-6": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-6, P.H2_AUTO, 2309090612),
+    "cube-n131072-yukawa-fp64-1e-4": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-4, P.H2_FP64, 2309090612),
+    "cube-n131072-yukawa-fp64-1e-6": ("cube", 131072, O.K_YUKAWA, 64, 1.5, 4, 1e-6, P.H2_FP64, 2309090612),
     "sphere-n524288-order5-mixed": ("sphere", 524288, O.K_LAPLACE, 64, 2.0, 5, 1e-6, P.H2_MIXED, 2309090614),
+    "sphere-n524288-order5-auto": ("sphere", 524288, O.K_LAPLACE, 64, 2.0, 5, 1e-6, P.H2_AUTO, 2309090614),
+    "sphere-n524288-order5-fp64": ("sphere", 524288, O.K_LAPLACE, 64, 2.0, 5, 1e-6, P.H2_FP64, 2309090614),
 }
 
 
