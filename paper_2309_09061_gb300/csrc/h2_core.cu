@@ -10,6 +10,7 @@
 #include <exception>
 #include <functional>
 #include <atomic>
+#include <condition_variable>
 #include <mutex>
 
 #include "h2_internal.h"
@@ -393,6 +394,108 @@ void Runner::term(const double* A, int ta, int lda, const double* B, int tb, int
     pend_bytes_ += 8.0 * ((double)J.m * k + (double)k * J.n);
 }
 
+// ---------------------------------------------------------------- grouped launches
+namespace {
+thread_local Combiner* tl_comb = nullptr;
+}
+Combiner* current_combiner() { return tl_comb; }
+CombinerScope::CombinerScope(Combiner* c) : prev_(tl_comb) { tl_comb = c; }
+CombinerScope::~CombinerScope() { tl_comb = prev_; }
+
+Combiner::Combiner(cudaStream_t st, int precision) : R_(st, precision) { R_.ensure_flag(); }
+
+Combiner::~Combiner() {
+    cudaStreamSynchronize(R_.stream());
+    for (cudaEvent_t e : events_) cudaEventDestroy(e);
+}
+
+cudaEvent_t Combiner::event() {
+    cudaEvent_t e;
+    H2_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    events_.push_back(e);
+    return e;
+}
+
+void Combiner::enter() {
+    std::lock_guard<std::mutex> lk(mu_);
+    ++active_;
+}
+
+void Combiner::leave() {
+    std::lock_guard<std::mutex> lk(mu_);
+    --active_;
+    cv_.notify_all();
+}
+
+void Combiner::launch(std::vector<Sub*>& subs) {
+    std::vector<int> prs;
+    for (Sub* s : subs)
+        if (std::find(prs.begin(), prs.end(), s->pr) == prs.end()) prs.push_back(s->pr);
+    for (int pr : prs) {
+        for (Sub* s : subs)
+            if (s->pr == pr) H2_CUDA(cudaStreamWaitEvent(R_.stream(), s->ready, 0));
+        const Arena::Mark mk = R_.mark();
+        for (Sub* s : subs) {
+            if (s->pr != pr) continue;
+            for (const GJob& J : s->jobs) {
+                R_.job(J.C, J.m, J.n, J.ldc, J.beta, J.sym != 0);
+                for (int i = 0; i < J.nt; ++i) {
+                    const GTerm& T = s->terms[J.t0 + i];
+                    R_.term(T.A, T.ta, T.lda, T.B, T.tb, T.ldb, T.k, T.alpha, T.scale);
+                }
+            }
+        }
+        R_.flush_gemm(pr);
+        R_.release(mk);  // descriptors and split-K slices: reused in stream order
+        cudaEvent_t done = event();
+        H2_CUDA(cudaEventRecord(done, R_.stream()));
+        for (Sub* s : subs)
+            if (s->pr == pr) H2_CUDA(cudaStreamWaitEvent(s->st, done, 0));
+    }
+}
+
+void Combiner::submit(int pr, std::vector<GTerm>& terms, std::vector<GJob>& jobs, cudaStream_t from) {
+    Sub s;
+    s.pr = pr;
+    s.terms.swap(terms);
+    s.jobs.swap(jobs);
+    s.st = from;
+    H2_CUDA(cudaEventCreateWithFlags(&s.ready, cudaEventDisableTiming));
+    H2_CUDA(cudaEventRecord(s.ready, from));
+    const auto t0 = std::chrono::steady_clock::now();
+    std::unique_lock<std::mutex> lk(mu_);
+    pending_.push_back(&s);
+    cv_.notify_all();
+    while (!s.done) {
+        const bool all_in = (int)pending_.size() >= active_;
+        const bool late = std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200);
+        if (!leading_ && !pending_.empty() && (all_in || late)) {
+            leading_ = true;
+            std::vector<Sub*> take;
+            take.swap(pending_);
+            lk.unlock();
+            std::string err;
+            try {
+                launch(take);
+            } catch (const std::exception& e) {
+                err = e.what();
+            }
+            lk.lock();
+            for (Sub* t : take) {
+                t->done = true;
+                t->error = err;
+            }
+            leading_ = false;
+            cv_.notify_all();
+            continue;
+        }
+        cv_.wait_for(lk, std::chrono::microseconds(50));
+    }
+    lk.unlock();
+    cudaEventDestroy(s.ready);
+    if (!s.error.empty()) throw Error(H2_ERR_CUDA, "grouped launch failed: " + s.error);
+}
+
 // ---------------------------------------------------------------- autotuner
 Tuner& Tuner::get() {
     static Tuner t;
@@ -449,6 +552,14 @@ void Runner::flush_gemm(int precision_override) {
     int pr = precision_override >= 0 ? precision_override : prec_;
     // FP64 products of the low-precision modes run in double-float arithmetic
     if (pr == H2_FP64 && prec_ != H2_FP64) pr = kGemmDF;
+    if (comb_ && !tune_) {  // a product of a batched call: one launch for all products at this step
+        pend_flops_ = pend_bytes_ = 0.0;
+        pend_tiles32_ = pend_tiles64_ = 0;
+        comb_->submit(pr, terms_, jobs_, st_);
+        terms_.clear();
+        jobs_.clear();
+        return;
+    }
     // autotuned schedule: the kernel of the FP32-class products and the split-K policy
     uint64_t tkey = 0;
     int tcand = -1, force_split = 0;

@@ -11,6 +11,7 @@
 #include <string>
 #include <unordered_map>
 #include <array>
+#include <condition_variable>
 #include <vector>
 
 #include "../../include/h2mul.h"
@@ -445,11 +446,27 @@ private:
     std::unordered_map<uint64_t, Entry> map_;
 };
 
+class Combiner;
+// The combiner of the batched call running on this thread (null outside
+// h2_mul_add_batched); Runners built while it is set hand it their GEMM batches.
+Combiner* current_combiner();
+struct CombinerScope {
+    explicit CombinerScope(Combiner* c);
+    ~CombinerScope();
+    CombinerScope(const CombinerScope&) = delete;
+    CombinerScope& operator=(const CombinerScope&) = delete;
+
+private:
+    Combiner* prev_;
+};
+
 // Host-side driver of batched ops: collects jobs, uploads, launches.
 class Runner {
 public:
-    explicit Runner(cudaStream_t st, int precision) : st_(st), prec_(precision), scratch_(st), persist_(st) {}
+    explicit Runner(cudaStream_t st, int precision)
+        : st_(st), prec_(precision), scratch_(st), persist_(st), comb_(current_combiner()) {}
     void set_autotune(bool on) { tune_ = on; }
+    Combiner* combiner() const { return comb_; }
     ~Runner();
     cudaStream_t stream() const { return st_; }
     int precision() const { return prec_; }
@@ -532,6 +549,7 @@ private:
         int tcand = -1;
     };
     bool tune_ = false;
+    Combiner* comb_ = nullptr;
     double* dev_counter();
     std::vector<Mark> marks_;
     std::vector<cudaEvent_t> pool_;
@@ -558,6 +576,52 @@ private:
     template <class A, class B, class C>
     void upload3(const std::vector<A>& a, A*& da, const std::vector<B>& b, B*& db, const std::vector<C>& c, C*& dc);
     void release_pinned();
+};
+
+// Grouped launches across the products of h2_mul_add_batched.  The products
+// run on their own host threads and streams; when one of them flushes a GEMM
+// batch it hands the batch to the combiner and waits.  Once every thread that
+// is running product code has handed over a batch, or 200 microseconds after
+// the oldest waiting batch, the thread whose wait ends first takes all waiting
+// batches, concatenates those of the same kernel (same effective precision)
+// into one job list, and launches each list once on the combiner's stream,
+// after events of the submitting streams; each submitting stream then waits for
+// the launch's event.  One launch per kernel serves every product at that step
+// of its level sweep (the products' levels and shapes differ; the segmented
+// batched kernels take any mix of jobs).
+class Combiner {
+public:
+    Combiner(cudaStream_t st, int precision);
+    ~Combiner();
+    void enter();  // a thread starts running product code (it may submit)
+    void leave();
+    // hands over a GEMM batch of precision tag pr (the jobs' term indices refer
+    // to `terms`); returns once the launch holding it is queued and `from` waits
+    // for it
+    void submit(int pr, std::vector<GTerm>& terms, std::vector<GJob>& jobs, cudaStream_t from);
+    Runner& runner() { return R_; }
+    int* flag() { return R_.svd_flag(); }
+    std::mutex& stats_mutex() { return smu_; }
+
+private:
+    struct Sub {
+        int pr;
+        std::vector<GTerm> terms;
+        std::vector<GJob> jobs;
+        cudaStream_t st;
+        cudaEvent_t ready;
+        bool done = false;
+        std::string error;
+    };
+    void launch(std::vector<Sub*>& subs);
+    cudaEvent_t event();
+    std::mutex mu_, smu_;
+    std::condition_variable cv_;
+    std::vector<Sub*> pending_;
+    int active_ = 0;
+    bool leading_ = false;
+    Runner R_;
+    std::vector<cudaEvent_t> events_;
 };
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

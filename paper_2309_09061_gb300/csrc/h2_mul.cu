@@ -26,6 +26,19 @@ namespace h2 {
 
 cudaStream_t stream_of(const h2_opts* o);
 
+// A product thread of a batched call that blocks on the host (a stream
+// synchronisation, a join) submits nothing meanwhile: the combiner does not
+// wait for it.
+struct CombIdle {
+    Combiner* c;
+    explicit CombIdle(Combiner* cc) : c(cc) {
+        if (c) c->leave();
+    }
+    ~CombIdle() {
+        if (c) c->enter();
+    }
+};
+
 // A matrix operand as stored: logical = tr ? stored^T : stored.
 struct Mv {
     const double* p;
@@ -477,7 +490,10 @@ static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
         int flag = 0;
         if (R.svd_flag())
             H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, R.stream()));
-        H2_CUDA(cudaStreamSynchronize(R.stream()));
+        {
+            CombIdle idle(R.combiner());
+            H2_CUDA(cudaStreamSynchronize(R.stream()));
+        }
         if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
         if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     }
@@ -1851,7 +1867,16 @@ public:
         int dev = 0;
         H2_CUDA(cudaGetDevice(&dev));
         const DevAlloc src = current_alloc();
-        th_ = std::thread([this, dev, src, st, f = std::forward<F>(f)]() mutable {
+        Combiner* comb = current_combiner();
+        if (comb) comb->enter();  // before the thread starts: the combiner must count it
+        th_ = std::thread([this, dev, src, st, comb, f = std::forward<F>(f)]() mutable {
+            CombinerScope cs(comb);
+            struct Leave {
+                Combiner* c;
+                ~Leave() {
+                    if (c) c->leave();
+                }
+            } leave{comb};
             try {
                 H2_CUDA(cudaSetDevice(dev));
                 AllocScope scope(src, st);
@@ -1862,6 +1887,7 @@ public:
         });
     }
     void join() {
+        CombIdle idle(current_combiner());
         if (th_.joinable()) th_.join();
         if (err_) {
             std::exception_ptr e = err_;
@@ -2063,12 +2089,17 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     const Coarse& cb = pb.cb;
     auto& res = pb.res;
     clk.mark();
-    int flag = 0, flag2 = 0;
+    int flag = 0, flag2 = 0, flag3 = 0;
     H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(&flag2, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (R.combiner() && R.combiner()->flag())  // grouped launches of a batched call
+        H2_CUDA(cudaMemcpyAsync(&flag3, R.combiner()->flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     H2_CUDA(cudaGetLastError());
-    H2_CUDA(cudaStreamSynchronize(st));
-    flag |= flag2;
+    {
+        CombIdle idle(R.combiner());
+        H2_CUDA(cudaStreamSynchronize(st));
+    }
+    flag |= flag2 | flag3;
     if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
     if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
@@ -2107,7 +2138,10 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     }
     R.release_all();
     R2.release_all();
-    H2_CUDA(cudaStreamSynchronize(st));
+    {
+        CombIdle idle(R.combiner());
+        H2_CUDA(cudaStreamSynchronize(st));
+    }
     // swap the result into Z (X and Y may alias Z; they are no longer read)
     Zm->V = res->V;
     Zm->W = res->W;
@@ -2252,12 +2286,17 @@ static void recompress(h2_matrix* A, const h2_opts* opts) {
     clk2.mark();
     PhaseB pb = coarsen_and_project(R, R2, st, side, low_precision(prec), T, B, A, G, eps, cnt, clk, clk2);
     clk.mark();
-    int flag = 0, flag2 = 0;
+    int flag = 0, flag2 = 0, flag3 = 0;
     H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(&flag2, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (R.combiner() && R.combiner()->flag())  // grouped launches of a batched call
+        H2_CUDA(cudaMemcpyAsync(&flag3, R.combiner()->flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     H2_CUDA(cudaGetLastError());
-    H2_CUDA(cudaStreamSynchronize(st));
-    flag |= flag2;
+    {
+        CombIdle idle(R.combiner());
+        H2_CUDA(cudaStreamSynchronize(st));
+    }
+    flag |= flag2 | flag3;
     if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
     if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
@@ -2341,6 +2380,28 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
     std::vector<int> codes(count, H2_OK);
     std::atomic<int> next{0};
     std::vector<h2_stats> stats(count);
+    // grouped launches: the GEMM batches of the concurrent products share launches
+    // (H2_BATCH_GROUPING=0 in the environment turns this off, for comparisons)
+    static const bool grouping = !(std::getenv("H2_BATCH_GROUPING") && std::getenv("H2_BATCH_GROUPING")[0] == '0');
+    cudaStream_t cst = nullptr;
+    std::unique_ptr<Combiner> comb;
+    if (grouping && count > 1) {
+        try {
+            if (cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking) != cudaSuccess) throw Error(H2_ERR_CUDA, "stream");
+            AllocScope as(alloc_of(opts), cst);
+            comb = std::make_unique<Combiner>(cst, resolve_precision(opts ? opts->precision : H2_FP64,
+                                                                     opts ? opts->eps : 1e-6));
+        } catch (const std::exception&) {
+            comb.reset();
+        }
+    }
+    const DevAlloc batch_alloc = [&] {
+        try {
+            return alloc_of(opts);
+        } catch (const std::exception&) {
+            return DevAlloc{};
+        }
+    }();
     auto work = [&]() {
         cudaSetDevice(dev);
         cudaStream_t st = nullptr;
@@ -2349,6 +2410,8 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
             return;
         }
         cudaStreamWaitEvent(st, start, 0);
+        CombinerScope cs(comb.get());
+        AllocScope as(batch_alloc, cst ? cst : st);  // the combiner's launches allocate on its stream
         for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
             h2_opts o{};
             if (opts) {
@@ -2359,7 +2422,9 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
             }
             o.stream = st;
             o.stats = opts && opts->stats ? &stats[i] : nullptr;
+            if (comb) comb->enter();
             codes[i] = h2_mul_add(Z[i], X[i], Y[i], &o);
+            if (comb) comb->leave();
         }
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
@@ -2368,8 +2433,16 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
     for (int w = 0; w < workers; ++w) pool.emplace_back(work);
     for (auto& t : pool) t.join();
     cudaEventDestroy(start);
+    h2_stats CS{};  // the grouped launches
+    if (comb) {
+        cudaStreamSynchronize(cst);
+        comb->runner().collect(CS.fam_ms, CS.fam_launches, CS.fam_flops, CS.fam_bytes);
+        CS.kernel_launches = comb->runner().launches;
+        comb.reset();
+    }
+    if (cst) cudaStreamDestroy(cst);
     if (opts && opts->stats) {  // sums over the products (times: device time of each product)
-        h2_stats S{};
+        h2_stats S = CS;
         for (const h2_stats& x : stats) {
             S.t_rows_a_ms += x.t_rows_a_ms;
             S.t_cols_a_ms += x.t_cols_a_ms;

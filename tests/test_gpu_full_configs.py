@@ -41,7 +41,16 @@ def lib():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     P.build()
-    return P.load()
+    lib = P.load()
+    # full sizes take the library's own device memory: its stream-ordered pool reuses
+    # freed memory across the streams of a call (PyTorch keeps a pool per stream, and
+    # the n = 131072 cube at eps 1e-6 needs over 250 GB at its peak)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    prev = P.allocator()
+    P.set_allocator("library")
+    yield lib
+    P._allocator = prev
 
 
 _oracle_cache = {}
