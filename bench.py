@@ -462,8 +462,8 @@ def ours_arm(args):
             "clocks": clocks,
             "e2e": {"value": r4(n_all / e2e_dt), "unit": "rows/s", "h2d_bytes_per_step": int(pts.nbytes),
                     "d2h_bytes_per_step": int(d2h),
-                    "note": "build from host points + clone + h2_mul_add + structure read-back (ranks, "
-                            "permutation; not the couplings: a lower bound on a full host round trip)"}}
+                    "note": "host points -> build + clone + h2_mul_add -> ranks and permutation back "
+                            "(not the couplings: a lower bound on a full round trip)"}}
     if rank == 0 and not args.no_cpu_baseline:
         v, dt = run_cpu_sample()
         line["cpu_baseline"] = cpu_baseline_record(v, dt)

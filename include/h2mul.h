@@ -242,9 +242,13 @@ H2_API int h2_mul_add(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, cons
 
 /* Z[i] <- Z[i] + X[i] Y[i] for count independent products (different sizes,
  * orders, geometries), each with the relations and semantics of h2_mul_add
- * and opts->eps / opts->precision.  The products run concurrently on
- * internal non-blocking streams that start after the work already issued on
- * opts->stream; the call returns when all of them are done.  A Z handle may
+ * and opts->eps / opts->precision.  The products run concurrently (up to 16
+ * at a time, each on its own host thread and internal non-blocking stream)
+ * after the work already issued on opts->stream; the call returns when all
+ * of them are done.  With H2_BATCH_GROUPING=1 in the environment the
+ * concurrent products' GEMM batches of the same kernel are grouped into
+ * shared launches (up to 8 products at a time); results then agree with
+ * those of single products to rounding, not bit for bit.  A Z handle may
  * not appear twice.  status (may be NULL) receives count per-product codes;
  * the return value is the first nonzero one (products that failed leave
  * their Z unchanged, the others are updated).  opts->stats receives sums over

@@ -446,7 +446,8 @@ void Combiner::launch(std::vector<Sub*>& subs) {
             }
         }
         R_.flush_gemm(pr);
-        R_.release(mk);  // descriptors and split-K slices: reused in stream order
+        R_.release(mk);         // descriptors and split-K slices: reused in stream order
+        R_.recycle_staging();  // and their pinned host staging
         cudaEvent_t done = event();
         H2_CUDA(cudaEventRecord(done, R_.stream()));
         for (Sub* s : subs)
@@ -468,7 +469,7 @@ void Combiner::submit(int pr, std::vector<GTerm>& terms, std::vector<GJob>& jobs
     cv_.notify_all();
     while (!s.done) {
         const bool all_in = (int)pending_.size() >= active_;
-        const bool late = std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200);
+        const bool late = std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(100);
         if (!leading_ && !pending_.empty() && (all_in || late)) {
             leading_ = true;
             std::vector<Sub*> take;
@@ -489,7 +490,7 @@ void Combiner::submit(int pr, std::vector<GTerm>& terms, std::vector<GJob>& jobs
             cv_.notify_all();
             continue;
         }
-        cv_.wait_for(lk, std::chrono::microseconds(50));
+        cv_.wait_for(lk, std::chrono::microseconds(25));
     }
     lk.unlock();
     cudaEventDestroy(s.ready);

@@ -448,7 +448,8 @@ private:
 
 class Combiner;
 // The combiner of the batched call running on this thread (null outside
-// h2_mul_add_batched); Runners built while it is set hand it their GEMM batches.
+// h2_mul_add_batched with H2_BATCH_GROUPING=1); Runners built while it is set
+// hand it their GEMM batches.
 Combiner* current_combiner();
 struct CombinerScope {
     explicit CombinerScope(Combiner* c);
@@ -517,6 +518,9 @@ public:
     template <class T>
     T* upload(const std::vector<T>& v);
     void release_all();  // frees every allocation of this runner (stream ordered)
+    // returns the pinned staging chunks of the uploads issued so far to the
+    // process-wide pool (each is reused once the pulls queued so far are done)
+    void recycle_staging() { release_pinned(); }
 
 private:
     cudaStream_t st_;
@@ -578,11 +582,12 @@ private:
     void release_pinned();
 };
 
-// Grouped launches across the products of h2_mul_add_batched.  The products
-// run on their own host threads and streams; when one of them flushes a GEMM
-// batch it hands the batch to the combiner and waits.  Once every thread that
-// is running product code has handed over a batch, or 200 microseconds after
-// the oldest waiting batch, the thread whose wait ends first takes all waiting
+// Grouped launches across the products of h2_mul_add_batched (opt-in:
+// H2_BATCH_GROUPING=1 in the environment).  The products run on their own host
+// threads and streams; when one of them flushes a GEMM batch it hands the batch
+// to the combiner and waits.  Once every thread that is running product code
+// has handed over a batch, or 100 microseconds after a batch was handed over,
+// the thread whose wait ends first takes all waiting
 // batches, concatenates those of the same kernel (same effective precision)
 // into one job list, and launches each list once on the combiner's stream,
 // after events of the submitting streams; each submitting stream then waits for

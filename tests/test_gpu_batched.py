@@ -58,3 +58,43 @@ def test_batched_against_oracle_and_errors():
     with pytest.raises(P.H2Error) as e:  # a Z may not be an operand of another product
         P.h2_mul_add_batched([Z, X], [X, Z], [X, Z], eps)
     assert e.value.code == -1
+
+
+_GROUPED = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import paper_2309_09061_gb300 as P, synth
+P.build(); P.load()
+eps = 1e-5
+cases = [("sphere", 2048, 3), ("cube_surface", 3000, 4), ("sphere", 4100, 5), ("cube_surface", 2500, 3),
+         ("sphere", 1500, 4), ("cube_surface", 5000, 3)]
+Zs, Xs, refs = [], [], []
+for i, (geom, n, m) in enumerate(cases):
+    X = P.h2_build_interp(synth.make_points(geom, n, 2309090613 + 1000 * i), P.H2_K_LAPLACE, 64, 2.0, m)
+    Z1 = P.h2_clone(X)
+    P.h2_mul_add(Z1, X, X, eps, {prec})
+    refs.append(P.h2_to_dense(Z1))
+    Xs.append(X)
+    Zs.append(P.h2_clone(X))
+st, codes = P.h2_mul_add_batched(Zs, Xs, Xs, eps, {prec})
+assert codes == [0] * len(cases), codes
+worst = max(float(np.linalg.norm(P.h2_to_dense(Z) - r) / np.linalg.norm(r)) for Z, r in zip(Zs, refs))
+print("worst", worst, "launches", st["kernel_launches"])
+assert worst <= 0.1 * eps, worst
+"""
+
+
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_TF32X3])
+def test_grouped_launches_match_single(precision):
+    """The opt-in grouped launches (H2_BATCH_GROUPING=1, read once per process:
+    run in a child process) give each product the result of the product run
+    alone, to rounding (the shared launches split K differently)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, H2_BATCH_GROUPING="1")
+    p = subprocess.run([sys.executable, "-c", _GROUPED.format(root=root, prec=precision)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stdout[-2000:] + p.stderr[-2000:]
+    assert "worst" in p.stdout
