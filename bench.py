@@ -433,6 +433,8 @@ def ours_arm(args):
         torch.cuda.synchronize(dev)
         torch.cuda.empty_cache()
         P.set_allocator("library")
+        # without the tuner: its exploration (forced split-K slices) raises the peak memory
+        P.set_autotune(False)
         for name, c in CONFIGS.items():
             pc = synth.make_points(c["geometry"], c["n"], c["seed"])
             Gc = P.h2_build_interp(pc, c["kernel"], c["leaf"], c["eta"], c["order"], stream=sptr)
@@ -474,6 +476,7 @@ def ours_arm(args):
     line["eps2"] = {"fast": r4(e2f), "fp64": r4(e264)}
     line["forms_ms"] = forms
     line["configs"] = configs
+    G.free()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -7,8 +7,10 @@ There is no CPU fallback: loading fails loudly when the library is missing.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -100,9 +102,13 @@ class TorchAllocator:
                 return
             self.live -= int(nbytes)
 
-        # the callback objects live as long as this allocator (module-wide singleton)
+        # the callback objects live as long as this allocator (module-wide singleton,
+        # and referenced by every handle made while it was in use)
         self.alloc = ALLOC_FN(_alloc)
         self.free = FREE_FN(_free)
+        # handles still alive at exit are freed before PyTorch shuts down (atexit
+        # runs the handlers registered last first, and torch registered its own on import)
+        atexit.register(_free_live)
 
 
 _allocator = None  # None: not chosen yet; "library" or a TorchAllocator
@@ -211,11 +217,23 @@ def _opts(eps=1e-6, precision=H2_FP64, stream=None, stats=None):
     return o
 
 
+_live = weakref.WeakSet()  # handles not yet freed (released at interpreter exit)
+
+
+def _free_live():
+    for A in list(_live):
+        A.free()
+
+
 class H2Matrix:
-    """Owning wrapper of an h2_matrix handle."""
+    """Owning wrapper of an h2_matrix handle.  It keeps the allocator its
+    buffers may have come from alive for as long as it lives (h2_free returns
+    them through its callbacks)."""
 
     def __init__(self, handle):
         self.handle = handle
+        self._alloc = _allocator
+        _live.add(self)
 
     def __del__(self):
         self.free()
@@ -224,6 +242,7 @@ class H2Matrix:
         if getattr(self, "handle", None):
             load().h2_free(self.handle)
             self.handle = None
+            _live.discard(self)
 
     def info(self) -> dict:
         inf = Info()

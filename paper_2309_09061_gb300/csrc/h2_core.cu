@@ -247,13 +247,13 @@ double* Arena::alloc(size_t n) {
 }
 
 void Arena::release(const Mark& m) {
-    // keep up to 1 GiB of released chunks for reuse (fewer allocator calls per
+    // keep up to 256 MiB of released chunks for reuse (fewer allocator calls per
     // level); the rest goes back to its source, where other arenas can use it
     size_t kept = 0;
     for (const Chunk& c : spare_) kept += c.bytes;
     while (chunks_.size() > m.nchunks) {
         const Chunk& c = chunks_.back();
-        if (kept + c.bytes <= ((size_t)1 << 30)) {
+        if (kept + c.bytes <= ((size_t)256 << 20)) {
             kept += c.bytes;
             spare_.push_back(c);
         } else {
