@@ -821,10 +821,13 @@ void Runner::flush_pre() {
     PreJob* d = upload(pres_);
     double by = 0.0;
     for (auto& j : pres_) by += 8.0 * ((double)j.m * j.n + (double)j.n * j.n);
-    size_t max_mn = 0;
-    for (auto& j : pres_) max_mn = std::max(max_mn, (size_t)j.m * j.n);
+    size_t max_mn = 0, max_mnv = 0;
+    for (auto& j : pres_) {
+        max_mn = std::max(max_mn, (size_t)j.m * j.n);
+        max_mnv = std::max(max_mnv, (size_t)(j.m + (j.V ? j.n : 0)) * j.n);
+    }
     begin(6);
-    launch_jacobi_pre(d, (int)pres_.size(), max_mn, st_);
+    launch_jacobi_pre(d, (int)pres_.size(), max_mn, max_mnv, st_);
     end(6, 0.0, by);
     marks_.back().dflops = cnt;
     ++launches;

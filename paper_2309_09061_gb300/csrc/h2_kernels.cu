@@ -182,6 +182,9 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
     const GTile tile = tiles[blockIdx.x];
     const GJob J = jobs[tile.job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // rows 4 tx + x, columns 4 ty + y
+    // warp w holds the columns 8 w .. 8 w + 7 of the tile (ty = 2 w, 2 w + 1): in an
+    // edge tile the warps wholly beyond the job skip their multiply-adds (warp-uniform)
+    const bool cols_live = tile.j0 + 8 * (int)(threadIdx.x >> 5) < J.n;
     auto sh = [](int kk) { return DF ? (kk >> 1) & 7 : (kk >> 2) & 7; };
     auto sidx = [&](int kk, int i) { return (((i >> 2) ^ sh(kk)) << 2) | ((i & 3) ^ (DF ? (kk & 1) << 1 : kk & 3)); };
     float acc[4][4], cor[4][4];  // cor: low parts of the double-float sums (DF only)
@@ -336,7 +339,9 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         constexpr std::integral_constant<int, 1> d1;
         constexpr std::integral_constant<int, 2> d2;
         constexpr std::integral_constant<int, 3> d3;
-        if (!DF && kc == KC) {  // (the double-float step is long: its loop stays rolled for the instruction cache)
+        if (!cols_live) {
+            // this warp's 8 columns lie wholly beyond the job (an edge tile): nothing to add
+        } else if (!DF && kc == KC) {  // (the double-float step is long: its loop stays rolled for the instruction cache)
 #pragma unroll
             for (int kk = 0; kk < KC; kk += 4) {
                 mac(kk, d0);
@@ -1203,8 +1208,12 @@ constexpr int PMAXSWEEP = 30;
 
 // W lives in dynamic shared memory when its m * n floats fit in the launch's
 // smem_bytes (sized for the largest job, at most kPreSmem), else in its
-// global workspace.
-constexpr int kPreSmem = 160 * 1024;
+// global workspace; V joins it there when (m + n) n floats fit.
+// (Carrying the squared column norms under the rotations, as the FP64 sweeps
+// do, was measured slower here: in FP32 the carried norms of columns that
+// shrink lose their accuracy within a sweep, and the convergence test then
+// asks for more sweeps.  Each pair forms its three inner products.)
+constexpr int kPreSmem = 200 * 1024;
 
 __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jobs, int smem_bytes) {
     extern __shared__ float pre_smem[];
@@ -1213,10 +1222,12 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     const int m = J.m, n = J.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
     const bool in_smem = (size_t)m * n * sizeof(float) <= (size_t)smem_bytes;
+    const bool v_smem = in_smem && J.V && (size_t)(m + n) * n * sizeof(float) <= (size_t)smem_bytes;
     float* W = in_smem ? pre_smem : J.W;
+    float* V = v_smem ? pre_smem + (size_t)m * n : J.V;
     for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) W[e] = (float)J.B[(e % m) + (size_t)(e / m) * J.ldb];
-    if (J.V)
-        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
+    if (V)
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) V[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
     __syncthreads();
     const int np = n + (n & 1);
     const float tol = (float)(m > 1 ? m : 1) * FLT_EPSILON;
@@ -1257,9 +1268,9 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
                         ap[i] = c * x - s * y;
                         aq[i] = s * x + c * y;
                     }
-                    if (J.V) {
-                        float* vp = J.V + (size_t)p * n;
-                        float* vq = J.V + (size_t)q * n;
+                    if (V) {
+                        float* vp = V + (size_t)p * n;
+                        float* vq = V + (size_t)q * n;
                         for (int i = lane; i < n; i += 32) {
                             float x = vp[i], y = vq[i];
                             vp[i] = c * x - s * y;
@@ -1278,7 +1289,7 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
         __syncthreads();
     }
     if (J.V64)
-        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)J.V[e];
+        for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += JT) J.V64[e] = (double)V[e];
     if (J.W64)
         for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += JT) J.W64[e] = (double)W[e];
     if (threadIdx.x == 0 && J.flops)
@@ -1707,7 +1718,7 @@ void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
     k_jacobi64<false><<<njobs, JT, smem, st>>>(jobs);
 }
 
-void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_t st) {
+void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_mnv, cudaStream_t st) {
     if (njobs <= 0) return;
     int cs = jacobi_cluster_size(njobs);
     if (cs <= 1 || !launch_clustered(k_jacobi_pre_cluster, njobs * cs, cs, kClusterDynSmem, st, jobs)) {
@@ -1718,7 +1729,9 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, cudaStream_
             cudaFuncSetAttribute(k_jacobi_pre, cudaFuncAttributeMaxDynamicSharedMemorySize, kPreSmem);
             attr_set[dev] = true;
         }
-        const int smem = (max_mn * sizeof(float) <= (size_t)kPreSmem) ? (int)(max_mn * sizeof(float)) : 0;
+        // W (and V) of the largest job in shared memory when they fit
+        const size_t want = (max_mnv * sizeof(float) <= (size_t)kPreSmem) ? max_mnv : max_mn;
+        const int smem = (want * sizeof(float) <= (size_t)kPreSmem) ? (int)(want * sizeof(float)) : 0;
         k_jacobi_pre<<<njobs, JT, smem, st>>>(jobs, smem);
     }
 }

@@ -39,8 +39,12 @@ def main():
         Z = P.h2_clone(G)
         st = P.h2_mul_add(Z, G, G, a.eps, prec)
         Z.free()
-    print(json.dumps({k: st[k] for k in ("t_rows_a_ms", "t_cols_a_ms", "t_mat_a_ms", "t_rows_b_ms", "t_cols_b_ms",
-                                          "t_mat_b_ms", "kernel_launches", "max_rank_a", "max_rank_b")}))
+    out = {k: st[k] for k in ("t_rows_a_ms", "t_cols_a_ms", "t_mat_a_ms", "t_rows_b_ms", "t_cols_b_ms",
+                              "t_mat_b_ms", "kernel_launches", "max_rank_a", "max_rank_b")}
+    # per kernel family: launches and algorithmic GFLOP of the last call
+    out["families"] = {P.FAMILIES[i]: {"launches": st["fam_launches"][i], "gflop": st["fam_flops"][i] / 1e9}
+                       for i in range(len(P.FAMILIES)) if st["fam_launches"][i]}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
