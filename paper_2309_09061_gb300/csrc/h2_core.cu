@@ -11,6 +11,7 @@
 #include <functional>
 #include <atomic>
 #include <condition_variable>
+#include <map>
 #include <mutex>
 
 #include "h2_internal.h"
@@ -50,6 +51,96 @@ struct HostWait {
     }
 };
 
+double host_clock_ms() {
+    static const auto t0 = std::chrono::steady_clock::now();
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+namespace {
+bool trace_on() {
+    static const bool on = std::getenv("H2_TRACE") != nullptr;
+    return on;
+}
+struct SpanSum {
+    double ms = 0.0;
+    int64_t n = 0;
+};
+std::mutex g_span_mu;
+std::map<std::pair<int, std::string>, SpanSum> g_spans;
+std::atomic<int> g_span_threads{0};
+thread_local int tl_span_thread = -1;
+}  // namespace
+
+HostSpan::HostSpan(const char* name) : name_(trace_on() ? name : nullptr) {
+    if (name_) t0_ = host_clock_ms();
+}
+
+HostSpan::~HostSpan() {
+    if (!name_) return;
+    const double ms = host_clock_ms() - t0_;
+    if (tl_span_thread < 0) tl_span_thread = g_span_threads.fetch_add(1);
+    std::lock_guard<std::mutex> lk(g_span_mu);
+    SpanSum& a = g_spans[{tl_span_thread, name_}];
+    a.ms += ms;
+    a.n += 1;
+}
+
+HostLap::HostLap() {
+    if (trace_on()) t_ = host_clock_ms();
+}
+
+void HostLap::mark(const char* name) {
+    if (!trace_on()) return;
+    const double now = host_clock_ms();
+    if (tl_span_thread < 0) tl_span_thread = g_span_threads.fetch_add(1);
+    {
+        std::lock_guard<std::mutex> lk(g_span_mu);
+        SpanSum& a = g_spans[{tl_span_thread, name}];
+        a.ms += now - t_;
+        a.n += 1;
+    }
+    t_ = now;
+}
+
+void host_spans_dump() {
+    if (!trace_on()) return;
+    std::lock_guard<std::mutex> lk(g_span_mu);
+    for (const auto& kv : g_spans)
+        std::fprintf(stderr, "h2span %d %s %.3f %lld\n", kv.first.first, kv.first.second.c_str(), kv.second.ms,
+                     (long long)kv.second.n);
+    g_spans.clear();
+}
+
+namespace {
+std::mutex g_stream_mu;
+std::vector<std::pair<int, cudaStream_t>> g_streams;  // (device, stream) not in use
+}  // namespace
+
+cudaStream_t stream_get() {
+    int dev = 0;
+    H2_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_stream_mu);
+        for (size_t i = 0; i < g_streams.size(); ++i)
+            if (g_streams[i].first == dev) {
+                cudaStream_t s = g_streams[i].second;
+                g_streams.erase(g_streams.begin() + (long)i);
+                return s;
+            }
+    }
+    cudaStream_t s = nullptr;
+    H2_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    return s;
+}
+
+void stream_put(cudaStream_t s) {
+    if (!s) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    g_streams.emplace_back(dev, s);
+}
+
 // ---------------------------------------------------------------- memory sources
 namespace {
 thread_local DevAlloc tl_alloc;
@@ -88,6 +179,7 @@ cudaStream_t current_alloc_stream() { return tl_alloc_stream; }
 // pooled: scratch from the library's stream-ordered pool; otherwise cudaMalloc
 // (the buffers of handles, returned to the driver when they are freed)
 void* dev_get(const DevAlloc& a, size_t bytes, cudaStream_t st, bool pooled) {
+    H2_SPAN("dev_get");
     void* p = nullptr;
     if (a.external()) {
         HostWait hw("alloc_callback", bytes);
@@ -128,6 +220,7 @@ void dev_put(const DevAlloc& a, void* p, size_t bytes, cudaStream_t st, bool poo
 }
 
 void DevBuf::alloc(size_t n) {
+    H2_SPAN("DevBuf::alloc");
     reset();
     if (n == 0) return;
     src = current_alloc();
@@ -174,6 +267,8 @@ double* Runner::dev_counter() {
 
 void Runner::begin(int fam) {
     (void)fam;
+    static const bool trace = std::getenv("H2_TRACE") != nullptr;
+    if (trace) cur_host_ = host_clock_ms();
     cur_ = get_event();
     H2_CUDA(cudaEventRecord(cur_, st_));
 }
@@ -182,13 +277,16 @@ void Runner::end(int fam, double flops, double bytes, int64_t units) {
     cudaEvent_t b = get_event();
     H2_CUDA(cudaEventRecord(b, st_));
     marks_.push_back(Mark{fam, cur_, b, flops, bytes, nullptr, units});
+    marks_.back().host_ms = cur_host_;
     cur_ = nullptr;
 }
 
 // With H2_TRACE set in the environment, every launch is also printed to
-// stderr as "h2trace <family> <units> <GFLOP> <MB> <ms> <start ms> <stream>" in
-// launch order (start relative to ref, else to the first launch collected here).
+// stderr as "h2trace <family> <units> <GFLOP> <MB> <ms> <start ms> <stream>
+// <host ms>" in launch order (start relative to ref, else to the first launch
+// collected here; host ms: host_clock_ms() when the launch was enqueued).
 void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes, cudaEvent_t ref) {
+    H2_SPAN("collect");
     static const bool trace = std::getenv("H2_TRACE") != nullptr;
     if (!ref && !marks_.empty()) ref = marks_.front().a;
     for (auto& m : marks_) {
@@ -204,8 +302,8 @@ void Runner::collect(double* ms, int64_t* launches, double* flops, double* bytes
         if (bytes) bytes[m.fam] += m.bytes;
         if (m.tcand >= 0 && m.flops > 0.0) Tuner::get().report(m.tkey, m.tcand, f / (m.flops * 1e-9));
         if (trace)
-            std::fprintf(stderr, "h2trace %d %lld %.6f %.3f %.6f %.3f %p\n", m.fam, (long long)m.units,
-                         (m.flops + df) * 1e-9, m.bytes * 1e-6, f, t0, (void*)st_);
+            std::fprintf(stderr, "h2trace %d %lld %.6f %.3f %.6f %.3f %p %.3f\n", m.fam, (long long)m.units,
+                         (m.flops + df) * 1e-9, m.bytes * 1e-6, f, t0, (void*)st_, m.host_ms);
         pool_.push_back(m.a);
         pool_.push_back(m.b);
     }
@@ -281,6 +379,20 @@ constexpr size_t kPinnedChunk = size_t(32) << 20;
 }  // namespace
 
 const void* Runner::stage(const void* src, size_t bytes) {
+    char* dh = nullptr;
+    char* h = carve_pinned(bytes, &dh);
+    std::memcpy(h, src, bytes);
+    return dh;
+}
+
+void* Runner::pinned_host(size_t bytes) {
+    char* dh = nullptr;
+    return carve_pinned(bytes, &dh);
+}
+
+// `bytes` (rounded up to 256) of this runner's pinned staging: the host
+// address, and the device address of the same memory in *dev
+char* Runner::carve_pinned(size_t bytes, char** dev) {
     const size_t need = (bytes + 255) & ~size_t(255);
     if (pinned_.empty() || pinned_used_ + need > pinned_.back().size) {
         Pinned c{nullptr, nullptr, 0, nullptr};
@@ -307,10 +419,9 @@ const void* Runner::stage(const void* src, size_t bytes) {
         pinned_used_ = 0;
     }
     char* h = pinned_.back().p + pinned_used_;
-    char* dh = pinned_.back().dp + pinned_used_;
+    *dev = pinned_.back().dp + pinned_used_;
     pinned_used_ += need;
-    std::memcpy(h, src, bytes);
-    return dh;
+    return h;
 }
 
 void Runner::release_pinned() {
@@ -326,6 +437,7 @@ void Runner::release_pinned() {
 // the arena (256-byte granules) by k_pull on this stream.
 template <class T>
 T* Runner::upload(const std::vector<T>& v) {
+    H2_SPAN("upload");
     size_t bytes = std::max<size_t>(v.size() * sizeof(T), 8);
     double* d = dalloc((bytes + 7) / 8);
     if (!v.empty()) {
@@ -362,6 +474,7 @@ template double* Runner::upload<double>(const std::vector<double>&);
 template double** Runner::upload<double*>(const std::vector<double*>&);
 
 void Runner::release_all() {
+    H2_SPAN("release_all");
     release_pinned();
     scratch_.release_all();
     persist_.release_all();
@@ -549,6 +662,7 @@ static int ilog2(double x) {
 }
 
 void Runner::flush_gemm(int precision_override) {
+    H2_SPAN("flush_gemm");
     if (jobs_.empty()) return;
     int pr = precision_override >= 0 ? precision_override : prec_;
     // FP64 products of the low-precision modes run in double-float arithmetic
@@ -755,6 +869,7 @@ void Runner::qr_wy(double* A, int m, int n, int lda, double* V, double* T) {
 }
 
 void Runner::flush_qr() {
+    H2_SPAN("flush_qr");
     if (!qrs32_.empty()) {
         QRJob* d = upload(qrs32_);
         double fl = 0.0, by = 0.0;
@@ -793,6 +908,7 @@ void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* s
 }
 
 void Runner::flush_svd() {
+    H2_SPAN("flush_svd");
     if (svds_.empty()) return;
     double* cnt = dev_counter();
     for (auto& j : svds_) j.flops = cnt;
@@ -815,6 +931,7 @@ void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64, dou
 }
 
 void Runner::flush_pre() {
+    H2_SPAN("flush_pre");
     if (pres_.empty()) return;
     double* cnt = dev_counter();
     for (auto& j : pres_) j.flops = cnt;
@@ -841,6 +958,7 @@ void Runner::pchol(const double* G, int k, int ldg, double* Z, int zrows, double
 }
 
 void Runner::flush_pchol() {
+    H2_SPAN("flush_pchol");
     if (chols_.empty()) return;
     CholJob* d = upload(chols_);
     double fl = 0.0, by = 0.0;
@@ -861,6 +979,7 @@ void Runner::norm(const double* A, int m, int n, int lda, double* inv, double* n
 }
 
 void Runner::flush_norm() {
+    H2_SPAN("flush_norm");
     if (norms_.empty()) return;
     NormJob* d = upload(norms_);
     double by = 0.0, fl = 0.0;
@@ -882,6 +1001,7 @@ void Runner::copy(const double* src, int lds, double* dst, int ldd, int rows, in
 }
 
 void Runner::flush_copy() {
+    H2_SPAN("flush_copy");
     if (copies_.empty()) return;
     CopyJob* d = upload(copies_);
     double by = 0.0;

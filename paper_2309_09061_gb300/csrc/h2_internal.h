@@ -192,6 +192,44 @@ struct h2_matrix {
 
 namespace h2 {
 
+// Host clock in ms since the first call (trace output only).
+double host_clock_ms();
+
+// With H2_TRACE set, the host time of a named scope is summed per thread;
+// host_spans_dump() prints the sums ("h2span <thread> <name> <ms> <count>")
+// and clears them.  Without it a span costs one test.
+struct HostSpan {
+    explicit HostSpan(const char* name);
+    ~HostSpan();
+    HostSpan(const HostSpan&) = delete;
+    HostSpan& operator=(const HostSpan&) = delete;
+
+private:
+    const char* name_;
+    double t0_ = 0.0;
+};
+void host_spans_dump();
+// Successive laps of a scope: mark(name) adds the host time since the previous
+// mark (or construction) to span `name` (with H2_TRACE set).
+struct HostLap {
+    HostLap();
+    void mark(const char* name);
+
+private:
+    double t_ = 0.0;
+};
+#define H2_SPAN_CAT2(a, b) a##b
+#define H2_SPAN_CAT(a, b) H2_SPAN_CAT2(a, b)
+#define H2_SPAN(name) ::h2::HostSpan H2_SPAN_CAT(h2_span_, __LINE__)(name)
+
+// Non-blocking streams kept for the life of the process and handed out per
+// call on the current device.  PyTorch's caching allocator keeps freed blocks
+// per stream, so a stream created per call would never reuse the blocks that
+// earlier calls freed on theirs.  stream_get throws H2_ERR_CUDA when no stream
+// can be created; a stream is returned with stream_put once its work is done.
+cudaStream_t stream_get();
+void stream_put(cudaStream_t s);
+
 // ---------------------------------------------------------------- batched ops
 // One term op(A) op(B) of a product sum; op transposes when the flag is set.
 // The effective factor is alpha * (*scale) when scale is not null.
@@ -522,6 +560,11 @@ public:
     // returns the pinned staging chunks of the uploads issued so far to the
     // process-wide pool (each is reused once the pulls queued so far are done)
     void recycle_staging() { release_pinned(); }
+    // host memory in this runner's pinned staging, for device-to-host reads on
+    // its stream (a read into pageable memory blocks the calling thread inside
+    // the copy call, and other host threads' CUDA calls with it); valid until
+    // the staging is recycled
+    void* pinned_host(size_t bytes);
 
 private:
     cudaStream_t st_;
@@ -552,6 +595,7 @@ private:
         int64_t units;   // CTAs of the launch (tiles for the products)
         uint64_t tkey = 0;  // autotuned batch: its key and candidate
         int tcand = -1;
+        double host_ms = 0.0;  // host clock at the launch (trace only)
     };
     bool tune_ = false;
     Combiner* comb_ = nullptr;
@@ -559,6 +603,7 @@ private:
     std::vector<Mark> marks_;
     std::vector<cudaEvent_t> pool_;
     cudaEvent_t cur_ = nullptr;
+    double cur_host_ = 0.0;
     cudaEvent_t get_event();
 public:
     // Uploads are staged in mapped pinned host memory and pulled into device
@@ -578,6 +623,7 @@ private:
     std::vector<Pinned> pinned_;
     size_t pinned_used_ = 0;
     const void* stage(const void* src, size_t bytes);  // returns the device-visible copy
+    char* carve_pinned(size_t bytes, char** dev);
     template <class A, class B, class C>
     void upload3(const std::vector<A>& a, A*& da, const std::vector<B>& b, B*& db, const std::vector<C>& c, C*& dc);
     void release_pinned();

@@ -136,6 +136,7 @@ struct Counts {
 // ------------------------------------------------------------------ prep: basis products
 // P_s = W_{X,s}^* V_{Y,s}: directly in leaves, sum_{s'} F_{s'}^* P_{s'} E_{s'} above.
 static PerCl basis_products(Runner& R, const Tree& T, const Basis& WX, const Basis& VY) {
+    H2_SPAN("basis_products");
     PerCl P;
     P.init(T.nc);
     for (int c = 0; c < T.nc; ++c) {
@@ -173,6 +174,7 @@ static PerCl basis_products(Runner& R, const Tree& T, const Basis& WX, const Bas
 // ------------------------------------------------------------------ prep: basis weights (Fig. 1)
 // R_r with W_r = Q_r R_r: QR of the leaf matrices, then QR of [R_{r1} F_{r1}; R_{r2} F_{r2}].
 static PerCl basis_weights(Runner& R, const Tree& T, const Basis& B) {
+    H2_SPAN("basis_weights");
     PerCl W;
     W.init(T.nc);
     for (int c = Tree::first(T.L); c < T.nc; ++c) {
@@ -213,6 +215,7 @@ static PerCl basis_weights(Runner& R, const Tree& T, const Basis& B) {
 // ------------------------------------------------------------------ prep: total weights (Fig. 2 + Sec. 5)
 // Z_s from the thin QR of [Z_{s+} E_s^*; R_r S_{sr}^* / ||S_{sr} R_r^*||_2 for admissible (s,r)].
 static PerCl total_weights(Runner& R, const OpView& Y, const PerCl& RW) {
+    H2_SPAN("total_weights");
     const Tree& T = Y.tree();
     const Basis& VY = Y.rowb();
     PerCl Z;
@@ -285,6 +288,7 @@ static constexpr double kGramMinEps = 1e-7;
 static constexpr double kCholTol = 1e-15;
 
 static PerCl total_weights_gram(Runner& R, const OpView& Y) {
+    H2_SPAN("total_weights_gram");
     const Tree& T = Y.tree();
     const Basis& VY = Y.rowb();
     const Basis& WY = Y.colb();
@@ -410,6 +414,7 @@ public:
     }
     // run every queued step in order; fills out[i] for job i
     std::vector<SvdOut> run() {
+        H2_SPAN("SvdBatch::run");
         R_.flush_gemm();
         R_.flush_copy();
         bool gram = false;
@@ -484,16 +489,26 @@ private:
 };
 
 static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
+    H2_SPAN("read_counts");
     std::vector<int> h(n, 0);
     if (n > 0) {
-        H2_CUDA(cudaMemcpyAsync(h.data(), d_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, R.stream()));
-        int flag = 0;
+        // into pinned memory: the copies stay asynchronous and the wait is the
+        // stream synchronisation below
+        int* hp = (int*)R.pinned_host(sizeof(int) * ((size_t)n + 1));
+        hp[n] = 0;
+        H2_CUDA(cudaMemcpyAsync(hp, d_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, R.stream()));
         if (R.svd_flag())
-            H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, R.stream()));
+            H2_CUDA(cudaMemcpyAsync(hp + n, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, R.stream()));
         {
+            static const bool trace = std::getenv("H2_TRACE") != nullptr;
+            const double h0 = trace ? host_clock_ms() : 0.0;
             CombIdle idle(R.combiner());
             H2_CUDA(cudaStreamSynchronize(R.stream()));
+            if (trace)  // "h2sync <stream> <host ms at the wait> <host ms after it>"
+                std::fprintf(stderr, "h2sync %p %.3f %.3f\n", (void*)R.stream(), h0, host_clock_ms());
         }
+        std::copy(hp, hp + n, h.begin());
+        const int flag = hp[n];
         if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
         if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     }
@@ -543,6 +558,7 @@ struct Induced {
 // VZ: a basis preserved beside V_X (Z's own row basis, "+Z" with bases of its own), or null
 static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double eps, Counts& cnt,
                             const Basis* VZ = nullptr) {
+    H2_SPAN("induced_rows");
     const Tree& T = X.tree();
     const Basis& VX = X.rowb();
     const Basis& VY = Y.rowb();
@@ -568,6 +584,8 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
     auto kz = [&](int t) { return VZ ? VZ->rank[t] : 0; };
     // per block of X (entries are set and used within the level of the block)
     std::vector<double*> M(X.bt().kind.size(), nullptr), inv(M.size(), nullptr), SPE(M.size(), nullptr);
+    HostLap lap;
+    lap.mark("ir:prep");
     for (int l = T.L; l >= 0; --l) {
         const Arena::Mark mkl = R.mark();  // scratch of this level
         const int c0 = Tree::first(l), nl = Tree::count(l);
@@ -586,6 +604,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             }
             R.flush_gemm();
         }
+        lap.mark("ir:pe");
         // VX-hat and the admissible-child chains S_X(a,b) PE_b
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i;
@@ -634,6 +653,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         }
         R.flush_copy();
         R.flush_gemm();
+        lap.mark("ir:vxhat");
         // the blocks M_ts = X|ts V_Y,s (leaf) or A-hat_ts (Eq. induced_Ahat)
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i;
@@ -671,9 +691,11 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             }
         }
         R.flush_gemm();
+        lap.mark("ir:M");
         for (int i = 0; i < nl; ++i)
             for (int b : C[i]) R.norm(M[b], rows[i], VY.rank[X.other(b)], std::max(1, rows[i]), inv[b], nullptr);
         R.flush_norm();
+        lap.mark("ir:norm");
         // complete QR of VX-hat; tall transposed remainder; SVD
         int* d_counts = (int*)R.dalloc(nl);
         H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
@@ -707,6 +729,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         }
         R.flush_copy();
         R.flush_qr();
+        lap.mark("ir:qr");
         {
             std::vector<double*> Wq(nl, nullptr);
             for (int i = 0; i < nl; ++i) {
@@ -723,6 +746,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
             }
             R.flush_gemm(H2_FP64);
         }
+        lap.mark("ir:wq");
         std::vector<double*> Vts(nl, nullptr), Tts(nl, nullptr);
         std::vector<int> ncols(nl, 0);
         for (int i = 0; i < nl; ++i) {
@@ -753,8 +777,11 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         for (int i = 0; i < nl; ++i)
             if (Vts[i]) sb.add(Vts[i], ncols[i], m2[i], eps, d_counts + i);
             else sb.add(nullptr, 0, 0, eps, d_counts + i);
+        lap.mark("ir:tt");
         std::vector<SvdOut> so = sb.run();
+        lap.mark("ir:svd");
         std::vector<int> k2 = read_counts(R, d_counts, nl);
+        lap.mark("ir:sync");
         // new basis: leaf matrices or transfers of the children
         size_t need = 0;
         for (int i = 0; i < nl; ++i) {
@@ -781,6 +808,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         }
         R.flush_copy();
         R.flush_gemm();
+        lap.mark("ir:newbasis");
         Carve trc(Q, leaf ? 0 : transfer_need(Q, c0, nl));  // the children's transfers of this level
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i, kt = Q.rank[t];
@@ -821,6 +849,7 @@ static Induced induced_rows(Runner& R, const OpView& X, const OpView& Y, double 
         R.flush_copy();
         R.flush_gemm();
         R.release(mkl);
+        lap.mark("ir:A");
     }
     R.release(mk0);
     return out;
@@ -843,6 +872,7 @@ struct Intermediate {
 
 static void induced_matrix(Runner& R, const OpView& X, const OpView& Y, const h2_matrix* Z, const Induced& ra,
                            const Induced& ca, Intermediate& G, Counts& cnt) {
+    H2_SPAN("induced_matrix");
     const Tree& T = X.tree();
     const Basis& Q = *ra.Q;
     const Basis& QW = *ca.Q;
@@ -1187,6 +1217,7 @@ struct ChainPool {
 };
 
 static void run_chains(Runner& R, std::vector<Chain>& items, const ChainPool& pool) {
+    H2_SPAN("run_chains");
     int maxlen = 0;
     for (auto& c : items) maxlen = std::max(maxlen, c.nf);
     std::vector<Mv> cur(items.size());
@@ -1223,6 +1254,7 @@ static bool is_desc(int a, int d) {  // a is an ancestor of d (or equal)
 
 static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cmap, const double* w,
                            const double* w2, double eps) {
+    H2_SPAN("coarsen_rows");
     const Tree& T = *G.tree;
     const Basis& Q = G.rowb();
     const Basis& QW = G.colb();
@@ -1325,6 +1357,8 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
     ChainPool pool;
     std::vector<std::pair<int, bool>> target;  // cluster -> admissible (all reps agree)
     std::vector<int> path;
+    HostLap lap;
+    lap.mark("cr:prep");
     for (int l = T.L; l >= 0; --l) {
         const Arena::Mark mkl = R.mark();
         const int c0 = Tree::first(l), nl = Tree::count(l);
@@ -1450,7 +1484,9 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             }
         }
         R.flush_gemm();
+        lap.mark("cr:reps");
         run_chains(R, chains, pool);
+        lap.mark("cr:chains");
         // condensed matrices (transposed): [Z_t V^*; w G_tr^* ...]; SVD
         int* d_counts = (int*)R.dalloc(nl);
         H2_CUDA(cudaMemsetAsync(d_counts, 0, sizeof(int) * nl, R.stream()));
@@ -1496,8 +1532,11 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             }
             sb.add(Ct, ncol, rows[i], eps, d_counts + i);
         }
+        lap.mark("cr:condensed");
         std::vector<SvdOut> so = sb.run();
+        lap.mark("cr:svd");
         std::vector<int> kk = read_counts(R, d_counts, nl);
+        lap.mark("cr:sync");
         size_t need = 0;
         for (int i = 0; i < nl; ++i) {
             Qn.rank[c0 + i] = (so[i].U ? kk[i] : 0);
@@ -1530,6 +1569,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             out.Rt.p[t] = R.palloc((size_t)std::max(1, kt * Q.rank[t]));
         }
         R.flush_copy();
+        lap.mark("cr:basis");
         for (int i = 0; i < nl; ++i) {
             int t = c0 + i, kt = Qn.rank[t];
             double* q = (leaf ? Qn.leaf[t] : nullptr);
@@ -1577,6 +1617,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
             pp[(l + 1) & 1]->release_all();
         }
         R.release(mkl);
+        lap.mark("cr:project");
     }
     R.release(mk0);
     return out;
@@ -1590,6 +1631,7 @@ static Coarse coarsen_rows(Runner& R, const GView& G, const std::vector<int>& cm
 static std::vector<double*> final_couplings(Runner& R, const Intermediate& G, const Tree& T,
                                             const std::vector<int>& cmap, const Coarse& rb, const Coarse& cb,
                                             const BlockTree& Zb, Counts& cnt) {
+    H2_SPAN("final_couplings");
     const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
     const Basis& Qn = *rb.Qn;
@@ -1813,6 +1855,7 @@ static void product_error(const h2_matrix* Zr, const h2_matrix* Z0, const h2_mat
 // The product block tree depends only on the two block trees: kept on the
 // structure of X, keyed by the fingerprint of Y's structure.
 static const ProductTree& cached_product_tree(Structure& xs, const Structure& ys) {
+    H2_SPAN("cached_product_tree");
     std::lock_guard<std::mutex> g(xs.plan_mutex);
     auto it = xs.product_trees.find(ys.fingerprint);
     if (it == xs.product_trees.end())
@@ -1840,11 +1883,11 @@ static bool same_col_basis(const h2_matrix* A, const h2_matrix* B) {
 // device and runs the sides in order on one stream.
 struct SideStream {
     cudaStream_t s = nullptr;
-    SideStream() { H2_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)); }
+    SideStream() : s(stream_get()) {}
     ~SideStream() {
         if (s) {
             cudaStreamSynchronize(s);
-            cudaStreamDestroy(s);
+            stream_put(s);
         }
     }
 };
@@ -1918,6 +1961,7 @@ struct PhaseB {
 static PhaseB coarsen_and_project(Runner& R, Runner& R2, cudaStream_t st, SideStream& side, bool beside,
                                   const Tree& T, const BlockTree& Zb, const h2_matrix* Zm, Intermediate& G,
                                   double eps, Counts& cnt, PhaseClock& clk, PhaseClock& clk2) {
+    H2_SPAN("coarsen_and_project");
     // phase B: coarsening to Z's block tree
     const BlockTree& N = G.PT->nodes;
     const int nn = (int)N.kind.size();
@@ -2031,6 +2075,7 @@ static PhaseB coarsen_and_project(Runner& R, Runner& R2, cudaStream_t st, SideSt
 }
 
 static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, const h2_opts* opts) {
+    H2_SPAN("mul_add");
     const double eps = opts ? opts->eps : 1e-6;
     const int prec = resolve_precision(opts ? opts->precision : H2_FP64, eps);
     cudaStream_t st = stream_of(opts);
@@ -2089,17 +2134,18 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     const Coarse& cb = pb.cb;
     auto& res = pb.res;
     clk.mark();
-    int flag = 0, flag2 = 0, flag3 = 0;
-    H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(&flag2, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    int* hf = (int*)R.pinned_host(3 * sizeof(int));  // pinned: the copies stay asynchronous
+    hf[0] = hf[1] = hf[2] = 0;
+    H2_CUDA(cudaMemcpyAsync(hf, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(hf + 1, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     if (R.combiner() && R.combiner()->flag())  // grouped launches of a batched call
-        H2_CUDA(cudaMemcpyAsync(&flag3, R.combiner()->flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA(cudaMemcpyAsync(hf + 2, R.combiner()->flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     H2_CUDA(cudaGetLastError());
     {
         CombIdle idle(R.combiner());
         H2_CUDA(cudaStreamSynchronize(st));
     }
-    flag |= flag2 | flag3;
+    const int flag = hf[0] | hf[1] | hf[2];
     if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
     if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
@@ -2286,17 +2332,18 @@ static void recompress(h2_matrix* A, const h2_opts* opts) {
     clk2.mark();
     PhaseB pb = coarsen_and_project(R, R2, st, side, low_precision(prec), T, B, A, G, eps, cnt, clk, clk2);
     clk.mark();
-    int flag = 0, flag2 = 0, flag3 = 0;
-    H2_CUDA(cudaMemcpyAsync(&flag, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
-    if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(&flag2, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    int* hf = (int*)R.pinned_host(3 * sizeof(int));  // pinned: the copies stay asynchronous
+    hf[0] = hf[1] = hf[2] = 0;
+    H2_CUDA(cudaMemcpyAsync(hf, R.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (R2.svd_flag()) H2_CUDA(cudaMemcpyAsync(hf + 1, R2.svd_flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     if (R.combiner() && R.combiner()->flag())  // grouped launches of a batched call
-        H2_CUDA(cudaMemcpyAsync(&flag3, R.combiner()->flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
+        H2_CUDA(cudaMemcpyAsync(hf + 2, R.combiner()->flag(), sizeof(int), cudaMemcpyDeviceToHost, st));
     H2_CUDA(cudaGetLastError());
     {
         CombIdle idle(R.combiner());
         H2_CUDA(cudaStreamSynchronize(st));
     }
-    flag |= flag2 | flag3;
+    const int flag = hf[0] | hf[1] | hf[2];
     if (flag & 2) throw Error(H2_ERR_NUMERIC, "non-finite value in the result");
     if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
     if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
@@ -2341,6 +2388,7 @@ void h2_set_last_error(const char* m);
 static int run_guarded_mul(h2_matrix* Z, const h2_matrix* X, const h2_matrix* Y, const h2_opts* opts) {
     try {
         h2::mul_add(Z, X, Y, opts);
+        h2::host_spans_dump();
         return H2_OK;
     } catch (const h2::Error& e) {
         h2_set_last_error(e.what());
@@ -2392,7 +2440,7 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
     std::unique_ptr<Combiner> comb;
     if (grouping && count > 1) {
         try {
-            if (cudaStreamCreateWithFlags(&cst, cudaStreamNonBlocking) != cudaSuccess) throw Error(H2_ERR_CUDA, "stream");
+            cst = stream_get();
             AllocScope as(alloc_of(opts), cst);
             comb = std::make_unique<Combiner>(cst, resolve_precision(opts ? opts->precision : H2_FP64,
                                                                      opts ? opts->eps : 1e-6));
@@ -2412,7 +2460,9 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
     auto work = [&]() {
         cudaSetDevice(dev);
         cudaStream_t st = nullptr;
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        try {
+            st = stream_get();
+        } catch (const std::exception&) {
             for (int i = next.fetch_add(count); i < count; ++i) codes[i] = H2_ERR_CUDA;
             return;
         }
@@ -2438,7 +2488,7 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
             }
         }
         cudaStreamSynchronize(st);
-        cudaStreamDestroy(st);
+        stream_put(st);
     };
     std::vector<std::thread> pool;
     for (int w = 0; w < workers; ++w) pool.emplace_back(work);
@@ -2451,7 +2501,10 @@ extern "C" int h2_mul_add_batched(h2_matrix* const* Z, const h2_matrix* const* X
         CS.kernel_launches = comb->runner().launches;
         comb.reset();
     }
-    if (cst) cudaStreamDestroy(cst);
+    if (cst) {
+        cudaStreamSynchronize(cst);
+        stream_put(cst);
+    }
     if (opts && opts->stats) {  // sums over the products (times: device time of each product)
         h2_stats S = CS;
         for (const h2_stats& x : stats) {
