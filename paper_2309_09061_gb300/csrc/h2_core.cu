@@ -901,9 +901,9 @@ void Runner::flush_qr() {
 }
 
 void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
-                 const int* rowperm) {
+                 const int* rowperm, const int* ncols) {
     ensure_flag();
-    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, nullptr, m, n, ldb, ldu, eps, rowperm});
+    svds_.push_back(SVDJob{B, U, sigma, count, d_flag_, nullptr, m, n, ldb, ldu, eps, rowperm, ncols});
     svd_maxn_ = std::max(svd_maxn_, n);
 }
 
@@ -924,10 +924,11 @@ void Runner::flush_svd() {
     svd_maxn_ = 0;
 }
 
-void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64, double* W64) {
+void Runner::jacobi_pre(const double* B, int m, int n, int ldb, double* V64, double* W64, const int* ncols) {
+    if (V64 && ncols) throw Error(H2_ERR_ARG, "jacobi_pre: accumulated rotations with a device column count");
     float* W = (float*)dalloc(((size_t)m * n + 1) / 2);
     float* V = V64 ? (float*)dalloc(((size_t)n * n + 1) / 2) : nullptr;
-    pres_.push_back(PreJob{B, W, V, V64, W64, nullptr, m, n, ldb});
+    pres_.push_back(PreJob{B, W, V, V64, W64, nullptr, m, n, ldb, ncols});
 }
 
 void Runner::flush_pre() {
@@ -951,10 +952,11 @@ void Runner::flush_pre() {
     pres_.clear();
 }
 
-void Runner::pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol) {
+void Runner::pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol, double abs_tol,
+                   int* rank) {
     if (k <= 0 || zrows <= 0) return;
     if (k > 1024) throw Error(H2_ERR_UNSUPPORTED, "weight matrix larger than 1024");
-    chols_.push_back(CholJob{G, dalloc((size_t)k * k), Z, k, ldg, zrows, rel_tol});
+    chols_.push_back(CholJob{G, dalloc((size_t)k * k), Z, k, ldg, zrows, rel_tol, abs_tol, rank});
 }
 
 void Runner::flush_pchol() {

@@ -290,6 +290,7 @@ struct SVDJob {
     int m, n, ldb, ldu;
     double eps;
     const int* rowperm;  // when set: row i of the singular vectors goes to row rowperm[i] of U
+    const int* ncols;    // when set: only the first min(n, *ncols) columns of B are nonzero
 };
 
 // FP32 preconditioning of a one-sided Jacobi SVD: sweeps on an FP32 copy W of
@@ -302,17 +303,23 @@ struct PreJob {
     double* W64;    // when set: the rotated W in FP64 (m x n, ld m)
     double* flops;  // optional accumulator: executed sweep flops
     int m, n, ldb;
+    const int* ncols;  // when set: only the first min(n, *ncols) columns of B are nonzero
 };
 
 // Pivoted Cholesky of a symmetric positive semidefinite G (k x k, FP64): Z
 // (k x k, ld k) receives a factor with Z^* Z = G up to the pivots below
-// rel_tol * max(diag G), which are dropped (their rows of Z stay zero).
+// rel_tol * max(diag G), which are dropped (their rows of Z stay zero).  With
+// abs_tol > 0 it also stops once the trace of the remaining Schur complement
+// is at most abs_tol: then G - Z^* Z is positive semidefinite with trace <=
+// abs_tol.  *rank (when set) receives the number of pivots taken.
 struct CholJob {
     const double* G;
     double* W;  // workspace k x k
     double* Z;  // zrows x k, ld zrows; at most zrows pivots are taken
     int k, ldg, zrows;
     double rel_tol;
+    double abs_tol;
+    int* rank;
 };
 
 // Spectral norm of A (m x n) by power iteration; writes 1/||A|| (0 if the norm
@@ -526,12 +533,16 @@ public:
     // Q = I - V T V^T with V (m x p) and T (p x p), p = min(m, n)
     void qr_wy(double* A, int m, int n, int lda, double* V, double* T);
     void flush_qr();
+    // ncols (device, optional): only the first min(n, *ncols) columns of B are
+    // nonzero; the sweeps and the outputs cover those columns only
     void svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
-             const int* rowperm = nullptr);
+             const int* rowperm = nullptr, const int* ncols = nullptr);
     void flush_svd();
-    void jacobi_pre(const double* B, int m, int n, int ldb, double* V64, double* W64 = nullptr);
+    void jacobi_pre(const double* B, int m, int n, int ldb, double* V64, double* W64 = nullptr,
+                    const int* ncols = nullptr);
     void flush_pre();
-    void pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol);
+    void pchol(const double* G, int k, int ldg, double* Z, int zrows, double rel_tol, double abs_tol = 0.0,
+               int* rank = nullptr);
     void flush_pchol();
     void norm(const double* A, int m, int n, int lda, double* inv, double* nrm);
     void flush_norm();

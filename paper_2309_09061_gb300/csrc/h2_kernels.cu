@@ -1219,7 +1219,7 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre(const PreJob* __restrict__ jo
     extern __shared__ float pre_smem[];
     __shared__ int rotated;
     const PreJob J = jobs[blockIdx.x];
-    const int m = J.m, n = J.n;
+    const int m = J.m, n = J.ncols ? min(J.n, max(*J.ncols, 0)) : J.n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
     const bool in_smem = (size_t)m * n * sizeof(float) <= (size_t)smem_bytes;
     const bool v_smem = in_smem && J.V && (size_t)(m + n) * n * sizeof(float) <= (size_t)smem_bytes;
@@ -1319,7 +1319,7 @@ __global__ void __launch_bounds__(JT) k_jacobi_pre_cluster(const PreJob* __restr
     const PreJob& J = jobs[blockIdx.x / cs];
     __shared__ int rotated, large;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
-    const int m = J.m, n = J.n;
+    const int m = J.m, n = J.ncols ? min(J.n, max(*J.ncols, 0)) : J.n;
     float* B = J.W;  // m x n, ld m
     float* V = J.V;  // n x n, ld n
     for (int64_t e = threadIdx.x + (int64_t)cr * JT; e < (int64_t)m * n; e += (int64_t)JT * cs)
@@ -1511,7 +1511,8 @@ __global__ void __launch_bounds__(JT) k_jacobi64(const SVDJob* __restrict__ jobs
         cr = (int)cg::this_cluster().block_rank();
     }
     const SVDJob& J = jobs[blockIdx.x / cs];
-    const int m = J.m, n = J.n, ldb = J.ldb, np = n + (n & 1), half = np / 2;
+    const int m = J.m, n = J.ncols ? min(J.n, max(*J.ncols, 0)) : J.n, ldb = J.ldb, np = n + (n & 1),
+              half = np / 2;
     const int kmax = (half + cs - 1) / cs;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = JT / 32;
     double* B = J.B;
@@ -1739,17 +1740,19 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_
 // ------------------------------------------------------------------ pivoted Cholesky
 // Symmetric pivoting on the largest remaining diagonal entry (Higham,
 // "Accuracy and Stability of Numerical Algorithms", Sec. 10.3), stopped when
-// the pivot falls below rel_tol times the largest initial diagonal entry.
-// Only the lower triangle of the working copy is read and updated.
+// the pivot falls below rel_tol times the largest initial diagonal entry, or
+// when the trace of the remaining Schur complement (the sum of the remaining
+// diagonal entries) is at most abs_tol.  Only the lower triangle of the
+// working copy is read and updated.
 constexpr int CT = 256;
 constexpr int CMAXK = 1024;
 
 __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) {
     __shared__ int perm[CMAXK];
-    __shared__ double rv[CT / 32];
+    __shared__ double rv[CT / 32], rt[CT / 32];
     __shared__ int ri[CT / 32];
     __shared__ int piv;
-    __shared__ double pval;
+    __shared__ double pval, ptrace;
     const CholJob J = jobs[blockIdx.x];
     const int k = J.k;
     double* W = J.W;
@@ -1774,29 +1777,34 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
     int rank = jmax;
     for (int j = 0; j < jmax; ++j) {
         // pivot: argmax of the remaining diagonal (lowest index on ties)
-        double best = -1.0;
+        double best = -1.0, tr = 0.0;
         int bi = j;
         for (int i = j + threadIdx.x; i < k; i += CT) {
             double d = W[i + (size_t)i * k];
             if (d > best) { best = d; bi = i; }
+            tr += fmax(d, 0.0);
         }
         for (int o = 16; o > 0; o >>= 1) {
             double ob = __shfl_xor_sync(0xffffffffu, best, o);
             int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            tr += __shfl_xor_sync(0xffffffffu, tr, o);
         }
-        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+        if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; rt[threadIdx.x >> 5] = tr; }
         __syncthreads();
         if (threadIdx.x == 0) {
-            double b = rv[0];
+            double b = rv[0], t = rt[0];
             int i0 = ri[0];
-            for (int w = 1; w < CT / 32; ++w)
+            for (int w = 1; w < CT / 32; ++w) {
                 if (rv[w] > b || (rv[w] == b && ri[w] < i0)) { b = rv[w]; i0 = ri[w]; }
+                t += rt[w];
+            }
             piv = i0;
             pval = b;
+            ptrace = t;
         }
         __syncthreads();
-        if (!(pval > tol) || !(pval > 0.0)) {
+        if (!(pval > tol) || !(pval > 0.0) || ptrace <= J.abs_tol) {
             rank = j;
             break;
         }
@@ -1841,6 +1849,7 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && J.rank) *J.rank = rank;
     // Z = L^* P^*: Z[j, perm[i]] = L[i, j] for i >= j, j < rank
     for (int64_t e = threadIdx.x; e < (int64_t)k * rank; e += CT) {
         int i = (int)(e % k), j = (int)(e / k);

@@ -386,6 +386,15 @@ static PerCl total_weights_gram(Runner& R, const OpView& Y) {
 // sweeps than on the matrix itself (Drmac & Veselic, SIAM J. Matrix Anal.
 // Appl. 29, 2008); the pivoted Cholesky factor is that factor (up to signs and
 // the column order), so both routes get the short sweep count.
+// The Cholesky factorisation stops once the trace of what is left is at most
+// (kSvdDrop eps)^2.  What is left, S = G - Z^* Z, is positive semidefinite, so
+// the singular values of Z^* differ from those of Bt by at most kSvdDrop eps
+// (Weyl's inequality on G), and the part of Bt outside the range of Z^* has
+// Frobenius norm at most kSvdDrop eps.  Ranks are decided by sigma > eps, so
+// only directions far below the truncation are dropped; the Jacobi sweeps
+// then run on the factor's r nonzero columns only (r read on the device).
+static constexpr double kSvdDrop = 0.1;
+
 struct SvdOut {
     double* U = nullptr;
     int ldu = 1;
@@ -396,12 +405,13 @@ public:
     explicit SvdBatch(Runner& R) : R_(R) {}
     // queue a job; the returned index identifies its output after run()
     int add(double* Bt, int ncol, int m, double eps, int* count_slot) {
-        Job j{Bt, ncol, m, eps, count_slot, nullptr, nullptr, nullptr, nullptr};
+        Job j{Bt, ncol, m, eps, count_slot, nullptr, nullptr, nullptr, nullptr, nullptr};
         if (m > 0 && ncol > 0) {
             if (ncol > m) {
                 j.Rt = R_.dalloc((size_t)m * m);
                 if ((low_precision(R_.precision()) || eps >= kGramMinEps) && m <= 1024) {
                     j.G = R_.dalloc((size_t)m * m);  // Gram route: formed and factored in run()
+                    j.r = (int*)R_.dalloc(1);        // the factor's rank, set on the device
                 } else {
                     if (m <= kQRPivMax) j.piv = (int*)R_.dalloc(((size_t)m + 1) / 2);
                     R_.qr(Bt, ncol, m, ncol, j.Rt, m, nullptr, 1, 0, low_precision(R_.precision()), j.piv);
@@ -426,8 +436,10 @@ public:
             }
         if (gram) {
             R_.flush_gemm(H2_FP64);
+            // the factorisation stops once the trace left is (kSvdDrop eps)^2: the
+            // columns it leaves out have Frobenius norm <= kSvdDrop eps together
             for (Job& j : jobs_)
-                if (j.G) R_.pchol(j.G, j.m, j.m, j.Rt, j.m, kCholTol);
+                if (j.G) R_.pchol(j.G, j.m, j.m, j.Rt, j.m, kCholTol, (kSvdDrop * j.eps) * (kSvdDrop * j.eps), j.r);
             R_.flush_pchol();
         }
         R_.flush_qr();
@@ -456,7 +468,7 @@ public:
                 int w = std::min(j.m, j.ncol);
                 if (w < 2) continue;
                 C[i] = R_.dalloc((size_t)j.m * w);
-                R_.jacobi_pre(j.B, j.m, w, j.m, nullptr, C[i]);
+                R_.jacobi_pre(j.B, j.m, w, j.m, nullptr, C[i], j.r);
             }
             R_.flush_pre();
             for (size_t i = 0; i < jobs_.size(); ++i)
@@ -466,7 +478,7 @@ public:
             Job& j = jobs_[i];
             if (!j.B) continue;
             int w = std::min(j.m, j.ncol);
-            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps, j.piv);
+            R_.svd(j.B, j.m, w, j.m, out[i].U, j.m, R_.dalloc(w), j.count, j.eps, j.piv, j.r);
         }
         R_.flush_svd();
         jobs_.clear();
@@ -483,6 +495,7 @@ private:
         double* B;
         int* piv;     // column pivots of the QR of Bt: rows of the wanted vectors
         double* G;    // Gram route: Bt^* Bt
+        int* r;       // Gram route: rank of the Cholesky factor (its nonzero columns of B)
     };
     Runner& R_;
     std::vector<Job> jobs_;
