@@ -964,12 +964,14 @@ void Runner::flush_pchol() {
     if (chols_.empty()) return;
     CholJob* d = upload(chols_);
     double fl = 0.0, by = 0.0;
+    int max_k = 0;
     for (auto& j : chols_) {
         fl += (double)j.k * j.k * j.k / 3.0;
         by += 16.0 * j.k * j.k;
+        max_k = std::max(max_k, j.k);
     }
     begin(4);
-    launch_pchol(d, (int)chols_.size(), st_);
+    launch_pchol(d, (int)chols_.size(), max_k, st_);
     end(4, fl, by);
     ++launches;
     chols_.clear();

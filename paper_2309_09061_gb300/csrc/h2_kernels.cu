@@ -302,6 +302,8 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         const float cf32 = DF ? 0.f : f64_to_f32(cf);
         const bool unit = (cf == 1.0 || cf == -1.0);  // the same for the whole block
         const float sgn = (cf < 0.0) ? -1.f : 1.f;
+        float fh = 0.f, fl = 0.f;  // the factor as a double-float pair (DF)
+        if constexpr (DF) split_f64(cf, fh, fl);
         float* const as0 = &As[0][0][0];
         float* const bs0 = &Bs[0][0][0];
         constexpr int PL = KC * kF32Tile;  // floats per plane
@@ -318,7 +320,17 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                     ah *= sgn;
                     al *= sgn;
                 } else {
-                    split_f64(ra[r] * cf, ah, al);  // the factor applied in FP64
+                    // the factor applied in double-float arithmetic on the FP32 pipe
+                    // (an FP64 multiply per element would load the 1/64-rate FP64 pipe):
+                    // (xh + xl)(fh + fl) = p + e exactly up to xl fl, then Fast2Sum
+                    float xh, xl;
+                    split_f64(ra[r], xh, xl);
+                    const float p = __fmul_rn(xh, fh);
+                    float e = __fmaf_rn(xh, fh, -p);
+                    e = __fmaf_rn(xh, fl, e);
+                    e = __fmaf_rn(xl, fh, e);
+                    ah = __fadd_rn(p, e);
+                    al = __fsub_rn(e, __fsub_rn(ah, p));
                 }
                 split_f64(rb[r], bh, bl);
                 as0[pa] = ah;
@@ -1743,11 +1755,17 @@ void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_
 // the pivot falls below rel_tol times the largest initial diagonal entry, or
 // when the trace of the remaining Schur complement (the sum of the remaining
 // diagonal entries) is at most abs_tol.  Only the lower triangle of the
-// working copy is read and updated.
+// working copy is read and updated.  It lives in shared memory, packed by
+// columns, when k (k + 1) / 2 doubles fit (SMEM): each column step then waits on
+// shared-memory latency instead of L2 latency.  Otherwise it is the job's
+// k x k workspace in global memory.
 constexpr int CT = 256;
 constexpr int CMAXK = 1024;
+constexpr int kCholSmem = 96 * 1024;
 
+template <bool SMEM>
 __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) {
+    extern __shared__ double cw[];
     __shared__ int perm[CMAXK];
     __shared__ double rv[CT / 32], rt[CT / 32];
     __shared__ int ri[CT / 32];
@@ -1755,14 +1773,24 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
     __shared__ double pval, ptrace;
     const CholJob J = jobs[blockIdx.x];
     const int k = J.k;
-    double* W = J.W;
-    for (int e = threadIdx.x; e < k * k; e += CT) W[e] = J.G[(e % k) + (size_t)(e / k) * J.ldg];
+    double* const W = SMEM ? cw : J.W;
+    // entry (i, j), i >= j, of the lower triangle
+    auto at = [&](int i, int j) -> double& {
+        if constexpr (SMEM)
+            return W[(size_t)j * k - ((size_t)j * (j - 1)) / 2 + (i - j)];
+        else
+            return W[i + (size_t)j * k];
+    };
+    for (int e = threadIdx.x; e < k * k; e += CT) {
+        const int i = e % k, j = e / k;
+        if (i >= j) at(i, j) = J.G[i + (size_t)j * J.ldg];
+    }
     for (int i = threadIdx.x; i < k; i += CT) perm[i] = i;
     for (int e = threadIdx.x; e < J.zrows * k; e += CT) J.Z[e] = 0.0;
     __syncthreads();
     // largest initial diagonal entry
     double md = 0.0;
-    for (int i = threadIdx.x; i < k; i += CT) md = fmax(md, W[i + (size_t)i * k]);
+    for (int i = threadIdx.x; i < k; i += CT) md = fmax(md, at(i, i));
     for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
     if ((threadIdx.x & 31) == 0) rv[threadIdx.x >> 5] = md;
     __syncthreads();
@@ -1776,11 +1804,11 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
     const int jmax = J.zrows < k ? J.zrows : k;
     int rank = jmax;
     for (int j = 0; j < jmax; ++j) {
-        // pivot: argmax of the remaining diagonal (lowest index on ties)
+        // pivot: argmax of the remaining diagonal (lowest index on ties), and its trace
         double best = -1.0, tr = 0.0;
         int bi = j;
         for (int i = j + threadIdx.x; i < k; i += CT) {
-            double d = W[i + (size_t)i * k];
+            double d = at(i, i);
             if (d > best) { best = d; bi = i; }
             tr += fmax(d, 0.0);
         }
@@ -1810,20 +1838,20 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
         }
         const int p = piv;
         if (p != j) {  // symmetric swap of j and p (j < p) on the lower triangle
-            auto sw = [&](size_t x, size_t y) {
-                double t = W[x];
-                W[x] = W[y];
-                W[y] = t;
+            auto sw = [&](double& x, double& y) {
+                double t = x;
+                x = y;
+                y = t;
             };
             for (int c = threadIdx.x; c < k; c += CT) {
                 if (c < j)
-                    sw(j + (size_t)c * k, p + (size_t)c * k);  // rows j and p left of column j
+                    sw(at(j, c), at(p, c));  // rows j and p left of column j
                 else if (c > j && c < p)
-                    sw(c + (size_t)j * k, p + (size_t)c * k);  // column j between j and p <-> row p
+                    sw(at(c, j), at(p, c));  // column j between j and p <-> row p
                 else if (c > p)
-                    sw(c + (size_t)j * k, c + (size_t)p * k);  // columns j and p below row p
+                    sw(at(c, j), at(c, p));  // columns j and p below row p
                 else if (c == j)
-                    sw(j + (size_t)j * k, p + (size_t)p * k);  // the diagonal entries
+                    sw(at(j, j), at(p, p));  // the diagonal entries
             }
             if (threadIdx.x == 0) {
                 int t = perm[j];
@@ -1832,19 +1860,19 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
             }
             __syncthreads();
         }
-        const double d = sqrt(W[j + (size_t)j * k]);
+        const double d = sqrt(at(j, j));
         const double inv = 1.0 / d;
         __syncthreads();
-        for (int i = j + 1 + threadIdx.x; i < k; i += CT) W[i + (size_t)j * k] *= inv;
-        if (threadIdx.x == 0) W[j + (size_t)j * k] = d;
+        for (int i = j + 1 + threadIdx.x; i < k; i += CT) at(i, j) *= inv;
+        if (threadIdx.x == 0) at(j, j) = d;
         __syncthreads();
         // trailing update of the lower triangle (one warp per column)
         {
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             for (int l = j + 1 + warp; l < k; l += CT / 32) {
-                const double wl = W[l + (size_t)j * k];
+                const double wl = at(l, j);
                 if (wl == 0.0) continue;
-                for (int i = l + lane; i < k; i += 32) W[i + (size_t)l * k] -= W[i + (size_t)j * k] * wl;
+                for (int i = l + lane; i < k; i += 32) at(i, l) -= at(i, j) * wl;
             }
         }
         __syncthreads();
@@ -1853,12 +1881,29 @@ __global__ void __launch_bounds__(CT) k_pchol(const CholJob* __restrict__ jobs) 
     // Z = L^* P^*: Z[j, perm[i]] = L[i, j] for i >= j, j < rank
     for (int64_t e = threadIdx.x; e < (int64_t)k * rank; e += CT) {
         int i = (int)(e % k), j = (int)(e / k);
-        if (i >= j) J.Z[j + (size_t)perm[i] * J.zrows] = W[i + (size_t)j * k];
+        if (i >= j) J.Z[j + (size_t)perm[i] * J.zrows] = at(i, j);
     }
 }
 
-void launch_pchol(const CholJob* jobs, int njobs, cudaStream_t st) {
-    if (njobs > 0) k_pchol<<<njobs, CT, 0, st>>>(jobs);
+void launch_pchol(const CholJob* jobs, int njobs, int max_k, cudaStream_t st) {
+    if (njobs <= 0) return;
+    const size_t tri = (size_t)max_k * (max_k + 1) / 2 * sizeof(double);
+    if (tri <= (size_t)kCholSmem) {
+        static bool attr_set[64] = {};
+        static std::mutex mu;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+                cudaFuncSetAttribute(k_pchol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmem);
+                attr_set[dev] = true;
+            }
+        }
+        k_pchol<true><<<njobs, CT, tri, st>>>(jobs);
+    } else {
+        k_pchol<false><<<njobs, CT, 0, st>>>(jobs);
+    }
 }
 
 // ------------------------------------------------------------------ spectral norm
