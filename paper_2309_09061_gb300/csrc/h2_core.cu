@@ -900,6 +900,23 @@ void Runner::flush_qr() {
     qrs_.clear();
 }
 
+// With H2_TRACE set: "h2jobs <kind> <jobs> <max m> <max n> <mean m> <mean n>" per launch
+template <class V>
+static void trace_jobs(const char* kind, const V& jobs) {
+    static const bool trace = std::getenv("H2_TRACE") != nullptr;
+    if (!trace || jobs.empty()) return;
+    double sm = 0, sn = 0;
+    int mm = 0, mn = 0;
+    for (const auto& j : jobs) {
+        sm += j.m;
+        sn += j.n;
+        mm = std::max(mm, j.m);
+        mn = std::max(mn, j.n);
+    }
+    std::fprintf(stderr, "h2jobs %s %zu %d %d %.1f %.1f\n", kind, jobs.size(), mm, mn, sm / jobs.size(),
+                 sn / jobs.size());
+}
+
 void Runner::svd(double* B, int m, int n, int ldb, double* U, int ldu, double* sigma, int* count, double eps,
                  const int* rowperm, const int* ncols) {
     ensure_flag();
@@ -912,11 +929,16 @@ void Runner::flush_svd() {
     if (svds_.empty()) return;
     double* cnt = dev_counter();
     for (auto& j : svds_) j.flops = cnt;
+    trace_jobs("svd", svds_);
     SVDJob* d = upload(svds_);
     double by = 0.0;
     for (auto& j : svds_) by += 8.0 * 3.0 * j.m * j.n;
     begin(5);
-    launch_svd(d, (int)svds_.size(), svd_maxn_, st_);
+    // the low-precision forms run the row and column sides on two streams at once: a
+    // cluster launch holds whole SMs that the other side's kernels could use (measured
+    // on the n = 32768 workload: 235 -> 224 ms per product without clusters there; the
+    // FP64 form, one stream, is faster with them: 1.33 against 1.34 s)
+    launch_svd(d, (int)svds_.size(), svd_maxn_, st_, !low_precision(prec_));
     end(5, 0.0, by);
     marks_.back().dflops = cnt;
     ++launches;
@@ -944,8 +966,9 @@ void Runner::flush_pre() {
         max_mn = std::max(max_mn, (size_t)j.m * j.n);
         max_mnv = std::max(max_mnv, (size_t)(j.m + (j.V ? j.n : 0)) * j.n);
     }
+    trace_jobs("pre", pres_);
     begin(6);
-    launch_jacobi_pre(d, (int)pres_.size(), max_mn, max_mnv, st_);
+    launch_jacobi_pre(d, (int)pres_.size(), max_mn, max_mnv, st_, !low_precision(prec_));
     end(6, 0.0, by);
     marks_.back().dflops = cnt;
     ++launches;

@@ -384,9 +384,12 @@ inline int resolve_precision(int p, double eps) {
 }
 void launch_qr(const QRJob* jobs, int njobs, cudaStream_t st);
 void launch_qr32(const QRJob* jobs, int njobs, cudaStream_t st);
-void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st);
+// clusters: a level with fewer matrices than SMs may spread each matrix over a
+// thread-block cluster (worth it when no other stream's kernels compete for the SMs)
+void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st, bool clusters = true);
 // max_mn: largest m n of the jobs; max_mnv: largest (m + n) n (W and V together)
-void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_mnv, cudaStream_t st);
+void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_mnv, cudaStream_t st,
+                       bool clusters = true);
 void launch_pchol(const CholJob* jobs, int njobs, int max_k, cudaStream_t st);
 void launch_norm(const NormJob* jobs, int njobs, int precision, cudaStream_t st);
 void launch_copy(const CopyJob* jobs, int njobs, cudaStream_t st);

@@ -1719,10 +1719,10 @@ static bool launch_clustered(void (*kern)(Args...), int nblocks, int cs, size_t 
     return true;
 }
 
-void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
+void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st, bool clusters) {
     if (max_n > JMAXN) throw Error(H2_ERR_UNSUPPORTED, "SVD wider than 2048 columns");
     if (njobs <= 0) return;
-    const int cs = jacobi_cluster_size(njobs);
+    const int cs = clusters ? jacobi_cluster_size(njobs) : 1;
     if (cs > 1 && launch_clustered(k_jacobi64<true>, njobs * cs, cs,
                                    std::max(j64_smem_bytes(max_n, cs), kClusterDynSmem), st, jobs))
         return;
@@ -1731,9 +1731,10 @@ void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st) {
     k_jacobi64<false><<<njobs, JT, smem, st>>>(jobs);
 }
 
-void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_mnv, cudaStream_t st) {
+void launch_jacobi_pre(const PreJob* jobs, int njobs, size_t max_mn, size_t max_mnv, cudaStream_t st,
+                       bool clusters) {
     if (njobs <= 0) return;
-    int cs = jacobi_cluster_size(njobs);
+    int cs = clusters ? jacobi_cluster_size(njobs) : 1;
     if (cs <= 1 || !launch_clustered(k_jacobi_pre_cluster, njobs * cs, cs, kClusterDynSmem, st, jobs)) {
         static bool attr_set[64] = {};
         int dev = 0;

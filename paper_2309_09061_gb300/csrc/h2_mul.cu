@@ -521,6 +521,16 @@ static std::vector<int> read_counts(Runner& R, int* d_counts, int n) {
                 std::fprintf(stderr, "h2sync %p %.3f %.3f\n", (void*)R.stream(), h0, host_clock_ms());
         }
         std::copy(hp, hp + n, h.begin());
+        static const bool trace_r = std::getenv("H2_TRACE") != nullptr;
+        if (trace_r) {  // "h2ranks <clusters> <mean rank> <max rank>"
+            double sr = 0;
+            int mr = 0;
+            for (int x : h) {
+                sr += x;
+                mr = std::max(mr, x);
+            }
+            std::fprintf(stderr, "h2ranks %d %.1f %d\n", n, sr / n, mr);
+        }
         const int flag = hp[n];
         if (flag & 1) throw Error(H2_ERR_TIMEOUT, "Jacobi SVD did not converge within its sweep limit");
         if (flag & 4) throw Error(H2_ERR_TIMEOUT, "tensor-core product wait timed out");
