@@ -174,8 +174,9 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
     // at g ^ sh(kk) and element c of a group at c ^ sq(kk).  Staging along a
     // row and along a column is then free of bank conflicts, and each thread
     // reads its 4 values of a row as one 16-byte load (2 wavefronts a warp).
-    __shared__ __align__(16) float As[NP][KC][kF32Tile];
-    __shared__ __align__(16) float Bs[NP][KC][kF32Tile];
+    // two stages: the chunk being multiplied and the next one being stored
+    __shared__ __align__(16) float As[2][NP][KC][kF32Tile];
+    __shared__ __align__(16) float Bs[2][NP][KC][kF32Tile];
     __shared__ GTerm tc[G32TB];
     __shared__ double tf[G32TB];
     __shared__ int tbase;
@@ -259,11 +260,11 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         }
     };
     // one k step; D = kk mod 4, known at compile time, fixes the in-group order
-    auto mac = [&](int kk, auto D) {
+    auto mac = [&](int sg, int kk, auto D) {
         constexpr int q = DF ? (decltype(D)::value & 1) << 1 : decltype(D)::value;
         float a[4], b[4];
-        const float4 va = *reinterpret_cast<const float4*>(&As[0][kk][(tx ^ sh(kk)) << 2]);
-        const float4 vb = *reinterpret_cast<const float4*>(&Bs[0][kk][(ty ^ sh(kk)) << 2]);
+        const float4 va = *reinterpret_cast<const float4*>(&As[sg][0][kk][(tx ^ sh(kk)) << 2]);
+        const float4 vb = *reinterpret_cast<const float4*>(&Bs[sg][0][kk][(ty ^ sh(kk)) << 2]);
         unpack4<q>(va, a);
         unpack4<q>(vb, b);
         if constexpr (!DF) {
@@ -273,8 +274,8 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                 for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
         } else {
             float al[4], bl[4];
-            unpack4<q>(*reinterpret_cast<const float4*>(&As[NP - 1][kk][(tx ^ sh(kk)) << 2]), al);
-            unpack4<q>(*reinterpret_cast<const float4*>(&Bs[NP - 1][kk][(ty ^ sh(kk)) << 2]), bl);
+            unpack4<q>(*reinterpret_cast<const float4*>(&As[sg][NP - 1][kk][(tx ^ sh(kk)) << 2]), al);
+            unpack4<q>(*reinterpret_cast<const float4*>(&Bs[sg][NP - 1][kk][(ty ^ sh(kk)) << 2]), bl);
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
@@ -292,24 +293,20 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                 }
         }
     };
-    int cit = -1, ck0 = 0;
-    GTerm CP;
-    double cf = 0.0;
-    bool have = advance(cit, ck0, CP, cf);
-    if (have) fetch(CP, ck0);
-    while (have) {
-        // the chunk in flight goes to shared memory (A scaled by the term's factor)
-        const float cf32 = DF ? 0.f : f64_to_f32(cf);
-        const bool unit = (cf == 1.0 || cf == -1.0);  // the same for the whole block
-        const float sgn = (cf < 0.0) ? -1.f : 1.f;
+    // the staged chunk (raw values of term P in ra / rb) goes to shared-memory stage sg,
+    // A scaled by the term's factor f
+    auto store = [&](int sg, const GTerm& P, double f) {
+        const float cf32 = DF ? 0.f : f64_to_f32(f);
+        const bool unit = (f == 1.0 || f == -1.0);  // the same for the whole block
+        const float sgn = (f < 0.0) ? -1.f : 1.f;
         float fh = 0.f, fl = 0.f;  // the factor as a double-float pair (DF)
-        if constexpr (DF) split_f64(cf, fh, fl);
-        float* const as0 = &As[0][0][0];
-        float* const bs0 = &Bs[0][0][0];
+        if constexpr (DF) split_f64(f, fh, fl);
+        float* const as0 = &As[sg][0][0][0];
+        float* const bs0 = &Bs[sg][0][0][0];
         constexpr int PL = KC * kF32Tile;  // floats per plane
 #pragma unroll
         for (int r = 0; r < NE; ++r) {
-            const int pa = soff(CP.ta != 0, r), pb = soff(CP.tb == 0, r);
+            const int pa = soff(P.ta != 0, r), pb = soff(P.tb == 0, r);
             if constexpr (!DF) {
                 as0[pa] = cf32 * f64_to_f32(ra[r]);
                 bs0[pb] = f64_to_f32(rb[r]);
@@ -339,12 +336,25 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                 bs0[PL + pb] = bl;
             }
         }
+    };
+    int cit = -1, ck0 = 0;
+    GTerm CP;
+    double cf = 0.0;
+    bool have = advance(cit, ck0, CP, cf);
+    int sg = 0;
+    if (have) {
+        fetch(CP, ck0);
+        store(0, CP, cf);
+    }
+    __syncthreads();
+    // one barrier per chunk: the next chunk is fetched before the multiply-adds of
+    // this one and stored into the other stage after them
+    while (have) {
         const int kc = min(KC, CP.k - ck0);
         int nit = cit, nk0 = ck0;
         GTerm NP_ = CP;
         double nf = cf;
         const bool more = advance(nit, nk0, NP_, nf);  // may sync (term cache)
-        __syncthreads();
         if (more) fetch(NP_, nk0);
         // rows kc .. KC-1 hold zeros, so a partial chunk may run to a multiple of 4
         constexpr std::integral_constant<int, 0> d0;
@@ -356,18 +366,18 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
         } else if (!DF && kc == KC) {  // (the double-float step is long: its loop stays rolled for the instruction cache)
 #pragma unroll
             for (int kk = 0; kk < KC; kk += 4) {
-                mac(kk, d0);
-                mac(kk + 1, d1);
-                mac(kk + 2, d2);
-                mac(kk + 3, d3);
+                mac(sg, kk, d0);
+                mac(sg, kk + 1, d1);
+                mac(sg, kk + 2, d2);
+                mac(sg, kk + 3, d3);
             }
         } else {
 #pragma unroll 1
             for (int kk = 0; kk < kc; kk += 4) {
-                mac(kk, d0);
-                mac(kk + 1, d1);
-                mac(kk + 2, d2);
-                mac(kk + 3, d3);
+                mac(sg, kk, d0);
+                mac(sg, kk + 1, d1);
+                mac(sg, kk + 2, d2);
+                mac(sg, kk + 3, d3);
             }
         }
         if constexpr (DF) {
@@ -381,7 +391,10 @@ __global__ void __launch_bounds__(GT, DF ? 2 : 3) k_gemm_f32(const GTerm* __rest
                     acc[x][y] = t;
                 }
         }
+        // the other stage was last read in the previous chunk, before the barrier below it
+        if (more) store(sg ^ 1, NP_, nf);
         __syncthreads();
+        sg ^= 1;
         cit = nit;
         ck0 = nk0;
         CP = NP_;
