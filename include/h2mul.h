@@ -301,6 +301,25 @@ H2_API int h2_recompress(h2_matrix* A, const h2_opts* opts);
 H2_API int h2_product_error(const h2_matrix* Zr, const h2_matrix* Z0, const h2_matrix* X, const h2_matrix* Y,
                             const double* x0, int steps, const h2_opts* opts, double* eps2, double* norm);
 
+/* Spectral norms of the blocks of A's block tree, computed on the device by
+ * the power iteration that the product uses for its block weights (Sec. 5 and
+ * Sec. 6: ranks are chosen relative to block norms).  For block b, 0 <= b <
+ * nblocks (h2_info), in the order of the block tree:
+ *   t[b], s[b]  its row and column clusters (indices as in h2_get_structure)
+ *   kind[b]     0 admissible, 1 dense (inadmissible leaf), 2 split
+ *   norm[b]     ||S_b||_2 of the coupling matrix of an admissible block
+ *               (rank(t) x rank(s)), ||N_b||_2 of a dense block, 0 for a split
+ *               block
+ * opts->precision selects the iteration as in the product: H2_FP64 (or
+ * H2_AUTO resolving to it) iterates in FP64 and stops when the estimate
+ * changes by less than 1e-10 (relative), every other mode in FP32 and stops
+ * at 1e-5; at most 60 steps from x_j = 1 + 0.37 j / n.  Each value is the
+ * length of A_b x for the last unit vector x: a lower bound of the norm up to
+ * rounding.  Any output pointer may be NULL (host arrays of nblocks entries).
+ * Errors: H2_ERR_ARG, H2_ERR_UNSUPPORTED (a block wider than 2048),
+ * H2_ERR_OOM, H2_ERR_CUDA. */
+H2_API int h2_block_norms(const h2_matrix* A, const h2_opts* opts, int* t, int* s, int* kind, double* norm);
+
 /* Sizes and structure of a handle.  Errors: H2_ERR_ARG. */
 H2_API int h2_info(const h2_matrix* A, h2_info_t* info);
 

@@ -27,7 +27,8 @@ PRECISIONS = {"fp64": H2_FP64, "mixed": H2_MIXED, "tf32x3": H2_TF32X3, "tf32": H
 
 EXPORTED = ["h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
             "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec", "h2_mul_add_batched", "h2_product_error",
-            "h2_recompress", "h2_library_memory", "h2_free", "h2_error_string", "h2_last_error_message"]
+            "h2_recompress", "h2_library_memory", "h2_free", "h2_error_string", "h2_last_error_message",
+            "h2_block_norms"]
 
 
 class H2Error(RuntimeError):
@@ -179,6 +180,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_mul_add_batched.argtypes = [vp, vp, vp, ci, vp, vp]
     lib.h2_product_error.argtypes = [vp, vp, vp, vp, vp, ci, vp, vp, vp]
     lib.h2_recompress.argtypes = [vp, vp]
+    lib.h2_block_norms.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.h2_library_memory.argtypes = [vp, vp, ci]
     lib.h2_library_memory.restype = ci
     lib.h2_free.argtypes = [vp]
@@ -188,7 +190,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     lib.h2_last_error_message.restype = ctypes.c_char_p
     for f in ("h2_build_interp", "h2_build_interp_normals", "h2_mul_add", "h2_to_dense", "h2_info",
               "h2_get_structure", "h2_clone", "h2_plan_structure", "h2_to_dense_noalloc", "h2_matvec",
-              "h2_mul_add_batched", "h2_product_error", "h2_recompress"):
+              "h2_mul_add_batched", "h2_product_error", "h2_recompress", "h2_block_norms"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -391,6 +393,21 @@ def h2_product_error(Zr: H2Matrix, Z0: H2Matrix, X: H2Matrix, Y: H2Matrix, x0=No
     _check(load().h2_product_error(Zr.handle, Z0.handle, X.handle, Y.handle, xp, int(steps), ctypes.byref(o),
                                    ctypes.byref(e), ctypes.byref(nrm)), "h2_product_error")
     return e.value, nrm.value
+
+
+def h2_block_norms(A: H2Matrix, precision: int = H2_FP64, eps: float = 1e-6, stream: int | None = None):
+    """(t, s, kind, norm) per block of A's block tree: clusters, kind (0 admissible,
+    1 dense, 2 split) and the spectral norm of the stored block by the library's
+    power iteration in the given precision (h2_block_norms)."""
+    nb = int(A.info()["nblocks"])
+    t = np.zeros(nb, np.int32)
+    s = np.zeros(nb, np.int32)
+    kind = np.zeros(nb, np.int32)
+    nrm = np.zeros(nb, np.float64)
+    o = _opts(eps=eps, precision=precision, stream=stream)
+    _check(load().h2_block_norms(A.handle, ctypes.byref(o), t.ctypes.data, s.ctypes.data, kind.ctypes.data,
+                                 nrm.ctypes.data), "h2_block_norms")
+    return t, s, kind, nrm
 
 
 def h2_rows(A: H2Matrix, idx):

@@ -703,7 +703,7 @@ void Runner::flush_gemm(int precision_override) {
     pend_flops_ = pend_bytes_ = 0.0;
     pend_tiles32_ = pend_tiles64_ = 0;
     static const bool trace = std::getenv("H2_TRACE") != nullptr;
-    if (trace) {  // "h2gemm <prec> <jobs> <terms> <mean m> <mean n> <mean K per job> <jobs with m,n <= 64> <max m> <max n> <max K>"
+    if (trace) {  // "h2gemm <prec> <jobs> <terms> <mean m> <mean n> <mean K per job> <jobs with m,n <= 64> <max m> <max n> <max K> <stream> <GFLOP>"
         double sm = 0, sn = 0, sk = 0;
         int64_t small = 0, mk = 0;
         int mm = 0, mn = 0;
@@ -719,8 +719,9 @@ void Runner::flush_gemm(int precision_override) {
             mn = std::max(mn, J.n);
         }
         const double nj = (double)jobs_.size();
-        std::fprintf(stderr, "h2gemm %d %zu %zu %.1f %.1f %.1f %lld %d %d %lld\n", pr, jobs_.size(), terms_.size(),
-                     sm / nj, sn / nj, sk / nj, (long long)small, mm, mn, (long long)mk);
+        std::fprintf(stderr, "h2gemm %d %zu %zu %.1f %.1f %.1f %lld %d %d %lld %p %.6f\n", pr, jobs_.size(),
+                     terms_.size(), sm / nj, sn / nj, sk / nj, (long long)small, mm, mn, (long long)mk, (void*)st_,
+                     fl * 1e-9);
     }
     std::vector<SliceSum> sums;
     int64_t nt_all = nt_est;

@@ -2598,6 +2598,49 @@ extern "C" int h2_product_error(const h2_matrix* Zr, const h2_matrix* Z0, const 
     }
 }
 
+extern "C" int h2_block_norms(const h2_matrix* A, const h2_opts* opts, int* t, int* s, int* kind, double* norm) {
+    using namespace h2;
+    if (!A) return H2_ERR_ARG;
+    if (opts && (!(opts->eps >= 0.0) || !std::isfinite(opts->eps) || !valid_precision(opts->precision)))
+        return H2_ERR_ARG;
+    try {
+        const BlockTree& B = A->st->blocks;
+        const Tree& T = A->st->tree;
+        const int nb = (int)B.kind.size();
+        for (int b = 0; b < nb; ++b) {
+            if (t) t[b] = B.t[b];
+            if (s) s[b] = B.s[b];
+            if (kind) kind[b] = B.kind[b] == ADM ? 0 : B.kind[b] == DENSE ? 1 : 2;
+        }
+        if (!norm || nb == 0) return H2_OK;
+        const cudaStream_t st = stream_of(opts);
+        AllocScope scope(alloc_of(opts), st);
+        Runner R(st, resolve_precision(opts ? opts->precision : H2_FP64, opts ? opts->eps : 1e-6));
+        double* d = R.dalloc((size_t)nb);
+        H2_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * nb, st));
+        for (int b = 0; b < nb; ++b) {
+            const int tb = B.t[b], sb = B.s[b];
+            if (B.kind[b] == ADM && A->V->rank[tb] > 0 && A->W->rank[sb] > 0)
+                R.norm(A->blk[b], A->V->rank[tb], A->W->rank[sb], A->V->rank[tb], nullptr, d + b);
+            else if (B.kind[b] == DENSE)
+                R.norm(A->blk[b], (int)T.size[tb], (int)T.size[sb], (int)T.size[tb], nullptr, d + b);
+        }
+        R.flush_norm();
+        double* hp = (double*)R.pinned_host(sizeof(double) * nb);
+        H2_CUDA(cudaMemcpyAsync(hp, d, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+        H2_CUDA(cudaStreamSynchronize(st));
+        std::copy(hp, hp + nb, norm);
+        R.release_all();
+        return H2_OK;
+    } catch (const Error& e) {
+        h2_set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        h2_set_last_error(e.what());
+        return H2_ERR_CUDA;
+    }
+}
+
 extern "C" int h2_recompress(h2_matrix* A, const h2_opts* opts) {
     using namespace h2;
     if (!A) return H2_ERR_ARG;
