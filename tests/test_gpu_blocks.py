@@ -36,7 +36,12 @@ CASES = {
     "cube-n4096-yukawa": ("cube", 4096, O.K_YUKAWA, O.K_YUKAWA, 32, 1.5, 3, 1e-5, 2309090612),
     # X != Y (Laplace x Yukawa) on the cube surface, ragged leaves
     "cube_surface-n3000-mixed-kernels": ("cube_surface", 3000, O.K_LAPLACE, O.K_YUKAWA, 24, 2.0, 3, 1e-5, 31),
+    # the n = 32768 workload's parameters at n = 4096 (leaf 64, order 4, rank 64): phase A's
+    # upper levels have jobs wider than 64 rows, which the tensor-core modes run on tcgen05
+    "sphere-n4096-order4": ("sphere", 4096, O.K_LAPLACE, O.K_LAPLACE, 64, 2.0, 4, 1e-5, 2309090611),
 }
+# cases whose tensor-core products must include tcgen05 launches
+TC_CASES = {"sphere-n4096-order4"}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -82,7 +87,9 @@ def test_every_block(name, precision):
     X = P.h2_build_interp(pts, kx, leaf, eta, order)
     Y = X if ky == kx else P.h2_build_interp(pts, ky, leaf, eta, order)
     Z = P.h2_clone(X)
-    P.h2_mul_add(Z, X, Y, eps, precision)
+    stats = P.h2_mul_add(Z, X, Y, eps, precision)
+    if name in TC_CASES and precision in (P.H2_TF32X3, P.H2_AUTO):
+        assert stats["fam_launches"][P.FAMILIES.index("gemm_tc")] > 0
     perm = Z.structure()[0]
     assert np.array_equal(perm, st.tree.perm)
     Zg = P.h2_to_dense(Z)[np.ix_(perm, perm)]  # original order -> tree order
