@@ -2054,29 +2054,25 @@ __device__ __forceinline__ double cheb_node(double a, double b, int i, int m) {
     return 0.5 * (a + b) + 0.5 * (b - a) * cos((2 * i + 1) * M_PI / (2 * m));
 }
 
-__device__ double lagrange(double a, double b, int m, int i, double x) {
-    double xi = cheb_node(a, b, i, m), v = 1.0;
+// l_i(x) = prod_{j != i} (x - x_j) / (x_i - x_j) for the nodes xs[0..m-1] (the
+// values cheb_node gives, computed once per cluster and kept in shared memory)
+__device__ double lagrange_n(const double* xs, int m, int i, double x) {
+    const double xi = xs[i];
+    double v = 1.0;
     for (int j = 0; j < m; ++j)
-        if (j != i) {
-            double xj = cheb_node(a, b, j, m);
-            v *= (x - xj) / (xi - xj);
-        }
+        if (j != i) v *= (x - xs[j]) / (xi - xs[j]);
     return v;
 }
 
-// l_i'(x): the product rule over the factors of l_i
-__device__ double lagrange_deriv(double a, double b, int m, int i, double x) {
-    const double xi = cheb_node(a, b, i, m);
+// l_i'(x) from the nodes xs[0..m-1]: the product rule over the factors of l_i
+__device__ double lagrange_deriv_n(const double* xs, int m, int i, double x) {
+    const double xi = xs[i];
     double sum = 0.0;
     for (int k = 0; k < m; ++k) {
         if (k == i) continue;
-        const double xk = cheb_node(a, b, k, m);
-        double term = 1.0 / (xi - xk);
+        double term = 1.0 / (xi - xs[k]);
         for (int j = 0; j < m; ++j)
-            if (j != i && j != k) {
-                const double xj = cheb_node(a, b, j, m);
-                term *= (x - xj) / (xi - xj);
-            }
+            if (j != i && j != k) term *= (x - xs[j]) / (xi - xs[j]);
         sum += term;
     }
     return sum;
@@ -2108,9 +2104,15 @@ __device__ double kernel_eval(int kernel, const double* x, const double* y, cons
 __global__ void k_interp_leaf(const double* pts, const double* nrm, const int64_t* perm, const int64_t* off,
                               const int64_t* size, const double* lo, const double* hi, double* const* leafp,
                               int first_leaf, int m) {
+    __shared__ double ln[3][8];  // the leaf's nodes (m <= 8)
     const int leaf = first_leaf + blockIdx.y;
     const int k = m * m * m;
     const int64_t cnt = size[leaf];
+    if (threadIdx.x < 3 * m) {
+        const int a = threadIdx.x / m, j = threadIdx.x % m;
+        ln[a][j] = cheb_node(lo[3 * leaf + a], hi[3 * leaf + a], j, m);
+    }
+    __syncthreads();
     double* out = leafp[leaf];
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt * k; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = e % cnt;
@@ -2118,16 +2120,14 @@ __global__ void k_interp_leaf(const double* pts, const double* nrm, const int64_
         int ix = nu % m, iy = (nu / m) % m, iz = nu / (m * m);
         const int64_t p = perm[off[leaf] + i];
         const double* x = pts + 3 * p;
-        const double* l = lo + 3 * leaf;
-        const double* h = hi + 3 * leaf;
-        const double lx = lagrange(l[0], h[0], m, ix, x[0]), ly = lagrange(l[1], h[1], m, iy, x[1]),
-                     lz = lagrange(l[2], h[2], m, iz, x[2]);
+        const double lx = lagrange_n(ln[0], m, ix, x[0]), ly = lagrange_n(ln[1], m, iy, x[1]),
+                     lz = lagrange_n(ln[2], m, iz, x[2]);
         double v;
         if (nrm) {
             const double* nv = nrm + 3 * p;
-            v = lagrange_deriv(l[0], h[0], m, ix, x[0]) * ly * lz * nv[0] +
-                lx * lagrange_deriv(l[1], h[1], m, iy, x[1]) * lz * nv[1] +
-                lx * ly * lagrange_deriv(l[2], h[2], m, iz, x[2]) * nv[2];
+            v = lagrange_deriv_n(ln[0], m, ix, x[0]) * ly * lz * nv[0] +
+                lx * lagrange_deriv_n(ln[1], m, iy, x[1]) * lz * nv[1] +
+                lx * ly * lagrange_deriv_n(ln[2], m, iz, x[2]) * nv[2];
         } else {
             v = lx * ly * lz;
         }
@@ -2146,18 +2146,23 @@ void launch_interp_leaf(const double* pts, const double* nrm, const int64_t* per
 
 // transfers: E_c[nu', nu] = l_{parent, nu}(xi_{c, nu'}), one block per cluster c >= 1
 __global__ void k_interp_transfer(const double* lo, const double* hi, double* const* trp, int m) {
+    __shared__ double cn[3][8], pn[3][8];  // the child's and the parent's nodes (m <= 8)
     const int c = blockIdx.x + 1, p = (c - 1) / 2;
     const int k = m * m * m;
     const double *lc = lo + 3 * c, *hc = hi + 3 * c, *lp = lo + 3 * p, *hp = hi + 3 * p;
+    if (threadIdx.x < 3 * m) {
+        const int a = threadIdx.x / m, i = threadIdx.x % m;
+        cn[a][i] = cheb_node(lc[a], hc[a], i, m);
+        pn[a][i] = cheb_node(lp[a], hp[a], i, m);
+    }
+    __syncthreads();
     double* out = trp[c];
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         int nu1 = e % k, nu = e / k;
         int a0 = nu1 % m, a1 = (nu1 / m) % m, a2 = nu1 / (m * m);
         int b0 = nu % m, b1 = (nu / m) % m, b2 = nu / (m * m);
-        double x0 = cheb_node(lc[0], hc[0], a0, m), x1 = cheb_node(lc[1], hc[1], a1, m),
-               x2 = cheb_node(lc[2], hc[2], a2, m);
-        out[nu1 + (size_t)nu * k] =
-            lagrange(lp[0], hp[0], m, b0, x0) * lagrange(lp[1], hp[1], m, b1, x1) * lagrange(lp[2], hp[2], m, b2, x2);
+        out[nu1 + (size_t)nu * k] = lagrange_n(pn[0], m, b0, cn[0][a0]) * lagrange_n(pn[1], m, b1, cn[1][a1]) *
+                                    lagrange_n(pn[2], m, b2, cn[2][a2]);
     }
 }
 
@@ -2168,16 +2173,23 @@ void launch_interp_transfer(const double* lo, const double* hi, double* const* t
 // couplings: S_ts[nu, mu] = g(xi_{t,nu}, xi_{s,mu}), one block per admissible block
 __global__ void k_interp_coupling(const double* lo, const double* hi, const int* bt, const int* bs,
                                   double* const* bp, int m, int kernel) {
+    // the 3 m node coordinates of each cluster, once per block: every entry of the
+    // coupling reuses them (a cosine per coordinate per entry had dominated the kernel)
+    __shared__ double xn[3][8], yn[3][8];  // m <= 8
     const int b = blockIdx.x, t = bt[b], s = bs[b];
     const int k = m * m * m;
     const double *lt = lo + 3 * t, *ht = hi + 3 * t, *ls = lo + 3 * s, *hs = hi + 3 * s;
+    if (threadIdx.x < 3 * m) {
+        const int a = threadIdx.x / m, i = threadIdx.x % m;
+        xn[a][i] = cheb_node(lt[a], ht[a], i, m);
+        yn[a][i] = cheb_node(ls[a], hs[a], i, m);
+    }
+    __syncthreads();
     double* out = bp[b];
     for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
         int nu = e % k, mu = e / k;
-        double x[3] = {cheb_node(lt[0], ht[0], nu % m, m), cheb_node(lt[1], ht[1], (nu / m) % m, m),
-                       cheb_node(lt[2], ht[2], nu / (m * m), m)};
-        double y[3] = {cheb_node(ls[0], hs[0], mu % m, m), cheb_node(ls[1], hs[1], (mu / m) % m, m),
-                       cheb_node(ls[2], hs[2], mu / (m * m), m)};
+        double x[3] = {xn[0][nu % m], xn[1][(nu / m) % m], xn[2][nu / (m * m)]};
+        double y[3] = {yn[0][mu % m], yn[1][(mu / m) % m], yn[2][mu / (m * m)]};
         // the double-layer kernel is the normal derivative (carried by W) of the Laplace kernel
         out[nu + (size_t)mu * k] = kernel_eval(kernel == H2_K_DLP ? H2_K_LAPLACE : kernel, x, y);
     }

@@ -18,6 +18,7 @@
 #include <atomic>
 #include <map>
 #include <mutex>
+#include <future>
 #include <thread>
 
 #include "h2_internal.h"
@@ -2116,6 +2117,10 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     const OpView X{Xm, false}, Y{Ym, false};
     const Tree& T = X.tree();
     clk.mark();
+    // The plan of T^XY (host work, cached per pair of structures) is built on a host
+    // thread of its own beside phase A, which needs none of it; t_mat waits for it.
+    std::future<const ProductTree*> plan =
+        std::async(std::launch::async, [Xm, Ym] { return &cached_product_tree(*Xm->st, *Ym->st); });
     // phase A: compressed induced row and column bases (prep included)
     const OpView Yt{Ym, true}, Xt{Xm, true};
     // "+Z" with bases of its own: V_Z (W_Z) preserved beside V_X (W_Y) in phase A
@@ -2140,7 +2145,7 @@ static void mul_add(h2_matrix* Zm, const h2_matrix* Xm, const h2_matrix* Ym, con
     stream_after(st, side.s);
     // the intermediate H^2-matrix on T^XY
     Intermediate G;
-    G.PT = &cached_product_tree(*Xm->st, *Ym->st);
+    G.PT = plan.get();
     G.Q = ra.Q;
     G.QW = ca.Q;
     const BlockTree& Zb = Zm->st->blocks;
