@@ -429,7 +429,14 @@ struct SumSqJob {
     const double* A;
     int rows, cols, lda, slot;
 };
-void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st);
+// out[b] = sum of the jobs' sums of squares over jobs seg[b] .. seg[b+1]-1, added
+// in job order (the jobs sorted by slot; seg has nslots + 1 entries, on the
+// device), so that the result does not depend on the order in which CTAs finish;
+// part: njobs doubles of scratch
+void launch_sumsq(const SumSqJob* jobs, int njobs, double* part, const int* seg, int nslots, double* out,
+                  cudaStream_t st);
+// sorts the jobs by slot (stable) and returns the nslots + 1 segment offsets
+std::vector<int> sumsq_segments(std::vector<SumSqJob>& jobs, int nslots);
 // w[i] = 1 / sqrt(v[i]) (0 where v[i] == 0), i < n
 void launch_inv_sqrt(const double* v, double* w, double* w2, int n, cudaStream_t st);
 

@@ -6,6 +6,7 @@
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <mutex>
@@ -2220,7 +2221,7 @@ void launch_interp_dense(const double* pts, const double* nrm, const int64_t* pe
 }
 
 // ------------------------------------------------------------------ block norms
-__global__ void k_sumsq(const SumSqJob* __restrict__ jobs, double* out) {
+__global__ void k_sumsq(const SumSqJob* __restrict__ jobs, double* part) {
     __shared__ double red[256 / 32];
     const SumSqJob J = jobs[blockIdx.x];
     double s = 0.0;
@@ -2229,11 +2230,32 @@ __global__ void k_sumsq(const SumSqJob* __restrict__ jobs, double* out) {
         s += v * v;
     }
     s = block_sum<256>(s, red);
-    if (threadIdx.x == 0) atomicAdd(out + J.slot, s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-void launch_sumsq(const SumSqJob* jobs, int njobs, double* out, cudaStream_t st) {
-    if (njobs > 0) k_sumsq<<<njobs, 256, 0, st>>>(jobs, out);
+// the jobs' sums added per slot in job order (no atomics: the same inputs give the
+// same bits on every run)
+__global__ void k_segment_sum(const double* __restrict__ part, const int* __restrict__ seg, int nslots,
+                              double* out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nslots) return;
+    double s = 0.0;
+    for (int j = seg[b]; j < seg[b + 1]; ++j) s += part[j];
+    out[b] = s;
+}
+
+void launch_sumsq(const SumSqJob* jobs, int njobs, double* part, const int* seg, int nslots, double* out,
+                  cudaStream_t st) {
+    if (njobs > 0) k_sumsq<<<njobs, 256, 0, st>>>(jobs, part);
+    if (nslots > 0) k_segment_sum<<<(int)ceil_div(nslots, 256), 256, 0, st>>>(part, seg, nslots, out);
+}
+
+std::vector<int> sumsq_segments(std::vector<SumSqJob>& jobs, int nslots) {
+    std::stable_sort(jobs.begin(), jobs.end(), [](const SumSqJob& a, const SumSqJob& b) { return a.slot < b.slot; });
+    std::vector<int> seg((size_t)nslots + 1, 0);
+    for (const SumSqJob& j : jobs) ++seg[(size_t)j.slot + 1];
+    for (int b = 0; b < nslots; ++b) seg[(size_t)b + 1] += seg[b];
+    return seg;
 }
 
 __global__ void k_inv_sqrt(const double* v, double* w, double* w2, int n) {

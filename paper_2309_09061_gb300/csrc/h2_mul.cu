@@ -1834,8 +1834,9 @@ static void product_error(const h2_matrix* Zr, const h2_matrix* Z0, const h2_mat
             const int len = (int)std::min(kPart, n - o);
             jobs.push_back(SumSqJob{v + o, len, 1, len, 0});
         }
-        H2_CUDA(cudaMemsetAsync(acc, 0, sizeof(double), st));
-        launch_sumsq(R.upload(jobs), (int)jobs.size(), acc, st);
+        const std::vector<int> seg = sumsq_segments(jobs, 1);
+        double* part = R.dalloc(std::max<size_t>(jobs.size(), 1));
+        launch_sumsq(R.upload(jobs), (int)jobs.size(), part, R.upload(seg), 1, acc, st);
         double h = 0.0;
         H2_CUDA(cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, st));
         H2_CUDA(cudaStreamSynchronize(st));
@@ -2026,12 +2027,15 @@ static PhaseB coarsen_and_project(Runner& R, Runner& R2, cudaStream_t st, SideSt
             else
                 jobs.push_back(SumSqJob{G.C[n], (int)T.size[t], (int)T.size[r], (int)T.size[t], cmap[n]});
         }
+        const std::vector<int> seg = sumsq_segments(jobs, (int)Zb.kind.size());
         SumSqJob* dj = R.upload(jobs);
+        const int* dseg = R.upload(seg);
+        double* part = R.dalloc(std::max<size_t>(jobs.size(), 1));
         R.begin(9);
-        launch_sumsq(dj, (int)jobs.size(), sq, st);
+        launch_sumsq(dj, (int)jobs.size(), part, dseg, (int)Zb.kind.size(), sq, st);
         launch_inv_sqrt(sq, w, w2, (int)Zb.kind.size(), st);
         R.end(9, 0.0, 0.0);
-        R.launches += 2;
+        R.launches += 3;
     }
     GView GR{&G, &T, false}, GC{&G, &T, true};
     PhaseB out;

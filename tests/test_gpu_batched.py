@@ -98,3 +98,29 @@ def test_grouped_launches_match_single(precision):
                        capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stdout[-2000:] + p.stderr[-2000:]
     assert "worst" in p.stdout
+
+
+@pytest.mark.parametrize("precision", [P.H2_FP64, P.H2_TF32X3])
+def test_products_are_deterministic(precision):
+    """The same product computed twice alone, and once inside a batched call
+    (whose default runs every product with its own launches), gives the same
+    bits: no kernel of the product depends on the order in which its CTAs
+    finish (the per-block sums of squares behind the truncation weights are
+    added in a fixed order, not with atomics)."""
+    eps = 1e-5
+    pts = synth.cube_surface(3000, 2309090617)
+    X = P.h2_build_interp(pts, P.H2_K_LAPLACE, 64, 2.0, 4)
+    outs = []
+    for _ in range(2):
+        Z = P.h2_clone(X)
+        P.h2_mul_add(Z, X, X, eps, precision)
+        outs.append(P.h2_to_dense(Z))
+        Z.free()
+    assert np.array_equal(outs[0], outs[1])
+    Y = P.h2_build_interp(synth.sphere(2048, 7), P.H2_K_LAPLACE, 64, 2.0, 3)
+    Zs = [P.h2_clone(X), P.h2_clone(Y)]
+    _, codes = P.h2_mul_add_batched(Zs, [X, Y], [X, Y], eps, precision)
+    assert codes == [0, 0]
+    assert np.array_equal(P.h2_to_dense(Zs[0]), outs[0])
+    for A in Zs + [X, Y]:
+        A.free()
