@@ -274,6 +274,9 @@ void Runner::begin(int fam) {
 }
 
 void Runner::end(int fam, double flops, double bytes, int64_t units) {
+    // a refused launch (an invalid configuration) fails here, not silently: its
+    // outputs would keep whatever the scratch held
+    H2_CUDA(cudaGetLastError());
     cudaEvent_t b = get_event();
     H2_CUDA(cudaEventRecord(b, st_));
     marks_.push_back(Mark{fam, cur_, b, flops, bytes, nullptr, units});

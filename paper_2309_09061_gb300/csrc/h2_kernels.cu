@@ -1740,8 +1740,23 @@ void launch_svd(const SVDJob* jobs, int njobs, int max_n, cudaStream_t st, bool 
     if (cs > 1 && launch_clustered(k_jacobi64<true>, njobs * cs, cs,
                                    std::max(j64_smem_bytes(max_n, cs), kClusterDynSmem), st, jobs))
         return;
+    // The attribute is a per-function limit shared by every host thread: it is set
+    // once per device to the largest size any launch asks for.  (Set per launch to
+    // that launch's size, a concurrent product's smaller setting could land between
+    // another thread's setting and its launch, and that launch would be refused.)
+    static bool attr_set[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            cudaFuncSetAttribute(k_jacobi64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)j64_smem_bytes(JMAXN, 1));
+            attr_set[dev] = true;
+        }
+    }
     const size_t smem = j64_smem_bytes(max_n, 1);
-    cudaFuncSetAttribute(k_jacobi64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_jacobi64<false><<<njobs, JT, smem, st>>>(jobs);
 }
 
