@@ -56,6 +56,7 @@ def test_argument_validation_without_device(lib):
     assert lib.h2_to_dense(None, None, 0, 0, None) == -1
     assert lib.h2_info(None, None) == -1
     assert lib.h2_clone(None, None, ctypes.byref(h)) == -1
+    assert lib.h2_block_norms(None, None, None, None, None, None) == -1
     lib.h2_free(None)
 
 
