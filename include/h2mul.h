@@ -84,7 +84,8 @@ extern "C" {
  * runs in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the
  * weights' Gram matrices and the other products that must be FP64-accurate
  * run in double-float FP32 arithmetic, and the pivoted Cholesky, the final
- * sweeps and every rank decision stay FP64. */
+ * sweeps and every rank decision stay FP64.  Every mode computes the same bits
+ * on every run (no reduction depends on the order in which CTAs finish). */
 #define H2_FP64 0
 #define H2_MIXED 1
 #define H2_TF32X3 2
@@ -172,7 +173,11 @@ typedef struct {
      * default rule, off, or over 2 or 4 slices), their device times are read
      * when the call ends, and later batches of the key run the fastest.  The
      * choices are kept per device for the life of the process.  Every
-     * candidate computes the same products, so results agree to rounding. */
+     * candidate computes the same products, so results agree to rounding.
+     * Zero (the default schedules): in the tensor-core modes, a batch whose
+     * jobs fit 64-row tiles runs on the CUDA-core FP32 kernel (faster there,
+     * and at least as accurate), wider jobs on the tensor cores; split-K by
+     * the default rule (when a batch would not fill the GPU). */
     int autotune;
 } h2_opts;
 
