@@ -84,8 +84,9 @@ extern "C" {
  * runs in FP32 and FP32 sweeps precondition the FP64 Jacobi sweeps; the
  * weights' Gram matrices and the other products that must be FP64-accurate
  * run in double-float FP32 arithmetic, and the pivoted Cholesky, the final
- * sweeps and every rank decision stay FP64.  Every mode computes the same bits
- * on every run (no reduction depends on the order in which CTAs finish). */
+ * sweeps and every rank decision stay FP64.  With the default schedules
+ * (h2_opts.autotune = 0) a product gives the same bits on every run: no
+ * reduction depends on the order in which CTAs finish. */
 #define H2_FP64 0
 #define H2_MIXED 1
 #define H2_TF32X3 2
