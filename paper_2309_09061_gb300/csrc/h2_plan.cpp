@@ -94,6 +94,7 @@ std::shared_ptr<Structure> build_structure(const double* pts, int64_t n, int lea
     const double pad = 1e-8 * std::max(rext, 1e-300);
     T.off[0] = 0;
     T.size[0] = n;
+    std::vector<int8_t> split_axis(T.nc, 0);
     for (int c = 0; c < T.nc; ++c) {
         int64_t* idx = T.perm.data() + T.off[c];
         int64_t cnt = T.size[c];
@@ -112,17 +113,31 @@ std::shared_ptr<Structure> build_structure(const double* pts, int64_t n, int lea
         int axis = 0;
         for (int a = 1; a < 3; ++a)
             if (ext[a] > ext[axis]) axis = a;
-        std::sort(idx, idx + cnt, [&](int64_t p, int64_t q) {
+        // the first cnt / 2 in (coordinate, index) order go to child 1: a selection,
+        // not a sort (only the leaves' order is kept, and it is sorted below)
+        int64_t h = cnt / 2;
+        split_axis[c] = (int8_t)axis;
+        std::nth_element(idx, idx + h, idx + cnt, [&](int64_t p, int64_t q) {
             double vp = pts[3 * p + axis], vq = pts[3 * q + axis];
             return vp < vq || (vp == vq && p < q);
         });
-        int64_t h = cnt / 2;
         int c1 = Tree::child(c, 0), c2 = Tree::child(c, 1);
         T.off[c1] = T.off[c];
         T.size[c1] = h;
         T.off[c2] = T.off[c] + h;
         T.size[c2] = cnt - h;
     }
+    // a leaf keeps its points in its parent's split order: (coordinate along the
+    // parent's split axis, index)
+    if (T.L > 0)
+        for (int c = Tree::first(T.L); c < T.nc; ++c) {
+            int64_t* idx = T.perm.data() + T.off[c];
+            const int axis = split_axis[Tree::parent(c)];
+            std::sort(idx, idx + T.size[c], [&](int64_t p, int64_t q) {
+                double vp = pts[3 * p + axis], vq = pts[3 * q + axis];
+                return vp < vq || (vp == vq && p < q);
+            });
+        }
     for (int c = 0; c < T.nc; ++c)
         if (T.size[c] <= 0) throw Error(H2_ERR_ARG, "empty cluster: fewer points than leaves");
     // block tree with the standard admissibility condition

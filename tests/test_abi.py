@@ -142,3 +142,17 @@ def test_precision_and_allocator_validation_without_device(lib):
     h = ctypes.c_void_p()
     # alloc given, free missing: refused (the check runs before the device is touched)
     assert lib.h2_build_interp(pts.ctypes.data, 64, 0, 16, 2.0, 2, ctypes.byref(o), ctypes.byref(h)) == -1
+
+
+def test_planner_matches_oracle_with_ties(lib):
+    """Points on a grid share coordinates along every axis, so the median splits
+    are decided by the tie-break on the point index (reading 1); the planner's
+    permutation and block counts must still match the oracle's exactly."""
+    g = np.arange(10, dtype=np.float64)
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3).copy()
+    pts = np.ascontiguousarray(np.concatenate([pts, pts[::7]]))  # duplicated points as well
+    perm, counts = P.h2_plan_structure(pts, 16, 2.0)
+    st = O.build_structure(pts, 16, 2.0, 2)
+    assert np.array_equal(perm, st.tree.perm)
+    kinds = list(st.blocks.kind.values())
+    assert counts[1:4].tolist() == [kinds.count(O.ADM), kinds.count(O.DENSE), kinds.count(O.SPLIT)]
